@@ -1,0 +1,250 @@
+"""Pins of the FP64 oracle against facts outside the oracle itself.
+
+Every check here compares the oracle with something it does not compute the
+same way: numbers the paper prints (convergence table, suite table), textbook
+closed forms (Kuhn's value), the sequence-form LP (a different algorithm),
+brute-force enumeration of pure strategies, hand-derived iterations of a toy
+game, and algebraic invariants. A plausible slip in the oracle (dropped term,
+wrong sign, wrong lane, wrong weight, clamp in the wrong place) fails one of
+them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gamegen as gg
+import oracle
+from oracle import lp
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
+
+
+def toy_game():
+    """P1 picks L (payoff +1) or R; after R, P2 picks l (-2) or r (+3)."""
+    return gg.from_lists(
+        [
+            (gg.P1, 0, [1, 2], None, 0.0),
+            (gg.TERMINAL, -1, [], None, 1.0),
+            (gg.P2, 1, [3, 4], None, 0.0),
+            (gg.TERMINAL, -1, [], None, -2.0),
+            (gg.TERMINAL, -1, [], None, 3.0),
+        ],
+        [(0, 2), (1, 2)],
+    )
+
+
+# ---------------------------------------------------------------- structure
+
+def test_kuhn_counts_match_suite_table():
+    k = gg.kuhn()
+    gg.validate(k)
+    pins = GOLDEN["kuhn_suite_row"]
+    states = int((k.kind != gg.CHANCE).sum())
+    assert states == pins["states"]
+    # Infosets in the paper's count: distinct (player, that player's
+    # information) over non-chance histories, terminals included. In Kuhn a
+    # player's information is (own card, betting sequence).
+    deals = [(a, b) for a in range(3) for b in range(3) if a != b]
+    pairs = set()
+    for d, root_child in enumerate(k.child[k.child_begin[0]:k.child_begin[1]]):
+        stack = [(int(root_child), ())]
+        while stack:
+            h, path = stack.pop()
+            for i in (0, 1):
+                pairs.add((i, deals[d][i], path))
+            for a, c in enumerate(k.child[k.child_begin[h]:k.child_begin[h + 1]]):
+                stack.append((int(c), path + (a,)))
+    assert len(pairs) == pins["infosets"]
+    # blocks = number of distinct parent depths
+    depth = np.zeros(k.n_nodes, dtype=int)
+    for v in range(k.n_nodes):
+        for c in k.child[k.child_begin[v]:k.child_begin[v + 1]]:
+            depth[c] = depth[v] + 1
+    parents = np.nonzero(np.diff(k.child_begin) > 0)[0]
+    assert len(set(depth[parents])) == pins["blocks"]
+    for p in (0, 1):
+        nseq = 1 + int(k.iset_nact[k.iset_player == p].sum())
+        assert nseq == GOLDEN["kuhn_sequences_per_player"]["value"]
+
+
+def test_tiny_card_counts():
+    g = gg.tiny_card()
+    gg.validate(g)
+    assert (g.n_nodes, g.n_edges, g.n_infosets, g.n_slots) == (301, 300, 30, 70)
+    # zero-sum chance-root deal: every deal equally likely
+    p = g.chance_prob[g.child_begin[0]:g.child_begin[1]]
+    assert np.allclose(p, 1.0 / 20)
+
+
+# ------------------------------------------------------- printed exploitability
+
+@pytest.mark.parametrize("rule,order,key", [
+    (oracle.CFR_PLUS, oracle.SIMULTANEOUS, "cfr_plus_simultaneous"),
+    (oracle.CFR, oracle.SIMULTANEOUS, "cfr_simultaneous"),
+    (oracle.CFR, oracle.ALTERNATING, "cfr_alternating"),
+])
+def test_kuhn_exploitability_matches_convergence_table(rule, order, key):
+    # printed to three significant figures from float32 runs: allow 0.3%
+    o = oracle.solve(gg.kuhn(), 1000, rule=rule, order=order)
+    ref = GOLDEN["kuhn_exploitability_T1000"][key]
+    assert abs(o.exploitability() - ref) <= 3e-3 * ref
+
+
+def test_kuhn_alternating_cfr_plus_close_to_table():
+    # The table prints 8.73e-5 (float32 CPU). Our FP64 reading of alternating
+    # CFR+ (each half accumulates only the acting player's average) gives
+    # 8.58e-5; the 2% gap is a reading difference recorded in the design notes.
+    o = oracle.solve(gg.kuhn(), 1000, rule=oracle.CFR_PLUS, order=oracle.ALTERNATING)
+    ref = GOLDEN["kuhn_exploitability_T1000"]["cfr_plus_alternating"]
+    assert abs(o.exploitability() - ref) / ref < 0.03
+
+
+# ----------------------------------------------------------- closed forms
+
+def test_kuhn_game_value_lp():
+    assert lp.game_value(gg.kuhn()) == pytest.approx(GOLDEN["kuhn_game_value"]["value"], abs=1e-9)
+
+
+def test_toy_iterations_closed_form():
+    g = toy_game()
+    o = oracle.Oracle(g)
+    o.iterate(1)
+    # t=1, uniform: v(P2 node)=0.5, v(root)=0.75; P1 regrets +-0.25;
+    # P2 (sign -1, opponent reach 0.5): -0.5*(-2.5)=1.25, -0.5*(2.5)=-1.25
+    np.testing.assert_array_equal(o.R, [0.25, 0.0, 1.25, 0.0])
+    np.testing.assert_array_equal(o.sbar, [0.5, 0.5, 0.5, 0.5])
+    assert o.root_value == 0.75
+    o.iterate(1)
+    # t=2: sigma1=(1,0), sigma2=(1,0); P1's R regret -3 clamps to 0; P2's
+    # opponent reach is 0; averages gain 2*(1,0) each
+    np.testing.assert_array_equal(o.R, [0.25, 0.0, 1.25, 0.0])
+    np.testing.assert_array_equal(o.sbar, [2.5, 0.5, 2.5, 0.5])
+    assert o.root_value == 1.0
+    v = oracle.Oracle(g, rule=oracle.CFR)
+    v.iterate(2)
+    np.testing.assert_array_equal(v.R, [0.25, -3.25, 1.25, -1.25])
+
+
+def test_chance_folding_root_value_all_chance_and_root_terminal():
+    # all-chance game (Proposition 1's degenerate case): value = sum pi_c u
+    g = gg.from_lists(
+        [
+            (gg.CHANCE, -1, [1, 2], [0.25, 0.75], 0.0),
+            (gg.CHANCE, -1, [3, 4], [0.5, 0.5], 0.0),
+            (gg.TERMINAL, -1, [], None, 4.0),
+            (gg.TERMINAL, -1, [], None, -1.0),
+            (gg.TERMINAL, -1, [], None, 2.0),
+        ],
+        [],
+    )
+    o = oracle.Oracle(g)
+    o.iterate(3)
+    assert o.root_value == pytest.approx(0.25 * 0.5 * -1.0 + 0.25 * 0.5 * 2.0 + 0.75 * 4.0)
+    assert o.A == 0
+    t = gg.from_lists([(gg.TERMINAL, -1, [], None, 1.5)], [])
+    o = oracle.Oracle(t)
+    o.iterate(2)
+    assert o.root_value == 1.5
+
+
+@pytest.mark.parametrize("game", ["tiny", "rt4", "rt5"])
+def test_folded_root_value_equals_expected_value(game):
+    """The chance-weighted root value of the CFR pass (chance folded into the
+    terminal factor) equals the expected payoff computed with chance applied
+    at chance nodes (Proposition 1)."""
+    g = {"tiny": gg.tiny_card(), "rt4": gg.random_tree(3, depth=4), "rt5": gg.random_tree(4, depth=5)}[game]
+    o = oracle.Oracle(g)
+    for _ in range(5):
+        sigma = o.current_strategy()
+        o.iterate(1)
+        assert o.root_value == pytest.approx(o.expected_value(sigma), abs=1e-12)
+
+
+# ------------------------------------------------------- best responses
+
+def random_strategy(g, rng):
+    s = rng.random(g.n_slots)
+    off = g.slot_offsets()
+    for I in range(g.n_infosets):
+        s[off[I]:off[I + 1]] /= s[off[I]:off[I + 1]].sum()
+    return s
+
+
+@pytest.mark.parametrize("game,seed", [("kuhn", 0), ("tiny", 1), ("rt", 2), ("rt", 3)])
+def test_exact_best_response_equals_brute_force(game, seed):
+    g = {"kuhn": gg.kuhn(), "tiny": gg.tiny_card(), "rt": gg.random_tree(seed, depth=5, max_group=3)}[game]
+    rng = np.random.default_rng(seed)
+    o = oracle.Oracle(g)
+    o.iterate(7)
+    for sigma in (o.avg_strategy(), o.current_strategy(), random_strategy(g, rng)):
+        b1, b2, _ = o.best_response(sigma)
+        assert b1 == pytest.approx(o.bruteforce_br(sigma, 0), abs=1e-12)
+        assert b2 == pytest.approx(o.bruteforce_br(sigma, 1), abs=1e-12)
+
+
+@pytest.mark.parametrize("game", ["kuhn", "tiny", "rt0", "rt1", "rt2"])
+def test_lp_value_bracketed_by_best_responses(game):
+    g = {"kuhn": gg.kuhn(), "tiny": gg.tiny_card(), "rt0": gg.random_tree(0, depth=6),
+         "rt1": gg.random_tree(1, depth=6), "rt2": gg.random_tree(2, depth=6)}[game]
+    v = lp.game_value(g)
+    rng = np.random.default_rng(0)
+    o = oracle.solve(g, 300)
+    for sigma in (o.avg_strategy(), random_strategy(g, rng)):
+        b1, b2, u = o.best_response(sigma)
+        assert b2 - 1e-9 <= v <= b1 + 1e-9
+        assert b2 - 1e-9 <= u <= b1 + 1e-9
+
+
+def test_tiny_exploitability_falls_toward_zero_and_value_converges():
+    g = gg.tiny_card()
+    v = lp.game_value(g)
+    o = oracle.Oracle(g)
+    prev = np.inf
+    for T in (10, 100, 1000, 10000):
+        o.iterate(T - o.t)
+        e = o.exploitability()
+        assert 0.0 <= e < prev
+        b1, b2, u = o.best_response(o.avg_strategy())
+        assert abs(u - v) <= 2 * e + 1e-12  # value certificate
+        prev = e
+    assert prev < 1e-3 * g.pot
+
+
+# ------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("game", ["tiny", "rt"])
+def test_invariants(game):
+    g = gg.tiny_card() if game == "tiny" else gg.random_tree(5, depth=7)
+    o = oracle.Oracle(g)
+    off = g.slot_offsets()
+    for _ in range(4):
+        o.iterate(25)
+        assert (o.R >= 0).all()
+        assert (o.sbar >= 0).all()
+        for s in (o.avg_strategy(), o.current_strategy()):
+            assert (s >= 0).all()
+            sums = np.add.reduceat(s, off[:-1])
+            np.testing.assert_allclose(sums, 1.0, atol=1e-12)
+        assert o.exploitability() >= -1e-12
+
+
+def test_split_calls_equal_one_call_bitwise():
+    g = gg.random_tree(7, depth=7)
+    a = oracle.Oracle(g)
+    for n in (2, 8, 3):
+        a.iterate(n)
+    b = oracle.solve(g, 13)
+    np.testing.assert_array_equal(a.R, b.R)
+    np.testing.assert_array_equal(a.sbar, b.sbar)
+
+
+def test_node_relabelling_does_not_change_results():
+    g = gg.tiny_card()
+    rng = np.random.default_rng(3)
+    perm = np.concatenate([[0], 1 + rng.permutation(g.n_nodes - 1)])
+    h = gg.permute_nodes(g, perm)
+    gg.validate(h)
+    a, b = oracle.solve(g, 50), oracle.solve(h, 50)
+    np.testing.assert_array_equal(a.avg_strategy(), b.avg_strategy())
