@@ -1,0 +1,187 @@
+/* cfr.h — C ABI of the GB300 CFR+ library (libcfr.so).
+ *
+ * One CFR+ iteration (simultaneous updates, regret matching+, linear
+ * averaging) over a two-player zero-sum game compiled once into static flat
+ * arrays (the paper's Section 4 and Algorithm 1): a depth-level forward pass
+ * of both players' reach (dual-lane buffer, eq. (lanes)), terminal utilities
+ * with chance folded in at compile time (eq. (template), Proposition 1), a
+ * depth-level backward pass of counterfactual values as deterministic
+ * segmented sums with no float atomics (eq. (opbwd)), and the per-information
+ * -set regret update, regret matching and average accumulation (eqs.
+ * (instregret), (regret), (rm), the CFR+ clamp).
+ *
+ * Conventions
+ *  - Every function returns CFR_OK (0) or a negative CFR_ERR_* code and never
+ *    throws or aborts; cfr_last_error() describes the last failure of the
+ *    calling thread.
+ *  - Device memory is owned by the caller: cfr_plan() reports the bytes one
+ *    solver needs, the caller allocates them (e.g. a PyTorch uint8 tensor)
+ *    and hands them to cfr_bind(). The library sub-allocates inside that
+ *    arena and never frees it. The caller keeps it alive until cfr_destroy()
+ *    or the next cfr_bind().
+ *  - Streams are plain cudaStream_t values passed as void*; NULL means the
+ *    legacy default stream. Kernels are enqueued asynchronously unless a
+ *    function says it synchronises.
+ *  - Host arrays passed in are read during the call only (the library copies
+ *    what it keeps). Slot-indexed vectors use the spec's order: information
+ *    set I owns slots off(I) .. off(I)+nact(I)-1, off = prefix sum of nact in
+ *    information-set id order.
+ */
+#ifndef CFR_H
+#define CFR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CFR_OK = 0,
+  CFR_ERR_ARG = -1,          /* null pointer, bad size or bad option */
+  CFR_ERR_INVALID_SPEC = -2, /* the game fails a structural check (Algorithm "Compile", step 1) */
+  CFR_ERR_NOT_BOUND = -3,    /* the call needs device memory: call cfr_bind first */
+  CFR_ERR_REBOUND = -4,      /* a captured graph refers to another arena */
+  CFR_ERR_ARENA_SMALL = -5,  /* the arena is smaller than cfr_plan reported */
+  CFR_ERR_TIMEOUT = -6,      /* a grid barrier of the persistent kernel gave up waiting */
+  CFR_ERR_DEVICE = -7,       /* a CUDA call failed (message in cfr_last_error) */
+  CFR_ERR_HOST_MEMORY = -8,  /* host allocation failed */
+  CFR_ERR_UNSUPPORTED = -9   /* option not available for this game */
+};
+
+/* Node kinds of the input game. */
+enum { CFR_TERMINAL = 0, CFR_CHANCE = 1, CFR_PLAYER1 = 2, CFR_PLAYER2 = 3 };
+
+/* The input game in the paper's tabular form (Appendix H, "Input
+ * representation"): node 0 is the root; children listed in action order.
+ * All arrays are host memory owned by the caller. */
+typedef struct cfr_game_spec {
+  int64_t n_nodes;            /* N >= 1, N < 2^31 */
+  int64_t n_infosets;         /* I >= 0 */
+  const int8_t *kind;         /* [N] CFR_TERMINAL / CFR_CHANCE / CFR_PLAYER1 / CFR_PLAYER2 */
+  const int32_t *infoset;     /* [N] acting player's information set (decision nodes), else -1 */
+  const int64_t *child_begin; /* [N+1] offsets into child[]; child_begin[N] = number of edges */
+  const int32_t *child;       /* [E] child ids in action order */
+  const double *chance_prob;  /* [E] outcome probability below chance nodes (others ignored) */
+  const double *payoff;       /* [N] payoff to player 1 at terminals (others ignored) */
+  const int8_t *iset_player;  /* [I] 0 = player 1, 1 = player 2 */
+  const int32_t *iset_nact;   /* [I] actions of each set, 1 .. 64 */
+} cfr_game_spec;
+
+enum { CFR_P64 = 0, CFR_P32 = 1 };
+enum { CFR_EXEC_AUTO = 0, CFR_EXEC_LEVELS = 1, CFR_EXEC_GRAPH = 2, CFR_EXEC_PERSISTENT = 3 };
+enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1 };
+
+typedef struct cfr_options {
+  /* CFR_P64: every value in FP64 (the parity mode). CFR_P32: reach, values,
+   * strategy and per-history terms in FP32; cumulative regret, average
+   * strategy and best-response sums in FP64 (Proposition 4). */
+  int precision;
+  /* CFR_EXEC_LEVELS: per-level kernels launched eagerly; CFR_EXEC_GRAPH: the
+   * same kernels captured once into a CUDA graph and replayed (Section 4.3);
+   * CFR_EXEC_PERSISTENT: one kernel per cfr_iterate call with a grid-wide
+   * barrier between depth levels; CFR_EXEC_AUTO picks by game size. */
+  int exec_form;
+  int rule;            /* CFR_RULE_CFR_PLUS (clamp) or CFR_RULE_CFR (no clamp) */
+  int lanes_per_set;   /* 0 = autotune; else 1..32 lanes aggregate one information set */
+  int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
+  int64_t barrier_spin_limit; /* 0 = default; polls before a grid barrier reports CFR_ERR_TIMEOUT */
+} cfr_options;
+
+typedef struct cfr_counts {
+  int64_t n_nodes, n_edges, n_infosets, n_slots;
+  int64_t n_internal, n_decision, n_chance, n_terminal;
+  int64_t depth_blocks;       /* D: number of distinct parent depths (eq. (blocks)) */
+  int64_t max_actions;
+  int64_t algo_bytes_per_iter; /* algorithmic HBM bytes of one iteration (design notes) */
+  int64_t iteration;          /* t: iterations completed since bind/reset */
+  int exec_form;              /* resolved execution form */
+  int lanes_per_set;          /* resolved lanes per information set */
+} cfr_counts;
+
+typedef struct cfr_handle cfr_handle;
+
+/* Compiles the game (Algorithm "Compile", steps 1-8): validation,
+ * breadth-first numbering (parent before child, siblings contiguous in action
+ * order), depth blocks, chance folding into the values template, slot and
+ * member index emission. Host only; no device memory is touched.
+ * opt may be NULL (P32, AUTO, CFR+). On success *out owns the result. */
+int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cfr_handle **out);
+
+/* Sizes of the compiled game. */
+int cfr_get_counts(const cfr_handle *h, cfr_counts *out);
+
+/* Device bytes one solver needs (arrays + state + evaluation scratch). */
+int cfr_plan(const cfr_handle *h, size_t *device_bytes);
+
+/* Binds the caller's device arena (>= cfr_plan bytes, 256-byte aligned),
+ * uploads the compiled arrays and initialises the state (R = 0, average = 0,
+ * uniform strategy, t = 0). Synchronises `stream`. Binding again re-uploads
+ * and drops any captured graph. */
+int cfr_bind(cfr_handle *h, void *device_arena, size_t bytes, void *stream);
+
+/* Runs n CFR+ iterations (t+1 .. t+n), asynchronously on `stream`.
+ * n = 0 is a no-op. Split calls give bitwise the same state as one call. */
+int cfr_iterate(cfr_handle *h, int64_t n, void *stream);
+
+/* Waits for `stream` and reports a device-side failure of earlier calls:
+ * CFR_ERR_TIMEOUT if a grid barrier of the persistent kernel gave up (the
+ * state is then undefined until cfr_reset). */
+int cfr_synchronize(cfr_handle *h, void *stream);
+
+/* Average strategy (eq. (rm): the linear-weighted sum normalised per set,
+ * uniform where it is zero), [A] doubles in spec slot order. out is a device
+ * pointer if out_on_device, else host memory (then the call synchronises). */
+int cfr_avg_strategy(cfr_handle *h, double *out, int out_on_device, void *stream);
+
+/* Current strategy sigma^{t+1} (regret matching of the cumulative regret),
+ * same layout and synchronisation rules as cfr_avg_strategy. */
+int cfr_current_strategy(cfr_handle *h, double *out, int out_on_device, void *stream);
+
+/* Exploitability of the average strategy, NashConv/2 by exact best response
+ * (eq. (exploitability)), on the GPU with FP64 sums. out_br (optional, [3])
+ * receives (br1, br2, u) in player-1 units: player 1's best-response value,
+ * player 2's best-response value, and the value of the average profile.
+ * Synchronises `stream`. */
+int cfr_exploitability(cfr_handle *h, double *out_expl, double *out_br, void *stream);
+
+/* Zeroes regrets, averages and t and restores the uniform strategy, in place
+ * (a captured graph stays valid). Asynchronous on `stream`. */
+int cfr_reset(cfr_handle *h, void *stream);
+
+/* Rewrites the terminal payoffs (payoff[N] in spec node order, host) into
+ * the values template from the retained chance products; no recompilation.
+ * Synchronises `stream`. */
+int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream);
+
+/* Copies the solver state out / in, host arrays in spec slot order:
+ * R[A] and avg[A] (un-normalised strategy sums) as doubles, and t. */
+int cfr_get_state(cfr_handle *h, double *R, double *avg, int64_t *t, void *stream);
+int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, void *stream);
+
+/* Host copies of the compiled index arrays, for bit-exact checks.
+ * which: 0 child_begin[N+1], 1 node_slot[N], 2 level_begin[D+2],
+ * 3 iset_slot[I+1], 4 iset_mem[I+1], 5 mem_node[N_dec], 6 chance_list,
+ * 7 level_chance[D+1], 8 level_iset[2D+1] (per level: player-1 sets then
+ * player-2 sets), 9 new id of each spec node [N], 10 template values [N]
+ * (doubles), 11 spec slot of each compiled slot [A].
+ * Integer arrays are int32. *count receives the element count; out may be
+ * NULL to query it. */
+int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);
+
+/* Fault-injection hook for tests (no effect unless set).
+ * CFR_DEBUG_BARRIER_MISSING_ARRIVALS = k: the persistent kernel's grid
+ * barriers wait for k blocks that do not exist, so every wait runs into its
+ * spin limit (cfr_options.barrier_spin_limit) and the launch ends with
+ * CFR_ERR_TIMEOUT reported by cfr_synchronize. Nothing faults or hangs: each
+ * block stops after its bounded wait. */
+enum { CFR_DEBUG_BARRIER_MISSING_ARRIVALS = 1 };
+int cfr_debug_set(cfr_handle *h, int key, int64_t value);
+
+const char *cfr_last_error(void);
+void cfr_destroy(cfr_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,609 @@
+// cfr_api.cu — the C ABI of libcfr.so (declared in include/cfr.h): arena
+// planning and binding, the three execution forms (per-level launches, one
+// replayed CUDA graph per iteration, one persistent kernel per call), the
+// FP64 exact best response, and state read-out in the caller's slot order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cfr.h"
+#include "compiled.h"
+#include "launch.h"
+
+using namespace cfr;
+
+static thread_local std::string g_err;
+
+static int set_err(int code, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return set_err(CFR_ERR_DEVICE, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                     __FILE__, __LINE__);                                                          \
+  } while (0)
+
+extern "C" const char *cfr_last_error(void) { return g_err.c_str(); }
+
+struct Buf {
+  size_t off = 0, bytes = 0;
+};
+
+struct cfr_handle {
+  Compiled c;
+  cfr_options opt{};
+  int precision = CFR_P32, exec_form = CFR_EXEC_GRAPH, rule = 0;
+  int maxa_tier = 8;           // 4, 8 or 64: register arrays of the per-set code
+  std::vector<int> level_lanes;  // lanes per information set, per depth
+  int persist_lanes = 8;
+  std::vector<LevelWork> levels;
+  // arena layout
+  Buf b_child_begin, b_node_slot, b_iset_slot, b_iset_mem, b_mem_node, b_chance_list, b_spec_slot, b_levels;
+  Buf b_wide_list, b_wide_chunk, b_wide_part, b_wide_cnt;
+  Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
+  size_t plan_bytes = 0;
+  char *arena = nullptr;
+  bool bound = false;
+  // graph form
+  cudaGraphExec_t gexec = nullptr;
+  char *graph_arena = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  // persistent form
+  int persist_grid = 0;
+  int test_missing_arrivals = 0;  // fault-injection hook: barriers wait for blocks that never come
+  int64_t iteration_host = 0;  // iterations enqueued since bind/reset (bookkeeping)
+  template <typename X> X *p(const Buf &b) const { return reinterpret_cast<X *>(arena + b.off); }
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void plan(cfr_handle *h) {
+  const Compiled &c = h->c;
+  const size_t T = h->precision == CFR_P64 ? 8 : 4;
+  size_t cur = 0;
+  auto take = [&](Buf &b, size_t bytes) {
+    b.off = cur;
+    b.bytes = bytes;
+    cur = align_up(cur + std::max<size_t>(bytes, 1));
+  };
+  take(h->b_child_begin, 4 * (c.N + 1));
+  take(h->b_node_slot, 4 * c.N);
+  take(h->b_iset_slot, 4 * (c.I + 1));
+  take(h->b_iset_mem, 4 * (c.I + 1));
+  take(h->b_mem_node, 4 * c.n_dec);
+  take(h->b_chance_list, 4 * c.n_chance);
+  take(h->b_spec_slot, 4 * c.A);
+  take(h->b_levels, sizeof(LevelWork) * std::max<int64_t>(c.D, 1));
+  take(h->b_wide_list, 4 * c.n_wide);
+  take(h->b_wide_chunk, 4 * (c.n_wide + 1));
+  take(h->b_wide_part, 3 * 8 * (size_t)c.wide_chunk.back());
+  take(h->b_wide_cnt, 4 * c.n_wide);
+  take(h->b_reach, 2 * T * c.N);
+  take(h->b_v, T * c.N);
+  take(h->b_sigma, T * (c.A + 1));
+  take(h->b_R, 8 * c.A);
+  take(h->b_avg, 8 * c.A);
+  take(h->b_tmpl, 8 * c.N);
+  take(h->b_sbs, 8 * c.A);
+  take(h->b_reach2, 16 * c.N);
+  take(h->b_vb, 16 * c.N);
+  take(h->b_vavg, 8 * c.N);
+  take(h->b_t, 8);
+  take(h->b_bar, 16);
+  take(h->b_err, 16);
+  take(h->b_out, 8 * std::max<int64_t>(c.A, 2) + 64);
+  h->plan_bytes = cur;
+}
+
+// --------------------------------------------------------------- compile
+extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cfr_handle **out) {
+  if (!spec || !out) return set_err(CFR_ERR_ARG, "cfr_compile: null argument");
+  *out = nullptr;
+  cfr_handle *h = new (std::nothrow) cfr_handle();
+  if (!h) return set_err(CFR_ERR_HOST_MEMORY, "cfr_compile: out of host memory");
+  if (opt) h->opt = *opt;
+  else { h->opt.precision = CFR_P32; h->opt.exec_form = CFR_EXEC_AUTO; }
+  if (h->opt.precision != CFR_P64 && h->opt.precision != CFR_P32) { delete h; return set_err(CFR_ERR_ARG, "bad precision"); }
+  if (h->opt.exec_form < 0 || h->opt.exec_form > 3) { delete h; return set_err(CFR_ERR_ARG, "bad exec_form"); }
+  if (h->opt.rule != CFR_RULE_CFR_PLUS && h->opt.rule != CFR_RULE_CFR) { delete h; return set_err(CFR_ERR_ARG, "bad rule"); }
+  const int lp = h->opt.lanes_per_set;
+  if (lp != 0 && lp != 4 && lp != 8 && lp != 16 && lp != 32) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 4, 8, 16 or 32"); }
+  std::string err;
+  int rc = compile_game(*spec, h->c, err);
+  if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
+  const Compiled &c = h->c;
+  h->precision = h->opt.precision;
+  h->rule = h->opt.rule;
+  h->maxa_tier = c.max_act <= 4 ? 4 : (c.max_act <= 8 ? 8 : 64);
+  h->exec_form = h->opt.exec_form;
+  if (h->exec_form == CFR_EXEC_AUTO) h->exec_form = c.N <= (1 << 16) ? CFR_EXEC_PERSISTENT : CFR_EXEC_GRAPH;
+  // lanes per information set: the smallest group that covers the mean set
+  auto pick = [](double mean) { return mean <= 4.0 ? 4 : mean <= 8.0 ? 8 : mean <= 16.0 ? 16 : 32; };
+  h->level_lanes.assign(c.D, 8);
+  double tot_mem = 0.0;
+  for (int64_t d = 0; d < c.D; ++d) {
+    h->level_lanes[d] = lp ? lp : pick(c.level_mean_members[d]);
+    tot_mem += c.level_mean_members[d] * (c.level_iset[2 * d + 2] - c.level_iset[2 * d]);
+  }
+  h->persist_lanes = lp ? lp : pick(c.I > 0 ? tot_mem / (double)c.I : 1.0);
+  h->levels.resize(c.D);
+  for (int64_t d = 0; d < c.D; ++d) {
+    LevelWork &w = h->levels[d];
+    w.lb = c.level_begin[d];
+    w.le = c.level_begin[d + 1];
+    w.ch0 = c.level_chance[d];
+    w.ch1 = c.level_chance[d + 1];
+    w.is0 = c.level_iset[2 * d];
+    w.is2 = c.level_iset[2 * d + 1];
+    w.is1 = c.level_iset[2 * d + 2];
+    w.wd0 = c.level_wide[d];
+    w.wd1 = c.level_wide[d + 1];
+    w.wc0 = c.wide_chunk[w.wd0];
+    w.wc1 = c.wide_chunk[w.wd1];
+    w.pad = 0;
+  }
+  plan(h);
+  *out = h;
+  return CFR_OK;
+}
+
+extern "C" void cfr_destroy(cfr_handle *h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
+  if (!h || !o) return set_err(CFR_ERR_ARG, "cfr_get_counts: null argument");
+  const Compiled &c = h->c;
+  o->n_nodes = c.N; o->n_edges = c.E; o->n_infosets = c.I; o->n_slots = c.A;
+  o->n_internal = c.n_int; o->n_decision = c.n_dec; o->n_chance = c.n_chance; o->n_terminal = c.n_term;
+  o->depth_blocks = c.D; o->max_actions = c.max_act;
+  o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision);
+  o->iteration = h->iteration_host;
+  o->exec_form = h->exec_form;
+  o->lanes_per_set = h->exec_form == CFR_EXEC_PERSISTENT ? h->persist_lanes : (c.D > 0 ? h->level_lanes[c.D - 1] : 0);
+  return CFR_OK;
+}
+
+extern "C" int cfr_plan(const cfr_handle *h, size_t *bytes) {
+  if (!h || !bytes) return set_err(CFR_ERR_ARG, "cfr_plan: null argument");
+  *bytes = h->plan_bytes;
+  return CFR_OK;
+}
+
+static GameView game_view(const cfr_handle *h) {
+  GameView g;
+  g.child_begin = h->p<int32_t>(h->b_child_begin);
+  g.node_slot = h->p<int32_t>(h->b_node_slot);
+  g.iset_slot = h->p<int32_t>(h->b_iset_slot);
+  g.iset_mem = h->p<int32_t>(h->b_iset_mem);
+  g.mem_node = h->p<int32_t>(h->b_mem_node);
+  g.chance_list = h->p<int32_t>(h->b_chance_list);
+  g.wide_list = h->p<int32_t>(h->b_wide_list);
+  g.wide_chunk = h->p<int32_t>(h->b_wide_chunk);
+  g.wide_part = h->p<double>(h->b_wide_part);
+  g.wide_cnt = h->p<unsigned>(h->b_wide_cnt);
+  return g;
+}
+
+template <typename T> static StateView<T> state_view(const cfr_handle *h) {
+  StateView<T> s;
+  s.reach = h->p<vec2_t<T>>(h->b_reach);
+  s.v = h->p<T>(h->b_v);
+  s.sigma = h->p<T>(h->b_sigma);
+  s.R = h->p<double>(h->b_R);
+  s.avg = h->p<double>(h->b_avg);
+  s.t = h->p<long long>(h->b_t);
+  return s;
+}
+
+static int grid_for(int64_t work, int per_block) {
+  int64_t b = (work + per_block - 1) / per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+template <typename T>
+static int init_state(cfr_handle *h, cudaStream_t s) {
+  const Compiled &c = h->c;
+  init_state_kernel<T><<<grid_for(std::max(c.A, c.I), kThreads), kThreads, 0, s>>>(
+      h->p<int32_t>(h->b_iset_slot), (int32_t)c.I, h->p<T>(h->b_sigma), h->p<double>(h->b_R),
+      h->p<double>(h->b_avg), (int32_t)c.A, h->p<long long>(h->b_t), h->p<vec2_t<T>>(h->b_reach),
+      h->p<double2>(h->b_reach2));
+  CK(cudaGetLastError());
+  h->iteration_host = 0;
+  return CFR_OK;
+}
+
+template <typename T>
+static int init_values(cfr_handle *h, cudaStream_t s) {
+  const Compiled &c = h->c;
+  CK(cudaMemcpyAsync(h->p<double>(h->b_tmpl), c.tmpl.data(), 8 * c.N, cudaMemcpyHostToDevice, s));
+  init_values_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
+      h->p<int32_t>(h->b_child_begin), h->p<double>(h->b_tmpl), (int32_t)c.N, h->p<T>(h->b_v),
+      h->p<double2>(h->b_vb), h->p<double>(h->b_vavg));
+  CK(cudaGetLastError());
+  return CFR_OK;
+}
+
+extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) {
+  if (!h || !arena) return set_err(CFR_ERR_ARG, "cfr_bind: null argument");
+  if (bytes < h->plan_bytes) return set_err(CFR_ERR_ARENA_SMALL, "cfr_bind: arena has %zu bytes, plan needs %zu", bytes, h->plan_bytes);
+  if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return set_err(CFR_ERR_ARG, "cfr_bind: arena must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->graph_arena = nullptr; }
+  h->arena = (char *)arena;
+  const Compiled &c = h->c;
+  auto up = [&](const Buf &b, const void *src, size_t n) -> int {
+    if (n) CK(cudaMemcpyAsync(h->arena + b.off, src, n, cudaMemcpyHostToDevice, s));
+    return CFR_OK;
+  };
+  int rc;
+  if ((rc = up(h->b_child_begin, c.child_begin.data(), 4 * (c.N + 1)))) return rc;
+  if ((rc = up(h->b_node_slot, c.node_slot.data(), 4 * c.N))) return rc;
+  if ((rc = up(h->b_iset_slot, c.iset_slot.data(), 4 * (c.I + 1)))) return rc;
+  if ((rc = up(h->b_iset_mem, c.iset_mem.data(), 4 * (c.I + 1)))) return rc;
+  if ((rc = up(h->b_mem_node, c.mem_node.data(), 4 * c.n_dec))) return rc;
+  if ((rc = up(h->b_chance_list, c.chance_list.data(), 4 * c.n_chance))) return rc;
+  if ((rc = up(h->b_spec_slot, c.spec_slot_of.data(), 4 * c.A))) return rc;
+  if ((rc = up(h->b_levels, h->levels.data(), sizeof(LevelWork) * c.D))) return rc;
+  if ((rc = up(h->b_wide_list, c.wide_list.data(), 4 * c.n_wide))) return rc;
+  if ((rc = up(h->b_wide_chunk, c.wide_chunk.data(), 4 * (c.n_wide + 1)))) return rc;
+  if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
+  CK(cudaMemsetAsync(h->arena + h->b_bar.off, 0, 16, s));
+  CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
+  if (h->precision == CFR_P64) {
+    if ((rc = init_state<double>(h, s))) return rc;
+    if ((rc = init_values<double>(h, s))) return rc;
+  } else {
+    if ((rc = init_state<float>(h, s))) return rc;
+    if ((rc = init_values<float>(h, s))) return rc;
+  }
+  CK(cudaStreamSynchronize(s));
+  h->bound = true;
+  return CFR_OK;
+}
+
+// ------------------------------------------------------------ iteration
+template <typename T>
+static int launch_bwd(cfr_handle *h, int d, cudaStream_t s) {
+  const LevelWork &w = h->levels[d];
+  const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
+  const int lanes = h->level_lanes[d];
+  const int nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
+  const int nb_wide = w.wc1 - w.wc0;
+  const int nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;
+  CK(launch_bwd_level<T>(h->maxa_tier, lanes, nb_ch + nb_wide + nb_is, s, game_view(h), state_view<T>(h), w, nb_ch,
+                         h->rule, d == 0 ? 1 : 0));
+  return CFR_OK;
+}
+
+template <typename T>
+static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
+  const Compiled &c = h->c;
+  GameView g = game_view(h);
+  for (int64_t d = 0; d < c.D; ++d) {
+    const LevelWork &w = h->levels[d];
+    const int nb = grid_for(w.le - w.lb, kThreads);
+    fwd_level_kernel<T><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach),
+                                                                   w, nb);
+    CK(cudaGetLastError());
+  }
+  for (int64_t d = c.D - 1; d >= 0; --d) {
+    int rc = launch_bwd<T>(h, (int)d, s);
+    if (rc) return rc;
+  }
+  return CFR_OK;
+}
+
+template <typename T>
+static int launch_persistent_form(cfr_handle *h, int64_t n, cudaStream_t s) {
+  const int L = h->persist_lanes;
+  PersistArgs<T> a;
+  a.g = game_view(h);
+  a.st = state_view<T>(h);
+  a.lw = h->p<LevelWork>(h->b_levels);
+  a.D = (int)h->c.D;
+  a.rule = h->rule;
+  a.n_iter = n;
+  unsigned *bar = h->p<unsigned>(h->b_bar);
+  a.bar.count = bar;
+  a.bar.gen = bar + 1;
+  a.bar.err = h->p<int>(h->b_err);
+  a.bar.spin_limit = h->opt.barrier_spin_limit > 0 ? h->opt.barrier_spin_limit : (int64_t)20000000;
+  if (h->persist_grid == 0) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(launch_persistent<T>(h->maxa_tier, L, 0, s, a, &per_sm));
+    int64_t cap = (int64_t)nsm * std::max(per_sm, 1);
+    if (h->opt.persistent_ctas > 0) cap = std::min<int64_t>(cap, h->opt.persistent_ctas);
+    // enough blocks for the widest depth, never more than co-resident
+    int64_t need = 1;
+    for (const LevelWork &w : h->levels) {
+      need = std::max<int64_t>(need, (w.le - w.lb + kThreads - 1) / kThreads);
+      need = std::max<int64_t>(need, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
+      need = std::max<int64_t>(need, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
+      need = std::max<int64_t>(need, w.wc1 - w.wc0);
+    }
+    h->persist_grid = (int)std::max<int64_t>(1, std::min(need, cap));
+  }
+  a.bar.expected = (unsigned)h->persist_grid + (unsigned)h->test_missing_arrivals;
+  CK(cudaMemsetAsync(bar, 0, 4, s));  // arrivals (a timed-out launch leaves them set)
+  CK(launch_persistent<T>(h->maxa_tier, L, h->persist_grid, s, a, nullptr));
+  return CFR_OK;
+}
+
+template <typename T>
+static int iterate_t(cfr_handle *h, int64_t n, cudaStream_t s) {
+  if (h->c.D == 0) {  // root is terminal: nothing to update but the counter
+    bump_t_kernel<<<1, 1, 0, s>>>(h->p<long long>(h->b_t), n);
+    CK(cudaGetLastError());
+    return CFR_OK;
+  }
+  if (h->exec_form == CFR_EXEC_LEVELS) {
+    for (int64_t i = 0; i < n; ++i) {
+      int rc = enqueue_iteration<T>(h, s);
+      if (rc) return rc;
+    }
+    return CFR_OK;
+  }
+  if (h->exec_form == CFR_EXEC_PERSISTENT) return launch_persistent_form<T>(h, n, s);
+  // graph form: capture one iteration once, replay it n times
+  if (h->gexec && h->graph_arena != h->arena)
+    return set_err(CFR_ERR_REBOUND, "captured graph refers to another arena");
+  if (!h->gexec) {
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration<T>(h, h->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) {
+      // capture failed: warn once, fall back to per-level launches (same kernels, same order)
+      static bool warned = false;
+      if (!warned) { fprintf(stderr, "cfr: graph capture failed (%s); using per-level launches\n", cudaGetErrorString(e)); warned = true; }
+      cudaGetLastError();
+      h->exec_form = CFR_EXEC_LEVELS;
+      return iterate_t<T>(h, n, s);
+    }
+    CK(cudaGraphInstantiate(&h->gexec, graph, 0));
+    cudaGraphDestroy(graph);
+    h->graph_arena = h->arena;
+  }
+  for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(h->gexec, s));
+  return CFR_OK;
+}
+
+extern "C" int cfr_iterate(cfr_handle *h, int64_t n, void *stream) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_iterate: null handle");
+  if (n < 0) return set_err(CFR_ERR_ARG, "cfr_iterate: negative n");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_iterate: call cfr_bind first");
+  if (n == 0) return CFR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = h->precision == CFR_P64 ? iterate_t<double>(h, n, s) : iterate_t<float>(h, n, s);
+  if (rc == CFR_OK) h->iteration_host += n;
+  return rc;
+}
+
+extern "C" int cfr_synchronize(cfr_handle *h, void *stream) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_synchronize: null handle");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_synchronize: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(s));
+  int err = 0;
+  CK(cudaMemcpy(&err, h->arena + h->b_err.off, 4, cudaMemcpyDeviceToHost));
+  if (err) {
+    CK(cudaMemset(h->arena + h->b_err.off, 0, 4));
+    return set_err(CFR_ERR_TIMEOUT, "persistent kernel: a grid barrier gave up waiting; the state is undefined until cfr_reset");
+  }
+  return CFR_OK;
+}
+
+// ------------------------------------------------------------- read-out
+static int deliver(cfr_handle *h, const double *dev_compiled, double *out, int on_device, cudaStream_t s) {
+  const Compiled &c = h->c;
+  if (c.A == 0) return CFR_OK;
+  double *dst = on_device ? out : h->p<double>(h->b_out);
+  permute_kernel<<<grid_for(c.A, kThreads), kThreads, 0, s>>>(h->p<int32_t>(h->b_spec_slot), dev_compiled, dst, (int32_t)c.A);
+  CK(cudaGetLastError());
+  if (!on_device) {
+    CK(cudaMemcpyAsync(out, dst, 8 * c.A, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return CFR_OK;
+}
+
+extern "C" int cfr_avg_strategy(cfr_handle *h, double *out, int on_device, void *stream) {
+  if (!h || (!out && h->c.A > 0)) return set_err(CFR_ERR_ARG, "cfr_avg_strategy: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_avg_strategy: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Compiled &c = h->c;
+  if (c.I == 0) return CFR_OK;
+  avg_normalize_kernel<<<grid_for(c.I, kThreads), kThreads, 0, s>>>(h->p<int32_t>(h->b_iset_slot), (int32_t)c.I,
+                                                                     h->p<double>(h->b_avg), h->p<double>(h->b_sbs));
+  CK(cudaGetLastError());
+  return deliver(h, h->p<double>(h->b_sbs), out, on_device, s);
+}
+
+extern "C" int cfr_current_strategy(cfr_handle *h, double *out, int on_device, void *stream) {
+  if (!h || (!out && h->c.A > 0)) return set_err(CFR_ERR_ARG, "cfr_current_strategy: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_current_strategy: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Compiled &c = h->c;
+  if (c.A == 0) return CFR_OK;
+  double *tmp = h->p<double>(h->b_sbs);
+  if (h->precision == CFR_P64) CK(cudaMemcpyAsync(tmp, h->p<double>(h->b_sigma), 8 * c.A, cudaMemcpyDeviceToDevice, s));
+  else {
+    to_double_kernel<float><<<grid_for(c.A, kThreads), kThreads, 0, s>>>(h->p<float>(h->b_sigma), tmp, (int32_t)c.A);
+    CK(cudaGetLastError());
+  }
+  return deliver(h, tmp, out, on_device, s);
+}
+
+static int launch_br(cfr_handle *h, int d, cudaStream_t s) {
+  const LevelWork &w = h->levels[d];
+  const int L = h->level_lanes[d];
+  const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
+  const int nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
+  const int nb_is = nis > 0 ? grid_for(nis, kThreads / L) : 0;
+  const int nb_wide = w.wc1 - w.wc0;
+  CK(launch_br_level(h->maxa_tier, L, std::max(1, nb_ch + nb_wide + nb_is), s, game_view(h), h->p<double2>(h->b_reach2),
+                     h->p<double>(h->b_sbs), h->p<double2>(h->b_vb), h->p<double>(h->b_vavg), w, nb_ch));
+  return CFR_OK;
+}
+
+extern "C" int cfr_exploitability(cfr_handle *h, double *out_expl, double *out_br, void *stream) {
+  if (!h || !out_expl) return set_err(CFR_ERR_ARG, "cfr_exploitability: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_exploitability: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Compiled &c = h->c;
+  GameView g = game_view(h);
+  if (c.I > 0)
+    avg_normalize_kernel<<<grid_for(c.I, kThreads), kThreads, 0, s>>>(h->p<int32_t>(h->b_iset_slot), (int32_t)c.I,
+                                                                       h->p<double>(h->b_avg), h->p<double>(h->b_sbs));
+  CK(cudaGetLastError());
+  for (int64_t d = 0; d < c.D; ++d) {
+    const LevelWork &w = h->levels[d];
+    const int nb = grid_for(w.le - w.lb, kThreads);
+    fwd_level_kernel<double><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<double>(h->b_sbs),
+                                                                        h->p<double2>(h->b_reach2), w, nb);
+    CK(cudaGetLastError());
+  }
+  for (int64_t d = c.D - 1; d >= 0; --d) {
+    int rc = launch_br(h, (int)d, s);
+    if (rc) return rc;
+  }
+  double root[3];
+  CK(cudaMemcpyAsync(root, h->p<double2>(h->b_vb), 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(root + 2, h->p<double>(h->b_vavg), 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *out_expl = 0.5 * (root[0] - root[1]);
+  if (out_br) { out_br[0] = root[0]; out_br[1] = root[1]; out_br[2] = root[2]; }
+  return CFR_OK;
+}
+
+// ------------------------------------------------------------- lifecycle
+extern "C" int cfr_reset(cfr_handle *h, void *stream) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_reset: null handle");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_reset: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
+  if (h->c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * h->c.n_wide, s));
+  return h->precision == CFR_P64 ? init_state<double>(h, s) : init_state<float>(h, s);
+}
+
+extern "C" int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream) {
+  if (!h || !payoff) return set_err(CFR_ERR_ARG, "cfr_set_payoffs: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_set_payoffs: not bound");
+  Compiled &c = h->c;
+  for (int64_t x = 0; x < c.N; ++x)
+    if (c.child_begin[x] == c.child_begin[x + 1]) {
+      const double u = payoff[c.spec_of_new[x]];
+      if (!std::isfinite(u)) return set_err(CFR_ERR_ARG, "cfr_set_payoffs: non-finite payoff");
+      c.tmpl[x] = c.pc[x] * u;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = h->precision == CFR_P64 ? init_values<double>(h, s) : init_values<float>(h, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return CFR_OK;
+}
+
+extern "C" int cfr_get_state(cfr_handle *h, double *R, double *avg, int64_t *t, void *stream) {
+  if (!h || ((!R || !avg) && h->c.A > 0) || !t) return set_err(CFR_ERR_ARG, "cfr_get_state: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_get_state: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Compiled &c = h->c;
+  std::vector<double> r(c.A), a(c.A);
+  long long tt = 0;
+  if (c.A) {
+    CK(cudaMemcpyAsync(r.data(), h->p<double>(h->b_R), 8 * c.A, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(a.data(), h->p<double>(h->b_avg), 8 * c.A, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaMemcpyAsync(&tt, h->p<long long>(h->b_t), 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int64_t q = 0; q < c.A; ++q) { R[c.spec_slot_of[q]] = r[q]; avg[c.spec_slot_of[q]] = a[q]; }
+  *t = tt;
+  return CFR_OK;
+}
+
+extern "C" int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, void *stream) {
+  if (!h || ((!R || !avg) && h->c.A > 0) || t < 0) return set_err(CFR_ERR_ARG, "cfr_set_state: bad argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_set_state: not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Compiled &c = h->c;
+  std::vector<double> r(c.A), a(c.A);
+  for (int64_t q = 0; q < c.A; ++q) { r[q] = R[c.spec_slot_of[q]]; a[q] = avg[c.spec_slot_of[q]]; }
+  long long tt = t;
+  if (c.A) {
+    CK(cudaMemcpyAsync(h->p<double>(h->b_R), r.data(), 8 * c.A, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->p<double>(h->b_avg), a.data(), 8 * c.A, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(h->p<long long>(h->b_t), &tt, 8, cudaMemcpyHostToDevice, s));
+  if (c.I) {
+    if (h->precision == CFR_P64)
+      rm_kernel<double><<<grid_for(c.I, kThreads), kThreads, 0, s>>>(h->p<int32_t>(h->b_iset_slot), (int32_t)c.I, h->p<double>(h->b_R), h->p<double>(h->b_sigma));
+    else
+      rm_kernel<float><<<grid_for(c.I, kThreads), kThreads, 0, s>>>(h->p<int32_t>(h->b_iset_slot), (int32_t)c.I, h->p<double>(h->b_R), h->p<float>(h->b_sigma));
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s));
+  h->iteration_host = t;
+  return CFR_OK;
+}
+
+extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count) {
+  if (!h || !count) return set_err(CFR_ERR_ARG, "cfr_export_array: null argument");
+  const Compiled &c = h->c;
+  const void *src = nullptr;
+  int64_t n = 0;
+  size_t esz = 4;
+  switch (which) {
+    case 0: src = c.child_begin.data(); n = (int64_t)c.child_begin.size(); break;
+    case 1: src = c.node_slot.data(); n = (int64_t)c.node_slot.size(); break;
+    case 2: src = c.level_begin.data(); n = (int64_t)c.level_begin.size(); break;
+    case 3: src = c.iset_slot.data(); n = (int64_t)c.iset_slot.size(); break;
+    case 4: src = c.iset_mem.data(); n = (int64_t)c.iset_mem.size(); break;
+    case 5: src = c.mem_node.data(); n = (int64_t)c.mem_node.size(); break;
+    case 6: src = c.chance_list.data(); n = (int64_t)c.chance_list.size(); break;
+    case 7: src = c.level_chance.data(); n = (int64_t)c.level_chance.size(); break;
+    case 8: src = c.level_iset.data(); n = (int64_t)c.level_iset.size(); break;
+    case 9: src = c.new_of_spec.data(); n = (int64_t)c.new_of_spec.size(); break;
+    case 10: src = c.tmpl.data(); n = (int64_t)c.tmpl.size(); esz = 8; break;
+    case 11: src = c.spec_slot_of.data(); n = (int64_t)c.spec_slot_of.size(); break;
+    default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
+  }
+  *count = n;
+  if (!out) return CFR_OK;
+  if (capacity < n) return set_err(CFR_ERR_ARG, "cfr_export_array: capacity %lld < %lld", (long long)capacity, (long long)n);
+  if (n) memcpy(out, src, esz * (size_t)n);
+  return CFR_OK;
+}
+
+extern "C" int cfr_debug_set(cfr_handle *h, int key, int64_t value) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_debug_set: null handle");
+  if (key == CFR_DEBUG_BARRIER_MISSING_ARRIVALS) {
+    if (value < 0 || value > 1024) return set_err(CFR_ERR_ARG, "cfr_debug_set: bad value");
+    h->test_missing_arrivals = (int)value;
+    return CFR_OK;
+  }
+  return set_err(CFR_ERR_ARG, "cfr_debug_set: unknown key %d", key);
+}

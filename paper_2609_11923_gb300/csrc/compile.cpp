@@ -1,0 +1,262 @@
+// compile.cpp — host game compiler (the paper's Algorithm "Compile", steps
+// 1-8, Appendix H): validation, slot prefix sums, breadth-first node arrays,
+// depth blocks (eq. (blocks)), chance folding into the values template
+// (eq. (template)) and index emission. Differences from the paper's layout:
+// edges are implicit (siblings are contiguous, so node h's children are
+// child_begin[h] .. child_begin[h+1]-1 and edge e leads to node e+1), indices
+// are int32, and information-set members are listed per set (member CSR) so
+// that the regret update is a per-set segmented reduction instead of a
+// scatter.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "compiled.h"
+
+namespace cfr {
+
+static int fail(std::string &err, const std::string &msg) {
+  err = msg;
+  return CFR_ERR_INVALID_SPEC;
+}
+
+int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
+  try {
+    const int64_t N = s.n_nodes, I = s.n_infosets;
+    if (N < 1 || N >= (int64_t(1) << 31) - 2) return fail(err, "n_nodes must be in [1, 2^31-2)");
+    if (I < 0 || I >= (int64_t(1) << 30)) return fail(err, "n_infosets out of range");
+    if (!s.kind || !s.infoset || !s.child_begin || (!s.child && s.child_begin[N] > 0) || !s.payoff ||
+        (I > 0 && (!s.iset_player || !s.iset_nact)))
+      return fail(err, "null array in game spec");
+    const int64_t E = s.child_begin[N];
+    if (s.child_begin[0] != 0 || E != N - 1) return fail(err, "child_begin must start at 0 and end at n_nodes-1 (a tree)");
+    if (E > 0 && !s.chance_prob) {
+      // probabilities are only needed below chance nodes
+      for (int64_t v = 0; v < N; ++v)
+        if (s.kind[v] == CFR_CHANCE) return fail(err, "chance_prob is null but the game has chance nodes");
+    }
+    // ---- step 1: structural checks
+    int64_t A = 0;
+    std::vector<int64_t> spec_off(I + 1, 0);
+    for (int64_t i = 0; i < I; ++i) {
+      if (s.iset_player[i] != 0 && s.iset_player[i] != 1) return fail(err, "iset_player must be 0 or 1");
+      if (s.iset_nact[i] < 1 || s.iset_nact[i] > kMaxActions) return fail(err, "iset_nact must be in [1, 64]");
+      spec_off[i + 1] = spec_off[i] + s.iset_nact[i];
+    }
+    A = spec_off[I];
+    if (A >= (int64_t(1) << 30)) return fail(err, "too many slots (>= 2^30)");
+    for (int64_t v = 0; v < N; ++v) {
+      const int k = s.kind[v];
+      const int64_t nch = s.child_begin[v + 1] - s.child_begin[v];
+      if (nch < 0) return fail(err, "child_begin must be non-decreasing");
+      if (k == CFR_TERMINAL) {
+        if (nch != 0) return fail(err, "terminal node with children");
+        if (!std::isfinite(s.payoff[v])) return fail(err, "non-finite payoff");
+      } else if (k == CFR_CHANCE) {
+        if (nch < 1) return fail(err, "chance node without children");
+        double sum = 0.0;
+        for (int64_t q = s.child_begin[v]; q < s.child_begin[v + 1]; ++q) {
+          const double p = s.chance_prob[q];
+          if (!(p >= 0.0) || !std::isfinite(p)) return fail(err, "chance probability must be finite and >= 0");
+          sum += p;
+        }
+        if (std::fabs(sum - 1.0) > 1e-6) return fail(err, "chance probabilities of a node must sum to 1");
+      } else if (k == CFR_PLAYER1 || k == CFR_PLAYER2) {
+        const int32_t is = s.infoset[v];
+        if (is < 0 || is >= I) return fail(err, "decision node with an information set out of range");
+        if (s.iset_player[is] != k - CFR_PLAYER1) return fail(err, "information set owned by another player");
+        if (s.iset_nact[is] != nch) return fail(err, "member's child count differs from its set's action count");
+      } else {
+        return fail(err, "unknown node kind");
+      }
+    }
+    // ---- step 3: breadth-first numbering (parents before children, siblings contiguous)
+    c.N = N; c.E = E; c.I = I; c.A = A;
+    c.new_of_spec.assign(N, -1);
+    c.spec_of_new.assign(N, -1);
+    std::vector<int32_t> depth(N, 0);
+    c.new_of_spec[0] = 0;
+    c.spec_of_new[0] = 0;
+    int64_t head = 0, tail = 1;
+    while (head < tail) {
+      const int32_t sv = c.spec_of_new[head];
+      for (int64_t q = s.child_begin[sv]; q < s.child_begin[sv + 1]; ++q) {
+        const int32_t ch = s.child[q];
+        if (ch <= 0 || ch >= N) return fail(err, "child id out of range (or the root listed as a child)");
+        if (c.new_of_spec[ch] >= 0) return fail(err, "node with two parents: not a tree");
+        c.new_of_spec[ch] = (int32_t)tail;
+        c.spec_of_new[tail] = ch;
+        depth[tail] = depth[head] + 1;
+        ++tail;
+      }
+      ++head;
+    }
+    if (tail != N) return fail(err, "nodes unreachable from the root");
+    // ---- step 5: depth schedule
+    const int32_t maxd = depth[N - 1];
+    int64_t D = 0;
+    {
+      int32_t maxd_int = -1;
+      for (int64_t h = 0; h < N; ++h) {
+        const int32_t sv = c.spec_of_new[h];
+        if (s.child_begin[sv + 1] > s.child_begin[sv]) maxd_int = std::max(maxd_int, depth[h]);
+      }
+      D = maxd_int + 1;  // number of parent depths (every depth below the deepest parent has one)
+    }
+    c.D = D;
+    c.level_begin.assign(D + 2, (int32_t)N);
+    c.level_begin[0] = 0;
+    for (int64_t h = N - 1; h >= 0; --h)
+      if (depth[h] <= D) c.level_begin[depth[h]] = (int32_t)h;
+    for (int64_t d = D; d >= 0; --d)  // depths with no node (impossible in a tree) stay consistent
+      if (c.level_begin[d] > c.level_begin[d + 1]) c.level_begin[d] = c.level_begin[d + 1];
+    (void)maxd;
+    // ---- node arrays and chance folding
+    c.child_begin.assign(N + 1, 0);
+    c.node_slot.assign(N, -1);
+    c.pc.assign(N, 0.0);
+    c.tmpl.assign(N, 0.0);
+    c.pc[0] = 1.0;
+    int64_t next = 1;
+    c.n_dec = c.n_chance = c.n_term = c.n_int = 0;
+    c.max_act = 0;
+    for (int64_t h = 0; h < N; ++h) {
+      const int32_t sv = c.spec_of_new[h];
+      const int k = s.kind[sv];
+      const int64_t b = s.child_begin[sv], e = s.child_begin[sv + 1];
+      c.child_begin[h] = (int32_t)next;
+      if (e > b && c.new_of_spec[s.child[b]] != next) return fail(err, "internal: children not contiguous");
+      next += e - b;
+      if (k == CFR_TERMINAL) {
+        ++c.n_term;
+        c.tmpl[h] = c.pc[h] * s.payoff[sv];  // values template, eq. (template)
+        continue;
+      }
+      ++c.n_int;
+      if (k != CFR_CHANCE) c.max_act = std::max<int64_t>(c.max_act, e - b);
+      for (int64_t q = b; q < e; ++q) {
+        const int32_t ch = c.new_of_spec[s.child[q]];
+        c.pc[ch] = (k == CFR_CHANCE) ? c.pc[h] * s.chance_prob[q] : c.pc[h];
+      }
+      if (k == CFR_CHANCE) ++c.n_chance; else ++c.n_dec;
+    }
+    c.child_begin[N] = (int32_t)next;
+    // ---- information sets: order by (depth, player, first member)
+    std::vector<int32_t> first(I, -1), cid_of_spec(I, -1);
+    std::vector<int32_t> enc;  // spec sets in order of their first member
+    enc.reserve(I);
+    for (int64_t h = 0; h < N; ++h) {
+      const int32_t sv = c.spec_of_new[h];
+      const int k = s.kind[sv];
+      if (k != CFR_PLAYER1 && k != CFR_PLAYER2) continue;
+      const int32_t is = s.infoset[sv];
+      if (first[is] < 0) { first[is] = (int32_t)h; enc.push_back(is); }
+      else if (depth[first[is]] != depth[h])
+        return fail(err, "information set with members at different depths");
+    }
+    if ((int64_t)enc.size() != I) return fail(err, "information set without members");
+    c.level_iset.assign(2 * D + 1, 0);
+    {
+      std::vector<int32_t> order;
+      order.reserve(I);
+      size_t i = 0;
+      for (int64_t d = 0; d < D; ++d) {
+        size_t j = i;
+        while (j < enc.size() && depth[first[enc[j]]] == d) ++j;
+        c.level_iset[2 * d] = (int32_t)order.size();
+        for (size_t q = i; q < j; ++q) if (s.iset_player[enc[q]] == 0) order.push_back(enc[q]);
+        c.level_iset[2 * d + 1] = (int32_t)order.size();
+        for (size_t q = i; q < j; ++q) if (s.iset_player[enc[q]] == 1) order.push_back(enc[q]);
+        i = j;
+      }
+      c.level_iset[2 * D] = (int32_t)order.size();
+      if (i != enc.size()) return fail(err, "internal: information set below the deepest parent");
+      for (size_t q = 0; q < order.size(); ++q) cid_of_spec[order[q]] = (int32_t)q;
+      c.iset_slot.assign(I + 1, 0);
+      c.spec_slot_of.assign(A, 0);
+      for (int64_t q = 0; q < I; ++q) {
+        const int32_t sp = order[q];
+        c.iset_slot[q + 1] = c.iset_slot[q] + s.iset_nact[sp];
+        for (int a = 0; a < s.iset_nact[sp]; ++a) c.spec_slot_of[c.iset_slot[q] + a] = (int32_t)(spec_off[sp] + a);
+      }
+    }
+    // member lists (counting sort by compiled set, ascending node id)
+    c.iset_mem.assign(I + 1, 0);
+    for (int64_t h = 0; h < N; ++h) {
+      const int32_t sv = c.spec_of_new[h];
+      const int k = s.kind[sv];
+      if (k == CFR_PLAYER1 || k == CFR_PLAYER2) c.iset_mem[cid_of_spec[s.infoset[sv]] + 1]++;
+    }
+    for (int64_t q = 0; q < I; ++q) c.iset_mem[q + 1] += c.iset_mem[q];
+    c.mem_node.assign(c.n_dec, 0);
+    {
+      std::vector<int32_t> fill(c.iset_mem.begin(), c.iset_mem.end() - 1);
+      for (int64_t h = 0; h < N; ++h) {
+        const int32_t sv = c.spec_of_new[h];
+        const int k = s.kind[sv];
+        if (k != CFR_PLAYER1 && k != CFR_PLAYER2) continue;
+        const int32_t cid = cid_of_spec[s.infoset[sv]];
+        c.mem_node[fill[cid]++] = (int32_t)h;
+        c.node_slot[h] = c.iset_slot[cid] | (k == CFR_PLAYER2 ? kSlotP2Bit : 0);
+      }
+    }
+    // chance nodes per depth (narrow ones per thread, wide ones by chunks)
+    c.chance_list.clear();
+    c.chance_list.reserve(c.n_chance);
+    c.wide_list.clear();
+    c.level_chance.assign(D + 1, 0);
+    c.level_wide.assign(D + 1, 0);
+    c.wide_chunk.assign(1, 0);
+    for (int64_t d = 0; d < D; ++d) {
+      c.level_chance[d] = (int32_t)c.chance_list.size();
+      c.level_wide[d] = (int32_t)c.wide_list.size();
+      for (int64_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h) {
+        if (s.kind[c.spec_of_new[h]] != CFR_CHANCE) continue;
+        const int64_t nch = c.child_begin[h + 1] - c.child_begin[h];
+        if (nch > kWide) {
+          c.wide_list.push_back((int32_t)h);
+          c.wide_chunk.push_back(c.wide_chunk.back() + (int32_t)((nch + kWideChunk - 1) / kWideChunk));
+        } else {
+          c.chance_list.push_back((int32_t)h);
+        }
+      }
+    }
+    c.level_chance[D] = (int32_t)c.chance_list.size();
+    c.level_wide[D] = (int32_t)c.wide_list.size();
+    c.n_wide = (int64_t)c.wide_list.size();
+    // per-depth member statistics (used to size the per-set lane groups)
+    c.level_max_members.assign(D, 0);
+    c.level_mean_members.assign(D, 0.0);
+    for (int64_t d = 0; d < D; ++d) {
+      const int32_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
+      int64_t tot = 0;
+      for (int32_t q = i0; q < i1; ++q) {
+        const int32_t m = c.iset_mem[q + 1] - c.iset_mem[q];
+        c.level_max_members[d] = std::max(c.level_max_members[d], m);
+        tot += m;
+      }
+      c.level_mean_members[d] = i1 > i0 ? (double)tot / (double)(i1 - i0) : 0.0;
+    }
+    return CFR_OK;
+  } catch (const std::bad_alloc &) {
+    err = "out of host memory while compiling";
+    return CFR_ERR_HOST_MEMORY;
+  }
+}
+
+int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
+  // Forward (levels 0..D-1): every node's child range + slot word (8 B), each
+  // internal node's two reach lanes, each child's two reach lanes written,
+  // the strategy vector read once. Backward: per set its slot and member
+  // offsets (8 B); per slot R and the average read+written (FP64) and the
+  // strategy read+written; per member its id, first child, reach lanes and
+  // its value written; per chance node its id, child range and value; every
+  // edge's child value read once.
+  const int64_t T = precision == CFR_P64 ? 8 : 4;
+  const int64_t n_upper = c.D > 0 ? c.level_begin[c.D] : 0;
+  return 8 * n_upper + 2 * T * c.n_int + 3 * T * c.E + 8 * c.I + (32 + 3 * T) * c.A +
+         (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance;
+}
+
+}  // namespace cfr

@@ -1,0 +1,60 @@
+// compiled.h — host-side compiled game (output of the compiler, input of the
+// runtime). Plain C++; no CUDA types so the compiler builds with any C++17
+// compiler.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cfr.h"
+
+namespace cfr {
+
+// Bit 30 of node_slot marks a player-2 decision node; the low 30 bits hold
+// the first slot of the node's information set. Chance and terminal nodes
+// hold -1.
+constexpr int32_t kSlotP2Bit = 1 << 30;
+constexpr int32_t kSlotMask = kSlotP2Bit - 1;
+constexpr int kMaxActions = 64;
+// Chance nodes with more than kWide children ("wide", e.g. a deal root) are
+// handled by chunks of kWideChunk children instead of one thread.
+constexpr int kWide = 1024;
+constexpr int kWideChunk = 2048;
+
+struct Compiled {
+  int64_t N = 0, E = 0, I = 0, A = 0, D = 0;
+  int64_t n_dec = 0, n_chance = 0, n_term = 0, n_int = 0, max_act = 0;
+  // Breadth-first node numbering: parent before child, siblings contiguous
+  // in action order. Node h's children are child_begin[h] .. child_begin[h+1]-1.
+  std::vector<int32_t> child_begin;  // [N+1]
+  std::vector<int32_t> node_slot;    // [N]
+  std::vector<int32_t> level_begin;  // [D+2]: nodes of depth d are level_begin[d] .. level_begin[d+1]-1
+  // Information sets in compiled order: by depth, player 1 before player 2,
+  // then by first member. Slots are contiguous per set in that order.
+  std::vector<int32_t> iset_slot;    // [I+1]
+  std::vector<int32_t> iset_mem;     // [I+1] offsets into mem_node
+  std::vector<int32_t> mem_node;     // [n_dec] members, ascending node id per set
+  std::vector<int32_t> level_iset;   // [2D+1]: depth d: P1 sets [2d, 2d+1), P2 sets [2d+1, 2d+2)
+  std::vector<int32_t> chance_list;  // [n_chance - n_wide] chance nodes with <= kWide children, ascending id
+  std::vector<int32_t> level_chance; // [D+1]
+  std::vector<int32_t> wide_list;    // [n_wide] chance nodes with > kWide children, ascending id
+  std::vector<int32_t> level_wide;   // [D+1]
+  std::vector<int32_t> wide_chunk;   // [n_wide+1] prefix of chunk counts (kWideChunk children each)
+  int64_t n_wide = 0;
+  std::vector<double> pc;            // [N] chance product root..h (retained for set_payoffs)
+  std::vector<double> tmpl;          // [N] pi_c(z) * u(z) at terminals, else 0 (eq. (template))
+  std::vector<int32_t> new_of_spec;  // [N] compiled id of each spec node
+  std::vector<int32_t> spec_of_new;  // [N]
+  std::vector<int32_t> spec_slot_of; // [A] spec slot of each compiled slot
+  std::vector<int32_t> level_max_members; // [D] largest information set per depth
+  std::vector<double> level_mean_members; // [D]
+};
+
+// Returns CFR_OK or CFR_ERR_INVALID_SPEC / CFR_ERR_HOST_MEMORY with a message.
+int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err);
+
+// Algorithmic device bytes of one iteration (each array element touched the
+// minimum number of times the layout allows; see the design notes).
+int64_t algo_bytes_per_iter(const Compiled &c, int precision);
+
+}  // namespace cfr

@@ -1,0 +1,627 @@
+// kernels.cuh — sm_103a kernels of one CFR+ iteration over the compiled game.
+//
+// Stage (a), forward reach (eq. (opfwd) on both lanes, eq. (lanes)): one
+//   thread per node of depth d writes both reach lanes of its children. The
+//   acting player's lane is multiplied by sigma(I, a); the other lane and
+//   chance edges copy through (the paper's sentinel multiplier 1 becomes a
+//   branch on the node's slot word, uniform over the node's children).
+// Stage (b), terminal utility: the value array holds pi_c(z) u(z) at every
+//   terminal from bind time on (eq. (template)); no kernel writes it again,
+//   which removes the per-iteration template copy.
+// Stages (c) + (d), backward (eqs. (opbwd), (instregret), (regret), (rm)):
+//   per depth, chance nodes sum their children's values (one thread each) and
+//   every information set of that depth is handled by one group of LANES
+//   lanes: members' values v(h) = sum_a sigma(I,a) v(h.a), the regret terms
+//   s * pi_{-i}(h) * (v(h.a) - v(h)) and the average terms pi_i(h) sigma(I,a)
+//   are summed over members in a fixed order (no atomics), then
+//   R <- max(R + r, 0) (CFR+), avg += t * m, and sigma^{t+1}(I,.) = RM(R) is
+//   written in place (nothing reads sigma(I,.) again in this iteration).
+//   P64 sums members strictly in ascending node order (lane order within each
+//   chunk of LANES members), the order of the recursive definition; P32 keeps
+//   per-lane partial sums and finishes with an xor butterfly (fixed shape,
+//   deterministic run to run).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cfr {
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using vec2_t = typename Vec2<T>::type;
+
+constexpr int kThreads = 256;
+constexpr int32_t kP2Bit = 1 << 30;
+constexpr int32_t kMask = kP2Bit - 1;
+
+// Loads of arrays that a persistent kernel rewrites between grid barriers go
+// around L1 (ld.global.cg): L1 is not coherent across SMs.
+template <bool PERSIST, typename X>
+__device__ __forceinline__ X ldm(const X *p) {
+  if constexpr (PERSIST) return __ldcg(p);
+  else return *p;
+}
+
+constexpr int32_t kWideNode = 1024;   // chance nodes above this fan-out go by chunks
+constexpr int32_t kWideChunkK = 2048; // children per chunk of a wide node
+
+struct GameView {
+  const int32_t *__restrict__ child_begin;
+  const int32_t *__restrict__ node_slot;
+  const int32_t *__restrict__ iset_slot;
+  const int32_t *__restrict__ iset_mem;
+  const int32_t *__restrict__ mem_node;
+  const int32_t *__restrict__ chance_list;
+  const int32_t *__restrict__ wide_list;   // wide chance nodes
+  const int32_t *__restrict__ wide_chunk;  // prefix of their chunk counts
+  double *wide_part;                       // [3 * chunks] partial sums
+  unsigned *wide_cnt;                      // [wide nodes] chunks finished (reset by the last one)
+};
+
+template <typename T> struct StateView {
+  vec2_t<T> *reach;
+  T *v;
+  T *sigma;
+  double *R;
+  double *avg;
+  long long *t;  // completed iterations; iteration t+1 uses weight w = t+1
+};
+
+struct LevelWork {
+  int32_t lb, le;         // nodes of depth d
+  int32_t ch0, ch1;       // chance_list range of depth d (narrow chance nodes)
+  int32_t is0, is2, is1;  // sets of depth d: player 1 [is0, is2), player 2 [is2, is1)
+  int32_t wd0, wd1;       // wide_list range of depth d
+  int32_t wc0, wc1;       // their chunks
+  int32_t pad;
+};
+
+// The wide node owning chunk q (binary search over the level's prefix).
+__device__ __forceinline__ int32_t wide_of_chunk(const GameView &g, const LevelWork &w, int32_t q) {
+  int32_t lo = w.wd0, hi = w.wd1 - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(g.wide_chunk + mid) <= q) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Fixed-shape block reduction (all threads call it; the result is valid in thread 0).
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double sm[kThreads];
+  __syncthreads();
+  sm[threadIdx.x] = x;
+  __syncthreads();
+#pragma unroll
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sm[0];
+}
+
+// ------------------------------------------------------------ forward reach
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void fwd_node(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t h) {
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  if (cb == ce || ce - cb > kWideNode) return;  // terminal, or wide (done by chunks)
+  const int32_t s = __ldg(g.node_slot + h);
+  const vec2_t<T> r = ldm<PERSIST>(reach + h);
+  if (s < 0) {
+    for (int32_t c = cb; c < ce; ++c) reach[c] = r;
+  } else {
+    const int32_t base = (s & kMask) - cb;
+    if (s & kP2Bit) {
+      for (int32_t c = cb; c < ce; ++c) {
+        vec2_t<T> o = r;
+        o.y = r.y * ldm<PERSIST>(sigma + base + c);
+        reach[c] = o;
+      }
+    } else {
+      for (int32_t c = cb; c < ce; ++c) {
+        vec2_t<T> o = r;
+        o.x = r.x * ldm<PERSIST>(sigma + base + c);
+        reach[c] = o;
+      }
+    }
+  }
+}
+
+// One chunk of a wide chance node: its children copy the node's reach.
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void fwd_wide_chunk(const GameView &g, const LevelWork &w, vec2_t<T> *reach, int32_t q) {
+  const int32_t wi = wide_of_chunk(g, w, q);
+  const int32_t h = __ldg(g.wide_list + wi);
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const int32_t c0 = cb + (q - __ldg(g.wide_chunk + wi)) * kWideChunkK;
+  const int32_t c1 = min(ce, c0 + kWideChunkK);
+  const vec2_t<T> r = ldm<PERSIST>(reach + h);
+  for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) reach[c] = r;
+}
+
+// Grid: nb_nodes blocks over the nodes of depth d, then one block per wide chunk.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T *sigma, vec2_t<T> *reach,
+                                                            LevelWork w, int nb_nodes) {
+  if ((int)blockIdx.x >= nb_nodes) {
+    fwd_wide_chunk<T, false>(g, w, reach, w.wc0 + (int32_t)blockIdx.x - nb_nodes);
+    return;
+  }
+  const int32_t stride = nb_nodes * blockDim.x;
+  for (int32_t h = w.lb + blockIdx.x * blockDim.x + threadIdx.x; h < w.le; h += stride)
+    fwd_node<T, false>(g, sigma, reach, h);
+}
+
+// ------------------------------------------------------------ group helpers
+template <int LANES>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (LANES == 32) return 0xffffffffu;
+  else return ((1u << LANES) - 1u) << (((threadIdx.x & 31) / LANES) * LANES);
+}
+
+template <int LANES, typename X>
+__device__ __forceinline__ X group_sum_butterfly(X x, unsigned mask) {
+#pragma unroll
+  for (int off = LANES / 2; off > 0; off >>= 1) x += __shfl_xor_sync(mask, x, off, LANES);
+  return x;
+}
+
+// ------------------------------------------------------------- backward
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void bwd_chance(const GameView &g, T *v, int32_t h) {
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  T s = T(0);
+  for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
+  v[h] = s;
+}
+
+// One chunk of a wide chance node's value sum. P32: every chunk block sums
+// its children (fixed shape), and the block that finishes last adds the
+// chunk partials in chunk order (an integer ticket decides who is last; no
+// float atomics). P64: the first chunk's block sums all children strictly
+// left to right, the order of the recursive definition.
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWork &w, T *v, int32_t q) {
+  const int32_t wi = wide_of_chunk(g, w, q);
+  const int32_t h = __ldg(g.wide_list + wi);
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const int32_t q0 = __ldg(g.wide_chunk + wi), nq = __ldg(g.wide_chunk + wi + 1) - q0;
+  if constexpr (sizeof(T) == 8) {
+    if (q == q0 && threadIdx.x == 0) {
+      T s = T(0);
+      for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
+      v[h] = s;
+    }
+    return;
+  } else {
+    const int32_t c0 = cb + (q - q0) * kWideChunkK, c1 = min(ce, c0 + kWideChunkK);
+    double x = 0.0;
+    for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) x += (double)ldm<PERSIST>(v + c);
+    x = block_sum(x);
+    __shared__ unsigned s_ticket;
+    if (threadIdx.x == 0) {
+      g.wide_part[q] = x;
+      __threadfence();
+      s_ticket = atomicAdd(g.wide_cnt + wi, 1u);
+    }
+    __syncthreads();
+    if (s_ticket == (unsigned)(nq - 1) && threadIdx.x == 0) {
+      __threadfence();
+      double tot = 0.0;
+      for (int32_t k = 0; k < nq; ++k) tot += __ldcg(g.wide_part + q0 + k);
+      v[h] = (T)tot;
+      g.wide_cnt[wi] = 0u;
+    }
+  }
+}
+
+// One information set, processed by the LANES lanes of one group.
+template <typename T, int MAXA, int LANES, bool PERSIST>
+__device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
+                                        int lane, unsigned mask, double wt, int rule) {
+  constexpr bool ORDERED = sizeof(T) == 8;
+  const int32_t sb = __ldg(g.iset_slot + I);
+  const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
+  const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+  T sig[MAXA], racc[MAXA], macc[MAXA];
+#pragma unroll
+  for (int a = 0; a < MAXA; ++a) {
+    sig[a] = a < na ? ldm<PERSIST>(st.sigma + sb + a) : T(0);
+    racc[a] = T(0);
+    macc[a] = T(0);
+  }
+  const T sgn = p2 ? T(-1) : T(1);
+  for (int32_t k0 = m0; k0 < m1; k0 += LANES) {
+    const int32_t k = k0 + lane;
+    T d[MAXA], mm[MAXA];
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
+    if (k < m1) {
+      const int32_t h = __ldg(g.mem_node + k);
+      const int32_t cb = __ldg(g.child_begin + h);
+      const vec2_t<T> r = ldm<PERSIST>(st.reach + h);
+      T vc[MAXA];
+      T vh = T(0);
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) {
+        if (a < na) {
+          vc[a] = ldm<PERSIST>(st.v + cb + a);
+          vh = vh + sig[a] * vc[a];
+        }
+      }
+      st.v[h] = vh;
+      const T po = p2 ? r.x : r.y;  // opponent's reach (chance is inside v)
+      const T pw = p2 ? r.y : r.x;  // own reach
+      const T f = sgn * po;
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) {
+        if (a < na) {
+          d[a] = f * (vc[a] - vh);
+          mm[a] = pw * sig[a];
+        }
+      }
+    }
+    if constexpr (ORDERED) {
+      const int cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
+      for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) {
+          if (a < na) {
+            racc[a] = racc[a] + __shfl_sync(mask, d[a], j, LANES);
+            macc[a] = macc[a] + __shfl_sync(mask, mm[a], j, LANES);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) {
+        racc[a] += d[a];
+        macc[a] += mm[a];
+      }
+    }
+  }
+  if constexpr (!ORDERED) {
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a) {
+      if (a < na) {
+        racc[a] = group_sum_butterfly<LANES>(racc[a], mask);
+        macc[a] = group_sum_butterfly<LANES>(macc[a], mask);
+      }
+    }
+  }
+  if (lane == 0) {
+    double pos[MAXA];
+    double tot = 0.0;
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a) {
+      if (a < na) {
+        double Rn = st.R[sb + a] + (double)racc[a];
+        if (rule == 0) Rn = Rn > 0.0 ? Rn : 0.0;  // CFR+ clamp
+        st.R[sb + a] = Rn;
+        st.avg[sb + a] += wt * (double)macc[a];    // linear averaging, sigma^t
+        pos[a] = Rn > 0.0 ? Rn : 0.0;
+        tot += pos[a];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a)
+      if (a < na) st.sigma[sb + a] = (T)(tot > 0.0 ? pos[a] / tot : 1.0 / (double)na);
+  }
+}
+
+// Grid: nb_chance blocks over narrow chance nodes, then one block per wide
+// chunk, then the information-set groups.
+template <typename T, int MAXA, int LANES>
+__global__ void __launch_bounds__(kThreads) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
+                                                            int nb_chance, int rule, int bump_t) {
+  const int nb_wide = w.wc1 - w.wc0;
+  if ((int)blockIdx.x < nb_chance) {
+    const int32_t stride = nb_chance * blockDim.x;
+    for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride)
+      bwd_chance<T, false>(g, st.v, __ldg(g.chance_list + i));
+  } else if ((int)blockIdx.x < nb_chance + nb_wide) {
+    bwd_wide_chunk<T, false>(g, w, st.v, w.wc0 + (int32_t)blockIdx.x - nb_chance);
+  } else {
+    constexpr int GPB = kThreads / LANES;
+    const int first = nb_chance + nb_wide;
+    const int gid = ((int)blockIdx.x - first) * GPB + (int)threadIdx.x / LANES;
+    const int ngroups = ((int)gridDim.x - first) * GPB;
+    const int lane = threadIdx.x % LANES;
+    const unsigned mask = group_mask<LANES>();
+    const double wt = (double)(*st.t + 1);
+    for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
+      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule);
+  }
+  if (bump_t) {  // depth 0 holds only the root: no other block reads t here
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *st.t += 1;
+  }
+}
+
+static __global__ void bump_t_kernel(long long *t, long long n) { *t += n; }
+
+// ------------------------------------------------------- persistent form
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct Barrier {
+  unsigned *count;     // arrivals at the current barrier
+  unsigned *gen;       // generation, bumped by the last arrival
+  int *err;            // set to 1 when a wait gives up
+  long long spin_limit;
+  unsigned expected;   // arrivals that complete a barrier (gridDim.x normally)
+};
+
+// Grid-wide barrier with a bounded wait: returns false (and sets *err) when
+// the spin budget runs out, or when another block has reported an error.
+__device__ __forceinline__ bool grid_sync(const Barrier &b) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (gridDim.x == 1 && b.expected == 1) return true;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned g0 = ld_acquire_gpu(b.gen);
+    const unsigned arrived = atomicAdd(b.count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == b.expected) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      st_release_gpu(b.gen, g0 + 1u);
+    } else {
+      long long spins = 0;
+      while (ld_acquire_gpu(b.gen) == g0) {
+        if (++spins > b.spin_limit) {
+          atomicExch(b.err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (ok && *(volatile int *)b.err != 0) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T> struct PersistArgs {
+  GameView g;
+  StateView<T> st;
+  const LevelWork *lw;
+  int D;
+  int rule;
+  long long n_iter;
+  Barrier bar;
+};
+
+// All n iterations in one launch; depth levels separated by grid barriers
+// (2D barriers per iteration). The grid is co-resident (cooperative launch).
+template <typename T, int MAXA, int LANES>
+__global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) {
+  const long long t0 = __ldcg(a.st.t);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthr = gridDim.x * blockDim.x;
+  const int gid = tid / LANES, ngroups = nthr / LANES, lane = tid % LANES;
+  const unsigned mask = group_mask<LANES>();
+  for (long long it = 0; it < a.n_iter; ++it) {
+    for (int d = 0; d < a.D; ++d) {
+      const LevelWork w = a.lw[d];
+      for (int32_t h = w.lb + tid; h < w.le; h += nthr) fwd_node<T, true>(a.g, a.st.sigma, a.st.reach, h);
+      for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
+      if (!grid_sync(a.bar)) return;
+    }
+    const double wt = (double)(t0 + it + 1);
+    for (int d = a.D - 1; d >= 0; --d) {
+      const LevelWork w = a.lw[d];
+      for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, __ldg(a.g.chance_list + i));
+      for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
+      for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
+        bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule);
+      if (!grid_sync(a.bar)) return;
+    }
+  }
+  if (tid == 0) *a.st.t = t0 + a.n_iter;
+}
+
+// ---------------------------------------------------------- state set-up
+template <typename T>
+__global__ void init_state_kernel(const int32_t *iset_slot, int32_t n_sets, T *sigma, double *R, double *avg,
+                                  int32_t A, long long *t, vec2_t<T> *reach, double2 *reach2) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int32_t q = tid; q < A; q += stride) { R[q] = 0.0; avg[q] = 0.0; }
+  for (int32_t I = tid; I < n_sets; I += stride) {
+    const int32_t sb = iset_slot[I], na = iset_slot[I + 1] - sb;
+    for (int32_t a = 0; a < na; ++a) sigma[sb + a] = (T)(1.0 / (double)na);  // RM of zero regret
+  }
+  if (tid == 0) {
+    *t = 0;
+    vec2_t<T> one;
+    one.x = T(1); one.y = T(1);
+    reach[0] = one;  // root reach of both lanes (never overwritten)
+    reach2[0] = make_double2(1.0, 1.0);
+  }
+}
+
+template <typename T>
+__global__ void init_values_kernel(const int32_t *child_begin, const double *tmpl, int32_t N, T *v, double2 *vb,
+                                   double *vavg) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < N; h += stride) {
+    if (child_begin[h] == child_begin[h + 1]) {  // terminal: pi_c(z) u(z), eq. (template)
+      const double x = tmpl[h];
+      v[h] = (T)x;
+      vb[h] = make_double2(x, x);
+      vavg[h] = x;
+    }
+  }
+}
+
+// sigma from R by regret matching (used after a state upload)
+template <typename T>
+__global__ void rm_kernel(const int32_t *iset_slot, int32_t n_sets, const double *R, T *sigma) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < n_sets; I += stride) {
+    const int32_t sb = iset_slot[I], na = iset_slot[I + 1] - sb;
+    double tot = 0.0;
+    for (int32_t a = 0; a < na; ++a) tot += R[sb + a] > 0.0 ? R[sb + a] : 0.0;
+    for (int32_t a = 0; a < na; ++a) {
+      const double p = R[sb + a] > 0.0 ? R[sb + a] : 0.0;
+      sigma[sb + a] = (T)(tot > 0.0 ? p / tot : 1.0 / (double)na);
+    }
+  }
+}
+
+// ------------------------------------------------------------- read-out
+static __global__ void avg_normalize_kernel(const int32_t *iset_slot, int32_t n_sets, const double *avg, double *out) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < n_sets; I += stride) {
+    const int32_t sb = iset_slot[I], na = iset_slot[I + 1] - sb;
+    double tot = 0.0;
+    for (int32_t a = 0; a < na; ++a) tot += avg[sb + a];
+    for (int32_t a = 0; a < na; ++a) out[sb + a] = tot > 0.0 ? avg[sb + a] / tot : 1.0 / (double)na;
+  }
+}
+
+template <typename T>
+__global__ void to_double_kernel(const T *in, double *out, int32_t n) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) out[q] = (double)in[q];
+}
+
+// out[spec_slot_of[q]] = in[q]: compiled slot order -> spec slot order
+static __global__ void permute_kernel(const int32_t *spec_slot_of, const double *in, double *out, int32_t A) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < A; q += stride) out[spec_slot_of[q]] = in[q];
+}
+
+// ------------------------------------------------ exact best response (FP64)
+// Lane x of vb: player 1 best-responds (maximises), player 2 plays the
+// average. Lane y: player 2 best-responds (minimises player 1's payoff),
+// player 1 plays the average. vavg: both play the average. All values are
+// chance-weighted (eq. (template)), so the counterfactual weight of a member
+// is the opponent's reach under the average strategy alone.
+// Wide chance node, best-response values: chunk partials of (x, y, avg),
+// finished in chunk order by the last block (as bwd_wide_chunk).
+__device__ __forceinline__ void br_wide_chunk(const GameView &g, const LevelWork &w, double2 *vb, double *vavg,
+                                              int32_t q) {
+  const int32_t wi = wide_of_chunk(g, w, q);
+  const int32_t h = __ldg(g.wide_list + wi);
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const int32_t q0 = __ldg(g.wide_chunk + wi), nq = __ldg(g.wide_chunk + wi + 1) - q0;
+  const int32_t c0 = cb + (q - q0) * kWideChunkK, c1 = min(ce, c0 + kWideChunkK);
+  double sx = 0.0, sy = 0.0, sa = 0.0;
+  for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const double2 x = vb[c];
+    sx += x.x; sy += x.y; sa += vavg[c];
+  }
+  sx = block_sum(sx);
+  sy = block_sum(sy);
+  sa = block_sum(sa);
+  __shared__ unsigned s_ticket;
+  if (threadIdx.x == 0) {
+    g.wide_part[3 * q] = sx; g.wide_part[3 * q + 1] = sy; g.wide_part[3 * q + 2] = sa;
+    __threadfence();
+    s_ticket = atomicAdd(g.wide_cnt + wi, 1u);
+  }
+  __syncthreads();
+  if (s_ticket == (unsigned)(nq - 1) && threadIdx.x == 0) {
+    __threadfence();
+    double tx = 0.0, ty = 0.0, ta = 0.0;
+    for (int32_t k = 0; k < nq; ++k) {
+      tx += __ldcg(g.wide_part + 3 * (q0 + k));
+      ty += __ldcg(g.wide_part + 3 * (q0 + k) + 1);
+      ta += __ldcg(g.wide_part + 3 * (q0 + k) + 2);
+    }
+    vb[h] = make_double2(tx, ty);
+    vavg[h] = ta;
+    g.wide_cnt[wi] = 0u;
+  }
+}
+
+template <int MAXA, int LANES>
+__global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const double2 *reach2, const double *sbs,
+                                                           double2 *vb, double *vavg, LevelWork w, int nb_chance) {
+  const int nb_wide = w.wc1 - w.wc0;
+  if ((int)blockIdx.x >= nb_chance && (int)blockIdx.x < nb_chance + nb_wide) {
+    br_wide_chunk(g, w, vb, vavg, w.wc0 + (int32_t)blockIdx.x - nb_chance);
+    return;
+  }
+  if ((int)blockIdx.x < nb_chance) {
+    const int32_t stride = nb_chance * blockDim.x;
+    for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride) {
+      const int32_t h = __ldg(g.chance_list + i);
+      const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+      double sx = 0.0, sy = 0.0, sa = 0.0;
+      for (int32_t c = cb; c < ce; ++c) { const double2 x = vb[c]; sx += x.x; sy += x.y; sa += vavg[c]; }
+      vb[h] = make_double2(sx, sy);
+      vavg[h] = sa;
+    }
+    return;
+  }
+  constexpr int GPB = kThreads / LANES;
+  const int first = nb_chance + nb_wide;
+  const int gid = ((int)blockIdx.x - first) * GPB + (int)threadIdx.x / LANES;
+  const int ngroups = ((int)gridDim.x - first) * GPB;
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups) {
+    const int p = I >= w.is2 ? 1 : 0;
+    const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
+    const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+    double sg[MAXA], Q[MAXA];
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a) { sg[a] = a < na ? sbs[sb + a] : 0.0; Q[a] = 0.0; }
+    for (int32_t k0 = m0; k0 < m1; k0 += LANES) {
+      const int32_t k = k0 + lane;
+      double q[MAXA];
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
+      if (k < m1) {
+        const int32_t h = __ldg(g.mem_node + k);
+        const int32_t cb = __ldg(g.child_begin + h);
+        const double2 r = reach2[h];
+        const double po = p ? r.x : r.y;
+        double oth = 0.0, va = 0.0;
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) {
+          if (a < na) {
+            const double2 x = vb[cb + a];
+            q[a] = po * (p ? x.y : x.x);
+            oth += sg[a] * (p ? x.x : x.y);
+            va += sg[a] * vavg[cb + a];
+          }
+        }
+        reinterpret_cast<double *>(vb + h)[1 - p] = oth;
+        vavg[h] = va;
+      }
+      const int cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
+      for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a)
+          if (a < na) Q[a] += __shfl_sync(mask, q[a], j, LANES);
+      }
+    }
+    int best = 0;
+    for (int a = 1; a < na; ++a)
+      if (p == 0 ? Q[a] > Q[best] : Q[a] < Q[best]) best = a;
+    // every lane computed the same Q (the ordered sums are broadcast), so
+    // best agrees across the group without another shuffle
+    for (int32_t k = m0 + lane; k < m1; k += LANES) {
+      const int32_t h = __ldg(g.mem_node + k);
+      const int32_t cb = __ldg(g.child_begin + h);
+      reinterpret_cast<double *>(vb + h)[p] = reinterpret_cast<const double *>(vb + cb + best)[p];
+    }
+  }
+}
+
+}  // namespace cfr

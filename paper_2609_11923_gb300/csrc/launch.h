@@ -1,0 +1,24 @@
+// launch.h — host wrappers that pick the kernel instance (actions tier x
+// lanes per information set). Each wrapper is defined in its own translation
+// unit so the instances compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace cfr {
+
+template <typename T>
+cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, GameView g, StateView<T> st,
+                             LevelWork w, int nb_chance, int rule, int bump);
+
+// query_occupancy != nullptr: only report resident blocks per SM of the
+// chosen instance (nothing is launched).
+template <typename T>
+cudaError_t launch_persistent(int maxa, int lanes, int grid, cudaStream_t s, PersistArgs<T> a,
+                              int *query_occupancy);
+
+cudaError_t launch_br_level(int maxa, int lanes, int grid, cudaStream_t s, GameView g, const double2 *reach2,
+                            const double *sbs, double2 *vb, double *vavg, LevelWork w, int nb_chance);
+
+}  // namespace cfr

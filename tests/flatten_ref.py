@@ -1,0 +1,92 @@
+"""Independent re-derivation of the compiled arrays from a GameSpec (tests only).
+
+Written from the definitions, not from the C++ compiler: breadth-first
+numbering (the paper's compile pass: parents before children, siblings in
+action order), depth blocks = distinct parent depths (eq. (blocks)),
+information sets ordered by (depth, player, first member), slots contiguous in
+that order, members ascending, chance product along the path and the values
+template pi_c(z) u(z) (eq. (template)).
+"""
+from collections import deque
+
+import numpy as np
+
+TERMINAL, CHANCE, P1, P2 = 0, 1, 2, 3
+P2BIT = 1 << 30
+WIDE = 1024
+WIDE_CHUNK = 2048
+
+
+def flatten(g):
+    N = g.n_nodes
+    order = []
+    depth_of = {}
+    q = deque([(0, 0)])
+    while q:
+        v, d = q.popleft()
+        order.append(v)
+        depth_of[v] = d
+        for c in g.child[g.child_begin[v]:g.child_begin[v + 1]]:
+            q.append((int(c), d + 1))
+    new = np.empty(N, dtype=np.int64)
+    new[np.array(order)] = np.arange(N)
+    depth = np.array([depth_of[v] for v in order])
+    nch = np.array([g.child_begin[v + 1] - g.child_begin[v] for v in order])
+    child_begin = np.concatenate([[1], 1 + np.cumsum(nch)]).astype(np.int32)
+    internal = nch > 0
+    D = int(depth[internal].max()) + 1 if internal.any() else 0
+    level_begin = np.array([int(np.searchsorted(depth, d)) for d in range(D + 1)] + [N], dtype=np.int32)
+    kinds = np.array([g.kind[v] for v in order])
+    # information sets
+    first = {}
+    for h, v in enumerate(order):
+        if kinds[h] in (P1, P2):
+            first.setdefault(int(g.infoset[v]), h)
+    sets = sorted(first, key=lambda s: (depth[first[s]], int(g.iset_player[s]), first[s]))
+    cid = {s: i for i, s in enumerate(sets)}
+    nact = np.array([g.iset_nact[s] for s in sets], dtype=np.int64)
+    iset_slot = np.concatenate([[0], np.cumsum(nact)]).astype(np.int32)
+    spec_off = g.slot_offsets()
+    spec_slot_of = np.concatenate([np.arange(spec_off[s], spec_off[s + 1]) for s in sets]).astype(np.int32) \
+        if sets else np.zeros(0, np.int32)
+    members = [[] for _ in sets]
+    node_slot = np.full(N, -1, dtype=np.int32)
+    for h, v in enumerate(order):
+        if kinds[h] in (P1, P2):
+            c = cid[int(g.infoset[v])]
+            members[c].append(h)
+            node_slot[h] = iset_slot[c] | (P2BIT if kinds[h] == P2 else 0)
+    iset_mem = np.concatenate([[0], np.cumsum([len(m) for m in members])]).astype(np.int32)
+    mem_node = np.array([h for m in members for h in m], dtype=np.int32)
+    level_iset = [0]
+    for d in range(D):
+        for p in (0, 1):
+            level_iset.append(sum(1 for s in sets if depth[first[s]] < d or
+                                  (depth[first[s]] == d and int(g.iset_player[s]) <= p)))
+    level_iset = np.array(level_iset, dtype=np.int32)
+    chance_list, wide_list, level_chance, level_wide = [], [], [], []
+    for d in range(D):
+        level_chance.append(len(chance_list))
+        level_wide.append(len(wide_list))
+        for h in range(level_begin[d], level_begin[d + 1]):
+            if kinds[h] == CHANCE:
+                (wide_list if nch[h] > WIDE else chance_list).append(h)
+    level_chance.append(len(chance_list))
+    level_wide.append(len(wide_list))
+    # chance product along the path, then the template
+    pc = np.zeros(N)
+    pc[0] = 1.0
+    tmpl = np.zeros(N)
+    for h, v in enumerate(order):
+        b, e = g.child_begin[v], g.child_begin[v + 1]
+        for q_, c in zip(range(b, e), g.child[b:e]):
+            pc[new[c]] = pc[h] * g.chance_prob[q_] if kinds[h] == CHANCE else pc[h]
+        if kinds[h] == TERMINAL:
+            tmpl[h] = pc[h] * g.payoff[v]
+    return {
+        "child_begin": child_begin, "node_slot": node_slot, "level_begin": level_begin,
+        "iset_slot": iset_slot, "iset_mem": iset_mem, "mem_node": mem_node,
+        "chance_list": np.array(chance_list, dtype=np.int32), "level_chance": np.array(level_chance, dtype=np.int32),
+        "level_iset": level_iset, "new_of_spec": new.astype(np.int32), "tmpl": tmpl, "spec_slot_of": spec_slot_of,
+        "D": D, "wide_list": wide_list,
+    }

@@ -1,0 +1,178 @@
+"""Host compiler: bit-exact arrays against an independent flattener, the
+compile invariants of the paper (tree coverage, parent depth < child depth,
+D = number of parent depths), validation errors, and the C-ABI surface.
+CPU only: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gamegen as gg
+from paper_2609_11923_gb300 import cfr
+from tests.flatten_ref import flatten
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+GAMES = {
+    "kuhn": lambda: gg.kuhn(),
+    "tiny": lambda: gg.tiny_card(),
+    "rt6": lambda: gg.random_tree(1, depth=6),
+    "rt8": lambda: gg.random_tree(2, depth=8, max_group=16),
+    "endgame": lambda: gg.endgame(3, 3000),
+    "card_small": lambda: gg.large_card(3, 2, 1, 1),
+    "wide_root": lambda: gg.endgame(11, 60000),
+}
+
+
+@pytest.mark.parametrize("name", list(GAMES))
+def test_arrays_bit_exact(name):
+    g = GAMES[name]()
+    ref = flatten(g)
+    h = cfr.cfr_compile(g)
+    try:
+        for key in cfr.EXPORT:
+            got = cfr.cfr_export_array(h, key)
+            np.testing.assert_array_equal(got, ref[key], err_msg=key)
+        assert cfr.cfr_get_counts(h)["depth_blocks"] == ref["D"]
+    finally:
+        cfr.cfr_destroy(h)
+
+
+def test_relabelled_spec_compiles_to_the_same_arrays():
+    g = gg.tiny_card()
+    rng = np.random.default_rng(0)
+    perm = np.concatenate([[0], 1 + rng.permutation(g.n_nodes - 1)])
+    h1, h2 = cfr.cfr_compile(g), cfr.cfr_compile(gg.permute_nodes(g, perm))
+    try:
+        for key in ("child_begin", "node_slot", "iset_slot", "iset_mem", "mem_node", "tmpl", "spec_slot_of"):
+            np.testing.assert_array_equal(cfr.cfr_export_array(h1, key), cfr.cfr_export_array(h2, key))
+    finally:
+        cfr.cfr_destroy(h1)
+        cfr.cfr_destroy(h2)
+
+
+@pytest.mark.parametrize("name", ["tiny", "rt8", "card_small"])
+def test_compile_invariants(name):
+    g = GAMES[name]()
+    h = cfr.cfr_compile(g)
+    try:
+        cb = cfr.cfr_export_array(h, "child_begin")
+        lb = cfr.cfr_export_array(h, "level_begin")
+        N = g.n_nodes
+        # every non-root node is written by exactly one forward edge (coverage)
+        cover = np.zeros(N, dtype=int)
+        for v in range(N):
+            cover[cb[v]:cb[v + 1]] += 1
+        assert cover[0] == 0 and (cover[1:] == 1).all()
+        # parents live one level above their children
+        depth = np.searchsorted(lb, np.arange(N), side="right") - 1
+        for v in range(N):
+            if cb[v + 1] > cb[v]:
+                assert (depth[cb[v]:cb[v + 1]] == depth[v] + 1).all()
+        # the template carries each terminal's full chance product exactly once
+        # (Prop. 1): with payoff 1 everywhere, folding values back up with
+        # chance edges as multiplier 1 and any strategy gives root value 1
+        ones = np.where(g.kind == gg.TERMINAL, 1.0, 0.0)
+        h1 = cfr.cfr_compile(_bad(g, payoff=ones))
+        try:
+            tm = cfr.cfr_export_array(h1, "tmpl")
+            slot = cfr.cfr_export_array(h1, "node_slot")
+            v = tm.copy()
+            for x in range(N - 1, -1, -1):
+                if cb[x + 1] > cb[x]:
+                    kids = v[cb[x]:cb[x + 1]]
+                    v[x] = kids.sum() if slot[x] < 0 else kids.mean()
+            assert v[0] == pytest.approx(1.0, abs=1e-12)
+        finally:
+            cfr.cfr_destroy(h1)
+    finally:
+        cfr.cfr_destroy(h)
+
+
+def test_template_is_chance_times_payoff_on_kuhn():
+    g = gg.kuhn()
+    h = cfr.cfr_compile(g)
+    try:
+        tm = cfr.cfr_export_array(h, "tmpl")
+        new = cfr.cfr_export_array(h, "new_of_spec")
+        term = np.nonzero(g.kind == gg.TERMINAL)[0]
+        np.testing.assert_array_equal(tm[new[term]], g.payoff[term] * (1.0 / 6.0))
+    finally:
+        cfr.cfr_destroy(h)
+
+
+def _bad(g, **changes):
+    kw = dict(kind=g.kind.copy(), infoset=g.infoset.copy(), child_begin=g.child_begin.copy(),
+              child=g.child.copy(), chance_prob=g.chance_prob.copy(), payoff=g.payoff.copy(),
+              iset_player=g.iset_player.copy(), iset_nact=g.iset_nact.copy(), pot=g.pot)
+    kw.update(changes)
+    return gg.GameSpec(**kw)
+
+
+def test_invalid_specs_are_rejected():
+    g = gg.kuhn()
+    child = g.child.copy()
+    child[3] = child[2]  # a node with two parents
+    cases = [
+        _bad(g, child=child),
+        _bad(g, chance_prob=g.chance_prob * 0.5),                # probabilities do not sum to 1
+        _bad(g, iset_player=1 - g.iset_player),                  # set owned by the other player
+        _bad(g, iset_nact=g.iset_nact + 1),                      # action count mismatch
+        _bad(g, payoff=np.where(g.kind == gg.TERMINAL, np.nan, 0.0)),
+    ]
+    for bad in cases:
+        with pytest.raises(cfr.CfrError) as ei:
+            cfr.cfr_compile(bad)
+        assert ei.value.code == -2
+
+
+def test_members_at_different_depths_are_rejected():
+    # P1 set 0 has members at depths 0 and 2
+    spec = gg.from_lists(
+        [
+            (gg.P1, 0, [1, 2], None, 0.0),
+            (gg.TERMINAL, -1, [], None, 1.0),
+            (gg.P2, 1, [3, 4], None, 0.0),
+            (gg.P1, 0, [5, 6], None, 0.0),
+            (gg.TERMINAL, -1, [], None, 0.0),
+            (gg.TERMINAL, -1, [], None, 2.0),
+            (gg.TERMINAL, -1, [], None, -1.0),
+        ],
+        [(0, 2), (1, 2)],
+    )
+    with pytest.raises(cfr.CfrError) as ei:
+        cfr.cfr_compile(spec)
+    assert "depth" in str(ei.value)
+
+
+def test_calls_before_bind_report_not_bound():
+    h = cfr.cfr_compile(gg.kuhn())
+    try:
+        with pytest.raises(cfr.CfrError) as ei:
+            cfr.cfr_iterate(h, 1, 0)
+        assert ei.value.code == -3
+        with pytest.raises(cfr.CfrError) as ei:
+            cfr.cfr_exploitability(h, 0)
+        assert ei.value.code == -3
+        assert cfr.cfr_plan(h) > 0
+    finally:
+        cfr.cfr_destroy(h)
+
+
+def test_bad_options_are_rejected():
+    with pytest.raises(cfr.CfrError):
+        cfr.cfr_compile(gg.kuhn(), cfr.make_options(precision=7))
+    with pytest.raises(cfr.CfrError):
+        cfr.cfr_compile(gg.kuhn(), cfr.make_options(lanes_per_set=3))
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "cfr.h")).read()
+    names = set(re.findall(r"^\s*(?:int|void|const char \*)\s*\**\s*(cfr_\w+)\s*\(", header, re.M))
+    assert {"cfr_compile", "cfr_iterate", "cfr_avg_strategy", "cfr_exploitability"} <= names
+    lib = ctypes.CDLL(cfr.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names <= set(cfr.EXPORTED)

@@ -1,0 +1,262 @@
+"""GPU parity of the sm_103a path (through the C ABI) against the FP64 oracle.
+
+Bars (from the method's target): the FP64 mode matches the oracle's average
+strategy within 1e-12 (entries are probabilities; we also expect bitwise
+equality where the summation order is the oracle's), and the FP32 mode
+reaches the oracle's exploitability within 1e-4 of the pot at equal
+iteration counts.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gamegen as gg
+import oracle
+from paper_2609_11923_gb300 import cfr
+
+pytestmark = pytest.mark.gpu
+
+FORMS = {"levels": cfr.EXEC_LEVELS, "graph": cfr.EXEC_GRAPH, "persistent": cfr.EXEC_PERSISTENT}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+    torch.cuda.synchronize()
+
+
+def solve_gpu(spec, iters, precision=cfr.P64, form=cfr.EXEC_GRAPH, **kw):
+    s = cfr.Solver(spec, precision=precision, exec_form=form, **kw)
+    if iters:
+        s.iterate(iters)
+    s.synchronize()
+    return s
+
+
+def assert_strategy_close(a, b, tol=1e-12):
+    d = np.abs(a - b)
+    assert d.max(initial=0.0) <= tol, "max |diff| %.3e at slot %d" % (d.max(), int(d.argmax()))
+
+
+# ------------------------------------------------------------- P64 parity
+@pytest.mark.parametrize("form", list(FORMS))
+def test_p64_tiny_card_10k_iterations_match_oracle_bitwise(form):
+    g = gg.tiny_card()
+    o = oracle.solve(g, 10000)
+    s = solve_gpu(g, 10000, form=FORMS[form])
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    R, avg, t = s.get_state()
+    np.testing.assert_array_equal(R, o.R)
+    np.testing.assert_array_equal(avg, o.sbar)
+    assert t == 10000
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_p64_random_tree_1000_iterations_match_oracle(seed, form):
+    g = gg.random_tree(seed, depth=9)
+    o = oracle.solve(g, 1000)
+    s = solve_gpu(g, 1000, form=FORMS[form])
+    a = s.avg_strategy()
+    assert_strategy_close(a, o.avg_strategy())
+    np.testing.assert_array_equal(a, o.avg_strategy())
+
+
+@pytest.mark.parametrize("name,make", [
+    ("kuhn", lambda: gg.kuhn()),
+    ("card_3x2", lambda: gg.large_card(3, 2, 1, 1)),
+    ("card_4x2", lambda: gg.large_card(4, 2, 2, 2)),
+    ("endgame_narrow_root", lambda: gg.endgame(5, 4000)),
+    ("single_member_sets", lambda: gg.random_tree(9, depth=8, max_group=1)),
+])
+def test_p64_other_games_match_oracle(name, make):
+    g = make()
+    o = oracle.solve(g, 1000)
+    s = solve_gpu(g, 1000)
+    assert_strategy_close(s.avg_strategy(), o.avg_strategy())
+
+
+def test_p64_wide_chance_root_matches_oracle():
+    g = gg.endgame(11, 60000)  # deal root with more than 1024 outcomes
+    assert np.diff(g.child_begin)[0] > 1024
+    o = oracle.solve(g, 300)
+    for form in FORMS.values():
+        s = solve_gpu(g, 300, form=form)
+        assert_strategy_close(s.avg_strategy(), o.avg_strategy())
+
+
+# ------------------------------------------------------------- P32 parity
+@pytest.mark.parametrize("name,make", [
+    ("random_tree", lambda: gg.random_tree(4, depth=10)),
+    ("card_4x2", lambda: gg.large_card(4, 2, 2, 2)),
+    ("endgame", lambda: gg.endgame(7, 200000)),
+    ("tiny", lambda: gg.tiny_card()),
+])
+def test_p32_exploitability_within_1e4_pot(name, make):
+    g = make()
+    o = oracle.solve(g, 1000)
+    e_or = o.exploitability()
+    s = solve_gpu(g, 1000, precision=cfr.P32)
+    e_gpu = s.exploitability()
+    assert abs(e_gpu - e_or) <= 1e-4 * g.pot, (e_gpu, e_or)
+
+
+# ------------------------------------------------------- exploitability
+@pytest.mark.parametrize("name,make", [
+    ("tiny", lambda: gg.tiny_card()),
+    ("random_tree", lambda: gg.random_tree(3, depth=9)),
+    ("card_4x2", lambda: gg.large_card(4, 2, 2, 2)),
+    ("wide_root", lambda: gg.endgame(11, 60000)),
+])
+def test_gpu_best_response_matches_oracle(name, make):
+    g = make()
+    s = solve_gpu(g, 200)
+    sigma = s.avg_strategy()
+    e, b1, b2, u = cfr.cfr_exploitability(s.h, s._s())
+    ob1, ob2, ou = oracle.Oracle(g).best_response(sigma)
+    assert b1 == pytest.approx(ob1, abs=1e-10)
+    assert b2 == pytest.approx(ob2, abs=1e-10)
+    assert u == pytest.approx(ou, abs=1e-10)
+    assert e == pytest.approx(0.5 * (ob1 - ob2), abs=1e-10)
+
+
+# ---------------------------------------------------- execution semantics
+def test_p32_forms_agree_bitwise_and_runs_repeat():
+    g = gg.random_tree(6, depth=10)
+    outs = []
+    for form in (cfr.EXEC_LEVELS, cfr.EXEC_GRAPH, cfr.EXEC_PERSISTENT, cfr.EXEC_GRAPH):
+        s = solve_gpu(g, 100, precision=cfr.P32, form=form, lanes_per_set=8)
+        outs.append(s.get_state())
+    for R, avg, t in outs[1:]:
+        np.testing.assert_array_equal(R, outs[0][0])
+        np.testing.assert_array_equal(avg, outs[0][1])
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_split_calls_equal_one_call(form):
+    g = gg.random_tree(8, depth=9)
+    a = cfr.Solver(g, precision=cfr.P32, exec_form=FORMS[form])
+    for n in (2, 8, 0, 3):
+        a.iterate(n)
+    b = solve_gpu(g, 13, precision=cfr.P32, form=FORMS[form])
+    ra, sa, ta = a.get_state()
+    rb, sb, tb = b.get_state()
+    assert ta == tb == 13
+    np.testing.assert_array_equal(ra, rb)
+    np.testing.assert_array_equal(sa, sb)
+
+
+def test_reset_replays_from_iteration_one():
+    g = gg.tiny_card()
+    s = solve_gpu(g, 57, precision=cfr.P32)
+    s.reset()
+    s.iterate(40)
+    ref = solve_gpu(g, 40, precision=cfr.P32)
+    np.testing.assert_array_equal(s.get_state()[0], ref.get_state()[0])
+    np.testing.assert_array_equal(s.avg_strategy(), ref.avg_strategy())
+
+
+def test_state_roundtrip_resumes_bitwise():
+    g = gg.random_tree(10, depth=9)
+    a = solve_gpu(g, 300)
+    R, avg, t = a.get_state()
+    b = cfr.Solver(g, precision=cfr.P64)
+    b.set_state(R, avg, t)
+    b.iterate(700)
+    ref = oracle.solve(g, 1000)
+    np.testing.assert_array_equal(b.avg_strategy(), ref.avg_strategy())
+
+
+def test_set_payoffs_equals_solving_the_new_game():
+    g = gg.tiny_card()
+    g2 = gg.tiny_card()
+    rng = np.random.default_rng(1)
+    new_pay = np.where(g.kind == gg.TERMINAL, rng.uniform(-2, 2, g.n_nodes), 0.0)
+    g2.payoff[:] = new_pay
+    s = cfr.Solver(g, precision=cfr.P64)
+    s.set_payoffs(new_pay)
+    s.iterate(500)
+    o = oracle.solve(g2, 500)
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+
+
+def test_barrier_timeout_reports_error_and_context_survives():
+    g = gg.random_tree(12, depth=10)
+    s = cfr.Solver(g, precision=cfr.P32, exec_form=cfr.EXEC_PERSISTENT, persistent_ctas=4,
+                   barrier_spin_limit=2000)
+    cfr.cfr_debug_set(s.h, cfr.DEBUG_BARRIER_MISSING_ARRIVALS, 1)
+    s.iterate(3)
+    with pytest.raises(cfr.CfrError) as ei:
+        s.synchronize()
+    assert ei.value.code == cfr.CFR_ERR_TIMEOUT
+    cfr.cfr_debug_set(s.h, cfr.DEBUG_BARRIER_MISSING_ARRIVALS, 0)
+    s.reset()
+    s.iterate(50)
+    s.synchronize()
+    ref = solve_gpu(g, 50, precision=cfr.P32, form=cfr.EXEC_PERSISTENT, persistent_ctas=4)
+    np.testing.assert_array_equal(s.get_state()[0], ref.get_state()[0])
+
+
+# ------------------------------------------------------------ edge cases
+def test_root_terminal_game():
+    g = gg.from_lists([(gg.TERMINAL, -1, [], None, 1.25)], [])
+    s = solve_gpu(g, 5)
+    assert s.get_state()[2] == 5
+    e, b1, b2, u = cfr.cfr_exploitability(s.h, s._s())
+    assert (e, b1, b2, u) == (0.0, 1.25, 1.25, 1.25)
+
+
+def test_all_chance_game():
+    g = gg.from_lists(
+        [
+            (gg.CHANCE, -1, [1, 2], [0.25, 0.75], 0.0),
+            (gg.CHANCE, -1, [3, 4], [0.5, 0.5], 0.0),
+            (gg.TERMINAL, -1, [], None, 4.0),
+            (gg.TERMINAL, -1, [], None, -1.0),
+            (gg.TERMINAL, -1, [], None, 2.0),
+        ],
+        [],
+    )
+    s = solve_gpu(g, 3)
+    e, b1, b2, u = cfr.cfr_exploitability(s.h, s._s())
+    assert e == 0.0 and u == pytest.approx(0.25 * 0.5 * 1.0 + 0.75 * 4.0)
+
+
+def test_sixty_four_action_sets_match_oracle():
+    # root P1 set with 64 actions, each leading to a P2 set of 3 actions
+    nodes = [(gg.P1, 0, list(range(1, 65)), None, 0.0)]
+    rng = np.random.default_rng(0)
+    nxt = 65
+    for a in range(64):
+        nodes.append((gg.P2, 1, [nxt, nxt + 1, nxt + 2], None, 0.0))
+        nxt += 3
+    for _ in range(64 * 3):
+        nodes.append((gg.TERMINAL, -1, [], None, float(rng.uniform(-1, 1))))
+    g = gg.from_lists(nodes, [(0, 64), (1, 3)])
+    o = oracle.solve(g, 300)
+    for form in FORMS.values():
+        s = solve_gpu(g, 300, form=form)
+        assert_strategy_close(s.avg_strategy(), o.avg_strategy())
+
+
+def test_vanilla_cfr_rule_matches_oracle():
+    g = gg.kuhn()
+    o = oracle.solve(g, 1000, rule=oracle.CFR)
+    s = solve_gpu(g, 1000, rule=cfr.RULE_CFR)
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    assert abs(s.exploitability() - 1.32e-2) <= 3e-3 * 1.32e-2
+
+
+def test_current_strategy_matches_regret_matching():
+    g = gg.random_tree(13, depth=8)
+    o = oracle.solve(g, 77)
+    s = solve_gpu(g, 77)
+    np.testing.assert_array_equal(s.current_strategy(), o.current_strategy())
+
+
+def test_device_output_equals_host_output():
+    g = gg.tiny_card()
+    s = solve_gpu(g, 100, precision=cfr.P32)
+    d = s.avg_strategy_device().cpu().numpy()
+    np.testing.assert_array_equal(d, s.avg_strategy())
