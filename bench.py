@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""CFR+ iteration throughput of the GB300 path (one JSON line on stdout).
+
+A step is one full CFR+ iteration over the compiled game: forward reach of
+both players, terminal values (chance folded at compile time), backward values
+with the fused regret / regret-matching+ / linear-average update. The default
+workload is the two-round card game (8 ranks x 4 suits, stack 2 antes, cap 3
+bets per round: 264,306,001 nodes) in the FP32 mode with FP64 accumulators,
+executed as per-level kernels replayed from one CUDA graph per iteration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large_card|random_tree|tiny]
+
+Multi-GPU runs (torchrun, one rank per GPU) solve independent replicas of the
+workload; value = all ranks' edges / the slowest rank's time ("weak").
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CFR iters/sec & edges/sec (HBM GB/s vs peak); batched time-to-1e-3 exploitability"
+UNIT = "edges/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workloads(deal_stride: int = 1):
+    import gamegen as gg
+
+    return {
+        "large_card": dict(
+            make=lambda: gg.large_card_sampled(deal_stride, 8, 4, 2, 3),
+            sample=lambda: (gg.large_card_sampled(200, 8, 4, 2, 3), "every 200th root deal of the same game"),
+            desc="two-round card game: 8 ranks x 4 suits, two private cards, one public card, "
+                 "bets {1/2 pot, pot, all-in}, cap 3 per round, stack 2 antes"),
+        "random_tree": dict(
+            make=lambda: gg.random_tree(0),
+            sample=lambda: (gg.random_tree(0), "the full tree"),
+            desc="seeded random perfect-recall tree, depth 14, branching U{2,3,4}, 20% chance, sets of 1-16"),
+        "tiny": dict(
+            make=lambda: gg.tiny_card(),
+            sample=lambda: (gg.tiny_card(), "the full game"),
+            desc="one-card poker, 5 ranks, cap 2 bets (301 nodes)"),
+    }
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=500)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="large_card", choices=["large_card", "random_tree", "tiny"])
+    p.add_argument("--exec", dest="exec_form", default="graph", choices=["graph", "levels", "persistent", "auto"])
+    p.add_argument("--precision", default="p32", choices=["p32", "p64"])
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--deal-stride", type=int, default=1,
+                   help="large_card only: keep every k-th root deal (a smaller instance for profiling)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampler: median SM clock under load and throttle reasons."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    rows.append((float(parts[2]), float(parts[3]), parts[6:10]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        busy = [r for r in rows if r[0] >= 0.5 * r[1]] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in busy for i in range(4) if r[2][i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(busy)}
+
+
+# -------------------------------------------------------------- cpu oracle
+def cpu_oracle(wl, seconds: float, min_iters: int = 3):
+    import oracle
+
+    spec, what = wl["sample"]()
+    o = oracle.Oracle(spec)
+    o.iterate(1)  # warm caches
+    n, t0 = 0, time.perf_counter()
+    while n < min_iters or time.perf_counter() - t0 < seconds:
+        o.iterate(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": spec.n_edges * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s (%d edges), %d FP64 iterations in %.1f s, one thread" % (what, spec.n_edges, n, dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    wl = workloads()[args.workload]
+    spec, what = wl["sample"]()
+    o = oracle.Oracle(spec)
+    for _ in range(args.warmup):
+        o.iterate(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.iterate(1)
+    dt = time.perf_counter() - t0
+    value = spec.n_edges * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "description": wl["desc"],
+                                        "sample": what, "edges": spec.n_edges},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%s (%d edges), each step one FP64 iteration, one thread" % (what, spec.n_edges)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("kernels.cuh", "launch_impl.cuh", "cfr_api.cu"):
+        with open(os.path.join(ROOT, "paper_2609_11923_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, kernel: str):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(workload, {}).get(kernel)
+    if ent and ent.get("source_hash") == kernel_source_hash():
+        return ent.get("bytes_per_launch")
+    return None
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2609_11923_gb300 import cfr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = workloads(args.deal_stride)[args.workload]
+    spec = wl["make"]()
+    forms = {"graph": cfr.EXEC_GRAPH, "levels": cfr.EXEC_LEVELS, "persistent": cfr.EXEC_PERSISTENT,
+             "auto": cfr.EXEC_AUTO}
+    prec = cfr.P32 if args.precision == "p32" else cfr.P64
+    solver = cfr.Solver(spec, precision=prec, exec_form=forms[args.exec_form], device=str(dev))
+    counts = solver.counts
+    E, D = counts["n_edges"], counts["depth_blocks"]
+    pot, n_nodes = spec.pot, spec.n_nodes
+    del spec  # the compiled copy lives in the handle
+    stream = torch.cuda.current_stream(dev)
+    s = int(stream.cuda_stream)
+
+    # warm-up (graph capture happens on the first call)
+    solver.iterate(args.warmup)
+    solver.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    cfr.cfr_iterate(solver.h, args.steps, s)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    solver.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([dt], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    iters_per_s = args.steps / dt
+    value = world * E * iters_per_s
+    algo_gbps = counts["algo_bytes_per_iter"] * iters_per_s / 1e9
+
+    # per-launch times of one iteration (same kernels, same stream; outside the timed region)
+    prof = [cfr.cfr_profile_iteration(solver.h, D, s) for _ in range(5)]
+    fwd_ms = [statistics.median(p[0][d] for p in prof) for d in range(D)]
+    bwd_ms = [statistics.median(p[1][d] for p in prof) for d in range(D)]
+    launches = []
+    for d in range(D):
+        fb, bb = cfr.cfr_level_bytes(solver.h, d)
+        launches.append(("fwd_level_kernel", d, fwd_ms[d], fb))
+        launches.append(("bwd_level_kernel", d, bwd_ms[d], bb))
+    total_ms = sum(x[2] for x in launches)
+    dom = max(launches, key=lambda x: x[2])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    peak = float(peaks["hbm_gbs"])
+    achieved = dom[3] / (dom[2] / 1e3) / 1e9
+    kname = "%s[depth %d]" % (dom[0], dom[1])
+    traffic = recorded_traffic(args.workload, kname)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "share_of_iteration": dom[2] / total_ms,
+                "algo_bytes_per_launch": dom[3], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    # end to end through the public API: upload (bind) + K iterations + average strategy to host
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+
+        out = np.empty(counts["n_slots"])
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        cfr.cfr_bind(solver.h, solver.arena_ptr, solver.arena_bytes, s)
+        cfr.cfr_iterate(solver.h, args.steps, s)
+        cfr.cfr_avg_strategy(solver.h, out, False, s)
+        t1 = time.perf_counter()
+        et = t1 - t0
+        if dist is not None:
+            t = torch.tensor([et], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": world * E * args.steps / et, "unit": UNIT,
+               "h2d_bytes_per_step": counts["upload_bytes"] / args.steps,
+               "d2h_bytes_per_step": 8.0 * counts["n_slots"] / args.steps,
+               "what": "cfr_bind (upload of the compiled game from host memory) + cfr_iterate(K) + "
+                       "cfr_avg_strategy to host, wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle(wl, args.cpu_seconds)
+
+    per_iter_launches = {cfr.EXEC_GRAPH: 2 * D, cfr.EXEC_LEVELS: 2 * D}.get(counts["exec_form"], 0)
+    gpu_launches = args.steps * per_iter_launches if per_iter_launches else 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == cfr.P32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ("" if args.deal_stride == 1 else " (every %dth deal)" % args.deal_stride),
+                   "description": wl["desc"], "nodes": n_nodes, "edges": E,
+                   "infosets": counts["n_infosets"], "slots": counts["n_slots"], "depth_blocks": D,
+                   "precision": args.precision + (" (FP64 regret/average accumulators)" if prec == cfr.P32 else ""),
+                   "exec_form": args.exec_form, "pot": pot, "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % (solver.arena_bytes / 1e9)},
+        "iters_per_s": world * iters_per_s,
+        "algo_gbps_per_gpu": algo_gbps,
+        "algo_bytes_per_iter": counts["algo_bytes_per_iter"],
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "launch_profile_ms": {"fwd": fwd_ms, "bwd": bwd_ms},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

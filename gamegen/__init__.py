@@ -136,6 +136,8 @@ def _load():
                                    ctypes.c_double, ctypes.c_int]
     lib.gg_large_card.restype = P
     lib.gg_large_card.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.gg_large_card_sampled.restype = P
+    lib.gg_large_card_sampled.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.gg_endgame.restype = P
     lib.gg_endgame.argtypes = [ctypes.c_uint64, ctypes.c_int64]
     lib.gg_free.argtypes = [P]
@@ -198,6 +200,12 @@ def random_tree(seed: int, depth: int = 14, bmin: int = 2, bmax: int = 4, p_chan
 def large_card(n_ranks: int = 8, n_suits: int = 4, stack: int = 2, cap: int = 3) -> GameSpec:
     """Two-round card game (8x4 deck, stack 2 antes: 264,306,001 nodes)."""
     return _wrap(_load().gg_large_card(n_ranks, n_suits, stack, cap))
+
+
+def large_card_sampled(deal_stride: int, n_ranks: int = 8, n_suits: int = 4, stack: int = 2,
+                       cap: int = 3) -> GameSpec:
+    """The two-round card game on every deal_stride-th root deal (a uniform sample)."""
+    return _wrap(_load().gg_large_card_sampled(n_ranks, n_suits, stack, cap, deal_stride))
 
 
 def endgame(seed: int, target_edges: int = 0) -> GameSpec:

@@ -669,7 +669,22 @@ static gg_spec *build_card_game(ptree *t, deck_ctx *d, double pot, int with_boar
   if (N >= (int64_t)2147483647) { free(order); free(loff); free(base); free(rep); set_err("game too large for 32-bit node ids"); return NULL; }
   gg_spec *g = spec_alloc(N, N - 1, ni, 1);
   if (!g) { free(order); free(loff); free(base); free(rep); return NULL; }
-  /* information-set metadata */
+  /* information-set metadata; compact (hand, board) ids decoded by table */
+  int32_t *pair_hand = NULL, *pair_card = NULL;
+  if (with_board_chance) {
+    pair_hand = (int32_t *)malloc(4 * (size_t)(d->npairs > 0 ? d->npairs : 1));
+    pair_card = (int32_t *)malloc(4 * (size_t)(d->npairs > 0 ? d->npairs : 1));
+    if (!pair_hand || !pair_card) {
+      free(pair_hand); free(pair_card); free(order); free(loff); free(base); free(rep); gg_free(g);
+      set_err("out of host memory");
+      return NULL;
+    }
+    for (int hh = 0; hh < d->nhands; ++hh)
+      for (int c = 0; c < d->ncards; ++c) {
+        const int32_t j = d->pair_idx[hh * d->ncards + c];
+        if (j >= 0) { pair_hand[j] = hh; pair_card[j] = c; }
+      }
+  }
   for (int32_t b = 0; b < nbet; ++b) {
     if (base[b] < 0) continue;
     const pnode *P = &t->p[rep[b]];
@@ -680,12 +695,12 @@ static gg_spec *build_card_game(ptree *t, deck_ctx *d, double pot, int with_boar
       g->iset_player[I] = (int8_t)(P->kind == GG_P1 ? 0 : 1);
       g->iset_nact[I] = P->nch;
       int32_t *f = &g->iset_feat[I * GG_NFEAT];
-      int h = d->hand_of_priv[pl][j], board = d->board_fixed;
-      if (P->round == 1 && with_board_chance) {
-        h = -1; /* decode the compact (hand, board) id */
-        for (int hh = 0; hh < d->nhands && h < 0; ++hh)
-          for (int c = 0; c < d->ncards; ++c)
-            if (d->pair_idx[hh * d->ncards + c] == j) { h = hh; board = c; break; }
+      int h, board = d->board_fixed;
+      if (P->round == 1 && with_board_chance) { /* decode the compact (hand, board) id */
+        h = pair_hand[j];
+        board = pair_card[j];
+      } else {
+        h = d->hand_of_priv[pl][j];
       }
       f[0] = P->kind == GG_P1 ? 0 : 1;
       f[1] = d->hand_a[h];
@@ -749,8 +764,30 @@ static gg_spec *build_card_game(ptree *t, deck_ctx *d, double pot, int with_boar
     next_level_base += d->ndeal * Hn;
   }
   g->child_begin[N] = cur_child;
-  free(order); free(loff); free(base); free(rep);
+  free(order); free(loff); free(base); free(rep); free(pair_hand); free(pair_card);
   g->pot = pot;
+  /* a subsample of the deals can leave information sets without members:
+   * drop them and renumber the rest in order */
+  {
+    int32_t *remap = (int32_t *)malloc(4 * (size_t)(ni > 0 ? ni : 1));
+    if (!remap) { gg_free(g); set_err("out of host memory"); return NULL; }
+    for (int64_t i = 0; i < ni; ++i) remap[i] = -1;
+    for (int64_t v = 0; v < N; ++v) if (g->infoset[v] >= 0) remap[g->infoset[v]] = 0;
+    int64_t m = 0;
+    for (int64_t i = 0; i < ni; ++i) {
+      if (remap[i] < 0) continue;
+      remap[i] = (int32_t)m;
+      g->iset_player[m] = g->iset_player[i];
+      g->iset_nact[m] = g->iset_nact[i];
+      for (int f = 0; f < GG_NFEAT; ++f) g->iset_feat[m * GG_NFEAT + f] = g->iset_feat[i * GG_NFEAT + f];
+      ++m;
+    }
+    if (m != ni) {
+      for (int64_t v = 0; v < N; ++v) if (g->infoset[v] >= 0) g->infoset[v] = remap[g->infoset[v]];
+      g->n_infosets = m;
+    }
+    free(remap);
+  }
   return g;
 }
 
@@ -765,7 +802,11 @@ static void deck_free(deck_ctx *d) {
 }
 
 gg_spec *gg_large_card(int n_ranks, int n_suits, int stack, int cap) {
-  if (n_ranks < 1 || n_suits < 1 || n_ranks * n_suits < 5 || n_ranks * n_suits > 64 || stack < 1 ||
+  return gg_large_card_sampled(n_ranks, n_suits, stack, cap, 1);
+}
+
+gg_spec *gg_large_card_sampled(int n_ranks, int n_suits, int stack, int cap, int deal_stride) {
+  if (deal_stride < 1 || n_ranks < 1 || n_suits < 1 || n_ranks * n_suits < 5 || n_ranks * n_suits > 64 || stack < 1 ||
       stack > 1000 || cap < 1 || cap > 8) {
     set_err("gg_large_card: bad parameters");
     return NULL;
@@ -789,6 +830,12 @@ gg_spec *gg_large_card(int n_ranks, int n_suits, int stack, int cap) {
         continue;
       d.deal_h1[k] = h1; d.deal_h2[k] = h2; d.deal_p[k] = 1.0 / (double)d.ndeal; ++k;
     }
+  if (deal_stride > 1) { /* uniform subsample of the deals (every deal_stride-th) */
+    int64_t m = 0;
+    for (int64_t q = 0; q < d.ndeal; q += deal_stride) { d.deal_h1[m] = d.deal_h1[q]; d.deal_h2[m] = d.deal_h2[q]; ++m; }
+    d.ndeal = m;
+    for (int64_t q = 0; q < m; ++q) d.deal_p[q] = 1.0 / (double)m;
+  }
   for (int h = 0; h < d.nhands; ++h)
     for (int c = 0; c < d.ncards; ++c) {
       int in = (c == d.hand_a[h] || c == d.hand_b[h]);

@@ -71,6 +71,11 @@ gg_spec *gg_random_tree(uint64_t seed, int depth, int bmin, int bmax,
  * Nodes are in breadth-first order. */
 gg_spec *gg_large_card(int n_ranks, int n_suits, int stack, int cap);
 
+/* The same game restricted to every deal_stride-th deal of the root (deal
+ * probabilities renormalised): a uniform sample of the full game's subtrees,
+ * used to time the CPU reference on a bounded part of the workload. */
+gg_spec *gg_large_card_sampled(int n_ranks, int n_suits, int stack, int cap, int deal_stride);
+
 /* River-style endgame subgame: one betting round over a fixed one-card board,
  * K1 and K2 distinct two-card hands per player drawn from the 8x4 deck minus
  * the board, ranges Dirichlet(0.5), 2..4 pot-fraction bet sizes, cap 2 bets.

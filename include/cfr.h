@@ -94,6 +94,7 @@ typedef struct cfr_counts {
   int64_t depth_blocks;       /* D: number of distinct parent depths (eq. (blocks)) */
   int64_t max_actions;
   int64_t algo_bytes_per_iter; /* algorithmic HBM bytes of one iteration (design notes) */
+  int64_t upload_bytes;       /* host-to-device bytes cfr_bind copies */
   int64_t iteration;          /* t: iterations completed since bind/reset */
   int exec_form;              /* resolved execution form */
   int lanes_per_set;          /* resolved lanes per information set */
@@ -168,6 +169,18 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);
+
+/* Algorithmic device bytes of depth level d (0 <= d < D) for the forward
+ * kernel and the backward kernel of one iteration: every array element the
+ * layout needs, touched once (the design notes list the per-element terms).
+ * Host only. */
+int cfr_level_bytes(const cfr_handle *h, int level, int64_t *fwd_bytes, int64_t *bwd_bytes);
+
+/* Measurement: runs ONE iteration (t -> t+1) as per-level launches on
+ * `stream` with a CUDA event pair around every launch, and writes each
+ * launch's device time in milliseconds: fwd_ms[d] and bwd_ms[d] for
+ * d = 0 .. D-1 (host arrays of D doubles). Synchronises `stream`. */
+int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *stream);
 
 /* Fault-injection hook for tests (no effect unless set).
  * CFR_DEBUG_BARRIER_MISSING_ARRIVALS = k: the persistent kernel's grid

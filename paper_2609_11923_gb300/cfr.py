@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
 class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_nodes", "n_edges", "n_infosets", "n_slots", "n_internal", "n_decision", "n_chance", "n_terminal",
-        "depth_blocks", "max_actions", "algo_bytes_per_iter", "iteration")] + [
+        "depth_blocks", "max_actions", "algo_bytes_per_iter", "upload_bytes", "iteration")] + [
         ("exec_form", ctypes.c_int), ("lanes_per_set", ctypes.c_int)]
 
     def as_dict(self):
@@ -88,6 +88,8 @@ def _load():
         "cfr_set_state": [H, dp, dp, i64, vp],
         "cfr_export_array": [H, ctypes.c_int, vp, i64, ctypes.POINTER(i64)],
         "cfr_debug_set": [H, ctypes.c_int, i64],
+        "cfr_level_bytes": [H, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "cfr_profile_iteration": [H, dp, dp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -104,7 +106,7 @@ _lib = _load()
 EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterate", "cfr_synchronize",
             "cfr_avg_strategy", "cfr_current_strategy", "cfr_exploitability", "cfr_reset", "cfr_set_payoffs",
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
-            "cfr_destroy"]
+            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration"]
 
 
 def _check(rc: int) -> None:
@@ -232,6 +234,20 @@ def cfr_export_array(h: int, name: str) -> np.ndarray:
 
 def cfr_debug_set(h: int, key: int, value: int) -> None:
     _check(_lib.cfr_debug_set(h, key, value))
+
+
+def cfr_level_bytes(h: int, level: int) -> Tuple[int, int]:
+    f, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.cfr_level_bytes(h, level, ctypes.byref(f), ctypes.byref(b)))
+    return f.value, b.value
+
+
+def cfr_profile_iteration(h: int, depth_blocks: int, stream: int = 0):
+    """Per-launch device times (ms) of one iteration: (fwd[D], bwd[D])."""
+    f = np.zeros(max(depth_blocks, 1))
+    b = np.zeros(max(depth_blocks, 1))
+    _check(_lib.cfr_profile_iteration(h, _dp(f), _dp(b), stream))
+    return f[:depth_blocks], b[:depth_blocks]
 
 
 def cfr_last_error() -> str:

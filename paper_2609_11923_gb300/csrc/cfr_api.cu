@@ -177,6 +177,9 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
   o->n_internal = c.n_int; o->n_decision = c.n_dec; o->n_chance = c.n_chance; o->n_terminal = c.n_term;
   o->depth_blocks = c.D; o->max_actions = c.max_act;
   o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision);
+  o->upload_bytes = (int64_t)(h->b_child_begin.bytes + h->b_node_slot.bytes + h->b_iset_slot.bytes + h->b_iset_mem.bytes +
+                              h->b_mem_node.bytes + h->b_chance_list.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
+                              h->b_wide_list.bytes + h->b_wide_chunk.bytes + h->b_tmpl.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
   o->lanes_per_set = h->exec_form == CFR_EXEC_PERSISTENT ? h->persist_lanes : (c.D > 0 ? h->level_lanes[c.D - 1] : 0);
@@ -606,4 +609,63 @@ extern "C" int cfr_debug_set(cfr_handle *h, int key, int64_t value) {
     return CFR_OK;
   }
   return set_err(CFR_ERR_ARG, "cfr_debug_set: unknown key %d", key);
+}
+
+extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t *bwd) {
+  if (!h || !fwd || !bwd) return set_err(CFR_ERR_ARG, "cfr_level_bytes: null argument");
+  const Compiled &c = h->c;
+  if (d < 0 || d >= c.D) return set_err(CFR_ERR_ARG, "cfr_level_bytes: level out of range");
+  const int64_t T = h->precision == CFR_P64 ? 8 : 4;
+  const int64_t n = c.level_begin[d + 1] - c.level_begin[d];
+  const int64_t e = c.level_begin[d + 2] - c.level_begin[d + 1];  // children = next level
+  const int64_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
+  const int64_t sets = i1 - i0;
+  const int64_t slots = c.iset_slot[i1] - c.iset_slot[i0];
+  const int64_t dec = c.iset_mem[i1] - c.iset_mem[i0];
+  const int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
+  const int64_t nint = dec + nch;
+  *fwd = 8 * n + 2 * T * nint + 2 * T * e + T * slots;
+  *bwd = 8 * sets + (32 + 2 * T) * slots + (8 + 3 * T) * dec + (12 + T) * nch + T * e;
+  return CFR_OK;
+}
+
+template <typename T>
+static int profile_t(cfr_handle *h, double *fwd_ms, double *bwd_ms, cudaStream_t s) {
+  const Compiled &c = h->c;
+  std::vector<cudaEvent_t> ev(4 * c.D + 2, nullptr);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  GameView g = game_view(h);
+  int rc = CFR_OK;
+  for (int64_t d = 0; d < c.D && rc == CFR_OK; ++d) {
+    const LevelWork &w = h->levels[d];
+    const int nb = grid_for(w.le - w.lb, kThreads);
+    CK(cudaEventRecord(ev[2 * d], s));
+    fwd_level_kernel<T><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach), w, nb);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ev[2 * d + 1], s));
+  }
+  for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
+    CK(cudaEventRecord(ev[2 * c.D + 2 * d], s));
+    rc = launch_bwd<T>(h, (int)d, s);
+    CK(cudaEventRecord(ev[2 * c.D + 2 * d + 1], s));
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int64_t d = 0; d < c.D; ++d) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, ev[2 * d], ev[2 * d + 1]));
+    CK(cudaEventElapsedTime(&b, ev[2 * c.D + 2 * d], ev[2 * c.D + 2 * d + 1]));
+    fwd_ms[d] = a;
+    bwd_ms[d] = b;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (rc == CFR_OK) h->iteration_host += 1;
+  return rc;
+}
+
+extern "C" int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *stream) {
+  if (!h || ((!fwd_ms || !bwd_ms) && h->c.D > 0)) return set_err(CFR_ERR_ARG, "cfr_profile_iteration: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_profile_iteration: not bound");
+  if (h->c.D == 0) return cfr_iterate(h, 1, stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  return h->precision == CFR_P64 ? profile_t<double>(h, fwd_ms, bwd_ms, s) : profile_t<float>(h, fwd_ms, bwd_ms, s);
 }

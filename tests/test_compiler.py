@@ -22,7 +22,7 @@ GAMES = {
     "rt8": lambda: gg.random_tree(2, depth=8, max_group=16),
     "endgame": lambda: gg.endgame(3, 3000),
     "card_small": lambda: gg.large_card(3, 2, 1, 1),
-    "wide_root": lambda: gg.endgame(11, 60000),
+    "wide_root": lambda: gg.endgame(2, 100000),
 }
 
 

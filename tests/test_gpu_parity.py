@@ -78,7 +78,7 @@ def test_p64_other_games_match_oracle(name, make):
 
 
 def test_p64_wide_chance_root_matches_oracle():
-    g = gg.endgame(11, 60000)  # deal root with more than 1024 outcomes
+    g = gg.endgame(2, 100000)  # deal root with more than 1024 outcomes
     assert np.diff(g.child_begin)[0] > 1024
     o = oracle.solve(g, 300)
     for form in FORMS.values():
@@ -107,7 +107,7 @@ def test_p32_exploitability_within_1e4_pot(name, make):
     ("tiny", lambda: gg.tiny_card()),
     ("random_tree", lambda: gg.random_tree(3, depth=9)),
     ("card_4x2", lambda: gg.large_card(4, 2, 2, 2)),
-    ("wide_root", lambda: gg.endgame(11, 60000)),
+    ("wide_root", lambda: gg.endgame(2, 100000)),
 ])
 def test_gpu_best_response_matches_oracle(name, make):
     g = make()
