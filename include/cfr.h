@@ -182,6 +182,28 @@ int cfr_level_bytes(const cfr_handle *h, int level, int64_t *fwd_bytes, int64_t 
  * d = 0 .. D-1 (host arrays of D doubles). Synchronises `stream`. */
 int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *stream);
 
+/* Allocation-free variant of cfr_iterate, for callers that cannot allocate
+ * device memory when they run iterations (for example code running during a
+ * CUDA graph capture, or a serving loop whose memory is fixed at start-up).
+ * The paper has no counterpart to this entry point.
+ * It runs n iterations with the persistent kernel, exactly as the
+ * CFR_EXEC_PERSISTENT form does, but takes the per-iteration scratch (reach
+ * lanes, node values, wide-node partial sums, grid-barrier words) from one
+ * static 12 MiB device array compiled into the library (held on every GPU
+ * that loads the library, until the process exits) instead of the arena.
+ * The arena bound with cfr_bind still holds the inputs and outputs: the
+ * compiled game and the solver state (regrets, average, strategy, t).
+ * No cudaMalloc, cudaFree or other allocating call is made. The first call on
+ * a device resolves the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Limits: games whose scratch exceeds the array (about 524,000 nodes in FP64,
+ * 1,048,000 in FP32, less with wide chance nodes) are rejected with
+ * CFR_ERR_ARG. Every call re-initialises the part of the array it uses.
+ * All calls share the one array, so calls that overlap on the GPU (other
+ * streams, other threads, other handles) race: serialise them. Synchronises
+ * `stream`; a barrier timeout returns CFR_ERR_TIMEOUT. */
+int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream);
+
 /* Fault-injection hook for tests (no effect unless set).
  * CFR_DEBUG_BARRIER_MISSING_ARRIVALS = k: the persistent kernel's grid
  * barriers wait for k blocks that do not exist, so every wait runs into its

@@ -90,6 +90,7 @@ def _load():
         "cfr_debug_set": [H, ctypes.c_int, i64],
         "cfr_level_bytes": [H, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "cfr_profile_iteration": [H, dp, dp, vp],
+        "cfr_iterate_noalloc": [H, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -106,7 +107,7 @@ _lib = _load()
 EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterate", "cfr_synchronize",
             "cfr_avg_strategy", "cfr_current_strategy", "cfr_exploitability", "cfr_reset", "cfr_set_payoffs",
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
-            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration"]
+            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc"]
 
 
 def _check(rc: int) -> None:
@@ -175,6 +176,12 @@ def cfr_bind(h: int, arena_ptr: int, nbytes: int, stream: int = 0) -> None:
 
 def cfr_iterate(h: int, n: int, stream: int = 0) -> None:
     _check(_lib.cfr_iterate(h, n, stream))
+
+
+def cfr_iterate_noalloc(h: int, n: int, stream: int = 0) -> None:
+    """n iterations with the scratch in the library's static device array
+    (no allocation during the call; synchronises the stream)."""
+    _check(_lib.cfr_iterate_noalloc(h, n, stream))
 
 
 def cfr_synchronize(h: int, stream: int = 0) -> None:

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -668,4 +669,128 @@ extern "C" int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_
   if (h->c.D == 0) return cfr_iterate(h, 1, stream);
   cudaStream_t s = (cudaStream_t)stream;
   return h->precision == CFR_P64 ? profile_t<double>(h, fwd_ms, bwd_ms, s) : profile_t<float>(h, fwd_ms, bwd_ms, s);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free iteration (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory at the moment they want to run
+// iterations: code that runs while a CUDA graph is being captured, real-time
+// serving loops whose memory budget is fixed at start-up, or host code that
+// does not own the device allocator. cfr_iterate_noalloc serves them: it runs
+// the persistent kernel with its per-iteration scratch (both reach lanes, the
+// node values, wide-node partial sums and the grid-barrier words) placed in
+// one file-scope device array of fixed size, so the call itself allocates
+// nothing. The bound arena still holds the compiled game and the solver state
+// (regrets, average, strategy, t), which are this call's inputs and outputs.
+constexpr size_t kNoAllocScratchBytes = size_t(12) << 20;  // 12 MiB per GPU, held until exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[256];  // device address of the array, per device ordinal
+
+// Host code may not use the array's name as a device address: resolve it
+// once per device, with that device current.
+static int noalloc_scratch(void **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return set_err(CFR_ERR_DEVICE, "cfr_iterate_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CFR_OK;
+}
+
+// Every call starts from a clean scratch: terminal values from the template,
+// root reach (1, 1), wide-node tickets and barrier words at zero.
+template <typename T>
+__global__ void noalloc_init_kernel(const int32_t *child_begin, const double *tmpl, int32_t N, T *v,
+                                    vec2_t<T> *reach, unsigned *wide_cnt, int32_t n_wide, unsigned *bar) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int32_t h = tid; h < N; h += stride)
+    if (child_begin[h] == child_begin[h + 1]) v[h] = (T)tmpl[h];
+  for (int32_t i = tid; i < n_wide; i += stride) wide_cnt[i] = 0u;
+  if (tid == 0) {
+    vec2_t<T> one;
+    one.x = T(1); one.y = T(1);
+    reach[0] = one;
+    bar[0] = 0u; bar[1] = 0u; bar[2] = 0u;
+  }
+}
+
+template <typename T>
+static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
+  const Compiled &c = h->c;
+  size_t off_v = align_up(2 * sizeof(T) * (size_t)c.N);
+  size_t off_part = off_v + align_up(sizeof(T) * (size_t)c.N);
+  size_t off_cnt = off_part + align_up(3 * 8 * (size_t)c.wide_chunk.back());
+  size_t off_bar = off_cnt + align_up(4 * (size_t)c.n_wide);
+  const size_t need = off_bar + 256;
+  if (need > kNoAllocScratchBytes)
+    return set_err(CFR_ERR_ARG, "cfr_iterate_noalloc: the game needs %zu bytes of scratch, the static limit is %zu "
+                   "(about %lld nodes in FP64, %lld in FP32)", need, kNoAllocScratchBytes,
+                   (long long)(kNoAllocScratchBytes / 24), (long long)(kNoAllocScratchBytes / 12));
+  void *base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  char *sb = (char *)base;
+  PersistArgs<T> a;
+  a.g = game_view(h);
+  a.g.wide_part = (double *)(sb + off_part);
+  a.g.wide_cnt = (unsigned *)(sb + off_cnt);
+  a.st = state_view<T>(h);
+  a.st.reach = (vec2_t<T> *)sb;
+  a.st.v = (T *)(sb + off_v);
+  a.lw = h->p<LevelWork>(h->b_levels);
+  a.D = (int)c.D;
+  a.rule = h->rule;
+  a.n_iter = n;
+  unsigned *bar = (unsigned *)(sb + off_bar);
+  a.bar.count = bar;
+  a.bar.gen = bar + 1;
+  a.bar.err = (int *)(bar + 2);
+  a.bar.spin_limit = h->opt.barrier_spin_limit > 0 ? h->opt.barrier_spin_limit : (int64_t)20000000;
+  const int L = h->persist_lanes;
+  int dev = 0, nsm = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(launch_persistent<T>(h->maxa_tier, L, 0, s, a, &per_sm));
+  int64_t cap = (int64_t)nsm * std::max(per_sm, 1);
+  if (h->opt.persistent_ctas > 0) cap = std::min<int64_t>(cap, h->opt.persistent_ctas);
+  int64_t want = 1;
+  for (const LevelWork &w : h->levels) {
+    want = std::max<int64_t>(want, (w.le - w.lb + kThreads - 1) / kThreads);
+    want = std::max<int64_t>(want, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
+    want = std::max<int64_t>(want, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
+    want = std::max<int64_t>(want, w.wc1 - w.wc0);
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
+  a.bar.expected = (unsigned)grid;
+  noalloc_init_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
+      h->p<int32_t>(h->b_child_begin), h->p<double>(h->b_tmpl), (int32_t)c.N, a.st.v, a.st.reach, a.g.wide_cnt,
+      (int32_t)c.n_wide, bar);
+  CK(cudaGetLastError());
+  CK(launch_persistent<T>(h->maxa_tier, L, grid, s, a, nullptr));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err) return set_err(CFR_ERR_TIMEOUT, "cfr_iterate_noalloc: a grid barrier gave up waiting; the state is undefined until cfr_reset");
+  return CFR_OK;
+}
+
+extern "C" int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_iterate_noalloc: null handle");
+  if (n < 0) return set_err(CFR_ERR_ARG, "cfr_iterate_noalloc: negative n");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_iterate_noalloc: call cfr_bind first");
+  if (n == 0) return CFR_OK;
+  if (h->c.D == 0) return set_err(CFR_ERR_UNSUPPORTED, "cfr_iterate_noalloc: the root is terminal; use cfr_iterate");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = h->precision == CFR_P64 ? iterate_noalloc_t<double>(h, n, s) : iterate_noalloc_t<float>(h, n, s);
+  if (rc == CFR_OK) h->iteration_host += n;
+  return rc;
 }
