@@ -37,12 +37,12 @@ UNIT = "edges/s"
 L2_BYTES = 129 * 1024 * 1024
 
 
-def workloads(deal_stride: int = 1):
+def workloads(deal_stride: int = 1, stack: int = 2, cap: int = 3):
     import gamegen as gg
 
     return {
         "large_card": dict(
-            make=lambda: gg.large_card_sampled(deal_stride, 8, 4, 2, 3),
+            make=lambda: gg.large_card_sampled(deal_stride, 8, 4, stack, cap),
             sample=lambda: (gg.large_card_sampled(200, 8, 4, 2, 3), "every 200th root deal of the same game"),
             desc="two-round card game: 8 ranks x 4 suits, two private cards, one public card, "
                  "bets {1/2 pot, pot, all-in}, cap 3 per round, stack 2 antes"),
@@ -69,8 +69,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--deal-stride", type=int, default=1,
                    help="large_card only: keep every k-th root deal (a smaller instance for profiling)")
+    p.add_argument("--stack", type=int, default=2, help="large_card only: stack behind the ante")
+    p.add_argument("--cap", type=int, default=3, help="large_card only: bets per round")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the lane counts picked from mean set sizes")
     return p.parse_args()
 
 
@@ -212,7 +215,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    wl = workloads(args.deal_stride)[args.workload]
+    wl = workloads(args.deal_stride, args.stack, args.cap)[args.workload]
     spec = wl["make"]()
     forms = {"graph": cfr.EXEC_GRAPH, "levels": cfr.EXEC_LEVELS, "persistent": cfr.EXEC_PERSISTENT,
              "auto": cfr.EXEC_AUTO}
@@ -224,6 +227,7 @@ def run_ours(args):
     del spec  # the compiled copy lives in the handle
     stream = torch.cuda.current_stream(dev)
     s = int(stream.cuda_stream)
+    lanes = solver.autotune() if not args.no_autotune else list(cfr.cfr_export_array(solver.h, "level_lanes"))
 
     # warm-up (graph capture happens on the first call)
     solver.iterate(args.warmup)
@@ -304,11 +308,14 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == cfr.P32 else "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload + ("" if args.deal_stride == 1 else " (every %dth deal)" % args.deal_stride),
+        "config": {"workload": args.workload + ("" if args.deal_stride == 1 else " (every %dth deal)" % args.deal_stride)
+                   + ("" if (args.stack, args.cap) == (2, 3) else " (stack %d, cap %d)" % (args.stack, args.cap)),
                    "description": wl["desc"], "nodes": n_nodes, "edges": E,
                    "infosets": counts["n_infosets"], "slots": counts["n_slots"], "depth_blocks": D,
                    "precision": args.precision + (" (FP64 regret/average accumulators)" if prec == cfr.P32 else ""),
                    "exec_form": args.exec_form, "pot": pot, "parallelism": "replicas x%d" % world,
+                   "lanes_per_set_by_depth": [int(x) for x in lanes],
+                   "autotuned": not args.no_autotune,
                    "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % (solver.arena_bytes / 1e9)},
         "iters_per_s": world * iters_per_s,
         "algo_gbps_per_gpu": algo_gbps,

@@ -83,7 +83,7 @@ typedef struct cfr_options {
    * barrier between depth levels; CFR_EXEC_AUTO picks by game size. */
   int exec_form;
   int rule;            /* CFR_RULE_CFR_PLUS (clamp) or CFR_RULE_CFR (no clamp) */
-  int lanes_per_set;   /* 0 = autotune; else 1..32 lanes aggregate one information set */
+  int lanes_per_set;   /* 0 = by mean set size (see cfr_autotune); else 1, 2, 4, 8, 16 or 32 lanes per set */
   int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
   int64_t barrier_spin_limit; /* 0 = default; polls before a grid barrier reports CFR_ERR_TIMEOUT */
 } cfr_options;
@@ -169,6 +169,18 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);
+
+/* Autotuner for the thread-to-work mapping: for every depth it times the
+ * backward launch with each supported number of lanes per information set
+ * (1, 2, 4, 8, 16, 32; `reps` launches each) and keeps the fastest; in the
+ * persistent form it also times whole persistent iterations per lane count.
+ * Trial launches overwrite the solver state, so the call ends by resetting it
+ * (as cfr_reset) and dropping a captured graph. The chosen counts are
+ * exported as array 12. In the FP32 mode the lane count fixes the shape of
+ * the member reductions, so a different choice changes the last bits of the
+ * iterates; pin it with cfr_options.lanes_per_set for bitwise repeatability
+ * across processes. Synchronises `stream`. */
+int cfr_autotune(cfr_handle *h, int reps, void *stream);
 
 /* Algorithmic device bytes of depth level d (0 <= d < D) for the forward
  * kernel and the backward kernel of one iteration: every array element the

@@ -29,7 +29,7 @@ RULE_CFR_PLUS, RULE_CFR = 0, 1
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
-          "spec_slot_of": 11}
+          "spec_slot_of": 11, "level_lanes": 12}
 
 
 class CfrError(RuntimeError):
@@ -91,6 +91,7 @@ def _load():
         "cfr_level_bytes": [H, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "cfr_profile_iteration": [H, dp, dp, vp],
         "cfr_iterate_noalloc": [H, i64, vp],
+        "cfr_autotune": [H, ctypes.c_int, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -107,7 +108,7 @@ _lib = _load()
 EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterate", "cfr_synchronize",
             "cfr_avg_strategy", "cfr_current_strategy", "cfr_exploitability", "cfr_reset", "cfr_set_payoffs",
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
-            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc"]
+            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune"]
 
 
 def _check(rc: int) -> None:
@@ -182,6 +183,11 @@ def cfr_iterate_noalloc(h: int, n: int, stream: int = 0) -> None:
     """n iterations with the scratch in the library's static device array
     (no allocation during the call; synchronises the stream)."""
     _check(_lib.cfr_iterate_noalloc(h, n, stream))
+
+
+def cfr_autotune(h: int, reps: int = 5, stream: int = 0) -> None:
+    """Pick lanes per information set for every depth by timing (resets the state)."""
+    _check(_lib.cfr_autotune(h, reps, stream))
 
 
 def cfr_synchronize(h: int, stream: int = 0) -> None:
@@ -294,6 +300,10 @@ class Solver:
 
     def iterate(self, n: int) -> None:
         cfr_iterate(self.h, n, self._s())
+
+    def autotune(self, reps: int = 5) -> list:
+        cfr_autotune(self.h, reps, self._s())
+        return list(cfr_export_array(self.h, "level_lanes"))
 
     def synchronize(self) -> None:
         cfr_synchronize(self.h, self._s())

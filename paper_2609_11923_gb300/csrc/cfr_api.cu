@@ -55,7 +55,7 @@ struct cfr_handle {
   int persist_lanes = 8;
   std::vector<LevelWork> levels;
   // arena layout
-  Buf b_child_begin, b_node_slot, b_iset_slot, b_iset_mem, b_mem_node, b_chance_list, b_spec_slot, b_levels;
+  Buf b_child_begin, b_node_slot, b_iset_slot, b_iset_mem, b_mem_node, b_mem_cb, b_chance_list, b_spec_slot, b_levels;
   Buf b_wide_list, b_wide_chunk, b_wide_part, b_wide_cnt;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
   size_t plan_bytes = 0;
@@ -88,6 +88,7 @@ static void plan(cfr_handle *h) {
   take(h->b_iset_slot, 4 * (c.I + 1));
   take(h->b_iset_mem, 4 * (c.I + 1));
   take(h->b_mem_node, 4 * c.n_dec);
+  take(h->b_mem_cb, 4 * c.n_dec);
   take(h->b_chance_list, 4 * c.n_chance);
   take(h->b_spec_slot, 4 * c.A);
   take(h->b_levels, sizeof(LevelWork) * std::max<int64_t>(c.D, 1));
@@ -124,11 +125,12 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (h->opt.exec_form < 0 || h->opt.exec_form > 3) { delete h; return set_err(CFR_ERR_ARG, "bad exec_form"); }
   if (h->opt.rule != CFR_RULE_CFR_PLUS && h->opt.rule != CFR_RULE_CFR) { delete h; return set_err(CFR_ERR_ARG, "bad rule"); }
   const int lp = h->opt.lanes_per_set;
-  if (lp != 0 && lp != 4 && lp != 8 && lp != 16 && lp != 32) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 4, 8, 16 or 32"); }
+  if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16 or 32"); }
   std::string err;
   int rc = compile_game(*spec, h->c, err);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
+  if (lp != 0 && lp < 4 && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1 or 2 needs sets of at most 8 actions"); }
   h->precision = h->opt.precision;
   h->rule = h->opt.rule;
   h->maxa_tier = c.max_act <= 4 ? 4 : (c.max_act <= 8 ? 8 : 64);
@@ -179,7 +181,7 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
   o->depth_blocks = c.D; o->max_actions = c.max_act;
   o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision);
   o->upload_bytes = (int64_t)(h->b_child_begin.bytes + h->b_node_slot.bytes + h->b_iset_slot.bytes + h->b_iset_mem.bytes +
-                              h->b_mem_node.bytes + h->b_chance_list.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
+                              h->b_mem_node.bytes + h->b_mem_cb.bytes + h->b_chance_list.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
                               h->b_wide_list.bytes + h->b_wide_chunk.bytes + h->b_tmpl.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
@@ -200,6 +202,7 @@ static GameView game_view(const cfr_handle *h) {
   g.iset_slot = h->p<int32_t>(h->b_iset_slot);
   g.iset_mem = h->p<int32_t>(h->b_iset_mem);
   g.mem_node = h->p<int32_t>(h->b_mem_node);
+  g.mem_cb = h->p<int32_t>(h->b_mem_cb);
   g.chance_list = h->p<int32_t>(h->b_chance_list);
   g.wide_list = h->p<int32_t>(h->b_wide_list);
   g.wide_chunk = h->p<int32_t>(h->b_wide_chunk);
@@ -265,6 +268,7 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_iset_slot, c.iset_slot.data(), 4 * (c.I + 1)))) return rc;
   if ((rc = up(h->b_iset_mem, c.iset_mem.data(), 4 * (c.I + 1)))) return rc;
   if ((rc = up(h->b_mem_node, c.mem_node.data(), 4 * c.n_dec))) return rc;
+  if ((rc = up(h->b_mem_cb, c.mem_cb.data(), 4 * c.n_dec))) return rc;
   if ((rc = up(h->b_chance_list, c.chance_list.data(), 4 * c.n_chance))) return rc;
   if ((rc = up(h->b_spec_slot, c.spec_slot_of.data(), 4 * c.A))) return rc;
   if ((rc = up(h->b_levels, h->levels.data(), sizeof(LevelWork) * c.D))) return rc;
@@ -593,6 +597,7 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 9: src = c.new_of_spec.data(); n = (int64_t)c.new_of_spec.size(); break;
     case 10: src = c.tmpl.data(); n = (int64_t)c.tmpl.size(); esz = 8; break;
     case 11: src = c.spec_slot_of.data(); n = (int64_t)c.spec_slot_of.size(); break;
+    case 12: src = h->level_lanes.data(); n = (int64_t)h->level_lanes.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -793,4 +798,73 @@ extern "C" int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream) {
   int rc = h->precision == CFR_P64 ? iterate_noalloc_t<double>(h, n, s) : iterate_noalloc_t<float>(h, n, s);
   if (rc == CFR_OK) h->iteration_host += n;
   return rc;
+}
+
+// Autotuner: per depth, time the backward launch with every lane count the
+// action tier has kernels for and keep the fastest; for the persistent form,
+// time whole persistent iterations per lane count. Trial launches change the
+// state, so the call ends with the state reset (as cfr_reset).
+extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_autotune: null handle");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_autotune: call cfr_bind first");
+  if (reps < 1 || reps > 1000) return set_err(CFR_ERR_ARG, "cfr_autotune: reps must be in [1, 1000]");
+  const Compiled &c = h->c;
+  if (c.D == 0) return CFR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> cand = h->maxa_tier <= 8 ? std::vector<int>{1, 2, 4, 8, 16, 32} : std::vector<int>{4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = CFR_OK;
+  auto run_iter = [&]() -> int {
+    return h->precision == CFR_P64 ? enqueue_iteration<double>(h, s) : enqueue_iteration<float>(h, s);
+  };
+  rc = run_iter();  // realistic reach and values for the trials
+  for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
+    int best = h->level_lanes[d];
+    float best_ms = 1e30f;
+    for (int L : cand) {
+      h->level_lanes[d] = L;
+      rc = h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
+      if (rc) break;
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps && rc == CFR_OK; ++r)
+        rc = h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best = L; }
+    }
+    h->level_lanes[d] = best;
+  }
+  if (rc == CFR_OK && h->exec_form == CFR_EXEC_PERSISTENT) {
+    int best = h->persist_lanes;
+    float best_ms = 1e30f;
+    for (int L : cand) {
+      h->persist_lanes = L;
+      h->persist_grid = 0;
+      rc = h->precision == CFR_P64 ? launch_persistent_form<double>(h, 1, s) : launch_persistent_form<float>(h, 1, s);
+      if (rc) break;
+      CK(cudaEventRecord(e0, s));
+      rc = h->precision == CFR_P64 ? launch_persistent_form<double>(h, reps, s) : launch_persistent_form<float>(h, reps, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best = L; }
+    }
+    h->persist_lanes = best;
+    h->persist_grid = 0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->graph_arena = nullptr; }
+  CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
+  if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
+  rc = h->precision == CFR_P64 ? init_state<double>(h, s) : init_state<float>(h, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return CFR_OK;
 }

@@ -201,6 +201,8 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
         c.node_slot[h] = c.iset_slot[cid] | (k == CFR_PLAYER2 ? kSlotP2Bit : 0);
       }
     }
+    c.mem_cb.resize(c.n_dec);
+    for (int64_t k = 0; k < c.n_dec; ++k) c.mem_cb[k] = c.child_begin[c.mem_node[k]];
     // chance nodes per depth (narrow ones per thread, wide ones by chunks)
     c.chance_list.clear();
     c.chance_list.reserve(c.n_chance);

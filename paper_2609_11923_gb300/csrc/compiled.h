@@ -34,6 +34,7 @@ struct Compiled {
   std::vector<int32_t> iset_slot;    // [I+1]
   std::vector<int32_t> iset_mem;     // [I+1] offsets into mem_node
   std::vector<int32_t> mem_node;     // [n_dec] members, ascending node id per set
+  std::vector<int32_t> mem_cb;       // [n_dec] first child of each member (member order)
   std::vector<int32_t> level_iset;   // [2D+1]: depth d: P1 sets [2d, 2d+1), P2 sets [2d+1, 2d+2)
   std::vector<int32_t> chance_list;  // [n_chance - n_wide] chance nodes with <= kWide children, ascending id
   std::vector<int32_t> level_chance; // [D+1]

@@ -8,8 +8,8 @@ cudaError_t launch_br_level(int maxa, int lanes, int grid, cudaStream_t s, GameV
     br_level_kernel<MA, L><<<grid, kThreads, 0, s>>>(g, reach2, sbs, vb, vavg, w, nb_chance); \
     return cudaGetLastError();                                                                \
   }
-  BR_CASE(4, 4) BR_CASE(4, 8) BR_CASE(4, 16) BR_CASE(4, 32)
-  BR_CASE(8, 4) BR_CASE(8, 8) BR_CASE(8, 16) BR_CASE(8, 32)
+  BR_CASE(4, 1) BR_CASE(4, 2) BR_CASE(4, 4) BR_CASE(4, 8) BR_CASE(4, 16) BR_CASE(4, 32)
+  BR_CASE(8, 1) BR_CASE(8, 2) BR_CASE(8, 4) BR_CASE(8, 8) BR_CASE(8, 16) BR_CASE(8, 32)
   BR_CASE(64, 4) BR_CASE(64, 8) BR_CASE(64, 16) BR_CASE(64, 32)
 #undef BR_CASE
   return cudaErrorInvalidValue;

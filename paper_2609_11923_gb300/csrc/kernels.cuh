@@ -52,6 +52,7 @@ struct GameView {
   const int32_t *__restrict__ iset_slot;
   const int32_t *__restrict__ iset_mem;
   const int32_t *__restrict__ mem_node;
+  const int32_t *__restrict__ mem_cb;      // first child of each member (member order)
   const int32_t *__restrict__ chance_list;
   const int32_t *__restrict__ wide_list;   // wide chance nodes
   const int32_t *__restrict__ wide_chunk;  // prefix of their chunk counts
@@ -103,11 +104,8 @@ __device__ __forceinline__ double block_sum(double x) {
 
 // ------------------------------------------------------------ forward reach
 template <typename T, bool PERSIST>
-__device__ __forceinline__ void fwd_node(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t h) {
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
-  if (cb == ce || ce - cb > kWideNode) return;  // terminal, or wide (done by chunks)
-  const int32_t s = __ldg(g.node_slot + h);
-  const vec2_t<T> r = ldm<PERSIST>(reach + h);
+__device__ __forceinline__ void fwd_write(const T *sigma, vec2_t<T> *reach, int32_t cb, int32_t ce, int32_t s,
+                                          vec2_t<T> r) {
   if (s < 0) {
     for (int32_t c = cb; c < ce; ++c) reach[c] = r;
   } else {
@@ -126,6 +124,39 @@ __device__ __forceinline__ void fwd_node(const GameView &g, const T *sigma, vec2
       }
     }
   }
+}
+
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void fwd_node(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t h) {
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const int32_t s = __ldg(g.node_slot + h);
+  if (cb == ce || ce - cb > kWideNode) return;  // terminal, or wide (done by chunks)
+  fwd_write<T, PERSIST>(sigma, reach, cb, ce, s, ldm<PERSIST>(reach + h));
+}
+
+// Four nodes h, h+stride, h+2 stride, h+3 stride per thread: their loads are
+// issued together, so each thread keeps four dependent chains in flight.
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void fwd_node4(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t h,
+                                          int32_t stride, int32_t le) {
+  int32_t cb[4], ce[4], sl[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int32_t x = h + u * stride;
+    cb[u] = 0; ce[u] = 0; sl[u] = -1;
+    if (x < le) {
+      cb[u] = __ldg(g.child_begin + x);
+      ce[u] = __ldg(g.child_begin + x + 1);
+      sl[u] = __ldg(g.node_slot + x);
+    }
+  }
+  vec2_t<T> r[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (cb[u] != ce[u] && ce[u] - cb[u] <= kWideNode) r[u] = ldm<PERSIST>(reach + h + u * stride);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (cb[u] != ce[u] && ce[u] - cb[u] <= kWideNode) fwd_write<T, PERSIST>(sigma, reach, cb[u], ce[u], sl[u], r[u]);
 }
 
 // One chunk of a wide chance node: its children copy the node's reach.
@@ -149,8 +180,8 @@ __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T
     return;
   }
   const int32_t stride = nb_nodes * blockDim.x;
-  for (int32_t h = w.lb + blockIdx.x * blockDim.x + threadIdx.x; h < w.le; h += stride)
-    fwd_node<T, false>(g, sigma, reach, h);
+  for (int32_t h = w.lb + blockIdx.x * blockDim.x + threadIdx.x; h < w.le; h += 4 * stride)
+    fwd_node4<T, false>(g, sigma, reach, h, stride, w.le);
 }
 
 // ------------------------------------------------------------ group helpers
@@ -216,11 +247,70 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
   }
 }
 
-// One information set, processed by the LANES lanes of one group.
+// Loads and per-member terms of one member (k < m1), or zeros.
+template <typename T, int MAXA, bool PERSIST>
+__device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m1,
+                                             int32_t na, bool p2, const T (&sig)[MAXA], T (&d)[MAXA],
+                                             T (&mm)[MAXA]) {
+#pragma unroll
+  for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
+  if (k >= m1) return;
+  const int32_t h = __ldg(g.mem_node + k);
+  const int32_t cb = __ldg(g.mem_cb + k);  // member order: a coalesced read
+  const vec2_t<T> r = ldm<PERSIST>(st.reach + h);
+  T vc[MAXA];
+  T vh = T(0);
+#pragma unroll
+  for (int a = 0; a < MAXA; ++a) {
+    if (a < na) {
+      vc[a] = ldm<PERSIST>(st.v + cb + a);
+      vh = vh + sig[a] * vc[a];
+    }
+  }
+  st.v[h] = vh;
+  const T po = p2 ? r.x : r.y;  // opponent's reach (chance is inside v)
+  const T pw = p2 ? r.y : r.x;  // own reach
+  const T f = (p2 ? T(-1) : T(1)) * po;
+#pragma unroll
+  for (int a = 0; a < MAXA; ++a) {
+    if (a < na) {
+      d[a] = f * (vc[a] - vh);
+      mm[a] = pw * sig[a];
+    }
+  }
+}
+
+// Adds one chunk's member terms to the group totals. P64: lane order (the
+// members' ascending order), every lane ends with the same totals. P32:
+// per-lane partial sums (finished by a butterfly).
+template <typename T, int MAXA, int LANES>
+__device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsigned mask, const T (&d)[MAXA],
+                                                 const T (&mm)[MAXA], T (&racc)[MAXA], T (&macc)[MAXA]) {
+  if constexpr (sizeof(T) == 8) {
+    for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) {
+        if (a < na) {
+          racc[a] = racc[a] + __shfl_sync(mask, d[a], j, LANES);
+          macc[a] = macc[a] + __shfl_sync(mask, mm[a], j, LANES);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a) {
+      racc[a] += d[a];
+      macc[a] += mm[a];
+    }
+  }
+}
+
+// One information set, processed by the LANES lanes of one group. Members go
+// in chunks of LANES, two chunks in flight per step; the update of the set's
+// slots runs one lane per action.
 template <typename T, int MAXA, int LANES, bool PERSIST>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
                                         int lane, unsigned mask, double wt, int rule) {
-  constexpr bool ORDERED = sizeof(T) == 8;
   const int32_t sb = __ldg(g.iset_slot + I);
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
@@ -231,57 +321,25 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
     racc[a] = T(0);
     macc[a] = T(0);
   }
-  const T sgn = p2 ? T(-1) : T(1);
-  for (int32_t k0 = m0; k0 < m1; k0 += LANES) {
-    const int32_t k = k0 + lane;
-    T d[MAXA], mm[MAXA];
-#pragma unroll
-    for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
-    if (k < m1) {
-      const int32_t h = __ldg(g.mem_node + k);
-      const int32_t cb = __ldg(g.child_begin + h);
-      const vec2_t<T> r = ldm<PERSIST>(st.reach + h);
-      T vc[MAXA];
-      T vh = T(0);
-#pragma unroll
-      for (int a = 0; a < MAXA; ++a) {
-        if (a < na) {
-          vc[a] = ldm<PERSIST>(st.v + cb + a);
-          vh = vh + sig[a] * vc[a];
-        }
-      }
-      st.v[h] = vh;
-      const T po = p2 ? r.x : r.y;  // opponent's reach (chance is inside v)
-      const T pw = p2 ? r.y : r.x;  // own reach
-      const T f = sgn * po;
-#pragma unroll
-      for (int a = 0; a < MAXA; ++a) {
-        if (a < na) {
-          d[a] = f * (vc[a] - vh);
-          mm[a] = pw * sig[a];
-        }
-      }
-    }
-    if constexpr (ORDERED) {
-      const int cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
-      for (int j = 0; j < cnt; ++j) {
-#pragma unroll
-        for (int a = 0; a < MAXA; ++a) {
-          if (a < na) {
-            racc[a] = racc[a] + __shfl_sync(mask, d[a], j, LANES);
-            macc[a] = macc[a] + __shfl_sync(mask, mm[a], j, LANES);
-          }
-        }
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < MAXA; ++a) {
-        racc[a] += d[a];
-        macc[a] += mm[a];
-      }
+  constexpr bool TWO = MAXA <= 8 && LANES <= 8;  // narrow groups keep two chunks in flight
+  int32_t k0 = m0;
+  if constexpr (TWO) {
+    for (; k0 + LANES < m1; k0 += 2 * LANES) {
+      T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m1, na, p2, sig, d0, mm0);
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m1, na, p2, sig, d1, mm1);
+      accumulate_chunk<T, MAXA, LANES>(LANES, na, mask, d0, mm0, racc, macc);
+      const int32_t c1 = (m1 - k0 - LANES) < LANES ? (m1 - k0 - LANES) : LANES;
+      accumulate_chunk<T, MAXA, LANES>(c1, na, mask, d1, mm1, racc, macc);
     }
   }
-  if constexpr (!ORDERED) {
+  for (; k0 < m1; k0 += LANES) {
+    T d[MAXA], mm[MAXA];
+    member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m1, na, p2, sig, d, mm);
+    const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
+    accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
+  }
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int a = 0; a < MAXA; ++a) {
       if (a < na) {
@@ -290,7 +348,33 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
       }
     }
   }
-  if (lane == 0) {
+  // every lane now holds the set's totals racc[a], macc[a]
+  if (na <= LANES) {
+    // lane a updates slot a: R <- max(R + r, 0) (CFR+), avg += t * m, then
+    // sigma^{t+1} = RM(R); the sum of positive regrets runs in action order
+    T r = T(0), m = T(0);
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a)
+      if (a == lane) { r = racc[a]; m = macc[a]; }
+    double pos = 0.0;
+    if (lane < na) {
+      double Rn = st.R[sb + lane] + (double)r;
+      if (rule == 0) Rn = Rn > 0.0 ? Rn : 0.0;
+      st.R[sb + lane] = Rn;
+      st.avg[sb + lane] += wt * (double)m;
+      pos = Rn > 0.0 ? Rn : 0.0;
+    }
+    if constexpr (sizeof(T) == 8) {
+      double tot = 0.0;
+      for (int a = 0; a < na; ++a) tot += __shfl_sync(mask, pos, a, LANES);
+      if (lane < na) st.sigma[sb + lane] = tot > 0.0 ? pos / tot : 1.0 / (double)na;
+    } else {
+      const float pf = (float)pos;
+      float tot = 0.f;
+      for (int a = 0; a < na; ++a) tot += __shfl_sync(mask, pf, a, LANES);
+      if (lane < na) st.sigma[sb + lane] = tot > 0.f ? pf / tot : 1.f / (float)na;
+    }
+  } else if (lane == 0) {
     double pos[MAXA];
     double tot = 0.0;
 #pragma unroll
@@ -304,16 +388,26 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
         tot += pos[a];
       }
     }
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-    for (int a = 0; a < MAXA; ++a)
-      if (a < na) st.sigma[sb + a] = (T)(tot > 0.0 ? pos[a] / tot : 1.0 / (double)na);
+      for (int a = 0; a < MAXA; ++a)
+        if (a < na) st.sigma[sb + a] = tot > 0.0 ? pos[a] / tot : 1.0 / (double)na;
+    } else {
+      float totf = 0.f;
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a)
+        if (a < na) totf += (float)pos[a];
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a)
+        if (a < na) st.sigma[sb + a] = totf > 0.f ? (float)pos[a] / totf : 1.f / (float)na;
+    }
   }
 }
 
 // Grid: nb_chance blocks over narrow chance nodes, then one block per wide
 // chunk, then the information-set groups.
 template <typename T, int MAXA, int LANES>
-__global__ void __launch_bounds__(kThreads) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
+__global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 5 : (MAXA <= 8 ? 3 : 1)) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
                                                             int nb_chance, int rule, int bump_t) {
   const int nb_wide = w.wc1 - w.wc0;
   if ((int)blockIdx.x < nb_chance) {
@@ -415,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
   for (long long it = 0; it < a.n_iter; ++it) {
     for (int d = 0; d < a.D; ++d) {
       const LevelWork w = a.lw[d];
-      for (int32_t h = w.lb + tid; h < w.le; h += nthr) fwd_node<T, true>(a.g, a.st.sigma, a.st.reach, h);
+      for (int32_t h = w.lb + tid; h < w.le; h += 4 * nthr) fwd_node4<T, true>(a.g, a.st.sigma, a.st.reach, h, nthr, w.le);
       for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
       if (!grid_sync(a.bar)) return;
     }

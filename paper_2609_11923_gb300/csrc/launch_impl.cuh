@@ -12,8 +12,8 @@ cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, Game
     bwd_level_kernel<T, MA, L><<<grid, kThreads, 0, s>>>(g, st, w, nb_chance, rule, bump);      \
     return cudaGetLastError();                                                                  \
   }
-  BWD_CASE(4, 4) BWD_CASE(4, 8) BWD_CASE(4, 16) BWD_CASE(4, 32)
-  BWD_CASE(8, 4) BWD_CASE(8, 8) BWD_CASE(8, 16) BWD_CASE(8, 32)
+  BWD_CASE(4, 1) BWD_CASE(4, 2) BWD_CASE(4, 4) BWD_CASE(4, 8) BWD_CASE(4, 16) BWD_CASE(4, 32)
+  BWD_CASE(8, 1) BWD_CASE(8, 2) BWD_CASE(8, 4) BWD_CASE(8, 8) BWD_CASE(8, 16) BWD_CASE(8, 32)
   BWD_CASE(64, 4) BWD_CASE(64, 8) BWD_CASE(64, 16) BWD_CASE(64, 32)
 #undef BWD_CASE
   return cudaErrorInvalidValue;
@@ -35,8 +35,8 @@ template <typename T>
 cudaError_t launch_persistent(int maxa, int lanes, int grid, cudaStream_t s, PersistArgs<T> a, int *occ) {
 #define P_CASE(MA, L) \
   if (maxa == MA && lanes == L) return persistent_one<T, MA, L>(grid, s, a, occ);
-  P_CASE(4, 4) P_CASE(4, 8) P_CASE(4, 16) P_CASE(4, 32)
-  P_CASE(8, 4) P_CASE(8, 8) P_CASE(8, 16) P_CASE(8, 32)
+  P_CASE(4, 1) P_CASE(4, 2) P_CASE(4, 4) P_CASE(4, 8) P_CASE(4, 16) P_CASE(4, 32)
+  P_CASE(8, 1) P_CASE(8, 2) P_CASE(8, 4) P_CASE(8, 8) P_CASE(8, 16) P_CASE(8, 32)
   P_CASE(64, 4) P_CASE(64, 8) P_CASE(64, 16) P_CASE(64, 32)
 #undef P_CASE
   return cudaErrorInvalidValue;

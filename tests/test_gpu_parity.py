@@ -260,3 +260,23 @@ def test_device_output_equals_host_output():
     s = solve_gpu(g, 100, precision=cfr.P32)
     d = s.avg_strategy_device().cpu().numpy()
     np.testing.assert_array_equal(d, s.avg_strategy())
+
+
+def test_autotune_keeps_fp64_parity_and_picks_valid_lanes():
+    g = gg.random_tree(14, depth=9)
+    s = cfr.Solver(g, precision=cfr.P64)
+    lanes = s.autotune(reps=2)
+    assert len(lanes) == s.counts["depth_blocks"]
+    assert set(lanes) <= {1, 2, 4, 8, 16, 32}
+    assert s.get_state()[2] == 0  # the trials were reset
+    s.iterate(300)
+    np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 300).avg_strategy())
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_every_lane_count_matches_oracle_in_fp64(lanes):
+    g = gg.large_card(3, 2, 1, 1)
+    s = solve_gpu(g, 200, lanes_per_set=lanes)
+    np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 200).avg_strategy())
+    p = solve_gpu(g, 200, precision=cfr.P32, form=cfr.EXEC_PERSISTENT, lanes_per_set=lanes)
+    assert abs(p.exploitability() - oracle.solve(g, 200).exploitability()) <= 1e-4 * g.pot
