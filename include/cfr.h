@@ -182,6 +182,28 @@ int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity
  * across processes. Synchronises `stream`. */
 int cfr_autotune(cfr_handle *h, int reps, void *stream);
 
+/* Batched solves (many independent games in one launch). Every handle must
+ * be bound (each to its own arena) and use the same precision, with sets of
+ * at most 8 actions. One CTA of `threads` threads (256 or 1024; 0 = 256)
+ * runs all iterations of one instance with `lanes` lanes per information set
+ * (2, 4, 8 or 32; 0 = 4). A solve's result depends only on its own data and
+ * on (threads, lanes): it is bitwise the same alone and in any mix.
+ * table_dev: caller-owned device buffer of at least cfr_batch_table_bytes(n)
+ * bytes (16-byte aligned) for the instance descriptors; it must stay
+ * untouched until the launch completes. */
+size_t cfr_batch_table_bytes(int n);
+
+/* Runs iters[i] iterations of instance i (iters may be NULL: every
+ * instance runs n_iter), asynchronously on `stream`. */
+int cfr_batch_iterate(cfr_handle *const *handles, int n, const int64_t *iters, int64_t n_iter, void *table_dev,
+                      size_t table_bytes, int threads, int lanes, void *stream);
+
+/* Exploitability of every instance's average strategy in one launch; out
+ * (host, [4n]) receives per instance (NashConv/2, br1, br2, u). Synchronises
+ * `stream`. */
+int cfr_batch_exploitability(cfr_handle *const *handles, int n, double *out, void *table_dev, size_t table_bytes,
+                             int threads, int lanes, void *stream);
+
 /* Algorithmic device bytes of depth level d (0 <= d < D) for the forward
  * kernel and the backward kernel of one iteration: every array element the
  * layout needs, touched once (the design notes list the per-element terms).

@@ -92,6 +92,10 @@ def _load():
         "cfr_profile_iteration": [H, dp, dp, vp],
         "cfr_iterate_noalloc": [H, i64, vp],
         "cfr_autotune": [H, ctypes.c_int, vp],
+        "cfr_batch_iterate": [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(i64), i64, vp, ctypes.c_size_t,
+                              ctypes.c_int, ctypes.c_int, vp],
+        "cfr_batch_exploitability": [ctypes.POINTER(H), ctypes.c_int, dp, vp, ctypes.c_size_t, ctypes.c_int,
+                                     ctypes.c_int, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -101,6 +105,8 @@ def _load():
     lib.cfr_last_error.argtypes = []
     lib.cfr_destroy.restype = None
     lib.cfr_destroy.argtypes = [H]
+    lib.cfr_batch_table_bytes.restype = ctypes.c_size_t
+    lib.cfr_batch_table_bytes.argtypes = [ctypes.c_int]
     return lib
 
 
@@ -108,7 +114,8 @@ _lib = _load()
 EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterate", "cfr_synchronize",
             "cfr_avg_strategy", "cfr_current_strategy", "cfr_exploitability", "cfr_reset", "cfr_set_payoffs",
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
-            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune"]
+            "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune",
+            "cfr_batch_table_bytes", "cfr_batch_iterate", "cfr_batch_exploitability"]
 
 
 def _check(rc: int) -> None:
@@ -261,6 +268,36 @@ def cfr_profile_iteration(h: int, depth_blocks: int, stream: int = 0):
     b = np.zeros(max(depth_blocks, 1))
     _check(_lib.cfr_profile_iteration(h, _dp(f), _dp(b), stream))
     return f[:depth_blocks], b[:depth_blocks]
+
+
+def cfr_batch_table_bytes(n: int) -> int:
+    return int(_lib.cfr_batch_table_bytes(n))
+
+
+def _handles(hs):
+    arr = (ctypes.c_void_p * len(hs))()
+    for i, h in enumerate(hs):
+        arr[i] = h
+    return arr
+
+
+def cfr_batch_iterate(hs, n_iter, table_ptr: int, table_bytes: int, threads: int = 0, lanes: int = 0,
+                      stream: int = 0, iters=None) -> None:
+    """n_iter iterations of every handle in one launch (or iters[i] each)."""
+    it = None
+    if iters is not None:
+        it = (ctypes.c_int64 * len(hs))(*[int(x) for x in iters])
+    _check(_lib.cfr_batch_iterate(_handles(hs), len(hs), it, n_iter, table_ptr, table_bytes, threads, lanes,
+                                  stream))
+
+
+def cfr_batch_exploitability(hs, table_ptr: int, table_bytes: int, threads: int = 0, lanes: int = 0,
+                             stream: int = 0) -> np.ndarray:
+    """[n, 4]: (exploitability, br1, br2, u) of every handle's average strategy."""
+    out = np.zeros(4 * len(hs))
+    _check(_lib.cfr_batch_exploitability(_handles(hs), len(hs), _dp(out), table_ptr, table_bytes, threads, lanes,
+                                         stream))
+    return out.reshape(len(hs), 4)
 
 
 def cfr_last_error() -> str:

@@ -1,0 +1,226 @@
+// batch.cuh — many independent solves in one launch (batched serving).
+//
+// One CTA owns one instance for the whole call: it runs that instance's n
+// CFR+ iterations with __syncthreads() between depth levels (no grid
+// barrier, no cross-CTA traffic), so a batch of hundreds of uneven
+// subgames is one launch whose CTAs the hardware schedules as SMs free up.
+// Each instance's arithmetic depends only on its own arrays and on the
+// launch shape (THREADS, LANES): a solve gives bitwise the same result alone
+// and inside any mix run with the same shape. The per-level device
+// functions are the ones of kernels.cuh; wide chance nodes are summed by the
+// whole CTA in a fixed order.
+#pragma once
+#include "kernels.cuh"
+
+namespace cfr {
+
+// Everything a CTA needs about one bound instance (device pointers into the
+// instance's own arena).
+struct InstDesc {
+  GameView g;
+  void *reach;
+  void *v;
+  void *sigma;
+  double *R;
+  double *avg;
+  long long *t;
+  const LevelWork *lw;
+  double2 *reach2;
+  double2 *vb;
+  double *vavg;
+  double *sbs;
+  double *out;      // exploitability result slot (batch_br_kernel)
+  long long n_iter; // iterations this call runs for the instance
+  int32_t D;
+  int32_t rule;
+  int32_t n_sets;
+  int32_t pad;
+};
+
+template <int THREADS>
+__device__ __forceinline__ double cta_sum(double x, double *sm) {
+  __syncthreads();
+  sm[threadIdx.x] = x;
+  __syncthreads();
+#pragma unroll
+  for (int s = THREADS / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+// Wide chance node inside one CTA: forward copies the reach to every child.
+template <typename T>
+__device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach, int32_t h) {
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const vec2_t<T> r = reach[h];
+  for (int32_t c = cb + threadIdx.x; c < ce; c += blockDim.x) reach[c] = r;
+}
+
+// Wide chance node inside one CTA: value = sum of the children's values.
+// P64 sums left to right (thread 0); P32 uses the fixed-shape CTA tree.
+template <typename T, int THREADS>
+__device__ __forceinline__ void cta_bwd_wide(const GameView &g, T *v, int32_t h, double *sm) {
+  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  if constexpr (sizeof(T) == 8) {
+    if (threadIdx.x == 0) {
+      T s = T(0);
+      for (int32_t c = cb; c < ce; ++c) s = s + v[c];
+      v[h] = s;
+    }
+  } else {
+    double x = 0.0;
+    for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) x += (double)v[c];
+    x = cta_sum<THREADS>(x, sm);
+    if (threadIdx.x == 0) v[h] = (T)x;
+  }
+}
+
+template <typename T, int MAXA, int LANES, int THREADS>
+__global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *table, int n_inst) {
+  __shared__ double sm[THREADS];
+  const int inst = blockIdx.x;
+  if (inst >= n_inst) return;
+  const InstDesc in = table[inst];
+  StateView<T> st;
+  st.reach = (vec2_t<T> *)in.reach;
+  st.v = (T *)in.v;
+  st.sigma = (T *)in.sigma;
+  st.R = in.R;
+  st.avg = in.avg;
+  st.t = in.t;
+  const long long t0 = *in.t;
+  const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;
+  constexpr int NG = THREADS / LANES;
+  const unsigned mask = group_mask<LANES>();
+  for (long long it = 0; it < in.n_iter; ++it) {
+    for (int d = 0; d < in.D; ++d) {
+      const LevelWork w = in.lw[d];
+      for (int32_t h = w.lb + threadIdx.x; h < w.le; h += 4 * THREADS)
+        fwd_node4<T, false>(in.g, st.sigma, st.reach, h, THREADS, w.le);
+      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, __ldg(in.g.wide_list + i));
+      __syncthreads();
+    }
+    const double wt = (double)(t0 + it + 1);
+    for (int d = in.D - 1; d >= 0; --d) {
+      const LevelWork w = in.lw[d];
+      for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS)
+        bwd_chance<T, false>(in.g, st.v, __ldg(in.g.chance_list + i));
+      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS>(in.g, st.v, __ldg(in.g.wide_list + i), sm);
+      for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
+        bwd_set<T, MAXA, LANES, false>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule);
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) *in.t = t0 + in.n_iter;
+}
+
+// Exploitability of every instance's average strategy (FP64), one CTA each:
+// normalise the average, forward reach under it, then both best responses by
+// depth (the same arithmetic as br_level_kernel, with CTA-wide loops).
+template <int MAXA, int LANES, int THREADS>
+__global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table, int n_inst) {
+  __shared__ double sm[THREADS];
+  const int inst = blockIdx.x;
+  if (inst >= n_inst) return;
+  const InstDesc in = table[inst];
+  const GameView &g = in.g;
+  // average strategy, normalised per set
+  for (int32_t I = threadIdx.x; I < in.n_sets; I += THREADS) {
+    const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
+    double tot = 0.0;
+    for (int32_t a = 0; a < na; ++a) tot += in.avg[sb + a];
+    for (int32_t a = 0; a < na; ++a) in.sbs[sb + a] = tot > 0.0 ? in.avg[sb + a] / tot : 1.0 / (double)na;
+  }
+  __syncthreads();
+  for (int d = 0; d < in.D; ++d) {
+    const LevelWork w = in.lw[d];
+    for (int32_t h = w.lb + threadIdx.x; h < w.le; h += 4 * THREADS)
+      fwd_node4<double, false>(g, in.sbs, in.reach2, h, THREADS, w.le);
+    for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double>(g, in.reach2, __ldg(g.wide_list + i));
+    __syncthreads();
+  }
+  const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;
+  constexpr int NG = THREADS / LANES;
+  const unsigned mask = group_mask<LANES>();
+  for (int d = in.D - 1; d >= 0; --d) {
+    const LevelWork w = in.lw[d];
+    for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS) {
+      const int32_t h = __ldg(g.chance_list + i);
+      const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+      double sx = 0.0, sy = 0.0, sa = 0.0;
+      for (int32_t c = cb; c < ce; ++c) { const double2 x = in.vb[c]; sx += x.x; sy += x.y; sa += in.vavg[c]; }
+      in.vb[h] = make_double2(sx, sy);
+      in.vavg[h] = sa;
+    }
+    for (int32_t i = w.wd0; i < w.wd1; ++i) {
+      const int32_t h = __ldg(g.wide_list + i);
+      const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+      double sx = 0.0, sy = 0.0, sa = 0.0;
+      for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) { const double2 x = in.vb[c]; sx += x.x; sy += x.y; sa += in.vavg[c]; }
+      sx = cta_sum<THREADS>(sx, sm);
+      sy = cta_sum<THREADS>(sy, sm);
+      sa = cta_sum<THREADS>(sa, sm);
+      if (threadIdx.x == 0) { in.vb[h] = make_double2(sx, sy); in.vavg[h] = sa; }
+    }
+    for (int32_t I = w.is0 + gid; I < w.is1; I += NG) {
+      const int p = I >= w.is2 ? 1 : 0;
+      const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
+      const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+      double sg[MAXA], Q[MAXA];
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) { sg[a] = a < na ? in.sbs[sb + a] : 0.0; Q[a] = 0.0; }
+      for (int32_t k0 = m0; k0 < m1; k0 += LANES) {
+        const int32_t k = k0 + lane;
+        double q[MAXA];
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
+        if (k < m1) {
+          const int32_t h = __ldg(g.mem_node + k);
+          const int32_t cb = __ldg(g.mem_cb + k);
+          const double2 r = in.reach2[h];
+          const double po = p ? r.x : r.y;
+          double oth = 0.0, va = 0.0;
+#pragma unroll
+          for (int a = 0; a < MAXA; ++a) {
+            if (a < na) {
+              const double2 x = in.vb[cb + a];
+              q[a] = po * (p ? x.y : x.x);
+              oth += sg[a] * (p ? x.x : x.y);
+              va += sg[a] * in.vavg[cb + a];
+            }
+          }
+          reinterpret_cast<double *>(in.vb + h)[1 - p] = oth;
+          in.vavg[h] = va;
+        }
+        const int cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
+        for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+          for (int a = 0; a < MAXA; ++a)
+            if (a < na) Q[a] += __shfl_sync(mask, q[a], j, LANES);
+        }
+      }
+      int best = 0;
+      for (int a = 1; a < na; ++a)
+        if (p == 0 ? Q[a] > Q[best] : Q[a] < Q[best]) best = a;
+      for (int32_t k = m0 + lane; k < m1; k += LANES) {
+        const int32_t h = __ldg(g.mem_node + k);
+        const int32_t cb = __ldg(g.mem_cb + k);
+        reinterpret_cast<double *>(in.vb + h)[p] = reinterpret_cast<const double *>(in.vb + cb + best)[p];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double2 root = in.vb[0];
+    in.out[0] = 0.5 * (root.x - root.y);
+    in.out[1] = root.x;
+    in.out[2] = root.y;
+    in.out[3] = in.vavg[0];
+  }
+}
+
+}  // namespace cfr

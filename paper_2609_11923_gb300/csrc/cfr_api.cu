@@ -868,3 +868,84 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   CK(cudaStreamSynchronize(s));
   return CFR_OK;
 }
+
+// ----------------------------------------------------------- batched solves
+static int batch_table(cfr_handle *const *hs, int n, const int64_t *iters, int64_t n_iter, void *table_dev,
+                       size_t table_bytes, int *maxa, int *precision, std::vector<InstDesc> &tab) {
+  if (!hs || n <= 0) return set_err(CFR_ERR_ARG, "batch: no instances");
+  if (!table_dev || table_bytes < sizeof(InstDesc) * (size_t)n)
+    return set_err(CFR_ERR_ARG, "batch: the descriptor table needs %zu bytes", sizeof(InstDesc) * (size_t)n);
+  if (reinterpret_cast<uintptr_t>(table_dev) % 16 != 0) return set_err(CFR_ERR_ARG, "batch: table must be 16-byte aligned");
+  tab.resize(n);
+  *maxa = 4;
+  *precision = -1;
+  for (int i = 0; i < n; ++i) {
+    cfr_handle *h = hs[i];
+    if (!h) return set_err(CFR_ERR_ARG, "batch: null handle %d", i);
+    if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "batch: instance %d is not bound", i);
+    if (*precision < 0) *precision = h->precision;
+    else if (*precision != h->precision) return set_err(CFR_ERR_ARG, "batch: instances mix precisions");
+    if (h->maxa_tier > 8) return set_err(CFR_ERR_UNSUPPORTED, "batch: instance %d has sets of more than 8 actions", i);
+    *maxa = std::max(*maxa, h->maxa_tier);
+    InstDesc &d = tab[i];
+    memset(&d, 0, sizeof d);
+    d.g = game_view(h);
+    d.reach = h->arena + h->b_reach.off;
+    d.v = h->arena + h->b_v.off;
+    d.sigma = h->arena + h->b_sigma.off;
+    d.R = h->p<double>(h->b_R);
+    d.avg = h->p<double>(h->b_avg);
+    d.t = h->p<long long>(h->b_t);
+    d.lw = h->p<LevelWork>(h->b_levels);
+    d.reach2 = h->p<double2>(h->b_reach2);
+    d.vb = h->p<double2>(h->b_vb);
+    d.vavg = h->p<double>(h->b_vavg);
+    d.sbs = h->p<double>(h->b_sbs);
+    d.out = h->p<double>(h->b_out);
+    d.n_iter = iters ? iters[i] : n_iter;
+    if (d.n_iter < 0) return set_err(CFR_ERR_ARG, "batch: negative iteration count");
+    d.D = (int32_t)h->c.D;
+    d.rule = h->rule;
+    d.n_sets = (int32_t)h->c.I;
+  }
+  return CFR_OK;
+}
+
+extern "C" size_t cfr_batch_table_bytes(int n) { return n > 0 ? sizeof(InstDesc) * (size_t)n : 0; }
+
+extern "C" int cfr_batch_iterate(cfr_handle *const *hs, int n, const int64_t *iters, int64_t n_iter, void *table_dev,
+                                 size_t table_bytes, int threads, int lanes, void *stream) {
+  std::vector<InstDesc> tab;
+  int maxa = 4, prec = 0;
+  int rc = batch_table(hs, n, iters, n_iter, table_dev, table_bytes, &maxa, &prec, tab);
+  if (rc) return rc;
+  if (threads == 0) threads = 256;
+  if (lanes == 0) lanes = 4;
+  if ((threads != 256 && threads != 1024) || (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32))
+    return set_err(CFR_ERR_ARG, "batch: threads must be 256 or 1024 and lanes 2, 4, 8 or 32");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(table_dev, tab.data(), sizeof(InstDesc) * (size_t)n, cudaMemcpyHostToDevice, s));
+  if (prec == CFR_P64) CK(launch_batch_iterate<double>(maxa, lanes, threads, n, s, (const InstDesc *)table_dev));
+  else CK(launch_batch_iterate<float>(maxa, lanes, threads, n, s, (const InstDesc *)table_dev));
+  for (int i = 0; i < n; ++i) hs[i]->iteration_host += tab[i].n_iter;
+  return CFR_OK;
+}
+
+extern "C" int cfr_batch_exploitability(cfr_handle *const *hs, int n, double *out, void *table_dev, size_t table_bytes,
+                                        int threads, int lanes, void *stream) {
+  if (!out) return set_err(CFR_ERR_ARG, "batch: null output");
+  std::vector<InstDesc> tab;
+  int maxa = 4, prec = 0;
+  int rc = batch_table(hs, n, nullptr, 0, table_dev, table_bytes, &maxa, &prec, tab);
+  if (rc) return rc;
+  if (threads == 0) threads = 256;
+  if (lanes == 0) lanes = 4;
+  if ((threads != 256 && threads != 1024) || (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32))
+    return set_err(CFR_ERR_ARG, "batch: threads must be 256 or 1024 and lanes 2, 4, 8 or 32");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(table_dev, tab.data(), sizeof(InstDesc) * (size_t)n, cudaMemcpyHostToDevice, s));
+  CK(launch_batch_br(maxa, lanes, threads, n, s, (const InstDesc *)table_dev));
+  for (int i = 0; i < n; ++i) CK(cudaMemcpyAsync(out + 4 * i, tab[i].out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return CFR_OK;
+}

@@ -22,3 +22,11 @@ cudaError_t launch_br_level(int maxa, int lanes, int grid, cudaStream_t s, GameV
                             const double *sbs, double2 *vb, double *vavg, LevelWork w, int nb_chance);
 
 }  // namespace cfr
+
+#include "batch.cuh"
+
+namespace cfr {
+template <typename T>
+cudaError_t launch_batch_iterate(int maxa, int lanes, int threads, int n, cudaStream_t s, const InstDesc *table);
+cudaError_t launch_batch_br(int maxa, int lanes, int threads, int n, cudaStream_t s, const InstDesc *table);
+}  // namespace cfr

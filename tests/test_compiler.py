@@ -172,7 +172,7 @@ def test_bad_options_are_rejected():
 
 def test_library_exports_every_declared_symbol():
     header = open(os.path.join(ROOT, "include", "cfr.h")).read()
-    names = set(re.findall(r"^\s*(?:int|void|const char \*)\s*\**\s*(cfr_\w+)\s*\(", header, re.M))
+    names = set(re.findall(r"^\s*(?:int|void|size_t|const char \*)\s*\**\s*(cfr_\w+)\s*\(", header, re.M))
     assert {"cfr_compile", "cfr_iterate", "cfr_avg_strategy", "cfr_exploitability"} <= names
     lib = ctypes.CDLL(cfr.LIB_PATH)
     for n in sorted(names):

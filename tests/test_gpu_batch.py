@@ -1,0 +1,118 @@
+"""Batched solves: one launch for many independent games (batched serving).
+
+Checks: FP64 batched iterates equal the oracle's; a solve's result is bitwise
+the same alone and inside a mix of other solves; batched exploitability
+equals the single-solve evaluator; the continuous-batching server admits by
+memory, overlaps arrivals with running solves, and returns for every request
+exactly what solving it alone returns.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gamegen as gg
+import oracle
+from paper_2609_11923_gb300 import cfr, serve
+
+pytestmark = pytest.mark.gpu
+
+
+def bound(specs, precision=cfr.P32):
+    opts = cfr.make_options(precision=precision)
+    hs = [cfr.cfr_compile(sp, opts) for sp in specs]
+    pool = serve.DevicePool(sum(cfr.cfr_plan(h) + 512 for h in hs) + 4096)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    for h in hs:
+        n = cfr.cfr_plan(h)
+        cfr.cfr_bind(h, pool.ptr(pool.alloc(n)), n, s)
+    tb = cfr.cfr_batch_table_bytes(len(hs))
+    table = torch.empty(tb + 16, dtype=torch.uint8, device="cuda")
+    return pool, hs, table, (table.data_ptr() + 15) & ~15, tb, s
+
+
+def mixed_specs(n, seed0=100):
+    out = []
+    for i in range(n):
+        out.append(gg.endgame(seed0 + i, 2000 + 3000 * (i % 5)) if i % 3 else gg.random_tree(seed0 + i, depth=7))
+    return out
+
+
+def test_batched_fp64_matches_oracle():
+    specs = [gg.tiny_card(), gg.kuhn(), gg.endgame(5, 4000), gg.endgame(2, 100000), gg.random_tree(3, depth=8),
+             gg.large_card(3, 2, 1, 1)]
+    pool, hs, table, tp, tb, s = bound(specs, cfr.P64)
+    cfr.cfr_batch_iterate(hs, 300, tp, tb, 256, 4, s)
+    for sp, h in zip(specs, hs):
+        out = np.empty(cfr.cfr_get_counts(h)["n_slots"])
+        cfr.cfr_avg_strategy(h, out, False, s)
+        np.testing.assert_array_equal(out, oracle.solve(sp, 300).avg_strategy())
+        cfr.cfr_destroy(h)
+
+
+@pytest.mark.parametrize("threads,lanes", [(256, 4), (1024, 8), (256, 32), (1024, 2)])
+def test_solve_alone_equals_solve_in_mix(threads, lanes):
+    specs = mixed_specs(12)
+    pick = [1, 5, 10]
+    pool, hs, table, tp, tb, s = bound(specs)
+    iters = [100 + 7 * i for i in range(len(specs))]  # uneven work in the mix
+    cfr.cfr_batch_iterate(hs, 0, tp, tb, threads, lanes, s, iters=iters)
+    for i in pick:
+        p2, h2, t2, tp2, tb2, _ = bound([specs[i]])
+        cfr.cfr_batch_iterate(h2, iters[i], tp2, tb2, threads, lanes, s)
+        a = cfr.cfr_get_state(hs[i], cfr.cfr_get_counts(hs[i])["n_slots"], s)
+        b = cfr.cfr_get_state(h2[0], cfr.cfr_get_counts(h2[0])["n_slots"], s)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+        assert a[2] == b[2] == iters[i]
+        cfr.cfr_destroy(h2[0])
+    for h in hs:
+        cfr.cfr_destroy(h)
+
+
+def test_batched_exploitability_equals_single():
+    specs = mixed_specs(8, seed0=300) + [gg.endgame(2, 100000)]
+    pool, hs, table, tp, tb, s = bound(specs, cfr.P64)
+    cfr.cfr_batch_iterate(hs, 120, tp, tb, 256, 4, s)
+    ex = cfr.cfr_batch_exploitability(hs, tp, tb, 256, 4, s)
+    for row, h in zip(ex, hs):
+        single = cfr.cfr_exploitability(h, s)
+        np.testing.assert_allclose(row, single, rtol=0, atol=1e-10)
+        cfr.cfr_destroy(h)
+
+
+def test_batched_fp32_reaches_oracle_exploitability():
+    specs = [gg.endgame(11, 20000), gg.endgame(12, 5000), gg.random_tree(13, depth=9)]
+    pool, hs, table, tp, tb, s = bound(specs, cfr.P32)
+    cfr.cfr_batch_iterate(hs, 1000, tp, tb, 256, 4, s)
+    ex = cfr.cfr_batch_exploitability(hs, tp, tb, 256, 4, s)
+    for sp, row, h in zip(specs, ex, hs):
+        assert abs(row[0] - oracle.solve(sp, 1000).exploitability()) <= 1e-4 * sp.pot
+        cfr.cfr_destroy(h)
+
+
+def test_server_continuous_batching_results_equal_alone():
+    rng = np.random.default_rng(0)
+    specs = [gg.endgame(400 + i, int(rng.integers(1000, 20000))) for i in range(16)]
+    arrivals = np.cumsum(rng.exponential(0.01, size=len(specs)))
+    reqs = [serve.Request(i, sp, float(t)) for i, (sp, t) in enumerate(zip(specs, arrivals))]
+    # a pool for about four solves at a time: admission is limited by memory
+    hs0 = [cfr.cfr_compile(sp) for sp in specs]
+    sizes = sorted(cfr.cfr_plan(h) for h in hs0)
+    for h in hs0:
+        cfr.cfr_destroy(h)
+    srv = serve.Server(pool_bytes=4 * sizes[-1] + 4096, max_active=64, check_every=50, max_iters=600,
+                       target=1e-3, keep_strategies=True)
+    res = srv.serve(reqs)
+    srv.close()
+    assert sorted(r.rid for r in res) == list(range(len(specs)))
+    assert srv.rounds > 1
+    for r in res:
+        assert r.finished >= r.admitted >= r.arrival - 1e-9
+        assert r.exploitability <= 1e-3 * r.pot or r.iterations == 600
+        # the same solve alone, same iteration count and launch shape
+        p2, h2, t2, tp2, tb2, s = bound([specs[r.rid]])
+        cfr.cfr_batch_iterate(h2, r.iterations, tp2, tb2, srv.threads, srv.lanes, s)
+        alone = np.empty(len(r.strategy))
+        cfr.cfr_avg_strategy(h2[0], alone, False, s)
+        np.testing.assert_array_equal(r.strategy, alone)
+        cfr.cfr_destroy(h2[0])
