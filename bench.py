@@ -63,7 +63,9 @@ def parse():
     p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="large_card", choices=["large_card", "random_tree", "tiny", "serving"])
+    p.add_argument("--workload", default="large_card", choices=["large_card", "random_tree", "tiny", "serving", "warmstart"])
+    p.add_argument("--train-games", type=int, default=4000, help="warmstart only: training solves")
+    p.add_argument("--heldout", type=int, default=512, help="warmstart only: held-out games")
     p.add_argument("--requests", type=int, default=512, help="serving only: number of endgame solves")
     p.add_argument("--max-iters", type=int, default=5000, help="serving only: iteration cap per solve")
     p.add_argument("--baseline-sample", type=int, default=48, help="serving only: solves timed one by one")
@@ -400,12 +402,59 @@ def run_serving(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start: train the MLP on solved endgames, then iterations
+    and wall time to 1e-3 pot exploitability, warm vs cold, on held-out seeds."""
+    import numpy as np
+    import torch
+
+    from paper_2609_11923_gb300 import warmstart as ws
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    train = ws.endgame_family(list(range(10000, 10000 + args.train_games)), 1e3, 1e5)
+    X, na, T = ws.make_dataset(train, iters=1000)
+    t_data = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    net = ws.train(X, na, T, epochs=6)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    val = ws.endgame_family(list(range(15000, 15064)), 1e3, 1e5)
+    kappa, ktable = ws.choose_kappa(net, val)
+    held = ws.endgame_family(list(range(20000, 20000 + args.heldout)), 1e3, 1e6)
+    cold, cold_fin, cold_wall = ws.iterations_to_target(held, max_iters=args.max_iters)
+    t2 = time.perf_counter()
+    init = [ws.warm_regrets(net, sp, kappa) for sp in held]
+    t_infer = time.perf_counter() - t2
+    warm, warm_fin, warm_wall = ws.iterations_to_target(held, init=init, max_iters=args.max_iters)
+    line = {
+        "metric": METRIC, "value": float(np.mean(warm)), "unit": "iterations to 1e-3 pot (mean, warm start)",
+        "n_gpus": 1, "steps": args.heldout, "warmup": 0, "ms_per_step": None, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network / f32 CFR", "data": "synthetic",
+        "config": {"workload": "warm start: MLP 3x256 on %d solved endgames (1e3-1e5 edges, 1000 iterations each), "
+                               "%d held-out endgames (1e3-1e6 edges)" % (args.train_games, args.heldout),
+                   "stop": "exploitability <= 1e-3 pot, checked every 50 iterations, cap %d" % args.max_iters},
+        "cold": {"mean_iters": float(np.mean(cold)), "median_iters": float(np.median(cold)),
+                 "finished": float(cold_fin.mean()), "wall_s": cold_wall},
+        "warm": {"mean_iters": float(np.mean(warm)), "median_iters": float(np.median(warm)),
+                 "finished": float(warm_fin.mean()), "wall_s": warm_wall + t_infer, "inference_s": t_infer},
+        "iteration_ratio_warm_over_cold": float(np.mean(warm) / np.mean(cold)),
+        "kappa": kappa, "kappa_validation_mean_iters": ktable,
+        "training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
+                     "loss_by_epoch": [float(x) for x in net.history]},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

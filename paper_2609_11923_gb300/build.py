@@ -15,7 +15,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # --fmad=false: no contraction of a*b+c, so FP64 kernels round exactly like
 # the plain definition (bitwise parity in the FP64 mode).
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC"]
-CU_UNITS = ["cfr_api", "k_bwd32", "k_bwd64", "k_pers32", "k_pers64", "k_br", "k_batch32", "k_batch64", "k_batchbr"]
+CU_UNITS = ["cfr_api", "k_bwd32", "k_bwd64", "k_pers32", "k_pers64", "k_br", "k_batch32", "k_batch64", "k_batchbr", "mlp"]
 # FP32-only units may contract a*b+c into one FMA (deterministic, and the
 # FP32 mode is held to the exploitability tolerance, not to bitwise parity).
 FMA_UNITS = {"k_bwd32", "k_pers32", "k_batch32"}
@@ -28,6 +28,7 @@ def _sources():
         if f.endswith((".cu", ".cuh", ".h", ".cpp")):
             out.append(os.path.join(CSRC, f))
     out.append(os.path.join(HERE, "..", "include", "cfr.h"))
+    out.append(os.path.join(HERE, "..", "include", "mlp.h"))
     return out
 
 

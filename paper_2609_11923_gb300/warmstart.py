@@ -1,0 +1,296 @@
+"""Learned warm start for the endgame family (no counterpart in the paper).
+
+Pipeline: solve many training games with the batched CFR+ kernels, take
+their average strategies as targets, train the MLP (mlp.py) on per-
+information-set features, then seed new solves with R0(I, a) = kappa * pot *
+sigma_hat(I, a) (so the first iterate plays the network's strategy) and let
+plain CFR+ continue. Cold-start CFR+ on the same games is the yardstick.
+
+Features of an information set (172 values, padded to 176): the two private
+cards (two-hot over 32 cards), the public card (one-hot), the three-card hand
+category (trips / pair / high) and its normalised showdown value, acting
+player, betting round, number of actions (one-hot), the betting history
+(8 positions x 11 action codes, one-hot), both contributions and the amount
+to call, the set's chance mass relative to the sets with the same public
+state (the weight of this private hand in the range), and the hand's
+equity against the opponent's range: the chance-weighted share of the set's
+deals that the acting player wins at the check-down showdown (value and a
+10-bucket one-hot).
+"""
+from __future__ import annotations
+
+import time
+from typing import List, Optional
+
+import numpy as np
+
+from . import cfr, serve
+from .mlp import MLP, N_OUT
+
+F_RAW = 183
+F_IN = 192
+N_CARDS, N_SUITS = 32, 4
+
+
+def _rank3(r0, r1, r2):
+    a, b, c = sorted((r0, r1, r2), reverse=True)
+    if a == c:
+        return 2, 2 * 4096 + a
+    if a == b:
+        return 1, 4096 + a * 64 + c
+    if b == c:
+        return 1, 4096 + b * 64 + a
+    return 0, a * 256 + b * 16 + c
+
+
+def chance_mass(spec, with_deal: bool = False):
+    """Chance probability of reaching every node (product along the path);
+    with_deal also returns the index of each node's root outcome."""
+    N = spec.n_nodes
+    pc = np.zeros(N)
+    pc[0] = 1.0
+    deal = np.full(N, -1, dtype=np.int64)
+    frontier = np.array([0], dtype=np.int64)
+    cb_all, ch_all = spec.child_begin, spec.child
+    while frontier.size:
+        cb = cb_all[frontier]
+        cnt = cb_all[frontier + 1] - cb
+        tot = int(cnt.sum())
+        if tot == 0:
+            break
+        start = np.repeat(cb, cnt)
+        off = np.arange(tot) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        e = start + off
+        kids = ch_all[e].astype(np.int64)
+        par = np.repeat(frontier, cnt)
+        mult = np.where(spec.kind[par] == 1, spec.chance_prob[e], 1.0)
+        pc[kids] = pc[par] * mult
+        deal[kids] = np.where(par == 0, off, deal[par])
+        frontier = kids
+    return (pc, deal) if with_deal else pc
+
+
+def checkdown_value(spec) -> np.ndarray:
+    """Player-1 payoff of the line that takes action 0 everywhere below each
+    root outcome (check-check to the showdown in the card games)."""
+    root = spec.child[spec.child_begin[0]:spec.child_begin[1]].astype(np.int64)
+    cur = root.copy()
+    for _ in range(64):
+        term = spec.kind[cur] == 0
+        if term.all():
+            break
+        cur = np.where(term, cur, spec.child[spec.child_begin[cur]].astype(np.int64))
+    return spec.payoff[cur]
+
+
+def features(spec) -> tuple:
+    """(X [I, F_IN] float32, nact [I] int32) for every information set."""
+    f = spec.iset_feat
+    if f is None:
+        raise ValueError("features need the card-game metadata of the generator")
+    I = spec.n_infosets
+    X = np.zeros((I, F_IN), dtype=np.float32)
+    rows = np.arange(I)
+    X[rows, f[:, 1]] = 1.0
+    X[rows, f[:, 2]] = 1.0
+    has_board = f[:, 3] >= 0
+    X[rows[has_board], 32 + f[has_board, 3]] = 1.0
+    for i in range(I):
+        if f[i, 3] >= 0:
+            cat, val = _rank3(f[i, 1] // N_SUITS, f[i, 2] // N_SUITS, f[i, 3] // N_SUITS)
+            X[i, 64 + cat] = 1.0
+            X[i, 67] = val / 8199.0
+    X[rows, 68 + f[:, 0]] = 1.0
+    X[rows, 70 + np.clip(f[:, 4], 0, 1)] = 1.0
+    X[rows, 72 + np.clip(f[:, 5] - 1, 0, 7)] = 1.0
+    for pos in range(8):
+        code = f[:, 6 + pos]
+        ok = code >= 0
+        X[rows[ok], 80 + pos * 11 + np.clip(code[ok], 0, 10)] = 1.0
+    c1, c2 = f[:, 14] / 2.0, f[:, 15] / 2.0
+    X[:, 168] = c1 / 10.0
+    X[:, 169] = c2 / 10.0
+    me, op = np.where(f[:, 0] == 0, c1, c2), np.where(f[:, 0] == 0, c2, c1)
+    X[:, 170] = (op - me) / 10.0
+    # relative range weight: chance mass of the set over the mean of its public state
+    pc, deal = chance_mass(spec, with_deal=True)
+    dec = spec.infoset >= 0
+    mass = np.bincount(spec.infoset[dec], weights=pc[dec], minlength=I)
+    # equity against the opponent's range at the check-down showdown
+    sd = checkdown_value(spec)
+    win1 = (1.0 + np.sign(sd)) / 2.0
+    node_w = np.where(deal[dec] >= 0, win1[np.maximum(deal[dec], 0)], 0.5)
+    eq1 = np.bincount(spec.infoset[dec], weights=pc[dec] * node_w, minlength=I) / np.maximum(mass, 1e-300)
+    eq = np.where(f[:, 0] == 0, eq1, 1.0 - eq1)
+    X[:, 172] = eq
+    X[rows, 173 + np.clip((eq * 10).astype(np.int64), 0, 9)] = 1.0
+    key = np.concatenate([f[:, [0, 3, 4]], f[:, 6:14]], axis=1)
+    _, grp = np.unique(key, axis=0, return_inverse=True)
+    grp = grp.reshape(-1)
+    gmean = np.bincount(grp, weights=mass) / np.maximum(np.bincount(grp), 1)
+    rel = mass / np.maximum(gmean[grp], 1e-300)
+    X[:, 171] = np.clip(np.log(np.maximum(rel, 1e-12)), -5.0, 5.0) / 5.0
+    nact = spec.iset_nact.astype(np.int32)
+    if nact.max(initial=0) > N_OUT:
+        raise ValueError("information sets with more than %d actions" % N_OUT)
+    return X, nact
+
+
+def _pad_slots(spec, vec) -> np.ndarray:
+    """Slot vector (spec order) -> [I, N_OUT] rows padded with zeros."""
+    off = spec.slot_offsets()
+    out = np.zeros((spec.n_infosets, N_OUT), dtype=np.float32)
+    na = spec.iset_nact
+    for a in range(N_OUT):
+        ok = na > a
+        out[ok, a] = vec[off[:-1][ok] + a]
+    return out
+
+
+def solve_batch(specs, iters: int, precision=cfr.P32, threads=1024, lanes=8, chunk=256, init=None):
+    """Average strategies of `specs` after `iters` CFR+ iterations (batched)."""
+    import torch
+
+    out = []
+    s = int(torch.cuda.current_stream().cuda_stream)
+    opts = cfr.make_options(precision=precision)
+    for c0 in range(0, len(specs), chunk):
+        part = specs[c0:c0 + chunk]
+        hs = [cfr.cfr_compile(sp, opts) for sp in part]
+        sizes = [cfr.cfr_plan(h) for h in hs]
+        pool = serve.DevicePool(sum(n + serve.ALIGN for n in sizes) + serve.ALIGN)
+        for j, (h, n) in enumerate(zip(hs, sizes)):
+            cfr.cfr_bind(h, pool.ptr(pool.alloc(n)), n, s)
+            if init is not None and init[c0 + j] is not None:
+                A = cfr.cfr_get_counts(h)["n_slots"]
+                cfr.cfr_set_state(h, init[c0 + j], np.zeros(A), 0, s)
+        tb = cfr.cfr_batch_table_bytes(len(hs))
+        table = torch.empty(tb + 16, dtype=torch.uint8, device="cuda")
+        cfr.cfr_batch_iterate(hs, iters, (table.data_ptr() + 15) & ~15, tb, threads, lanes, s)
+        for h in hs:
+            v = np.empty(cfr.cfr_get_counts(h)["n_slots"])
+            cfr.cfr_avg_strategy(h, v, False, s)
+            out.append(v)
+            cfr.cfr_destroy(h)
+    return out
+
+
+def make_dataset(specs, iters: int = 1000, max_sets_per_game: int = 256, seed: int = 0):
+    """Features and target strategies of (a sample of) every game's sets."""
+    rng = np.random.default_rng(seed)
+    strat = solve_batch(specs, iters)
+    Xs, Ns, Ts = [], [], []
+    for sp, st in zip(specs, strat):
+        X, na = features(sp)
+        T = _pad_slots(sp, st)
+        idx = np.arange(sp.n_infosets)
+        if len(idx) > max_sets_per_game:
+            idx = rng.choice(idx, size=max_sets_per_game, replace=False)
+        Xs.append(X[idx]); Ns.append(na[idx]); Ts.append(T[idx])
+    return np.concatenate(Xs), np.concatenate(Ns), np.concatenate(Ts)
+
+
+def train(X, nact, T, epochs: int = 3, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None) -> MLP:
+    import torch
+
+    net = MLP(F_IN, seed=seed)
+    dev = net.dev
+    Xd = torch.tensor(X, device=dev)
+    Nd = torch.tensor(nact, device=dev)
+    Td = torch.tensor(T, device=dev)
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        perm = torch.tensor(rng.permutation(n), device=dev)
+        tot, cnt = 0.0, 0
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            loss = net.loss_and_grad(Xd[idx].contiguous(), Nd[idx].contiguous(), Td[idx].contiguous())
+            net.adam_step(lr * (0.5 ** ep))
+            tot += loss
+            cnt += 1
+        hist.append(tot / max(cnt, 1))
+        if log:
+            log("epoch %d loss %.4f" % (ep, hist[-1]))
+    net.history = hist
+    return net
+
+
+def warm_regrets(net: MLP, spec, kappa: float) -> np.ndarray:
+    """R0 in spec slot order: kappa * pot * mass(I) * sigma_hat(I, a), i.e.
+    about kappa iterations' worth of regret pointing at the network's
+    strategy (mass(I) = chance probability of reaching I, the scale of one
+    iteration's regret increment at I)."""
+    import torch
+
+    X, na = features(spec)
+    prob = net.predict(torch.tensor(X, device=net.dev), torch.tensor(na, device=net.dev)).cpu().numpy()
+    pc = chance_mass(spec)
+    dec = spec.infoset >= 0
+    mass = np.bincount(spec.infoset[dec], weights=pc[dec], minlength=spec.n_infosets)
+    off = spec.slot_offsets()
+    R0 = np.zeros(int(off[-1]))
+    for a in range(N_OUT):
+        ok = spec.iset_nact > a
+        R0[off[:-1][ok] + a] = prob[ok, a] * mass[ok]
+    return kappa * spec.pot * R0
+
+
+def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iters=5000, threads=1024, lanes=8):
+    """Iterations each game needs to reach target * pot (checked every
+    `check_every`), all games in one batch, and the wall time."""
+    import torch
+
+    s = int(torch.cuda.current_stream().cuda_stream)
+    opts = cfr.make_options(precision=cfr.P32)
+    t0 = time.perf_counter()
+    hs = [cfr.cfr_compile(sp, opts) for sp in specs]
+    sizes = [cfr.cfr_plan(h) for h in hs]
+    pool = serve.DevicePool(sum(n + serve.ALIGN for n in sizes) + serve.ALIGN)
+    for j, (h, n) in enumerate(zip(hs, sizes)):
+        cfr.cfr_bind(h, pool.ptr(pool.alloc(n)), n, s)
+        if init is not None:
+            cfr.cfr_set_state(h, init[j], np.zeros(len(init[j])), 0, s)
+    tb = cfr.cfr_batch_table_bytes(len(hs))
+    table = torch.empty(tb + 16, dtype=torch.uint8, device="cuda")
+    tp = (table.data_ptr() + 15) & ~15
+    done = np.zeros(len(hs), dtype=np.int64)
+    finished = np.zeros(len(hs), dtype=bool)
+    active = list(range(len(hs)))
+    while active:
+        sub = [hs[i] for i in active]
+        cfr.cfr_batch_iterate(sub, check_every, tp, tb, threads, lanes, s)
+        ex = cfr.cfr_batch_exploitability(sub, tp, tb, threads, lanes, s)
+        keep = []
+        for i, row in zip(active, ex):
+            done[i] += check_every
+            if row[0] <= target * specs[i].pot:
+                finished[i] = True
+            elif done[i] < max_iters:
+                keep.append(i)
+        active = keep
+    wall = time.perf_counter() - t0
+    for h in hs:
+        cfr.cfr_destroy(h)
+    return done, finished, wall
+
+
+def endgame_family(seeds, lo: float = 1e3, hi: float = 1e6):
+    """Endgames with edge targets log-uniform in [lo, hi] (seeded per list)."""
+    import gamegen as gg
+
+    rng = np.random.default_rng(int(seeds[0]) if len(seeds) else 0)
+    return [gg.endgame(int(s), int(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for s in seeds]
+
+
+def choose_kappa(net: MLP, specs, kappas=(4.0, 8.0, 16.0), max_iters: int = 3000):
+    """The kappa with the fewest mean iterations to 1e-3 pot on `specs`."""
+    best, best_it, table = None, float("inf"), {}
+    for k in kappas:
+        done, fin, _ = iterations_to_target(specs, init=[warm_regrets(net, sp, k) for sp in specs],
+                                            max_iters=max_iters)
+        table[k] = float(np.mean(done))
+        if table[k] < best_it:
+            best, best_it = k, table[k]
+    return best, table
