@@ -43,6 +43,19 @@ def _rank3(r0, r1, r2):
     return 0, a * 256 + b * 16 + c
 
 
+def _rank3_vec(r0, r1, r2):
+    """Vectorised _rank3: (category, value) arrays."""
+    r = np.sort(np.stack([r0, r1, r2], axis=1), axis=1)[:, ::-1]
+    a, b, c = r[:, 0].astype(np.int64), r[:, 1].astype(np.int64), r[:, 2].astype(np.int64)
+    trips = a == c
+    pair_hi = (a == b) & ~trips
+    pair_lo = (b == c) & ~trips
+    cat = np.where(trips, 2, np.where(pair_hi | pair_lo, 1, 0))
+    val = np.where(trips, 2 * 4096 + a,
+                   np.where(pair_hi, 4096 + a * 64 + c, np.where(pair_lo, 4096 + b * 64 + a, a * 256 + b * 16 + c)))
+    return cat, val
+
+
 def chance_mass(spec, with_deal: bool = False):
     """Chance probability of reaching every node (product along the path);
     with_deal also returns the index of each node's root outcome."""
@@ -83,8 +96,9 @@ def checkdown_value(spec) -> np.ndarray:
     return spec.payoff[cur]
 
 
-def features(spec) -> tuple:
-    """(X [I, F_IN] float32, nact [I] int32) for every information set."""
+def features(spec, return_mass: bool = False) -> tuple:
+    """(X [I, F_IN] float32, nact [I] int32) for every information set
+    (and the sets' chance masses when return_mass)."""
     f = spec.iset_feat
     if f is None:
         raise ValueError("features need the card-game metadata of the generator")
@@ -95,11 +109,10 @@ def features(spec) -> tuple:
     X[rows, f[:, 2]] = 1.0
     has_board = f[:, 3] >= 0
     X[rows[has_board], 32 + f[has_board, 3]] = 1.0
-    for i in range(I):
-        if f[i, 3] >= 0:
-            cat, val = _rank3(f[i, 1] // N_SUITS, f[i, 2] // N_SUITS, f[i, 3] // N_SUITS)
-            X[i, 64 + cat] = 1.0
-            X[i, 67] = val / 8199.0
+    if has_board.any():
+        cat, val = _rank3_vec(f[has_board, 1] // N_SUITS, f[has_board, 2] // N_SUITS, f[has_board, 3] // N_SUITS)
+        X[rows[has_board], 64 + cat] = 1.0
+        X[rows[has_board], 67] = val / 8199.0
     X[rows, 68 + f[:, 0]] = 1.0
     X[rows, 70 + np.clip(f[:, 4], 0, 1)] = 1.0
     X[rows, 72 + np.clip(f[:, 5] - 1, 0, 7)] = 1.0
@@ -133,7 +146,7 @@ def features(spec) -> tuple:
     nact = spec.iset_nact.astype(np.int32)
     if nact.max(initial=0) > N_OUT:
         raise ValueError("information sets with more than %d actions" % N_OUT)
-    return X, nact
+    return (X, nact, mass) if return_mass else (X, nact)
 
 
 def _pad_slots(spec, vec) -> np.ndarray:
@@ -224,11 +237,8 @@ def warm_regrets(net: MLP, spec, kappa: float) -> np.ndarray:
     iteration's regret increment at I)."""
     import torch
 
-    X, na = features(spec)
+    X, na, mass = features(spec, return_mass=True)
     prob = net.predict(torch.tensor(X, device=net.dev), torch.tensor(na, device=net.dev)).cpu().numpy()
-    pc = chance_mass(spec)
-    dec = spec.infoset >= 0
-    mass = np.bincount(spec.infoset[dec], weights=pc[dec], minlength=spec.n_infosets)
     off = spec.slot_offsets()
     R0 = np.zeros(int(off[-1]))
     for a in range(N_OUT):
