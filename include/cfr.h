@@ -230,9 +230,10 @@ int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *s
  * No cudaMalloc, cudaFree or other allocating call is made. The first call on
  * a device resolves the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
- * Limits: games whose scratch exceeds the array (about 524,000 nodes in FP64,
- * 1,048,000 in FP32, less with wide chance nodes) are rejected with
- * CFR_ERR_ARG. Every call re-initialises the part of the array it uses.
+ * Limits: games whose scratch exceeds the array are rejected with
+ * CFR_ERR_ARG; the scratch is both reach lanes of every internal node and
+ * every node's value, at most 24 bytes per node in FP64 and 12 in FP32
+ * (about 524,000 and 1,048,000 nodes for any tree shape). Every call re-initialises the part of the array it uses.
  * All calls share the one array, so calls that overlap on the GPU (other
  * streams, other threads, other handles) race: serialise them. Synchronises
  * `stream`; a barrier timeout returns CFR_ERR_TIMEOUT. */

@@ -52,12 +52,17 @@ __device__ __forceinline__ double cta_sum(double x, double *sm) {
   return r;
 }
 
-// Wide chance node inside one CTA: forward copies the reach to every child.
+// Wide chance node inside one CTA: its internal children copy its reach.
 template <typename T>
-__device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach, int32_t h) {
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
-  const vec2_t<T> r = reach[h];
-  for (int32_t c = cb + threadIdx.x; c < ce; c += blockDim.x) reach[c] = r;
+__device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach, int32_t wi) {
+  const int32_t ir = __ldg(g.wide_irank + wi);
+  const int32_t off = __ldg(g.int_cirank + ir);
+  const int32_t nch = __ldg(g.big_irank + off);
+  const vec2_t<T> r = reach[ir];
+  for (int32_t j = threadIdx.x; j < nch; j += blockDim.x) {
+    const int32_t c = __ldg(g.big_irank + off + 1 + j);
+    if (c >= 0) reach[c] = r;
+  }
 }
 
 // Wide chance node inside one CTA: value = sum of the children's values.
@@ -99,9 +104,9 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
   for (long long it = 0; it < in.n_iter; ++it) {
     for (int d = 0; d < in.D; ++d) {
       const LevelWork w = in.lw[d];
-      for (int32_t h = w.lb + threadIdx.x; h < w.le; h += 4 * THREADS)
-        fwd_node4<T, false>(in.g, st.sigma, st.reach, h, THREADS, w.le);
-      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, __ldg(in.g.wide_list + i));
+      for (int32_t q = w.ib + threadIdx.x; q < w.ie; q += 4 * THREADS)
+        fwd_int4<T, false>(in.g, st.sigma, st.reach, q, THREADS, w.ie);
+      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, i);
       __syncthreads();
     }
     const double wt = (double)(t0 + it + 1);
@@ -138,9 +143,9 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
   __syncthreads();
   for (int d = 0; d < in.D; ++d) {
     const LevelWork w = in.lw[d];
-    for (int32_t h = w.lb + threadIdx.x; h < w.le; h += 4 * THREADS)
-      fwd_node4<double, false>(g, in.sbs, in.reach2, h, THREADS, w.le);
-    for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double>(g, in.reach2, __ldg(g.wide_list + i));
+    for (int32_t q = w.ib + threadIdx.x; q < w.ie; q += 4 * THREADS)
+      fwd_int4<double, false>(g, in.sbs, in.reach2, q, THREADS, w.ie);
+    for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double>(g, in.reach2, i);
     __syncthreads();
   }
   const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
         if (k < m1) {
           const int32_t h = __ldg(g.mem_node + k);
           const int32_t cb = __ldg(g.mem_cb + k);
-          const double2 r = in.reach2[h];
+          const double2 r = in.reach2[__ldg(g.mem_irank + k)];
           const double po = p ? r.x : r.y;
           double oth = 0.0, va = 0.0;
 #pragma unroll

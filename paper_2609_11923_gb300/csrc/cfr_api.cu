@@ -57,6 +57,7 @@ struct cfr_handle {
   // arena layout
   Buf b_child_begin, b_node_slot, b_iset_slot, b_iset_mem, b_mem_node, b_mem_cb, b_chance_list, b_spec_slot, b_levels;
   Buf b_wide_list, b_wide_chunk, b_wide_part, b_wide_cnt;
+  Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_mem_irank, b_wide_irank;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
   size_t plan_bytes = 0;
   char *arena = nullptr;
@@ -96,14 +97,20 @@ static void plan(cfr_handle *h) {
   take(h->b_wide_chunk, 4 * (c.n_wide + 1));
   take(h->b_wide_part, 3 * 8 * (size_t)c.wide_chunk.back());
   take(h->b_wide_cnt, 4 * c.n_wide);
-  take(h->b_reach, 2 * T * c.N);
+  take(h->b_int_slot, 4 * c.n_int);
+  take(h->b_int_mask, 4 * c.n_int);
+  take(h->b_int_cirank, 4 * c.n_int);
+  take(h->b_big_irank, 4 * c.big_irank.size());
+  take(h->b_mem_irank, 4 * c.n_dec);
+  take(h->b_wide_irank, 4 * c.n_wide);
+  take(h->b_reach, 2 * T * std::max<int64_t>(c.n_int, 1));  // internal nodes only
   take(h->b_v, T * c.N);
   take(h->b_sigma, T * (c.A + 1));
   take(h->b_R, 8 * c.A);
   take(h->b_avg, 8 * c.A);
   take(h->b_tmpl, 8 * c.N);
   take(h->b_sbs, 8 * c.A);
-  take(h->b_reach2, 16 * c.N);
+  take(h->b_reach2, 16 * std::max<int64_t>(c.n_int, 1));
   take(h->b_vb, 16 * c.N);
   take(h->b_vavg, 8 * c.N);
   take(h->b_t, 8);
@@ -148,6 +155,8 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   h->levels.resize(c.D);
   for (int64_t d = 0; d < c.D; ++d) {
     LevelWork &w = h->levels[d];
+    w.ib = c.level_int[d];
+    w.ie = c.level_int[d + 1];
     w.lb = c.level_begin[d];
     w.le = c.level_begin[d + 1];
     w.ch0 = c.level_chance[d];
@@ -182,7 +191,9 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
   o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision);
   o->upload_bytes = (int64_t)(h->b_child_begin.bytes + h->b_node_slot.bytes + h->b_iset_slot.bytes + h->b_iset_mem.bytes +
                               h->b_mem_node.bytes + h->b_mem_cb.bytes + h->b_chance_list.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
-                              h->b_wide_list.bytes + h->b_wide_chunk.bytes + h->b_tmpl.bytes);
+                              h->b_wide_list.bytes + h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
+                              h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes +
+                              h->b_mem_irank.bytes + h->b_wide_irank.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
   o->lanes_per_set = h->exec_form == CFR_EXEC_PERSISTENT ? h->persist_lanes : (c.D > 0 ? h->level_lanes[c.D - 1] : 0);
@@ -208,6 +219,12 @@ static GameView game_view(const cfr_handle *h) {
   g.wide_chunk = h->p<int32_t>(h->b_wide_chunk);
   g.wide_part = h->p<double>(h->b_wide_part);
   g.wide_cnt = h->p<unsigned>(h->b_wide_cnt);
+  g.int_slot = h->p<int32_t>(h->b_int_slot);
+  g.int_mask = h->p<uint32_t>(h->b_int_mask);
+  g.int_cirank = h->p<int32_t>(h->b_int_cirank);
+  g.big_irank = h->p<int32_t>(h->b_big_irank);
+  g.mem_irank = h->p<int32_t>(h->b_mem_irank);
+  g.wide_irank = h->p<int32_t>(h->b_wide_irank);
   return g;
 }
 
@@ -309,7 +326,7 @@ static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
   GameView g = game_view(h);
   for (int64_t d = 0; d < c.D; ++d) {
     const LevelWork &w = h->levels[d];
-    const int nb = grid_for(w.le - w.lb, kThreads);
+    const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
     fwd_level_kernel<T><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach),
                                                                    w, nb);
     CK(cudaGetLastError());
@@ -346,7 +363,7 @@ static int launch_persistent_form(cfr_handle *h, int64_t n, cudaStream_t s) {
     // enough blocks for the widest depth, never more than co-resident
     int64_t need = 1;
     for (const LevelWork &w : h->levels) {
-      need = std::max<int64_t>(need, (w.le - w.lb + kThreads - 1) / kThreads);
+      need = std::max<int64_t>(need, (w.ie - w.ib + 4 * kThreads - 1) / (4 * kThreads));
       need = std::max<int64_t>(need, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
       need = std::max<int64_t>(need, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
       need = std::max<int64_t>(need, w.wc1 - w.wc0);
@@ -490,7 +507,7 @@ extern "C" int cfr_exploitability(cfr_handle *h, double *out_expl, double *out_b
   CK(cudaGetLastError());
   for (int64_t d = 0; d < c.D; ++d) {
     const LevelWork &w = h->levels[d];
-    const int nb = grid_for(w.le - w.lb, kThreads);
+    const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
     fwd_level_kernel<double><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<double>(h->b_sbs),
                                                                         h->p<double2>(h->b_reach2), w, nb);
     CK(cudaGetLastError());
@@ -598,6 +615,12 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 10: src = c.tmpl.data(); n = (int64_t)c.tmpl.size(); esz = 8; break;
     case 11: src = c.spec_slot_of.data(); n = (int64_t)c.spec_slot_of.size(); break;
     case 12: src = h->level_lanes.data(); n = (int64_t)h->level_lanes.size(); break;
+    case 13: src = c.int_slot.data(); n = (int64_t)c.int_slot.size(); break;
+    case 14: src = c.int_mask.data(); n = (int64_t)c.int_mask.size(); break;
+    case 15: src = c.int_cirank.data(); n = (int64_t)c.int_cirank.size(); break;
+    case 16: src = c.big_irank.data(); n = (int64_t)c.big_irank.size(); break;
+    case 17: src = c.mem_irank.data(); n = (int64_t)c.mem_irank.size(); break;
+    case 18: src = c.level_int.data(); n = (int64_t)c.level_int.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -622,16 +645,19 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   const Compiled &c = h->c;
   if (d < 0 || d >= c.D) return set_err(CFR_ERR_ARG, "cfr_level_bytes: level out of range");
   const int64_t T = h->precision == CFR_P64 ? 8 : 4;
-  const int64_t n = c.level_begin[d + 1] - c.level_begin[d];
   const int64_t e = c.level_begin[d + 2] - c.level_begin[d + 1];  // children = next level
+  const int64_t nint = c.level_int[d + 1] - c.level_int[d];
+  const int64_t nint_kids = (d + 1 < c.D) ? c.level_int[d + 2] - c.level_int[d + 1] : 0;
   const int64_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
   const int64_t sets = i1 - i0;
   const int64_t slots = c.iset_slot[i1] - c.iset_slot[i0];
   const int64_t dec = c.iset_mem[i1] - c.iset_mem[i0];
   const int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
-  const int64_t nint = dec + nch;
-  *fwd = 8 * n + 2 * T * nint + 2 * T * e + T * slots;
-  *bwd = 8 * sets + (32 + 2 * T) * slots + (8 + 3 * T) * dec + (12 + T) * nch + T * e;
+  int64_t big = 0;  // child lists of nodes with more than 31 children
+  for (int64_t q = c.level_int[d]; q < c.level_int[d + 1]; ++q)
+    if (c.int_mask[q] & kBigNode) big += 1 + c.big_irank[c.int_cirank[q]];
+  *fwd = 12 * nint + 2 * T * nint + 2 * T * nint_kids + T * slots + 4 * big;
+  *bwd = 8 * sets + (32 + 2 * T) * slots + (12 + 3 * T) * dec + (12 + T) * nch + T * e;
   return CFR_OK;
 }
 
@@ -644,7 +670,7 @@ static int profile_t(cfr_handle *h, double *fwd_ms, double *bwd_ms, cudaStream_t
   int rc = CFR_OK;
   for (int64_t d = 0; d < c.D && rc == CFR_OK; ++d) {
     const LevelWork &w = h->levels[d];
-    const int nb = grid_for(w.le - w.lb, kThreads);
+    const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
     CK(cudaEventRecord(ev[2 * d], s));
     fwd_level_kernel<T><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach), w, nb);
     CK(cudaGetLastError());
@@ -731,7 +757,7 @@ __global__ void noalloc_init_kernel(const int32_t *child_begin, const double *tm
 template <typename T>
 static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   const Compiled &c = h->c;
-  size_t off_v = align_up(2 * sizeof(T) * (size_t)c.N);
+  size_t off_v = align_up(2 * sizeof(T) * (size_t)std::max<int64_t>(c.n_int, 1));
   size_t off_part = off_v + align_up(sizeof(T) * (size_t)c.N);
   size_t off_cnt = off_part + align_up(3 * 8 * (size_t)c.wide_chunk.back());
   size_t off_bar = off_cnt + align_up(4 * (size_t)c.n_wide);
@@ -769,7 +795,7 @@ static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   if (h->opt.persistent_ctas > 0) cap = std::min<int64_t>(cap, h->opt.persistent_ctas);
   int64_t want = 1;
   for (const LevelWork &w : h->levels) {
-    want = std::max<int64_t>(want, (w.le - w.lb + kThreads - 1) / kThreads);
+    want = std::max<int64_t>(want, (w.ie - w.ib + 4 * kThreads - 1) / (4 * kThreads));
     want = std::max<int64_t>(want, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
     want = std::max<int64_t>(want, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
     want = std::max<int64_t>(want, w.wc1 - w.wc0);

@@ -227,6 +227,50 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
     c.level_chance[D] = (int32_t)c.chance_list.size();
     c.level_wide[D] = (int32_t)c.wide_list.size();
     c.n_wide = (int64_t)c.wide_list.size();
+    // compact internal-node index space
+    {
+      std::vector<int32_t> rank(N, -1);
+      int32_t r = 0;
+      for (int64_t h = 0; h < N; ++h)
+        if (c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;
+      c.level_int.assign(D + 1, 0);
+      for (int64_t h = 0; h < N; ++h)  // internal nodes sit at depths < D
+        if (rank[h] >= 0 && depth[h] < D) c.level_int[depth[h] + 1]++;
+      for (int64_t d = 0; d < D; ++d) c.level_int[d + 1] += c.level_int[d];
+      c.int_slot.resize(r);
+      c.int_mask.resize(r);
+      c.int_cirank.resize(r);
+      c.big_irank.clear();
+      for (int64_t h = 0; h < N; ++h) {
+        const int32_t q = rank[h];
+        if (q < 0) continue;
+        const int32_t cb = c.child_begin[h], ce = c.child_begin[h + 1];
+        const int32_t nch = ce - cb;
+        c.int_slot[q] = c.node_slot[h];
+        if (nch <= 31) {
+          uint32_t mask = 0;
+          int32_t first = 0;
+          bool got = false;
+          for (int32_t a = 0; a < nch; ++a)
+            if (rank[cb + a] >= 0) {
+              mask |= 1u << a;
+              if (!got) { first = rank[cb + a]; got = true; }
+            }
+          c.int_mask[q] = mask;
+          c.int_cirank[q] = first;
+        } else {
+          c.int_mask[q] = kBigNode;
+          c.int_cirank[q] = (int32_t)c.big_irank.size();
+          c.big_irank.push_back(nch);
+          for (int32_t a = 0; a < nch; ++a) c.big_irank.push_back(rank[cb + a]);
+        }
+      }
+      c.mem_irank.resize(c.n_dec);
+      for (int64_t k = 0; k < c.n_dec; ++k) c.mem_irank[k] = rank[c.mem_node[k]];
+      c.wide_irank.resize(c.n_wide);
+      for (int64_t w = 0; w < c.n_wide; ++w) c.wide_irank[w] = rank[c.wide_list[w]];
+      if ((int64_t)c.big_irank.size() >= (int64_t(1) << 31)) return fail(err, "too many children of large nodes");
+    }
     // per-depth member statistics (used to size the per-set lane groups)
     c.level_max_members.assign(D, 0);
     c.level_mean_members.assign(D, 0.0);
@@ -248,17 +292,18 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
 }
 
 int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
-  // Forward (levels 0..D-1): every node's child range + slot word (8 B), each
-  // internal node's two reach lanes, each child's two reach lanes written,
-  // the strategy vector read once. Backward: per set its slot and member
-  // offsets (8 B); per slot R and the average read+written (FP64) and the
-  // strategy read+written; per member its id, first child, reach lanes and
-  // its value written; per chance node its id, child range and value; every
-  // edge's child value read once.
+  // Forward: every internal node's record (slot word, child mask, first
+  // internal child: 12 B) and its two reach lanes read, every internal
+  // child's reach lanes written, the strategy read once. Backward: per set
+  // its slot and member offsets (8 B); per slot R and the average read and
+  // written (FP64) and the strategy read and written; per member its node id,
+  // first child and internal rank (12 B), its reach lanes and its value
+  // written; per chance node its id, child range and value; every edge's
+  // child value read once.
   const int64_t T = precision == CFR_P64 ? 8 : 4;
-  const int64_t n_upper = c.D > 0 ? c.level_begin[c.D] : 0;
-  return 8 * n_upper + 2 * T * c.n_int + 3 * T * c.E + 8 * c.I + (32 + 3 * T) * c.A +
-         (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance;
+  const int64_t int_kids = c.n_int > 0 ? c.n_int - 1 : 0;  // every internal node but the root
+  return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 8 * c.I +
+         (32 + 3 * T) * c.A + (12 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
 }
 
 }  // namespace cfr

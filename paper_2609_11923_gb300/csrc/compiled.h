@@ -20,6 +20,7 @@ constexpr int kMaxActions = 64;
 // handled by chunks of kWideChunk children instead of one thread.
 constexpr int kWide = 1024;
 constexpr int kWideChunk = 2048;
+constexpr uint32_t kBigNode = 0x80000000u;  // int_mask flag: children listed in big_irank
 
 struct Compiled {
   int64_t N = 0, E = 0, I = 0, A = 0, D = 0;
@@ -42,6 +43,23 @@ struct Compiled {
   std::vector<int32_t> level_wide;   // [D+1]
   std::vector<int32_t> wide_chunk;   // [n_wide+1] prefix of chunk counts (kWideChunk children each)
   int64_t n_wide = 0;
+  // Compact index space of the internal nodes (reach lives only there:
+  // terminal reach is never read). Internal node h has rank int_rank(h) =
+  // number of internal nodes before it; the internal nodes of depth d are
+  // ranks level_int[d] .. level_int[d+1]-1. Per internal node (rank order):
+  //   int_slot  = node_slot (set's first slot | player-2 bit, or -1 for chance)
+  //   int_mask  = bit a set if child a is internal (nodes with <= 31 children),
+  //               or kBigNode for nodes with more children
+  //   int_cirank= rank of the first internal child (mask nodes), or the offset
+  //               of [nch, rank of child 0, rank of child 1, ...] in big_irank
+  //               (-1 for terminal children)
+  std::vector<int32_t> level_int;    // [D+1]
+  std::vector<int32_t> int_slot;     // [n_int]
+  std::vector<uint32_t> int_mask;    // [n_int]
+  std::vector<int32_t> int_cirank;   // [n_int]
+  std::vector<int32_t> big_irank;    // [...]
+  std::vector<int32_t> mem_irank;    // [n_dec] internal rank of each member
+  std::vector<int32_t> wide_irank;   // [n_wide] internal rank of each wide node
   std::vector<double> pc;            // [N] chance product root..h (retained for set_payoffs)
   std::vector<double> tmpl;          // [N] pi_c(z) * u(z) at terminals, else 0 (eq. (template))
   std::vector<int32_t> new_of_spec;  // [N] compiled id of each spec node

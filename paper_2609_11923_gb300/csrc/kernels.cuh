@@ -58,7 +58,16 @@ struct GameView {
   const int32_t *__restrict__ wide_chunk;  // prefix of their chunk counts
   double *wide_part;                       // [3 * chunks] partial sums
   unsigned *wide_cnt;                      // [wide nodes] chunks finished (reset by the last one)
+  // compact index space of the internal nodes (reach is stored only there)
+  const int32_t *__restrict__ int_slot;    // slot word of each internal node
+  const uint32_t *__restrict__ int_mask;   // internal children (bit a), or kBigBit
+  const int32_t *__restrict__ int_cirank;  // rank of the first internal child, or big_irank offset
+  const int32_t *__restrict__ big_irank;   // [nch, child ranks...] of nodes with > 31 children
+  const int32_t *__restrict__ mem_irank;   // internal rank of each member (member order)
+  const int32_t *__restrict__ wide_irank;  // internal rank of each wide node
 };
+
+constexpr uint32_t kBigBit = 0x80000000u;
 
 template <typename T> struct StateView {
   vec2_t<T> *reach;
@@ -70,6 +79,7 @@ template <typename T> struct StateView {
 };
 
 struct LevelWork {
+  int32_t ib, ie;         // internal ranks of depth d
   int32_t lb, le;         // nodes of depth d
   int32_t ch0, ch1;       // chance_list range of depth d (narrow chance nodes)
   int32_t is0, is2, is1;  // sets of depth d: player 1 [is0, is2), player 2 [is2, is1)
@@ -103,75 +113,85 @@ __device__ __forceinline__ double block_sum(double x) {
 }
 
 // ------------------------------------------------------------ forward reach
+// reach of child a of an internal node with slot word s and reach r
 template <typename T, bool PERSIST>
-__device__ __forceinline__ void fwd_write(const T *sigma, vec2_t<T> *reach, int32_t cb, int32_t ce, int32_t s,
-                                          vec2_t<T> r) {
-  if (s < 0) {
-    for (int32_t c = cb; c < ce; ++c) reach[c] = r;
+__device__ __forceinline__ vec2_t<T> child_reach(const T *sigma, int32_t s, vec2_t<T> r, int a) {
+  if (s >= 0) {
+    const T sa = ldm<PERSIST>(sigma + (s & kMask) + a);
+    if (s & kP2Bit) r.y = r.y * sa;
+    else r.x = r.x * sa;
+  }
+  return r;
+}
+
+// Writes the reach of the internal children of one internal node: children
+// flagged in the mask get consecutive internal ranks from cir on; nodes with
+// more than 31 children list their children's ranks in big_irank (terminal
+// children -1, never written: nothing reads a terminal's reach).
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void fwd_write(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t s,
+                                          uint32_t mask, int32_t cir, vec2_t<T> r) {
+  if (mask & kBigBit) {
+    const int32_t nch = __ldg(g.big_irank + cir);
+    if (nch > kWideNode) return;  // wide: done by chunks
+    for (int32_t a = 0; a < nch; ++a) {
+      const int32_t q = __ldg(g.big_irank + cir + 1 + a);
+      if (q >= 0) reach[q] = child_reach<T, PERSIST>(sigma, s, r, a);
+    }
   } else {
-    const int32_t base = (s & kMask) - cb;
-    if (s & kP2Bit) {
-      for (int32_t c = cb; c < ce; ++c) {
-        vec2_t<T> o = r;
-        o.y = r.y * ldm<PERSIST>(sigma + base + c);
-        reach[c] = o;
-      }
-    } else {
-      for (int32_t c = cb; c < ce; ++c) {
-        vec2_t<T> o = r;
-        o.x = r.x * ldm<PERSIST>(sigma + base + c);
-        reach[c] = o;
-      }
+    int32_t q = cir;
+    while (mask) {
+      const int a = __ffs(mask) - 1;
+      mask &= mask - 1;
+      reach[q++] = child_reach<T, PERSIST>(sigma, s, r, a);
     }
   }
 }
 
+// Four internal nodes q, q+stride, q+2 stride, q+3 stride per thread: their
+// records and reach are read together (coalesced), then their children's
+// reach is written.
 template <typename T, bool PERSIST>
-__device__ __forceinline__ void fwd_node(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t h) {
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
-  const int32_t s = __ldg(g.node_slot + h);
-  if (cb == ce || ce - cb > kWideNode) return;  // terminal, or wide (done by chunks)
-  fwd_write<T, PERSIST>(sigma, reach, cb, ce, s, ldm<PERSIST>(reach + h));
-}
-
-// Four nodes h, h+stride, h+2 stride, h+3 stride per thread: their loads are
-// issued together, so each thread keeps four dependent chains in flight.
-template <typename T, bool PERSIST>
-__device__ __forceinline__ void fwd_node4(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t h,
-                                          int32_t stride, int32_t le) {
-  int32_t cb[4], ce[4], sl[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int32_t x = h + u * stride;
-    cb[u] = 0; ce[u] = 0; sl[u] = -1;
-    if (x < le) {
-      cb[u] = __ldg(g.child_begin + x);
-      ce[u] = __ldg(g.child_begin + x + 1);
-      sl[u] = __ldg(g.node_slot + x);
-    }
-  }
+__device__ __forceinline__ void fwd_int4(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t q,
+                                         int32_t stride, int32_t qe) {
+  int32_t sl[4], ci[4];
+  uint32_t mk[4];
   vec2_t<T> r[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if (cb[u] != ce[u] && ce[u] - cb[u] <= kWideNode) r[u] = ldm<PERSIST>(reach + h + u * stride);
+  for (int u = 0; u < 4; ++u) {
+    const int32_t x = q + u * stride;
+    mk[u] = 0u; sl[u] = -1; ci[u] = 0;
+    r[u].x = T(0); r[u].y = T(0);
+    if (x < qe) {
+      sl[u] = __ldg(g.int_slot + x);
+      mk[u] = __ldg(g.int_mask + x);
+      ci[u] = __ldg(g.int_cirank + x);
+      r[u] = ldm<PERSIST>(reach + x);
+    }
+  }
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    if (cb[u] != ce[u] && ce[u] - cb[u] <= kWideNode) fwd_write<T, PERSIST>(sigma, reach, cb[u], ce[u], sl[u], r[u]);
+    if (mk[u]) fwd_write<T, PERSIST>(g, sigma, reach, sl[u], mk[u], ci[u], r[u]);
 }
 
-// One chunk of a wide chance node: its children copy the node's reach.
+// One chunk of a wide chance node: its internal children copy its reach.
 template <typename T, bool PERSIST>
 __device__ __forceinline__ void fwd_wide_chunk(const GameView &g, const LevelWork &w, vec2_t<T> *reach, int32_t q) {
   const int32_t wi = wide_of_chunk(g, w, q);
-  const int32_t h = __ldg(g.wide_list + wi);
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
-  const int32_t c0 = cb + (q - __ldg(g.wide_chunk + wi)) * kWideChunkK;
-  const int32_t c1 = min(ce, c0 + kWideChunkK);
-  const vec2_t<T> r = ldm<PERSIST>(reach + h);
-  for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) reach[c] = r;
+  const int32_t ir = __ldg(g.wide_irank + wi);
+  const int32_t off = __ldg(g.int_cirank + ir);
+  const int32_t nch = __ldg(g.big_irank + off);
+  const int32_t j0 = (q - __ldg(g.wide_chunk + wi)) * kWideChunkK;
+  const int32_t j1 = min(nch, j0 + kWideChunkK);
+  const vec2_t<T> r = ldm<PERSIST>(reach + ir);
+  for (int32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const int32_t c = __ldg(g.big_irank + off + 1 + j);
+    if (c >= 0) reach[c] = r;
+  }
 }
 
-// Grid: nb_nodes blocks over the nodes of depth d, then one block per wide chunk.
+// Grid: nb_nodes blocks over the internal nodes of depth d, then one block
+// per wide chunk.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T *sigma, vec2_t<T> *reach,
                                                             LevelWork w, int nb_nodes) {
@@ -180,8 +200,8 @@ __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T
     return;
   }
   const int32_t stride = nb_nodes * blockDim.x;
-  for (int32_t h = w.lb + blockIdx.x * blockDim.x + threadIdx.x; h < w.le; h += 4 * stride)
-    fwd_node4<T, false>(g, sigma, reach, h, stride, w.le);
+  for (int32_t q = w.ib + blockIdx.x * blockDim.x + threadIdx.x; q < w.ie; q += 4 * stride)
+    fwd_int4<T, false>(g, sigma, reach, q, stride, w.ie);
 }
 
 // ------------------------------------------------------------ group helpers
@@ -257,7 +277,7 @@ __device__ __forceinline__ void member_terms(const GameView &g, const StateView<
   if (k >= m1) return;
   const int32_t h = __ldg(g.mem_node + k);
   const int32_t cb = __ldg(g.mem_cb + k);  // member order: a coalesced read
-  const vec2_t<T> r = ldm<PERSIST>(st.reach + h);
+  const vec2_t<T> r = ldm<PERSIST>(st.reach + __ldg(g.mem_irank + k));
   T vc[MAXA];
   T vh = T(0);
 #pragma unroll
@@ -509,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
   for (long long it = 0; it < a.n_iter; ++it) {
     for (int d = 0; d < a.D; ++d) {
       const LevelWork w = a.lw[d];
-      for (int32_t h = w.lb + tid; h < w.le; h += 4 * nthr) fwd_node4<T, true>(a.g, a.st.sigma, a.st.reach, h, nthr, w.le);
+      for (int32_t q = w.ib + tid; q < w.ie; q += 4 * nthr) fwd_int4<T, true>(a.g, a.st.sigma, a.st.reach, q, nthr, w.ie);
       for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
       if (!grid_sync(a.bar)) return;
     }
@@ -682,8 +702,8 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
       for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
       if (k < m1) {
         const int32_t h = __ldg(g.mem_node + k);
-        const int32_t cb = __ldg(g.child_begin + h);
-        const double2 r = reach2[h];
+        const int32_t cb = __ldg(g.mem_cb + k);
+        const double2 r = reach2[__ldg(g.mem_irank + k)];
         const double po = p ? r.x : r.y;
         double oth = 0.0, va = 0.0;
 #pragma unroll
@@ -712,7 +732,7 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
     // best agrees across the group without another shuffle
     for (int32_t k = m0 + lane; k < m1; k += LANES) {
       const int32_t h = __ldg(g.mem_node + k);
-      const int32_t cb = __ldg(g.child_begin + h);
+      const int32_t cb = __ldg(g.mem_cb + k);
       reinterpret_cast<double *>(vb + h)[p] = reinterpret_cast<const double *>(vb + cb + best)[p];
     }
   }

@@ -83,7 +83,34 @@ def flatten(g):
             pc[new[c]] = pc[h] * g.chance_prob[q_] if kinds[h] == CHANCE else pc[h]
         if kinds[h] == TERMINAL:
             tmpl[h] = pc[h] * g.payoff[v]
+    # compact space of internal nodes (reach lives only there)
+    internal = nch > 0
+    rank = np.full(N, -1, dtype=np.int64)
+    rank[internal] = np.arange(int(internal.sum()))
+    level_int = np.array([int(internal[:level_begin[d]].sum()) for d in range(D + 1)], dtype=np.int32)
+    int_slot, int_mask, int_cirank, big = [], [], [], []
+    for h in np.nonzero(internal)[0]:
+        cb, ce = child_begin[h], child_begin[h + 1]
+        kids = rank[cb:ce]
+        int_slot.append(node_slot[h])
+        if ce - cb <= 31:
+            m = 0
+            for a, r in enumerate(kids):
+                if r >= 0:
+                    m |= 1 << a
+            int_mask.append(m)
+            firsts = [r for r in kids if r >= 0]
+            int_cirank.append(firsts[0] if firsts else 0)
+        else:
+            int_mask.append(1 << 31)
+            int_cirank.append(len(big))
+            big.append(ce - cb)
+            big.extend(int(r) for r in kids)
+    mem_irank = rank[mem_node] if len(mem_node) else np.zeros(0, np.int64)
     return {
+        "int_slot": np.array(int_slot, dtype=np.int32), "int_mask": np.array(int_mask, dtype=np.uint32).view(np.int32),
+        "int_cirank": np.array(int_cirank, dtype=np.int32), "big_irank": np.array(big, dtype=np.int32),
+        "mem_irank": mem_irank.astype(np.int32), "level_int": level_int,
         "child_begin": child_begin, "node_slot": node_slot, "level_begin": level_begin,
         "iset_slot": iset_slot, "iset_mem": iset_mem, "mem_node": mem_node,
         "chance_list": np.array(chance_list, dtype=np.int32), "level_chance": np.array(level_chance, dtype=np.int32),

@@ -40,7 +40,7 @@ def test_noalloc_matches_persistent_form_on_consecutive_calls(name, make, precis
 
 
 def test_noalloc_rejects_games_beyond_its_static_scratch():
-    g = gg.random_tree(1, depth=13)  # about a million nodes: beyond the FP64 limit
+    g = gg.random_tree(1, depth=14)  # about 2.5 million nodes: beyond the FP64 limit
     s = cfr.Solver(g, precision=cfr.P64, exec_form=cfr.EXEC_PERSISTENT)
     with pytest.raises(cfr.CfrError) as ei:
         cfr.cfr_iterate_noalloc(s.h, 1, s._s())
