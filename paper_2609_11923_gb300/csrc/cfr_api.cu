@@ -291,6 +291,12 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_levels, h->levels.data(), sizeof(LevelWork) * c.D))) return rc;
   if ((rc = up(h->b_wide_list, c.wide_list.data(), 4 * c.n_wide))) return rc;
   if ((rc = up(h->b_wide_chunk, c.wide_chunk.data(), 4 * (c.n_wide + 1)))) return rc;
+  if ((rc = up(h->b_int_slot, c.int_slot.data(), 4 * c.n_int))) return rc;
+  if ((rc = up(h->b_int_mask, c.int_mask.data(), 4 * c.n_int))) return rc;
+  if ((rc = up(h->b_int_cirank, c.int_cirank.data(), 4 * c.n_int))) return rc;
+  if ((rc = up(h->b_big_irank, c.big_irank.data(), 4 * c.big_irank.size()))) return rc;
+  if ((rc = up(h->b_mem_irank, c.mem_irank.data(), 4 * c.n_dec))) return rc;
+  if ((rc = up(h->b_wide_irank, c.wide_irank.data(), 4 * c.n_wide))) return rc;
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
   CK(cudaMemsetAsync(h->arena + h->b_bar.off, 0, 16, s));
   CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
