@@ -83,7 +83,9 @@ typedef struct cfr_options {
    * barrier between depth levels; CFR_EXEC_AUTO picks by game size. */
   int exec_form;
   int rule;            /* CFR_RULE_CFR_PLUS (clamp) or CFR_RULE_CFR (no clamp) */
-  int lanes_per_set;   /* 0 = by mean set size (see cfr_autotune); else 1, 2, 4, 8, 16 or 32 lanes per set */
+  int lanes_per_set;   /* 0 = by mean set size (see cfr_autotune); else 1, 2, 4, 8, 16 or 32 lanes per set,
+                          or 256 = one thread block per set in the per-level kernels (sets of at most 8
+                          actions; the persistent kernel then uses 32) */
   int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
   int64_t barrier_spin_limit; /* 0 = default; polls before a grid barrier reports CFR_ERR_TIMEOUT */
 } cfr_options;
@@ -162,17 +164,28 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
 
 /* Host copies of the compiled index arrays, for bit-exact checks.
  * which: 0 child_begin[N+1], 1 node_slot[N], 2 level_begin[D+2],
- * 3 iset_slot[I+1], 4 iset_mem[I+1], 5 mem_node[N_dec], 6 chance_list,
- * 7 level_chance[D+1], 8 level_iset[2D+1] (per level: player-1 sets then
- * player-2 sets), 9 new id of each spec node [N], 10 template values [N]
- * (doubles), 11 spec slot of each compiled slot [A].
+ * 3 iset_slot[I+1], 4 iset_mem[I+1], 5 mem_node[N_dec], 6 chance_list
+ * (chance nodes with at most 1024 children), 7 level_chance[D+1],
+ * 8 level_iset[2D+1] (per level: player-1 sets then player-2 sets), 9 new id
+ * of each spec node [N], 10 template values [N] (doubles, node order),
+ * 11 spec slot of each compiled slot [A], 12 lanes per set of each depth (a
+ * runtime choice), 13 int_slot, 14 int_mask (bit pattern), 15 int_cirank
+ * [N_int each: the internal-node records], 16 big_irank, 17 mem_irank
+ * [N_dec], 18 level_int[D+1], 19 vslot[N] (value slot of each node; the
+ * root's is N-1), 20 iset_vb[I] (first slot of the block holding set I's
+ * members' children), 21 mem_vs[N_dec] (value slot of each member),
+ * 22 ch_vb, 23 ch_nch, 24 ch_vs (per chance node of list 6: first child
+ * slot, child count, own slot), 25 wide_vb, 26 wide_nch, 27 wide_vs (the
+ * same for chance nodes with more than 1024 children), 28 template values
+ * in value-slot order [N] (doubles).
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);
 
 /* Autotuner for the thread-to-work mapping: for every depth it times the
  * backward launch with each supported number of lanes per information set
- * (1, 2, 4, 8, 16, 32; `reps` launches each) and keeps the fastest; in the
+ * (1, 2, 4, 8, 16, 32, and 256 = one block per set when sets have at most 8
+ * actions; `reps` launches each) and keeps the fastest; in the
  * persistent form it also times whole persistent iterations per lane count.
  * Trial launches overwrite the solver state, so the call ends by resetting it
  * (as cfr_reset) and dropping a captured graph. The chosen counts are

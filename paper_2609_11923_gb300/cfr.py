@@ -30,7 +30,8 @@ DEBUG_BARRIER_MISSING_ARRIVALS = 1
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
           "spec_slot_of": 11, "level_lanes": 12, "int_slot": 13, "int_mask": 14, "int_cirank": 15,
-          "big_irank": 16, "mem_irank": 17, "level_int": 18}
+          "big_irank": 16, "mem_irank": 17, "level_int": 18, "vslot": 19, "iset_vb": 20, "mem_vs": 21,
+          "ch_vb": 22, "ch_nch": 23, "ch_vs": 24, "wide_vb": 25, "wide_nch": 26, "wide_vs": 27, "tmpl_vs": 28}
 
 
 class CfrError(RuntimeError):
@@ -248,7 +249,7 @@ def cfr_export_array(h: int, name: str) -> np.ndarray:
     which = EXPORT[name]
     n = ctypes.c_int64()
     _check(_lib.cfr_export_array(h, which, None, 0, ctypes.byref(n)))
-    out = np.empty(n.value, dtype=np.float64 if name == "tmpl" else np.int32)
+    out = np.empty(n.value, dtype=np.float64 if name in ("tmpl", "tmpl_vs") else np.int32)
     _check(_lib.cfr_export_array(h, which, out.ctypes.data if n.value else None, n.value, ctypes.byref(n)))
     return out
 

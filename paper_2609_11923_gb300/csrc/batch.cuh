@@ -34,7 +34,7 @@ struct InstDesc {
   int32_t D;
   int32_t rule;
   int32_t n_sets;
-  int32_t pad;
+  int32_t root_vs;  // the root's value slot (N - 1)
 };
 
 template <int THREADS>
@@ -65,11 +65,12 @@ __device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach
   }
 }
 
-// Wide chance node inside one CTA: value = sum of the children's values.
+// Wide chance node wi inside one CTA: value = sum of the children's values.
 // P64 sums left to right (thread 0); P32 uses the fixed-shape CTA tree.
 template <typename T, int THREADS>
-__device__ __forceinline__ void cta_bwd_wide(const GameView &g, T *v, int32_t h, double *sm) {
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+__device__ __forceinline__ void cta_bwd_wide(const GameView &g, T *v, int32_t wi, double *sm) {
+  const int32_t h = __ldg(g.wide_vs + wi);
+  const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   if constexpr (sizeof(T) == 8) {
     if (threadIdx.x == 0) {
       T s = T(0);
@@ -104,8 +105,10 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
   for (long long it = 0; it < in.n_iter; ++it) {
     for (int d = 0; d < in.D; ++d) {
       const LevelWork w = in.lw[d];
-      for (int32_t q = w.ib + threadIdx.x; q < w.ie; q += 4 * THREADS)
-        fwd_int4<T, false>(in.g, st.sigma, st.reach, q, THREADS, w.ie);
+      for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
+        if (w.fan) fwd_int4<T, false, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
+        else fwd_int4<T, false, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
+      }
       for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, i);
       __syncthreads();
     }
@@ -113,8 +116,8 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
     for (int d = in.D - 1; d >= 0; --d) {
       const LevelWork w = in.lw[d];
       for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS)
-        bwd_chance<T, false>(in.g, st.v, __ldg(in.g.chance_list + i));
-      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS>(in.g, st.v, __ldg(in.g.wide_list + i), sm);
+        bwd_chance<T, false>(in.g, st.v, i);
+      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS>(in.g, st.v, i, sm);
       for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
         bwd_set<T, MAXA, LANES, false>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule);
       __syncthreads();
@@ -143,8 +146,10 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
   __syncthreads();
   for (int d = 0; d < in.D; ++d) {
     const LevelWork w = in.lw[d];
-    for (int32_t q = w.ib + threadIdx.x; q < w.ie; q += 4 * THREADS)
-      fwd_int4<double, false>(g, in.sbs, in.reach2, q, THREADS, w.ie);
+    for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
+      if (w.fan) fwd_int4<double, false, true>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
+      else fwd_int4<double, false, false>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
+    }
     for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double>(g, in.reach2, i);
     __syncthreads();
   }
@@ -154,16 +159,16 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
   for (int d = in.D - 1; d >= 0; --d) {
     const LevelWork w = in.lw[d];
     for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS) {
-      const int32_t h = __ldg(g.chance_list + i);
-      const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+      const int32_t h = __ldg(g.ch_vs + i);
+      const int32_t cb = __ldg(g.ch_vb + i), ce = cb + __ldg(g.ch_nch + i);
       double sx = 0.0, sy = 0.0, sa = 0.0;
       for (int32_t c = cb; c < ce; ++c) { const double2 x = in.vb[c]; sx += x.x; sy += x.y; sa += in.vavg[c]; }
       in.vb[h] = make_double2(sx, sy);
       in.vavg[h] = sa;
     }
     for (int32_t i = w.wd0; i < w.wd1; ++i) {
-      const int32_t h = __ldg(g.wide_list + i);
-      const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+      const int32_t h = __ldg(g.wide_vs + i);
+      const int32_t cb = __ldg(g.wide_vb + i), ce = cb + __ldg(g.wide_nch + i);
       double sx = 0.0, sy = 0.0, sa = 0.0;
       for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) { const double2 x = in.vb[c]; sx += x.x; sy += x.y; sa += in.vavg[c]; }
       sx = cta_sum<THREADS>(sx, sm);
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
       const int p = I >= w.is2 ? 1 : 0;
       const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
       const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+      const int32_t vb0 = __ldg(g.iset_vb + I);
       double sg[MAXA], Q[MAXA];
 #pragma unroll
       for (int a = 0; a < MAXA; ++a) { sg[a] = a < na ? in.sbs[sb + a] : 0.0; Q[a] = 0.0; }
@@ -184,8 +190,8 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
 #pragma unroll
         for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
         if (k < m1) {
-          const int32_t h = __ldg(g.mem_node + k);
-          const int32_t cb = __ldg(g.mem_cb + k);
+          const int32_t h = __ldg(g.mem_vs + k);
+          const int32_t cb = vb0 + (k - m0) * na;
           const double2 r = in.reach2[__ldg(g.mem_irank + k)];
           const double po = p ? r.x : r.y;
           double oth = 0.0, va = 0.0;
@@ -212,19 +218,19 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
       for (int a = 1; a < na; ++a)
         if (p == 0 ? Q[a] > Q[best] : Q[a] < Q[best]) best = a;
       for (int32_t k = m0 + lane; k < m1; k += LANES) {
-        const int32_t h = __ldg(g.mem_node + k);
-        const int32_t cb = __ldg(g.mem_cb + k);
+        const int32_t h = __ldg(g.mem_vs + k);
+        const int32_t cb = vb0 + (k - m0) * na;
         reinterpret_cast<double *>(in.vb + h)[p] = reinterpret_cast<const double *>(in.vb + cb + best)[p];
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double2 root = in.vb[0];
+    const double2 root = in.vb[in.root_vs];
     in.out[0] = 0.5 * (root.x - root.y);
     in.out[1] = root.x;
     in.out[2] = root.y;
-    in.out[3] = in.vavg[0];
+    in.out[3] = in.vavg[in.root_vs];
   }
 }
 

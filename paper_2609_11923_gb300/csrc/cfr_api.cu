@@ -55,8 +55,8 @@ struct cfr_handle {
   int persist_lanes = 8;
   std::vector<LevelWork> levels;
   // arena layout
-  Buf b_child_begin, b_node_slot, b_iset_slot, b_iset_mem, b_mem_node, b_mem_cb, b_chance_list, b_spec_slot, b_levels;
-  Buf b_wide_list, b_wide_chunk, b_wide_part, b_wide_cnt;
+  Buf b_iset_slot, b_iset_mem, b_iset_vb, b_mem_vs, b_ch_vb, b_ch_nch, b_ch_vs, b_spec_slot, b_levels;
+  Buf b_wide_vb, b_wide_nch, b_wide_vs, b_wide_chunk, b_wide_part, b_wide_cnt;
   Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_mem_irank, b_wide_irank;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
   size_t plan_bytes = 0;
@@ -84,16 +84,19 @@ static void plan(cfr_handle *h) {
     b.bytes = bytes;
     cur = align_up(cur + std::max<size_t>(bytes, 1));
   };
-  take(h->b_child_begin, 4 * (c.N + 1));
-  take(h->b_node_slot, 4 * c.N);
+  const size_t n_narrow = c.ch_vb.size();
   take(h->b_iset_slot, 4 * (c.I + 1));
   take(h->b_iset_mem, 4 * (c.I + 1));
-  take(h->b_mem_node, 4 * c.n_dec);
-  take(h->b_mem_cb, 4 * c.n_dec);
-  take(h->b_chance_list, 4 * c.n_chance);
+  take(h->b_iset_vb, 4 * c.I);
+  take(h->b_mem_vs, 4 * c.n_dec);
+  take(h->b_ch_vb, 4 * n_narrow);
+  take(h->b_ch_nch, 4 * n_narrow);
+  take(h->b_ch_vs, 4 * n_narrow);
   take(h->b_spec_slot, 4 * c.A);
   take(h->b_levels, sizeof(LevelWork) * std::max<int64_t>(c.D, 1));
-  take(h->b_wide_list, 4 * c.n_wide);
+  take(h->b_wide_vb, 4 * c.n_wide);
+  take(h->b_wide_nch, 4 * c.n_wide);
+  take(h->b_wide_vs, 4 * c.n_wide);
   take(h->b_wide_chunk, 4 * (c.n_wide + 1));
   take(h->b_wide_part, 3 * 8 * (size_t)c.wide_chunk.back());
   take(h->b_wide_cnt, 4 * c.n_wide);
@@ -104,11 +107,11 @@ static void plan(cfr_handle *h) {
   take(h->b_mem_irank, 4 * c.n_dec);
   take(h->b_wide_irank, 4 * c.n_wide);
   take(h->b_reach, 2 * T * std::max<int64_t>(c.n_int, 1));  // internal nodes only
-  take(h->b_v, T * c.N);
+  take(h->b_v, T * c.N);  // value slots
   take(h->b_sigma, T * (c.A + 1));
   take(h->b_R, 8 * c.A);
   take(h->b_avg, 8 * c.A);
-  take(h->b_tmpl, 8 * c.N);
+  take(h->b_tmpl, 8 * c.N);  // template in slot order
   take(h->b_sbs, 8 * c.A);
   take(h->b_reach2, 16 * std::max<int64_t>(c.n_int, 1));
   take(h->b_vb, 16 * c.N);
@@ -132,12 +135,12 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (h->opt.exec_form < 0 || h->opt.exec_form > 3) { delete h; return set_err(CFR_ERR_ARG, "bad exec_form"); }
   if (h->opt.rule != CFR_RULE_CFR_PLUS && h->opt.rule != CFR_RULE_CFR) { delete h; return set_err(CFR_ERR_ARG, "bad rule"); }
   const int lp = h->opt.lanes_per_set;
-  if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16 or 32"); }
+  if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32 or 256"); }
   std::string err;
   int rc = compile_game(*spec, h->c, err);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
-  if (lp != 0 && lp < 4 && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1 or 2 needs sets of at most 8 actions"); }
+  if (lp != 0 && (lp < 4 || lp == kThreads) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2 or 256 needs sets of at most 8 actions"); }
   h->precision = h->opt.precision;
   h->rule = h->opt.rule;
   h->maxa_tier = c.max_act <= 4 ? 4 : (c.max_act <= 8 ? 8 : 64);
@@ -151,7 +154,8 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
     h->level_lanes[d] = lp ? lp : pick(c.level_mean_members[d]);
     tot_mem += c.level_mean_members[d] * (c.level_iset[2 * d + 2] - c.level_iset[2 * d]);
   }
-  h->persist_lanes = lp ? lp : pick(c.I > 0 ? tot_mem / (double)c.I : 1.0);
+  // the persistent kernel runs lane groups of at most a warp
+  h->persist_lanes = lp ? std::min(lp, 32) : pick(c.I > 0 ? tot_mem / (double)c.I : 1.0);
   h->levels.resize(c.D);
   for (int64_t d = 0; d < c.D; ++d) {
     LevelWork &w = h->levels[d];
@@ -168,7 +172,11 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
     w.wd1 = c.level_wide[d + 1];
     w.wc0 = c.wide_chunk[w.wd0];
     w.wc1 = c.wide_chunk[w.wd1];
-    w.pad = 0;
+    w.fan = 0;  // a chance node of this depth has its children written warp-wide
+    for (int64_t q = c.level_int[d]; q < c.level_int[d + 1] && !w.fan; ++q) {
+      const uint32_t m = c.int_mask[q];
+      if (c.int_slot[q] < 0 && m != 0u && ((m & kBigNode) || __builtin_popcount(m) > kFanLight)) w.fan = 1;
+    }
   }
   plan(h);
   *out = h;
@@ -189,9 +197,10 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
   o->n_internal = c.n_int; o->n_decision = c.n_dec; o->n_chance = c.n_chance; o->n_terminal = c.n_term;
   o->depth_blocks = c.D; o->max_actions = c.max_act;
   o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision);
-  o->upload_bytes = (int64_t)(h->b_child_begin.bytes + h->b_node_slot.bytes + h->b_iset_slot.bytes + h->b_iset_mem.bytes +
-                              h->b_mem_node.bytes + h->b_mem_cb.bytes + h->b_chance_list.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
-                              h->b_wide_list.bytes + h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
+  o->upload_bytes = (int64_t)(h->b_iset_slot.bytes + h->b_iset_mem.bytes + h->b_iset_vb.bytes + h->b_mem_vs.bytes +
+                              h->b_ch_vb.bytes + h->b_ch_nch.bytes + h->b_ch_vs.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
+                              h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes +
+                              h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
                               h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes +
                               h->b_mem_irank.bytes + h->b_wide_irank.bytes);
   o->iteration = h->iteration_host;
@@ -208,14 +217,16 @@ extern "C" int cfr_plan(const cfr_handle *h, size_t *bytes) {
 
 static GameView game_view(const cfr_handle *h) {
   GameView g;
-  g.child_begin = h->p<int32_t>(h->b_child_begin);
-  g.node_slot = h->p<int32_t>(h->b_node_slot);
   g.iset_slot = h->p<int32_t>(h->b_iset_slot);
   g.iset_mem = h->p<int32_t>(h->b_iset_mem);
-  g.mem_node = h->p<int32_t>(h->b_mem_node);
-  g.mem_cb = h->p<int32_t>(h->b_mem_cb);
-  g.chance_list = h->p<int32_t>(h->b_chance_list);
-  g.wide_list = h->p<int32_t>(h->b_wide_list);
+  g.iset_vb = h->p<int32_t>(h->b_iset_vb);
+  g.mem_vs = h->p<int32_t>(h->b_mem_vs);
+  g.ch_vb = h->p<int32_t>(h->b_ch_vb);
+  g.ch_nch = h->p<int32_t>(h->b_ch_nch);
+  g.ch_vs = h->p<int32_t>(h->b_ch_vs);
+  g.wide_vb = h->p<int32_t>(h->b_wide_vb);
+  g.wide_nch = h->p<int32_t>(h->b_wide_nch);
+  g.wide_vs = h->p<int32_t>(h->b_wide_vs);
   g.wide_chunk = h->p<int32_t>(h->b_wide_chunk);
   g.wide_part = h->p<double>(h->b_wide_part);
   g.wide_cnt = h->p<unsigned>(h->b_wide_cnt);
@@ -244,6 +255,18 @@ static int grid_for(int64_t work, int per_block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+// Forward launch of one depth: nb blocks over the internal nodes, then one
+// block per wide chunk; depths with many-child chance nodes take the form
+// that writes those children warp-wide.
+template <typename T>
+static int launch_fwd(const LevelWork &w, cudaStream_t s, const GameView &g, const T *sigma, vec2_t<T> *reach) {
+  const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
+  if (w.fan) fwd_level_kernel<T, true><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, sigma, reach, w, nb);
+  else fwd_level_kernel<T, false><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, sigma, reach, w, nb);
+  CK(cudaGetLastError());
+  return CFR_OK;
+}
+
 template <typename T>
 static int init_state(cfr_handle *h, cudaStream_t s) {
   const Compiled &c = h->c;
@@ -259,10 +282,9 @@ static int init_state(cfr_handle *h, cudaStream_t s) {
 template <typename T>
 static int init_values(cfr_handle *h, cudaStream_t s) {
   const Compiled &c = h->c;
-  CK(cudaMemcpyAsync(h->p<double>(h->b_tmpl), c.tmpl.data(), 8 * c.N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->p<double>(h->b_tmpl), c.tmpl_vs.data(), 8 * c.N, cudaMemcpyHostToDevice, s));
   init_values_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
-      h->p<int32_t>(h->b_child_begin), h->p<double>(h->b_tmpl), (int32_t)c.N, h->p<T>(h->b_v),
-      h->p<double2>(h->b_vb), h->p<double>(h->b_vavg));
+      h->p<double>(h->b_tmpl), (int32_t)c.N, h->p<T>(h->b_v), h->p<double2>(h->b_vb), h->p<double>(h->b_vavg));
   CK(cudaGetLastError());
   return CFR_OK;
 }
@@ -280,16 +302,18 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
     return CFR_OK;
   };
   int rc;
-  if ((rc = up(h->b_child_begin, c.child_begin.data(), 4 * (c.N + 1)))) return rc;
-  if ((rc = up(h->b_node_slot, c.node_slot.data(), 4 * c.N))) return rc;
   if ((rc = up(h->b_iset_slot, c.iset_slot.data(), 4 * (c.I + 1)))) return rc;
   if ((rc = up(h->b_iset_mem, c.iset_mem.data(), 4 * (c.I + 1)))) return rc;
-  if ((rc = up(h->b_mem_node, c.mem_node.data(), 4 * c.n_dec))) return rc;
-  if ((rc = up(h->b_mem_cb, c.mem_cb.data(), 4 * c.n_dec))) return rc;
-  if ((rc = up(h->b_chance_list, c.chance_list.data(), 4 * c.n_chance))) return rc;
+  if ((rc = up(h->b_iset_vb, c.iset_vb.data(), 4 * c.I))) return rc;
+  if ((rc = up(h->b_mem_vs, c.mem_vs.data(), 4 * c.n_dec))) return rc;
+  if ((rc = up(h->b_ch_vb, c.ch_vb.data(), 4 * c.ch_vb.size()))) return rc;
+  if ((rc = up(h->b_ch_nch, c.ch_nch.data(), 4 * c.ch_nch.size()))) return rc;
+  if ((rc = up(h->b_ch_vs, c.ch_vs.data(), 4 * c.ch_vs.size()))) return rc;
   if ((rc = up(h->b_spec_slot, c.spec_slot_of.data(), 4 * c.A))) return rc;
   if ((rc = up(h->b_levels, h->levels.data(), sizeof(LevelWork) * c.D))) return rc;
-  if ((rc = up(h->b_wide_list, c.wide_list.data(), 4 * c.n_wide))) return rc;
+  if ((rc = up(h->b_wide_vb, c.wide_vb.data(), 4 * c.n_wide))) return rc;
+  if ((rc = up(h->b_wide_nch, c.wide_nch.data(), 4 * c.n_wide))) return rc;
+  if ((rc = up(h->b_wide_vs, c.wide_vs.data(), 4 * c.n_wide))) return rc;
   if ((rc = up(h->b_wide_chunk, c.wide_chunk.data(), 4 * (c.n_wide + 1)))) return rc;
   if ((rc = up(h->b_int_slot, c.int_slot.data(), 4 * c.n_int))) return rc;
   if ((rc = up(h->b_int_mask, c.int_mask.data(), 4 * c.n_int))) return rc;
@@ -331,11 +355,8 @@ static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
   const Compiled &c = h->c;
   GameView g = game_view(h);
   for (int64_t d = 0; d < c.D; ++d) {
-    const LevelWork &w = h->levels[d];
-    const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
-    fwd_level_kernel<T><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach),
-                                                                   w, nb);
-    CK(cudaGetLastError());
+    int rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
+    if (rc) return rc;
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
     int rc = launch_bwd<T>(h, (int)d, s);
@@ -491,7 +512,7 @@ extern "C" int cfr_current_strategy(cfr_handle *h, double *out, int on_device, v
 
 static int launch_br(cfr_handle *h, int d, cudaStream_t s) {
   const LevelWork &w = h->levels[d];
-  const int L = h->level_lanes[d];
+  const int L = std::min(h->level_lanes[d], 32);  // best response: lane groups of at most a warp
   const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
   const int nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
   const int nb_is = nis > 0 ? grid_for(nis, kThreads / L) : 0;
@@ -512,19 +533,17 @@ extern "C" int cfr_exploitability(cfr_handle *h, double *out_expl, double *out_b
                                                                        h->p<double>(h->b_avg), h->p<double>(h->b_sbs));
   CK(cudaGetLastError());
   for (int64_t d = 0; d < c.D; ++d) {
-    const LevelWork &w = h->levels[d];
-    const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
-    fwd_level_kernel<double><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<double>(h->b_sbs),
-                                                                        h->p<double2>(h->b_reach2), w, nb);
-    CK(cudaGetLastError());
+    int rc = launch_fwd<double>(h->levels[d], s, g, h->p<double>(h->b_sbs), h->p<double2>(h->b_reach2));
+    if (rc) return rc;
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
     int rc = launch_br(h, (int)d, s);
     if (rc) return rc;
   }
   double root[3];
-  CK(cudaMemcpyAsync(root, h->p<double2>(h->b_vb), 16, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(root + 2, h->p<double>(h->b_vavg), 8, cudaMemcpyDeviceToHost, s));
+  const int64_t rs = c.N - 1;  // the root's value slot
+  CK(cudaMemcpyAsync(root, h->p<double2>(h->b_vb) + rs, 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(root + 2, h->p<double>(h->b_vavg) + rs, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *out_expl = 0.5 * (root[0] - root[1]);
   if (out_br) { out_br[0] = root[0]; out_br[1] = root[1]; out_br[2] = root[2]; }
@@ -550,6 +569,7 @@ extern "C" int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream
       const double u = payoff[c.spec_of_new[x]];
       if (!std::isfinite(u)) return set_err(CFR_ERR_ARG, "cfr_set_payoffs: non-finite payoff");
       c.tmpl[x] = c.pc[x] * u;
+      c.tmpl_vs[c.vslot[x]] = c.tmpl[x];
     }
   cudaStream_t s = (cudaStream_t)stream;
   int rc = h->precision == CFR_P64 ? init_values<double>(h, s) : init_values<float>(h, s);
@@ -627,6 +647,16 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 16: src = c.big_irank.data(); n = (int64_t)c.big_irank.size(); break;
     case 17: src = c.mem_irank.data(); n = (int64_t)c.mem_irank.size(); break;
     case 18: src = c.level_int.data(); n = (int64_t)c.level_int.size(); break;
+    case 19: src = c.vslot.data(); n = (int64_t)c.vslot.size(); break;
+    case 20: src = c.iset_vb.data(); n = (int64_t)c.iset_vb.size(); break;
+    case 21: src = c.mem_vs.data(); n = (int64_t)c.mem_vs.size(); break;
+    case 22: src = c.ch_vb.data(); n = (int64_t)c.ch_vb.size(); break;
+    case 23: src = c.ch_nch.data(); n = (int64_t)c.ch_nch.size(); break;
+    case 24: src = c.ch_vs.data(); n = (int64_t)c.ch_vs.size(); break;
+    case 25: src = c.wide_vb.data(); n = (int64_t)c.wide_vb.size(); break;
+    case 26: src = c.wide_nch.data(); n = (int64_t)c.wide_nch.size(); break;
+    case 27: src = c.wide_vs.data(); n = (int64_t)c.wide_vs.size(); break;
+    case 28: src = c.tmpl_vs.data(); n = (int64_t)c.tmpl_vs.size(); esz = 8; break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -663,7 +693,7 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   for (int64_t q = c.level_int[d]; q < c.level_int[d + 1]; ++q)
     if (c.int_mask[q] & kBigNode) big += 1 + c.big_irank[c.int_cirank[q]];
   *fwd = 12 * nint + 2 * T * nint + 2 * T * nint_kids + T * slots + 4 * big;
-  *bwd = 8 * sets + (32 + 2 * T) * slots + (12 + 3 * T) * dec + (12 + T) * nch + T * e;
+  *bwd = 12 * sets + (32 + 2 * T) * slots + (8 + 3 * T) * dec + (12 + T) * nch + T * e;
   return CFR_OK;
 }
 
@@ -675,11 +705,8 @@ static int profile_t(cfr_handle *h, double *fwd_ms, double *bwd_ms, cudaStream_t
   GameView g = game_view(h);
   int rc = CFR_OK;
   for (int64_t d = 0; d < c.D && rc == CFR_OK; ++d) {
-    const LevelWork &w = h->levels[d];
-    const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
     CK(cudaEventRecord(ev[2 * d], s));
-    fwd_level_kernel<T><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach), w, nb);
-    CK(cudaGetLastError());
+    rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
     CK(cudaEventRecord(ev[2 * d + 1], s));
   }
   for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
@@ -742,15 +769,14 @@ static int noalloc_scratch(void **out) {
   return CFR_OK;
 }
 
-// Every call starts from a clean scratch: terminal values from the template,
+// Every call starts from a clean scratch: value slots from the template,
 // root reach (1, 1), wide-node tickets and barrier words at zero.
 template <typename T>
-__global__ void noalloc_init_kernel(const int32_t *child_begin, const double *tmpl, int32_t N, T *v,
-                                    vec2_t<T> *reach, unsigned *wide_cnt, int32_t n_wide, unsigned *bar) {
+__global__ void noalloc_init_kernel(const double *tmpl_vs, int32_t N, T *v, vec2_t<T> *reach, unsigned *wide_cnt,
+                                    int32_t n_wide, unsigned *bar) {
   const int32_t stride = gridDim.x * blockDim.x;
   const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int32_t h = tid; h < N; h += stride)
-    if (child_begin[h] == child_begin[h + 1]) v[h] = (T)tmpl[h];
+  for (int32_t h = tid; h < N; h += stride) v[h] = (T)tmpl_vs[h];
   for (int32_t i = tid; i < n_wide; i += stride) wide_cnt[i] = 0u;
   if (tid == 0) {
     vec2_t<T> one;
@@ -809,7 +835,7 @@ static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
   a.bar.expected = (unsigned)grid;
   noalloc_init_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
-      h->p<int32_t>(h->b_child_begin), h->p<double>(h->b_tmpl), (int32_t)c.N, a.st.v, a.st.reach, a.g.wide_cnt,
+      h->p<double>(h->b_tmpl), (int32_t)c.N, a.st.v, a.st.reach, a.g.wide_cnt,
       (int32_t)c.n_wide, bar);
   CK(cudaGetLastError());
   CK(launch_persistent<T>(h->maxa_tier, L, grid, s, a, nullptr));
@@ -843,7 +869,9 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   const Compiled &c = h->c;
   if (c.D == 0) return CFR_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<int> cand = h->maxa_tier <= 8 ? std::vector<int>{1, 2, 4, 8, 16, 32} : std::vector<int>{4, 8, 16, 32};
+  // per-level candidates (kThreads = one set per block); the persistent kernel takes groups of at most a warp
+  std::vector<int> cand = h->maxa_tier <= 8 ? std::vector<int>{1, 2, 4, 8, 16, 32, kThreads} : std::vector<int>{4, 8, 16, 32};
+  std::vector<int> cand_p = h->maxa_tier <= 8 ? std::vector<int>{1, 2, 4, 8, 16, 32} : std::vector<int>{4, 8, 16, 32};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -873,7 +901,7 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   if (rc == CFR_OK && h->exec_form == CFR_EXEC_PERSISTENT) {
     int best = h->persist_lanes;
     float best_ms = 1e30f;
-    for (int L : cand) {
+    for (int L : cand_p) {
       h->persist_lanes = L;
       h->persist_grid = 0;
       rc = h->precision == CFR_P64 ? launch_persistent_form<double>(h, 1, s) : launch_persistent_form<float>(h, 1, s);
@@ -939,6 +967,7 @@ static int batch_table(cfr_handle *const *hs, int n, const int64_t *iters, int64
     d.D = (int32_t)h->c.D;
     d.rule = h->rule;
     d.n_sets = (int32_t)h->c.I;
+    d.root_vs = (int32_t)(h->c.N - 1);
   }
   return CFR_OK;
 }

@@ -271,6 +271,50 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
       for (int64_t w = 0; w < c.n_wide; ++w) c.wide_irank[w] = rank[c.wide_list[w]];
       if ((int64_t)c.big_irank.size() >= (int64_t(1) << 31)) return fail(err, "too many children of large nodes");
     }
+    // value slots (see Compiled::vslot)
+    {
+      c.vslot.assign(N, -1);
+      c.iset_vb.assign(c.I, 0);
+      int64_t next = 0;
+      for (int64_t d = 0; d < D; ++d) {
+        for (int32_t q = c.level_iset[2 * d]; q < c.level_iset[2 * d + 2]; ++q) {
+          c.iset_vb[q] = (int32_t)next;
+          for (int32_t k = c.iset_mem[q]; k < c.iset_mem[q + 1]; ++k) {
+            const int32_t h = c.mem_node[k];
+            for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
+          }
+        }
+        for (int64_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h) {
+          if (s.kind[c.spec_of_new[h]] != CFR_CHANCE) continue;
+          for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
+        }
+      }
+      if (next != N - 1) return fail(err, "internal error: value slots do not cover the tree");
+      c.vslot[0] = (int32_t)(N - 1);
+      c.mem_vs.resize(c.n_dec);
+      for (int64_t k = 0; k < c.n_dec; ++k) c.mem_vs[k] = c.vslot[c.mem_node[k]];
+      const size_t nn = c.chance_list.size();
+      c.ch_vb.resize(nn);
+      c.ch_nch.resize(nn);
+      c.ch_vs.resize(nn);
+      for (size_t i = 0; i < nn; ++i) {
+        const int32_t h = c.chance_list[i];
+        c.ch_vb[i] = c.vslot[c.child_begin[h]];
+        c.ch_nch[i] = c.child_begin[h + 1] - c.child_begin[h];
+        c.ch_vs[i] = c.vslot[h];
+      }
+      c.wide_vb.resize(c.n_wide);
+      c.wide_nch.resize(c.n_wide);
+      c.wide_vs.resize(c.n_wide);
+      for (int64_t i = 0; i < c.n_wide; ++i) {
+        const int32_t h = c.wide_list[i];
+        c.wide_vb[i] = c.vslot[c.child_begin[h]];
+        c.wide_nch[i] = c.child_begin[h + 1] - c.child_begin[h];
+        c.wide_vs[i] = c.vslot[h];
+      }
+      c.tmpl_vs.assign(N, 0.0);
+      for (int64_t h = 0; h < N; ++h) c.tmpl_vs[c.vslot[h]] = c.tmpl[h];
+    }
     // per-depth member statistics (used to size the per-set lane groups)
     c.level_max_members.assign(D, 0);
     c.level_mean_members.assign(D, 0.0);
@@ -295,15 +339,15 @@ int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
   // Forward: every internal node's record (slot word, child mask, first
   // internal child: 12 B) and its two reach lanes read, every internal
   // child's reach lanes written, the strategy read once. Backward: per set
-  // its slot and member offsets (8 B); per slot R and the average read and
-  // written (FP64) and the strategy read and written; per member its node id,
-  // first child and internal rank (12 B), its reach lanes and its value
-  // written; per chance node its id, child range and value; every edge's
-  // child value read once.
+  // its slot, member and value-block offsets (12 B); per slot R and the
+  // average read and written (FP64) and the strategy read and written; per
+  // member its value slot and internal rank (8 B), its reach lanes read and
+  // its value written; per chance node its block, child count and value slot
+  // (12 B) and its value written; every edge's child value read once.
   const int64_t T = precision == CFR_P64 ? 8 : 4;
   const int64_t int_kids = c.n_int > 0 ? c.n_int - 1 : 0;  // every internal node but the root
-  return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 8 * c.I +
-         (32 + 3 * T) * c.A + (12 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
+  return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 12 * c.I +
+         (32 + 3 * T) * c.A + (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
 }
 
 }  // namespace cfr

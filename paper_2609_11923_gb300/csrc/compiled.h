@@ -60,6 +60,20 @@ struct Compiled {
   std::vector<int32_t> big_irank;    // [...]
   std::vector<int32_t> mem_irank;    // [n_dec] internal rank of each member
   std::vector<int32_t> wide_irank;   // [n_wide] internal rank of each wide node
+  // Value slots. The value of node h lives in slot vslot[h] of the value
+  // array (not at h): the children of the members of one information set
+  // fill one block of slots (members in member order, each member's children
+  // in action order), the children of one chance node another. Blocks go by
+  // parent depth; within a depth the sets' blocks (set order) come before the
+  // chance nodes' (node order). The root takes the last slot, N-1. A set's
+  // backward pass therefore reads its members' children as one contiguous
+  // run; each node writes its own value to the one slot its parent reads.
+  std::vector<int32_t> vslot;        // [N]
+  std::vector<int32_t> iset_vb;      // [I] first slot of set I's block
+  std::vector<int32_t> mem_vs;       // [n_dec] own value slot of each member (member order)
+  std::vector<int32_t> ch_vb, ch_nch, ch_vs;        // [narrow chance nodes] block, children, own slot
+  std::vector<int32_t> wide_vb, wide_nch, wide_vs;  // [n_wide] the same for wide chance nodes
+  std::vector<double> tmpl_vs;       // [N] the values template in slot order
   std::vector<double> pc;            // [N] chance product root..h (retained for set_payoffs)
   std::vector<double> tmpl;          // [N] pi_c(z) * u(z) at terminals, else 0 (eq. (template))
   std::vector<int32_t> new_of_spec;  // [N] compiled id of each spec node

@@ -1,17 +1,21 @@
 // kernels.cuh — sm_103a kernels of one CFR+ iteration over the compiled game.
 //
-// Stage (a), forward reach (eq. (opfwd) on both lanes, eq. (lanes)): one
-//   thread per node of depth d writes both reach lanes of its children. The
-//   acting player's lane is multiplied by sigma(I, a); the other lane and
-//   chance edges copy through (the paper's sentinel multiplier 1 becomes a
-//   branch on the node's slot word, uniform over the node's children).
-// Stage (b), terminal utility: the value array holds pi_c(z) u(z) at every
-//   terminal from bind time on (eq. (template)); no kernel writes it again,
-//   which removes the per-iteration template copy.
+// Stage (a), forward reach (eq. (opfwd) on both lanes, eq. (lanes)): reach
+//   is stored for internal nodes only (terminal reach is never read), by
+//   internal rank; each thread takes four internal nodes of depth d and
+//   writes both reach lanes of their internal children. The acting player's
+//   lane is multiplied by sigma(I, a); the other lane and chance edges copy
+//   through (the paper's sentinel multiplier 1 becomes a branch on the node's
+//   slot word, uniform over the node's children).
+// Stage (b), terminal utility: the value array holds pi_c(z) u(z) in every
+//   terminal's value slot from bind time on (eq. (template)); no kernel
+//   writes it again, which removes the per-iteration template copy.
 // Stages (c) + (d), backward (eqs. (opbwd), (instregret), (regret), (rm)):
-//   per depth, chance nodes sum their children's values (one thread each) and
-//   every information set of that depth is handled by one group of LANES
-//   lanes: members' values v(h) = sum_a sigma(I,a) v(h.a), the regret terms
+//   values live in value slots: the children of one set's members form one
+//   contiguous block, and every node writes its own value into its parent's
+//   block. Per depth, chance nodes sum their children's values (one thread
+//   each) and every information set of that depth is handled by one group of
+//   LANES lanes: members' values v(h) = sum_a sigma(I,a) v(h.a), the regret terms
 //   s * pi_{-i}(h) * (v(h.a) - v(h)) and the average terms pi_i(h) sigma(I,a)
 //   are summed over members in a fixed order (no atomics), then
 //   R <- max(R + r, 0) (CFR+), avg += t * m, and sigma^{t+1}(I,.) = RM(R) is
@@ -47,14 +51,19 @@ constexpr int32_t kWideNode = 1024;   // chance nodes above this fan-out go by c
 constexpr int32_t kWideChunkK = 2048; // children per chunk of a wide node
 
 struct GameView {
-  const int32_t *__restrict__ child_begin;
-  const int32_t *__restrict__ node_slot;
   const int32_t *__restrict__ iset_slot;
   const int32_t *__restrict__ iset_mem;
-  const int32_t *__restrict__ mem_node;
-  const int32_t *__restrict__ mem_cb;      // first child of each member (member order)
-  const int32_t *__restrict__ chance_list;
-  const int32_t *__restrict__ wide_list;   // wide chance nodes
+  // value slots: a set's members' children form one block starting at
+  // iset_vb[I] (member-major, action-minor); every node writes its own value
+  // to the slot its parent reads (mem_vs, ch_vs, wide_vs)
+  const int32_t *__restrict__ iset_vb;
+  const int32_t *__restrict__ mem_vs;
+  const int32_t *__restrict__ ch_vb;       // narrow chance nodes: children's block,
+  const int32_t *__restrict__ ch_nch;      //   child count,
+  const int32_t *__restrict__ ch_vs;       //   own value slot
+  const int32_t *__restrict__ wide_vb;     // wide chance nodes: the same
+  const int32_t *__restrict__ wide_nch;
+  const int32_t *__restrict__ wide_vs;
   const int32_t *__restrict__ wide_chunk;  // prefix of their chunk counts
   double *wide_part;                       // [3 * chunks] partial sums
   unsigned *wide_cnt;                      // [wide nodes] chunks finished (reset by the last one)
@@ -81,11 +90,11 @@ template <typename T> struct StateView {
 struct LevelWork {
   int32_t ib, ie;         // internal ranks of depth d
   int32_t lb, le;         // nodes of depth d
-  int32_t ch0, ch1;       // chance_list range of depth d (narrow chance nodes)
+  int32_t ch0, ch1;       // narrow chance nodes of depth d (ch_* arrays)
   int32_t is0, is2, is1;  // sets of depth d: player 1 [is0, is2), player 2 [is2, is1)
-  int32_t wd0, wd1;       // wide_list range of depth d
+  int32_t wd0, wd1;       // wide chance nodes of depth d (wide_* arrays)
   int32_t wc0, wc1;       // their chunks
-  int32_t pad;
+  int32_t fan;            // 1 if a chance node of depth d has more than kFanLight internal children
 };
 
 // The wide node owning chunk q (binary search over the level's prefix).
@@ -148,10 +157,16 @@ __device__ __forceinline__ void fwd_write(const GameView &g, const T *sigma, vec
   }
 }
 
+constexpr int kFanLight = 4;  // chance nodes with more internal children are written by the whole warp
+
 // Four internal nodes q, q+stride, q+2 stride, q+3 stride per thread: their
 // records and reach are read together (coalesced), then their children's
-// reach is written.
-template <typename T, bool PERSIST>
+// reach is written. A chance node's internal children all copy its reach, so
+// a chance node with many of them (a card dealt mid-game) is written by the
+// whole warp as one coalesced run instead of by its own thread alone. All 32
+// lanes of the warp call this together (q = warp base + lane; a lane whose
+// nodes lie past qe still takes part in the warp-wide writes).
+template <typename T, bool PERSIST, bool FAN>
 __device__ __forceinline__ void fwd_int4(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t q,
                                          int32_t stride, int32_t qe) {
   int32_t sl[4], ci[4];
@@ -169,9 +184,51 @@ __device__ __forceinline__ void fwd_int4(const GameView &g, const T *sigma, vec2
       r[u] = ldm<PERSIST>(reach + x);
     }
   }
+  if constexpr (!FAN) {  // depths without chance nodes of many internal children
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if (mk[u]) fwd_write<T, PERSIST>(g, sigma, reach, sl[u], mk[u], ci[u], r[u]);
+    for (int u = 0; u < 4; ++u)
+      if (mk[u]) fwd_write<T, PERSIST>(g, sigma, reach, sl[u], mk[u], ci[u], r[u]);
+    return;
+  }
+  bool hvy[4], any = false;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    hvy[u] = sl[u] < 0 && mk[u] != 0u && ((mk[u] & kBigBit) || __popc(mk[u]) > kFanLight);
+    any = any || hvy[u];
+  }
+  if (!__any_sync(0xffffffffu, any)) {  // the common case: every node of the warp is light
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (mk[u]) fwd_write<T, PERSIST>(g, sigma, reach, sl[u], mk[u], ci[u], r[u]);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const bool heavy = hvy[u];
+    unsigned hv = __ballot_sync(0xffffffffu, heavy);
+    if (mk[u] && !heavy) fwd_write<T, PERSIST>(g, sigma, reach, sl[u], mk[u], ci[u], r[u]);
+    while (hv) {
+      const int j = __ffs(hv) - 1;
+      hv &= hv - 1;
+      const uint32_t m = __shfl_sync(0xffffffffu, mk[u], j);
+      const int32_t c0 = __shfl_sync(0xffffffffu, ci[u], j);
+      vec2_t<T> rr;
+      rr.x = __shfl_sync(0xffffffffu, r[u].x, j);
+      rr.y = __shfl_sync(0xffffffffu, r[u].y, j);
+      if (m & kBigBit) {
+        const int32_t nch = __ldg(g.big_irank + c0);
+        if (nch <= kWideNode)  // wide nodes go by chunks
+          for (int32_t a = lane; a < nch; a += 32) {
+            const int32_t c = __ldg(g.big_irank + c0 + 1 + a);
+            if (c >= 0) reach[c] = rr;
+          }
+      } else {
+        const int n = __popc(m);
+        for (int i = lane; i < n; i += 32) reach[c0 + i] = rr;
+      }
+    }
+  }
 }
 
 // One chunk of a wide chance node: its internal children copy its reach.
@@ -192,7 +249,7 @@ __device__ __forceinline__ void fwd_wide_chunk(const GameView &g, const LevelWor
 
 // Grid: nb_nodes blocks over the internal nodes of depth d, then one block
 // per wide chunk.
-template <typename T>
+template <typename T, bool FAN>
 __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T *sigma, vec2_t<T> *reach,
                                                             LevelWork w, int nb_nodes) {
   if ((int)blockIdx.x >= nb_nodes) {
@@ -200,8 +257,9 @@ __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T
     return;
   }
   const int32_t stride = nb_nodes * blockDim.x;
-  for (int32_t q = w.ib + blockIdx.x * blockDim.x + threadIdx.x; q < w.ie; q += 4 * stride)
-    fwd_int4<T, false>(g, sigma, reach, q, stride, w.ie);
+  const int lane = threadIdx.x & 31;
+  for (int32_t qw = w.ib + blockIdx.x * blockDim.x + (threadIdx.x & ~31); qw < w.ie; qw += 4 * stride)
+    fwd_int4<T, false, FAN>(g, sigma, reach, qw + lane, stride, w.ie);
 }
 
 // ------------------------------------------------------------ group helpers
@@ -219,12 +277,13 @@ __device__ __forceinline__ X group_sum_butterfly(X x, unsigned mask) {
 }
 
 // ------------------------------------------------------------- backward
+// Narrow chance node i: the sum of its children's values (left to right).
 template <typename T, bool PERSIST>
-__device__ __forceinline__ void bwd_chance(const GameView &g, T *v, int32_t h) {
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+__device__ __forceinline__ void bwd_chance(const GameView &g, T *v, int32_t i) {
+  const int32_t cb = __ldg(g.ch_vb + i), ce = cb + __ldg(g.ch_nch + i);
   T s = T(0);
   for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
-  v[h] = s;
+  v[__ldg(g.ch_vs + i)] = s;
 }
 
 // One chunk of a wide chance node's value sum. P32: every chunk block sums
@@ -235,8 +294,8 @@ __device__ __forceinline__ void bwd_chance(const GameView &g, T *v, int32_t h) {
 template <typename T, bool PERSIST>
 __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWork &w, T *v, int32_t q) {
   const int32_t wi = wide_of_chunk(g, w, q);
-  const int32_t h = __ldg(g.wide_list + wi);
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const int32_t h = __ldg(g.wide_vs + wi);  // the node's own value slot
+  const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   const int32_t q0 = __ldg(g.wide_chunk + wi), nq = __ldg(g.wide_chunk + wi + 1) - q0;
   if constexpr (sizeof(T) == 8) {
     if (q == q0 && threadIdx.x == 0) {
@@ -257,26 +316,31 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
       s_ticket = atomicAdd(g.wide_cnt + wi, 1u);
     }
     __syncthreads();
-    if (s_ticket == (unsigned)(nq - 1) && threadIdx.x == 0) {
+    if (s_ticket == (unsigned)(nq - 1)) {  // the last chunk's block adds the partials (fixed shape)
       __threadfence();
-      double tot = 0.0;
-      for (int32_t k = 0; k < nq; ++k) tot += __ldcg(g.wide_part + q0 + k);
-      v[h] = (T)tot;
-      g.wide_cnt[wi] = 0u;
+      double y = 0.0;
+      for (int32_t k = threadIdx.x; k < nq; k += blockDim.x) y += __ldcg(g.wide_part + q0 + k);
+      y = block_sum(y);
+      if (threadIdx.x == 0) {
+        v[h] = (T)y;
+        g.wide_cnt[wi] = 0u;
+      }
     }
   }
 }
 
-// Loads and per-member terms of one member (k < m1), or zeros.
+// Loads and per-member terms of one member (k < m1), or zeros. The member's
+// children are slots vb + (k - m0) * na .. + na - 1 of the set's block: the
+// group's lanes read consecutive members' children as one run.
 template <typename T, int MAXA, bool PERSIST>
-__device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m1,
-                                             int32_t na, bool p2, const T (&sig)[MAXA], T (&d)[MAXA],
-                                             T (&mm)[MAXA]) {
+__device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
+                                             int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
+                                             T (&d)[MAXA], T (&mm)[MAXA]) {
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
   if (k >= m1) return;
-  const int32_t h = __ldg(g.mem_node + k);
-  const int32_t cb = __ldg(g.mem_cb + k);  // member order: a coalesced read
+  const int32_t h = __ldg(g.mem_vs + k);   // own value slot (member order: a coalesced read)
+  const int32_t cb = vb + (k - m0) * na;
   const vec2_t<T> r = ldm<PERSIST>(st.reach + __ldg(g.mem_irank + k));
   T vc[MAXA];
   T vh = T(0);
@@ -334,6 +398,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   const int32_t sb = __ldg(g.iset_slot + I);
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+  const int32_t vb = __ldg(g.iset_vb + I);
   T sig[MAXA], racc[MAXA], macc[MAXA];
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) {
@@ -346,8 +411,8 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   if constexpr (TWO) {
     for (; k0 + LANES < m1; k0 += 2 * LANES) {
       T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m1, na, p2, sig, d0, mm0);
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m1, na, p2, sig, d1, mm1);
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d0, mm0);
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, d1, mm1);
       accumulate_chunk<T, MAXA, LANES>(LANES, na, mask, d0, mm0, racc, macc);
       const int32_t c1 = (m1 - k0 - LANES) < LANES ? (m1 - k0 - LANES) : LANES;
       accumulate_chunk<T, MAXA, LANES>(c1, na, mask, d1, mm1, racc, macc);
@@ -355,7 +420,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   }
   for (; k0 < m1; k0 += LANES) {
     T d[MAXA], mm[MAXA];
-    member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m1, na, p2, sig, d, mm);
+    member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d, mm);
     const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
     accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
   }
@@ -424,8 +489,107 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   }
 }
 
+// One information set per block, for depths with few sets of hundreds of
+// members each: all kThreads threads load members tid, tid + kThreads, ...
+// at once. P64: each chunk's member terms are staged in shared memory and
+// thread a adds column a in ascending member order, the order the group form
+// uses, so the result is bitwise the same; P32: per-thread partial sums
+// finished by a fixed-shape tree. The slot update runs one thread per action.
+template <typename T, int MAXA>
+__device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
+                                              double wt, int rule) {
+  __shared__ T s_d[kThreads * MAXA], s_m[kThreads * MAXA];  // [member][action]
+  __shared__ double s_pos[MAXA];
+  const int tid = threadIdx.x;
+  const int32_t sb = __ldg(g.iset_slot + I);
+  const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
+  const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+  const int32_t vb = __ldg(g.iset_vb + I);
+  T sig[MAXA], racc[MAXA], macc[MAXA];
+#pragma unroll
+  for (int a = 0; a < MAXA; ++a) {
+    sig[a] = a < na ? st.sigma[sb + a] : T(0);
+    racc[a] = T(0);
+    macc[a] = T(0);
+  }
+  T r = T(0), m = T(0);  // P64: column tid's running sums (tid < na)
+  for (int32_t k0 = m0; k0 < m1; k0 += kThreads) {
+    T d[MAXA], mm[MAXA];
+    member_terms<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, d, mm);
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) {
+        s_d[tid * MAXA + a] = d[a];
+        s_m[tid * MAXA + a] = mm[a];
+      }
+      __syncthreads();
+      if (tid < na) {
+        const int cnt = (m1 - k0) < kThreads ? (m1 - k0) : kThreads;
+        for (int j = 0; j < cnt; ++j) {
+          r = r + s_d[j * MAXA + tid];
+          m = m + s_m[j * MAXA + tid];
+        }
+      }
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int a = 0; a < MAXA; ++a) {
+        racc[a] += d[a];
+        macc[a] += mm[a];
+      }
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int a = 0; a < MAXA; ++a) {
+      s_d[tid * MAXA + a] = racc[a];
+      s_m[tid * MAXA + a] = macc[a];
+    }
+    __syncthreads();
+    for (int off = kThreads / 2; off > 0; off >>= 1) {
+      if (tid < off) {
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) {
+          s_d[tid * MAXA + a] += s_d[(tid + off) * MAXA + a];
+          s_m[tid * MAXA + a] += s_m[(tid + off) * MAXA + a];
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < na) {
+      r = s_d[tid];
+      m = s_m[tid];
+    }
+  }
+  // thread a updates slot a: R <- max(R + r, 0) (CFR+), avg += t * m, then
+  // sigma^{t+1} = RM(R) with the positive regrets summed in action order
+  double pos = 0.0;
+  if (tid < na) {
+    double Rn = st.R[sb + tid] + (double)r;
+    if (rule == 0) Rn = Rn > 0.0 ? Rn : 0.0;
+    st.R[sb + tid] = Rn;
+    st.avg[sb + tid] += wt * (double)m;
+    pos = Rn > 0.0 ? Rn : 0.0;
+    s_pos[tid] = pos;
+  }
+  __syncthreads();
+  if (tid < na) {
+    if constexpr (sizeof(T) == 8) {
+      double tot = 0.0;
+      for (int a = 0; a < na; ++a) tot += s_pos[a];
+      st.sigma[sb + tid] = tot > 0.0 ? pos / tot : 1.0 / (double)na;
+    } else {
+      float tot = 0.f;
+      for (int a = 0; a < na; ++a) tot += (float)s_pos[a];
+      st.sigma[sb + tid] = tot > 0.f ? (float)pos / tot : 1.f / (float)na;
+    }
+  }
+  __syncthreads();  // shared arrays are reused by the block's next set
+}
+
 // Grid: nb_chance blocks over narrow chance nodes, then one block per wide
-// chunk, then the information-set groups.
+// chunk, then the information-set groups (LANES == kThreads: one set per
+// block).
 template <typename T, int MAXA, int LANES>
 __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 5 : (MAXA <= 8 ? 3 : 1)) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
                                                             int nb_chance, int rule, int bump_t) {
@@ -433,9 +597,14 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 5 : (MAXA <= 8 ? 3 : 1))
   if ((int)blockIdx.x < nb_chance) {
     const int32_t stride = nb_chance * blockDim.x;
     for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride)
-      bwd_chance<T, false>(g, st.v, __ldg(g.chance_list + i));
+      bwd_chance<T, false>(g, st.v, i);
   } else if ((int)blockIdx.x < nb_chance + nb_wide) {
     bwd_wide_chunk<T, false>(g, w, st.v, w.wc0 + (int32_t)blockIdx.x - nb_chance);
+  } else if constexpr (LANES == kThreads) {
+    const int first = nb_chance + nb_wide;
+    const double wt = (double)(*st.t + 1);
+    for (int32_t I = w.is0 + ((int)blockIdx.x - first); I < w.is1; I += (int)gridDim.x - first)
+      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule);
   } else {
     constexpr int GPB = kThreads / LANES;
     const int first = nb_chance + nb_wide;
@@ -529,14 +698,17 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
   for (long long it = 0; it < a.n_iter; ++it) {
     for (int d = 0; d < a.D; ++d) {
       const LevelWork w = a.lw[d];
-      for (int32_t q = w.ib + tid; q < w.ie; q += 4 * nthr) fwd_int4<T, true>(a.g, a.st.sigma, a.st.reach, q, nthr, w.ie);
+      for (int32_t qw = w.ib + (tid & ~31); qw < w.ie; qw += 4 * nthr) {
+        if (w.fan) fwd_int4<T, true, true>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+        else fwd_int4<T, true, false>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+      }
       for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
       if (!grid_sync(a.bar)) return;
     }
     const double wt = (double)(t0 + it + 1);
     for (int d = a.D - 1; d >= 0; --d) {
       const LevelWork w = a.lw[d];
-      for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, __ldg(a.g.chance_list + i));
+      for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
       for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
       for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
         bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule);
@@ -566,17 +738,17 @@ __global__ void init_state_kernel(const int32_t *iset_slot, int32_t n_sets, T *s
   }
 }
 
+// Every value slot from the template in slot order: terminals get
+// pi_c(z) u(z) (eq. (template)), internal nodes 0 (overwritten by every
+// backward pass before their parents read them).
 template <typename T>
-__global__ void init_values_kernel(const int32_t *child_begin, const double *tmpl, int32_t N, T *v, double2 *vb,
-                                   double *vavg) {
+__global__ void init_values_kernel(const double *tmpl_vs, int32_t N, T *v, double2 *vb, double *vavg) {
   const int32_t stride = gridDim.x * blockDim.x;
   for (int32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < N; h += stride) {
-    if (child_begin[h] == child_begin[h + 1]) {  // terminal: pi_c(z) u(z), eq. (template)
-      const double x = tmpl[h];
-      v[h] = (T)x;
-      vb[h] = make_double2(x, x);
-      vavg[h] = x;
-    }
+    const double x = tmpl_vs[h];
+    v[h] = (T)x;
+    vb[h] = make_double2(x, x);
+    vavg[h] = x;
   }
 }
 
@@ -629,8 +801,8 @@ static __global__ void permute_kernel(const int32_t *spec_slot_of, const double 
 __device__ __forceinline__ void br_wide_chunk(const GameView &g, const LevelWork &w, double2 *vb, double *vavg,
                                               int32_t q) {
   const int32_t wi = wide_of_chunk(g, w, q);
-  const int32_t h = __ldg(g.wide_list + wi);
-  const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+  const int32_t h = __ldg(g.wide_vs + wi);
+  const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   const int32_t q0 = __ldg(g.wide_chunk + wi), nq = __ldg(g.wide_chunk + wi + 1) - q0;
   const int32_t c0 = cb + (q - q0) * kWideChunkK, c1 = min(ce, c0 + kWideChunkK);
   double sx = 0.0, sy = 0.0, sa = 0.0;
@@ -648,17 +820,22 @@ __device__ __forceinline__ void br_wide_chunk(const GameView &g, const LevelWork
     s_ticket = atomicAdd(g.wide_cnt + wi, 1u);
   }
   __syncthreads();
-  if (s_ticket == (unsigned)(nq - 1) && threadIdx.x == 0) {
+  if (s_ticket == (unsigned)(nq - 1)) {  // the last chunk's block adds the partials (fixed shape)
     __threadfence();
     double tx = 0.0, ty = 0.0, ta = 0.0;
-    for (int32_t k = 0; k < nq; ++k) {
+    for (int32_t k = threadIdx.x; k < nq; k += blockDim.x) {
       tx += __ldcg(g.wide_part + 3 * (q0 + k));
       ty += __ldcg(g.wide_part + 3 * (q0 + k) + 1);
       ta += __ldcg(g.wide_part + 3 * (q0 + k) + 2);
     }
-    vb[h] = make_double2(tx, ty);
-    vavg[h] = ta;
-    g.wide_cnt[wi] = 0u;
+    tx = block_sum(tx);
+    ty = block_sum(ty);
+    ta = block_sum(ta);
+    if (threadIdx.x == 0) {
+      vb[h] = make_double2(tx, ty);
+      vavg[h] = ta;
+      g.wide_cnt[wi] = 0u;
+    }
   }
 }
 
@@ -673,8 +850,8 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
   if ((int)blockIdx.x < nb_chance) {
     const int32_t stride = nb_chance * blockDim.x;
     for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride) {
-      const int32_t h = __ldg(g.chance_list + i);
-      const int32_t cb = __ldg(g.child_begin + h), ce = __ldg(g.child_begin + h + 1);
+      const int32_t h = __ldg(g.ch_vs + i);
+      const int32_t cb = __ldg(g.ch_vb + i), ce = cb + __ldg(g.ch_nch + i);
       double sx = 0.0, sy = 0.0, sa = 0.0;
       for (int32_t c = cb; c < ce; ++c) { const double2 x = vb[c]; sx += x.x; sy += x.y; sa += vavg[c]; }
       vb[h] = make_double2(sx, sy);
@@ -692,6 +869,7 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
     const int p = I >= w.is2 ? 1 : 0;
     const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
     const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+    const int32_t vb0 = __ldg(g.iset_vb + I);
     double sg[MAXA], Q[MAXA];
 #pragma unroll
     for (int a = 0; a < MAXA; ++a) { sg[a] = a < na ? sbs[sb + a] : 0.0; Q[a] = 0.0; }
@@ -701,8 +879,8 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
 #pragma unroll
       for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
       if (k < m1) {
-        const int32_t h = __ldg(g.mem_node + k);
-        const int32_t cb = __ldg(g.mem_cb + k);
+        const int32_t h = __ldg(g.mem_vs + k);
+        const int32_t cb = vb0 + (k - m0) * na;
         const double2 r = reach2[__ldg(g.mem_irank + k)];
         const double po = p ? r.x : r.y;
         double oth = 0.0, va = 0.0;
@@ -731,8 +909,8 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
     // every lane computed the same Q (the ordered sums are broadcast), so
     // best agrees across the group without another shuffle
     for (int32_t k = m0 + lane; k < m1; k += LANES) {
-      const int32_t h = __ldg(g.mem_node + k);
-      const int32_t cb = __ldg(g.mem_cb + k);
+      const int32_t h = __ldg(g.mem_vs + k);
+      const int32_t cb = vb0 + (k - m0) * na;
       reinterpret_cast<double *>(vb + h)[p] = reinterpret_cast<const double *>(vb + cb + best)[p];
     }
   }

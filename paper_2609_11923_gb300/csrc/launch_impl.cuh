@@ -12,8 +12,8 @@ cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, Game
     bwd_level_kernel<T, MA, L><<<grid, kThreads, 0, s>>>(g, st, w, nb_chance, rule, bump);      \
     return cudaGetLastError();                                                                  \
   }
-  BWD_CASE(4, 1) BWD_CASE(4, 2) BWD_CASE(4, 4) BWD_CASE(4, 8) BWD_CASE(4, 16) BWD_CASE(4, 32)
-  BWD_CASE(8, 1) BWD_CASE(8, 2) BWD_CASE(8, 4) BWD_CASE(8, 8) BWD_CASE(8, 16) BWD_CASE(8, 32)
+  BWD_CASE(4, 1) BWD_CASE(4, 2) BWD_CASE(4, 4) BWD_CASE(4, 8) BWD_CASE(4, 16) BWD_CASE(4, 32) BWD_CASE(4, kThreads)
+  BWD_CASE(8, 1) BWD_CASE(8, 2) BWD_CASE(8, 4) BWD_CASE(8, 8) BWD_CASE(8, 16) BWD_CASE(8, 32) BWD_CASE(8, kThreads)
   BWD_CASE(64, 4) BWD_CASE(64, 8) BWD_CASE(64, 16) BWD_CASE(64, 32)
 #undef BWD_CASE
   return cudaErrorInvalidValue;

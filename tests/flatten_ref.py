@@ -107,7 +107,45 @@ def flatten(g):
             big.append(ce - cb)
             big.extend(int(r) for r in kids)
     mem_irank = rank[mem_node] if len(mem_node) else np.zeros(0, np.int64)
+    # value slots: per parent depth, the blocks of the sets' members' children
+    # (set order, member order, action order), then the chance nodes' children
+    # (node order); the root's value goes last
+    vslot = np.full(N, -1, dtype=np.int64)
+    iset_vb = np.zeros(len(sets), dtype=np.int64)
+    nxt = 0
+    for d in range(D):
+        for ci, s_ in enumerate(sets):
+            if depth[first[s_]] != d:
+                continue
+            iset_vb[ci] = nxt
+            for h in members[ci]:
+                for x in range(child_begin[h], child_begin[h + 1]):
+                    vslot[x] = nxt
+                    nxt += 1
+        for h in range(level_begin[d], level_begin[d + 1]):
+            if kinds[h] == CHANCE:
+                for x in range(child_begin[h], child_begin[h + 1]):
+                    vslot[x] = nxt
+                    nxt += 1
+    assert nxt == N - 1
+    vslot[0] = N - 1
+    tmpl_vs = np.zeros(N)
+    tmpl_vs[vslot] = tmpl
+
+    def chance_arrays(lst):
+        lst = np.array(lst, dtype=np.int64)
+        if len(lst) == 0:
+            z = np.zeros(0, np.int32)
+            return z, z, z
+        return (vslot[child_begin[lst]].astype(np.int32), (child_begin[lst + 1] - child_begin[lst]).astype(np.int32),
+                vslot[lst].astype(np.int32))
+    ch_vb, ch_nch, ch_vs = chance_arrays(chance_list)
+    wide_vb, wide_nch, wide_vs = chance_arrays(wide_list)
     return {
+        "vslot": vslot.astype(np.int32), "iset_vb": iset_vb.astype(np.int32),
+        "mem_vs": (vslot[mem_node] if len(mem_node) else np.zeros(0, np.int64)).astype(np.int32),
+        "ch_vb": ch_vb, "ch_nch": ch_nch, "ch_vs": ch_vs, "wide_vb": wide_vb, "wide_nch": wide_nch,
+        "wide_vs": wide_vs, "tmpl_vs": tmpl_vs,
         "int_slot": np.array(int_slot, dtype=np.int32), "int_mask": np.array(int_mask, dtype=np.uint32).view(np.int32),
         "int_cirank": np.array(int_cirank, dtype=np.int32), "big_irank": np.array(big, dtype=np.int32),
         "mem_irank": mem_irank.astype(np.int32), "level_int": level_int,

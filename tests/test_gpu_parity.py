@@ -267,16 +267,39 @@ def test_autotune_keeps_fp64_parity_and_picks_valid_lanes():
     s = cfr.Solver(g, precision=cfr.P64)
     lanes = s.autotune(reps=2)
     assert len(lanes) == s.counts["depth_blocks"]
-    assert set(lanes) <= {1, 2, 4, 8, 16, 32}
+    assert set(lanes) <= {1, 2, 4, 8, 16, 32, 256}
     assert s.get_state()[2] == 0  # the trials were reset
     s.iterate(300)
     np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 300).avg_strategy())
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32, 256])
 def test_every_lane_count_matches_oracle_in_fp64(lanes):
     g = gg.large_card(3, 2, 1, 1)
     s = solve_gpu(g, 200, lanes_per_set=lanes)
     np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 200).avg_strategy())
     p = solve_gpu(g, 200, precision=cfr.P32, form=cfr.EXEC_PERSISTENT, lanes_per_set=lanes)
     assert abs(p.exploitability() - oracle.solve(g, 200).exploitability()) <= 1e-4 * g.pot
+
+
+@pytest.mark.parametrize("precision", [cfr.P64, cfr.P32])
+def test_one_block_per_set_handles_sets_longer_than_a_block(precision):
+    # one information set of 412 members: two member chunks of the block form
+    g = gg.random_tree(4, depth=10, p_chance=0.6, max_group=1000)
+    o = oracle.solve(g, 300)
+    s = solve_gpu(g, 300, precision=precision, form=cfr.EXEC_LEVELS, lanes_per_set=256)
+    if precision == cfr.P64:
+        np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    else:
+        assert abs(s.exploitability() - o.exploitability()) <= 1e-4 * g.pot
+
+
+@pytest.mark.parametrize("form", [cfr.EXEC_GRAPH, cfr.EXEC_PERSISTENT])
+def test_p64_mid_game_card_deals_match_oracle_bitwise(form):
+    # 10,920 chance nodes of 12 internal children each (written warp-wide)
+    # under a wide deal root
+    g = gg.large_card(4, 4, 1, 1)
+    o = oracle.solve(g, 60)
+    s = solve_gpu(g, 60, form=form)
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    assert abs(s.exploitability() - o.exploitability()) <= 1e-12
