@@ -79,6 +79,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the lane counts picked from mean set sizes")
+    p.add_argument("--profile-iteration", action="store_true",
+                   help="set up and warm up as usual, then run exactly one iteration between profiler start and "
+                        "stop (for ncu --profile-from-start off) and exit without timing")
     return p.parse_args()
 
 
@@ -237,6 +240,16 @@ def run_ours(args):
     # warm-up (graph capture happens on the first call)
     solver.iterate(args.warmup)
     solver.synchronize()
+    if args.profile_iteration:
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.start()
+        cfr.cfr_iterate(solver.h, 1, s)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"profile_iteration": args.workload, "lanes_per_set_by_depth": [int(x) for x in lanes],
+                              "source_hash": kernel_source_hash()}))
+        return 0
     clocks = Clocks(local)
     clocks.start()
     barrier()

@@ -329,19 +329,30 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
   }
 }
 
-// Loads and per-member terms of one member (k < m1), or zeros. The member's
-// children are slots vb + (k - m0) * na .. + na - 1 of the set's block: the
-// group's lanes read consecutive members' children as one run.
+// A member's two indices (member order: coalesced reads): its own value slot
+// and its internal rank (where its reach lives). Past the set's end: -1.
+__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, int32_t &ps, int32_t &ir) {
+  ps = -1;
+  ir = -1;
+  if (k < m1) {
+    ps = __ldg(g.mem_vs + k);
+    ir = __ldg(g.mem_irank + k);
+  }
+}
+
+// Loads and per-member terms of one member (k < m1) whose indices are
+// already known, or zeros. The member's children are slots
+// vb + (k - m0) * na .. + na - 1 of the set's block: the group's lanes read
+// consecutive members' children as one run.
 template <typename T, int MAXA, bool PERSIST>
-__device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
-                                             int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
-                                             T (&d)[MAXA], T (&mm)[MAXA]) {
+__device__ __forceinline__ void member_data(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
+                                            int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
+                                            int32_t h, int32_t ir, T (&d)[MAXA], T (&mm)[MAXA]) {
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
   if (k >= m1) return;
-  const int32_t h = __ldg(g.mem_vs + k);   // own value slot (member order: a coalesced read)
   const int32_t cb = vb + (k - m0) * na;
-  const vec2_t<T> r = ldm<PERSIST>(st.reach + __ldg(g.mem_irank + k));
+  const vec2_t<T> r = ldm<PERSIST>(st.reach + ir);
   T vc[MAXA];
   T vh = T(0);
 #pragma unroll
@@ -362,6 +373,16 @@ __device__ __forceinline__ void member_terms(const GameView &g, const StateView<
       mm[a] = pw * sig[a];
     }
   }
+}
+
+// Indices, loads and per-member terms of one member (k < m1), or zeros.
+template <typename T, int MAXA, bool PERSIST>
+__device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
+                                             int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
+                                             T (&d)[MAXA], T (&mm)[MAXA]) {
+  int32_t h, ir;
+  member_idx(g, k, m1, h, ir);
+  member_data<T, MAXA, PERSIST>(g, st, k, m0, m1, vb, na, p2, sig, h, ir, d, mm);
 }
 
 // Adds one chunk's member terms to the group totals. P64: lane order (the
@@ -390,8 +411,10 @@ __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsign
 }
 
 // One information set, processed by the LANES lanes of one group. Members go
-// in chunks of LANES, two chunks in flight per step; the update of the set's
-// slots runs one lane per action.
+// in chunks of LANES (two chunks per step for narrow groups); each step loads
+// the next step's member indices while its own reach and child values are in
+// flight, so a step waits for one memory round trip, not two. The update of
+// the set's slots runs one lane per action.
 template <typename T, int MAXA, int LANES, bool PERSIST>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
                                         int lane, unsigned mask, double wt, int rule) {
@@ -409,20 +432,41 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   constexpr bool TWO = MAXA <= 8 && LANES <= 8;  // narrow groups keep two chunks in flight
   int32_t k0 = m0;
   if constexpr (TWO) {
-    for (; k0 + LANES < m1; k0 += 2 * LANES) {
-      T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d0, mm0);
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, d1, mm1);
-      accumulate_chunk<T, MAXA, LANES>(LANES, na, mask, d0, mm0, racc, macc);
-      const int32_t c1 = (m1 - k0 - LANES) < LANES ? (m1 - k0 - LANES) : LANES;
-      accumulate_chunk<T, MAXA, LANES>(c1, na, mask, d1, mm1, racc, macc);
+    if (k0 + LANES < m1) {
+      int32_t ps0, ir0, ps1, ir1;
+      member_idx(g, k0 + lane, m1, ps0, ir0);
+      member_idx(g, k0 + LANES + lane, m1, ps1, ir1);
+      for (; k0 + LANES < m1; k0 += 2 * LANES) {
+        int32_t qs0, jr0, qs1, jr1;  // the next step's indices
+        member_idx(g, k0 + 2 * LANES + lane, m1, qs0, jr0);
+        member_idx(g, k0 + 3 * LANES + lane, m1, qs1, jr1);
+        T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
+        member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps0, ir0, d0, mm0);
+        member_data<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, ps1, ir1, d1, mm1);
+        accumulate_chunk<T, MAXA, LANES>(LANES, na, mask, d0, mm0, racc, macc);
+        const int32_t c1 = (m1 - k0 - LANES) < LANES ? (m1 - k0 - LANES) : LANES;
+        accumulate_chunk<T, MAXA, LANES>(c1, na, mask, d1, mm1, racc, macc);
+        ps0 = qs0; ir0 = jr0; ps1 = qs1; ir1 = jr1;
+      }
     }
-  }
-  for (; k0 < m1; k0 += LANES) {
-    T d[MAXA], mm[MAXA];
-    member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d, mm);
-    const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
-    accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
+    for (; k0 < m1; k0 += LANES) {
+      T d[MAXA], mm[MAXA];
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d, mm);
+      const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
+      accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
+    }
+  } else {
+    int32_t ps, ir;
+    member_idx(g, k0 + lane, m1, ps, ir);
+    for (; k0 < m1; k0 += LANES) {
+      int32_t qs, jr;  // the next step's indices
+      member_idx(g, k0 + LANES + lane, m1, qs, jr);
+      T d[MAXA], mm[MAXA];
+      member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
+      const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
+      accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
+      ps = qs; ir = jr;
+    }
   }
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -513,9 +557,15 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
     macc[a] = T(0);
   }
   T r = T(0), m = T(0);  // P64: column tid's running sums (tid < na)
+  int32_t ps, ir;
+  member_idx(g, m0 + tid, m1, ps, ir);
   for (int32_t k0 = m0; k0 < m1; k0 += kThreads) {
+    int32_t qs, jr;  // the next chunk's indices
+    member_idx(g, k0 + kThreads + tid, m1, qs, jr);
     T d[MAXA], mm[MAXA];
-    member_terms<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, d, mm);
+    member_data<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
+    ps = qs;
+    ir = jr;
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
       for (int a = 0; a < MAXA; ++a) {
@@ -591,7 +641,7 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
 // chunk, then the information-set groups (LANES == kThreads: one set per
 // block).
 template <typename T, int MAXA, int LANES>
-__global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 5 : (MAXA <= 8 ? 3 : 1)) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
+__global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1)) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
                                                             int nb_chance, int rule, int bump_t) {
   const int nb_wide = w.wc1 - w.wc0;
   if ((int)blockIdx.x < nb_chance) {
