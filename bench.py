@@ -291,6 +291,12 @@ def run_ours(args):
                 "traffic": traffic, "kernel": kname, "share_of_iteration": dom[2] / total_ms,
                 "algo_bytes_per_launch": dom[3], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
+    # the launch structure alone (empty kernels, same grids / same barriers), for comparison with ms_per_step
+    floor_graph, floor_pers = cfr.cfr_launch_floor(solver.h, 200, s)
+    launch_floor = {"graph_ms": floor_graph, "persistent_ms": floor_pers,
+                    "what": "per iteration: a graph of the same %d launches (same grids) of an empty kernel; one "
+                            "cooperative empty kernel with the persistent form's grid and %d grid barriers" % (2 * D, 2 * D)}
+
     # end to end through the public API: upload (bind) + K iterations + average strategy to host
     e2e = None
     if not args.no_e2e:
@@ -344,6 +350,7 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "clocks": clk,
         "launch_profile_ms": {"fwd": fwd_ms, "bwd": bwd_ms},
+        "launch_floor": launch_floor,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -195,6 +195,17 @@ int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity
  * across processes. Synchronises `stream`. */
 int cfr_autotune(cfr_handle *h, int reps, void *stream);
 
+/* The launch floor of one iteration (no counterpart in the paper's API; its
+ * Section 4.3 discusses the graph-launch floor): the mean time of one
+ * iteration's launch structure with no work in it, over n iterations.
+ * graph_ms: a CUDA graph of the same 2D launches with the same grid sizes
+ * as the per-level form (depth-first forward, then backward), each an empty
+ * kernel. persistent_ms: one cooperative launch of an empty kernel with the
+ * persistent form's grid and its 2D grid barriers per iteration (bounded
+ * waits: CFR_ERR_TIMEOUT if one gives up). The handle must be bound; solver
+ * state is untouched. Synchronises `stream`. */
+int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *graph_ms, double *persistent_ms);
+
 /* Batched solves (many independent games in one launch). Every handle must
  * be bound (each to its own arena) and use the same precision, with sets of
  * at most 8 actions. One CTA of `threads` threads (256 or 1024; 0 = 256)

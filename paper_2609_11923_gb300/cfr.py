@@ -94,6 +94,7 @@ def _load():
         "cfr_profile_iteration": [H, dp, dp, vp],
         "cfr_iterate_noalloc": [H, i64, vp],
         "cfr_autotune": [H, ctypes.c_int, vp],
+        "cfr_launch_floor": [H, i64, vp, dp, dp],
         "cfr_batch_iterate": [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(i64), i64, vp, ctypes.c_size_t,
                               ctypes.c_int, ctypes.c_int, vp],
         "cfr_batch_exploitability": [ctypes.POINTER(H), ctypes.c_int, dp, vp, ctypes.c_size_t, ctypes.c_int,
@@ -117,7 +118,7 @@ EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterat
             "cfr_avg_strategy", "cfr_current_strategy", "cfr_exploitability", "cfr_reset", "cfr_set_payoffs",
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
             "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune",
-            "cfr_batch_table_bytes", "cfr_batch_iterate", "cfr_batch_exploitability"]
+            "cfr_batch_table_bytes", "cfr_batch_iterate", "cfr_batch_exploitability", "cfr_launch_floor"]
 
 
 def _check(rc: int) -> None:
@@ -262,6 +263,13 @@ def cfr_level_bytes(h: int, level: int) -> Tuple[int, int]:
     f, b = ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.cfr_level_bytes(h, level, ctypes.byref(f), ctypes.byref(b)))
     return f.value, b.value
+
+
+def cfr_launch_floor(h: int, n: int, stream: int = 0) -> Tuple[float, float]:
+    """Per-iteration ms of the launch structure alone: (graph of empty kernels, empty persistent kernel)."""
+    g, p = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.cfr_launch_floor(h, n, stream, ctypes.byref(g), ctypes.byref(p)))
+    return g.value, p.value
 
 
 def cfr_profile_iteration(h: int, depth_blocks: int, stream: int = 0):

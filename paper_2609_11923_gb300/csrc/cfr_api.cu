@@ -365,6 +365,30 @@ static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
   return CFR_OK;
 }
 
+// Blocks of the persistent form: enough for the widest depth, never more than
+// can be co-resident (computed once per lane count).
+template <typename T>
+static int ensure_persist_grid(cfr_handle *h, cudaStream_t s) {
+  if (h->persist_grid != 0) return CFR_OK;
+  const int L = h->persist_lanes;
+  PersistArgs<T> a{};
+  int dev = 0, nsm = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(launch_persistent<T>(h->maxa_tier, L, 0, s, a, &per_sm));
+  int64_t cap = (int64_t)nsm * std::max(per_sm, 1);
+  if (h->opt.persistent_ctas > 0) cap = std::min<int64_t>(cap, h->opt.persistent_ctas);
+  int64_t need = 1;
+  for (const LevelWork &w : h->levels) {
+    need = std::max<int64_t>(need, (w.ie - w.ib + 4 * kThreads - 1) / (4 * kThreads));
+    need = std::max<int64_t>(need, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
+    need = std::max<int64_t>(need, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
+    need = std::max<int64_t>(need, w.wc1 - w.wc0);
+  }
+  h->persist_grid = (int)std::max<int64_t>(1, std::min(need, cap));
+  return CFR_OK;
+}
+
 template <typename T>
 static int launch_persistent_form(cfr_handle *h, int64_t n, cudaStream_t s) {
   const int L = h->persist_lanes;
@@ -380,23 +404,8 @@ static int launch_persistent_form(cfr_handle *h, int64_t n, cudaStream_t s) {
   a.bar.gen = bar + 1;
   a.bar.err = h->p<int>(h->b_err);
   a.bar.spin_limit = h->opt.barrier_spin_limit > 0 ? h->opt.barrier_spin_limit : (int64_t)20000000;
-  if (h->persist_grid == 0) {
-    int dev = 0, nsm = 0, per_sm = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(launch_persistent<T>(h->maxa_tier, L, 0, s, a, &per_sm));
-    int64_t cap = (int64_t)nsm * std::max(per_sm, 1);
-    if (h->opt.persistent_ctas > 0) cap = std::min<int64_t>(cap, h->opt.persistent_ctas);
-    // enough blocks for the widest depth, never more than co-resident
-    int64_t need = 1;
-    for (const LevelWork &w : h->levels) {
-      need = std::max<int64_t>(need, (w.ie - w.ib + 4 * kThreads - 1) / (4 * kThreads));
-      need = std::max<int64_t>(need, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
-      need = std::max<int64_t>(need, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
-      need = std::max<int64_t>(need, w.wc1 - w.wc0);
-    }
-    h->persist_grid = (int)std::max<int64_t>(1, std::min(need, cap));
-  }
+  int rc = ensure_persist_grid<T>(h, s);
+  if (rc) return rc;
   a.bar.expected = (unsigned)h->persist_grid + (unsigned)h->test_missing_arrivals;
   CK(cudaMemsetAsync(bar, 0, 4, s));  // arrivals (a timed-out launch leaves them set)
   CK(launch_persistent<T>(h->maxa_tier, L, h->persist_grid, s, a, nullptr));
@@ -862,6 +871,100 @@ extern "C" int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream) {
 // action tier has kernels for and keep the fastest; for the persistent form,
 // time whole persistent iterations per lane count. Trial launches change the
 // state, so the call ends with the state reset (as cfr_reset).
+// ------------------------------------------------------------ launch floor
+// The iteration's launch structure with no work in it: the same 2D launches
+// (same grid sizes) of an empty kernel captured in one graph, and one
+// cooperative launch of an empty kernel with the persistent form's grid and
+// its 2D grid barriers per iteration.
+static __global__ void empty_level_kernel() {}
+
+static __global__ void __launch_bounds__(kThreads) empty_persistent_kernel(Barrier bar, int n_sync, long long n_iter) {
+  for (long long it = 0; it < n_iter; ++it)
+    for (int k = 0; k < n_sync; ++k)
+      if (!grid_sync(bar)) return;
+}
+
+extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *graph_ms, double *persistent_ms) {
+  if (!h || !graph_ms || !persistent_ms) return set_err(CFR_ERR_ARG, "cfr_launch_floor: null argument");
+  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_launch_floor: call cfr_bind first");
+  if (n < 1 || n > 1000000) return set_err(CFR_ERR_ARG, "cfr_launch_floor: n must be in [1, 1e6]");
+  *graph_ms = 0.0;
+  *persistent_ms = 0.0;
+  const Compiled &c = h->c;
+  if (c.D == 0) return CFR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> grids;
+  for (int64_t d = 0; d < c.D; ++d) {
+    const LevelWork &w = h->levels[d];
+    grids.push_back(grid_for((w.ie - w.ib + 3) / 4, kThreads) + (w.wc1 - w.wc0));
+  }
+  for (int64_t d = c.D - 1; d >= 0; --d) {
+    const LevelWork &w = h->levels[d];
+    const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
+    grids.push_back((nch > 0 ? grid_for(nch, kThreads) : 0) + (w.wc1 - w.wc0) +
+                    (nis > 0 ? grid_for(nis, kThreads / h->level_lanes[d]) : 0));
+  }
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int gsz : grids) empty_level_kernel<<<std::max(gsz, 1), kThreads, 0, h->cap_stream>>>();
+  CK(cudaStreamEndCapture(h->cap_stream, &graph));
+  cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return set_err(CFR_ERR_DEVICE, "cfr_launch_floor: %s", cudaGetErrorString(e));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = CFR_OK;
+  float ms = 0.f;
+  e = cudaGraphLaunch(ge, s);  // warm
+  for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
+    if (i == 0) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) rc = set_err(CFR_ERR_DEVICE, "cfr_launch_floor: %s", cudaGetErrorString(e));
+  if (rc == CFR_OK) {
+    *graph_ms = (double)ms / (double)n;
+    rc = h->precision == CFR_P64 ? ensure_persist_grid<double>(h, s) : ensure_persist_grid<float>(h, s);
+  }
+  if (rc == CFR_OK) {
+    unsigned *bar = h->p<unsigned>(h->b_bar);
+    Barrier b;
+    b.count = bar;
+    b.gen = bar + 1;
+    b.err = h->p<int>(h->b_err);
+    b.spin_limit = h->opt.barrier_spin_limit > 0 ? h->opt.barrier_spin_limit : (int64_t)20000000;
+    b.expected = (unsigned)h->persist_grid;
+    int n_sync = (int)(2 * c.D);
+    long long iters = (long long)n;
+    void *args[] = {&b, &n_sync, &iters};
+    e = cudaMemsetAsync(bar, 0, 4, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess)
+      e = cudaLaunchCooperativeKernel((const void *)empty_persistent_kernel, dim3(h->persist_grid), dim3(kThreads), args, 0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, b.err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = set_err(CFR_ERR_DEVICE, "cfr_launch_floor: %s", cudaGetErrorString(e));
+    else if (err) {
+      cudaMemset(b.err, 0, 4);
+      rc = set_err(CFR_ERR_TIMEOUT, "cfr_launch_floor: a grid barrier gave up waiting");
+    } else {
+      *persistent_ms = (double)ms / (double)n;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   if (!h) return set_err(CFR_ERR_ARG, "cfr_autotune: null handle");
   if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_autotune: call cfr_bind first");

@@ -303,3 +303,17 @@ def test_p64_mid_game_card_deals_match_oracle_bitwise(form):
     s = solve_gpu(g, 60, form=form)
     np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
     assert abs(s.exploitability() - o.exploitability()) <= 1e-12
+
+
+def test_launch_floor_is_positive_and_leaves_the_state_alone():
+    g = gg.random_tree(5, depth=9)
+    s = solve_gpu(g, 20, precision=cfr.P32)
+    before = s.get_state()
+    gms, pms = cfr.cfr_launch_floor(s.h, 20, s._s())
+    assert 0.0 < gms < 50.0 and 0.0 < pms < 50.0
+    after = s.get_state()
+    np.testing.assert_array_equal(before[0], after[0])
+    np.testing.assert_array_equal(before[1], after[1])
+    assert before[2] == after[2]
+    s.iterate(10)  # the solver still works after the floor measurement
+    s.synchronize()
