@@ -20,7 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-CFR_PLUS, CFR = 0, 1
+CFR_PLUS, CFR, PCFR_PLUS = 0, 1, 2
 SIMULTANEOUS, ALTERNATING = 0, 1
 
 
@@ -65,11 +65,11 @@ def _load():
     lib = ctypes.CDLL(_LIB_PATH)
     G = ctypes.POINTER(_Game)
     dp = ctypes.POINTER(ctypes.c_double)
-    lib.or_cfr_run.argtypes = [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    lib.or_cfr_run.argtypes = [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
     lib.or_cfr_run.restype = ctypes.c_int
     lib.or_avg_strategy.argtypes = [G, dp, dp]
     lib.or_avg_strategy.restype = None
-    lib.or_current_strategy.argtypes = [G, dp, dp]
+    lib.or_current_strategy.argtypes = [G, dp, dp, dp]
     lib.or_current_strategy.restype = None
     lib.or_expected_value.argtypes = [G, dp]
     lib.or_expected_value.restype = ctypes.c_double
@@ -113,13 +113,14 @@ class Oracle:
         self.A = int(spec.iset_nact.sum())
         self.R = np.zeros(self.A)
         self.sbar = np.zeros(self.A)
+        self.pred = np.zeros(self.A)  # PCFR+ prediction: each slot's last instantaneous regret
         self.t = 0
         self.root_value = 0.0
 
     def iterate(self, n: int) -> None:
         rv = ctypes.c_double(0.0)
         rc = _load().or_cfr_run(ctypes.byref(self._g), self.t, n, self.rule, self.order,
-                                _dp(self.R), _dp(self.sbar), ctypes.byref(rv))
+                                _dp(self.R), _dp(self.sbar), _dp(self.pred), ctypes.byref(rv))
         if rc != 0:
             raise RuntimeError("oracle: or_cfr_run failed (%d)" % rc)
         self.t += n
@@ -132,7 +133,8 @@ class Oracle:
 
     def current_strategy(self) -> np.ndarray:
         out = np.empty(self.A)
-        _load().or_current_strategy(ctypes.byref(self._g), _dp(self.R), _dp(out))
+        pred = _dp(self.pred) if self.rule == PCFR_PLUS else None
+        _load().or_current_strategy(ctypes.byref(self._g), _dp(self.R), pred, _dp(out))
         return out
 
     # evaluation helpers (also usable on arbitrary strategies)

@@ -99,23 +99,31 @@ static int64_t *slot_offsets(const or_game *g) {
 }
 
 /* Regret matching (eq. (rm)): sigma proportional to the positive part of R,
- * uniform when that part sums to zero. */
-static void regret_matching(const or_game *g, const int64_t *off, const double *R, double *sigma,
-                            int player_mask) {
+ * uniform when that part sums to zero. With a prediction (PCFR+), the
+ * positive part of R + pred. */
+static void regret_matching(const or_game *g, const int64_t *off, const double *R, const double *pred,
+                            double *sigma, int player_mask) {
   for (int64_t I = 0; I < g->n_infosets; ++I) {
     if (!(player_mask & (1 << g->iset_player[I]))) continue;
     const int64_t s0 = off[I];
     const int na = g->iset_nact[I];
     double tot = 0.0;
-    for (int a = 0; a < na; ++a) tot += R[s0 + a] > 0.0 ? R[s0 + a] : 0.0;
-    for (int a = 0; a < na; ++a)
-      sigma[s0 + a] = tot > 0.0 ? (R[s0 + a] > 0.0 ? R[s0 + a] : 0.0) / tot : 1.0 / (double)na;
+    for (int a = 0; a < na; ++a) {
+      const double x = pred ? R[s0 + a] + pred[s0 + a] : R[s0 + a];
+      tot += x > 0.0 ? x : 0.0;
+    }
+    for (int a = 0; a < na; ++a) {
+      const double x = pred ? R[s0 + a] + pred[s0 + a] : R[s0 + a];
+      sigma[s0 + a] = tot > 0.0 ? (x > 0.0 ? x : 0.0) / tot : 1.0 / (double)na;
+    }
   }
 }
 
 int or_cfr_run(const or_game *g, int64_t t0, int64_t T, int rule, int order, double *R, double *sbar,
-               double *root_value) {
+               double *pred, double *root_value) {
   if (!g || T < 0 || !R || !sbar) return -1;
+  if (rule == OR_PCFR_PLUS && !pred) return -1;
+  const double *pr = rule == OR_PCFR_PLUS ? pred : NULL;
   int64_t *off = slot_offsets(g);
   if (!off) return -2;
   const int64_t A = off[g->n_infosets];
@@ -129,11 +137,15 @@ int or_cfr_run(const or_game *g, int64_t t0, int64_t T, int rule, int order, dou
   int rc = 0;
   double v = 0.0;
   for (int64_t it = 1; it <= T && rc == 0; ++it) {
-    const double wt = (double)(t0 + it); /* linear averaging weight w_t = t */
+    /* averaging weight: linear w_t = t (CFR, CFR+); quadratic w_t = t^2 for
+     * PCFR+ (the reading that reproduces the alternating Kuhn cell of the
+     * convergence table) */
+    const double tt = (double)(t0 + it);
+    const double wt = rule == OR_PCFR_PLUS ? tt * tt : tt;
     const int halves = order == OR_ALTERNATING ? 2 : 1;
     for (int hlf = 0; hlf < halves; ++hlf) {
       const int mask = order == OR_ALTERNATING ? (1 << hlf) : 3;
-      regret_matching(g, off, R, sigma, 3);
+      regret_matching(g, off, R, pr, sigma, 3);
       memset(r, 0, sizeof(double) * (size_t)A);
       memset(m, 0, sizeof(double) * (size_t)A);
       w.update_mask = mask;
@@ -144,7 +156,8 @@ int or_cfr_run(const or_game *g, int64_t t0, int64_t T, int rule, int order, dou
         for (int64_t q = off[I]; q < off[I + 1]; ++q) {
           sbar[q] += wt * m[q]; /* average accumulates sigma^t before the clamp */
           const double nr = R[q] + r[q];
-          R[q] = (rule == OR_CFR_PLUS) ? (nr > 0.0 ? nr : 0.0) : nr;
+          R[q] = (rule == OR_CFR) ? nr : (nr > 0.0 ? nr : 0.0); /* CFR+ and PCFR+ clamp */
+          if (rule == OR_PCFR_PLUS) pred[q] = r[q];               /* next prediction */
         }
       }
     }
@@ -165,10 +178,10 @@ void or_avg_strategy(const or_game *g, const double *sbar, double *out) {
   }
 }
 
-void or_current_strategy(const or_game *g, const double *R, double *out) {
+void or_current_strategy(const or_game *g, const double *R, const double *pred, double *out) {
   int64_t *off = slot_offsets(g);
   if (!off) return;
-  regret_matching(g, off, R, out, 3);
+  regret_matching(g, off, R, pred, out, 3);
   free(off);
 }
 

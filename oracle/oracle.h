@@ -29,21 +29,27 @@ typedef struct or_game {
   const int32_t *iset_nact;   /* [I] */
 } or_game;
 
-enum { OR_CFR_PLUS = 0, OR_CFR = 1 };
+enum { OR_CFR_PLUS = 0, OR_CFR = 1, OR_PCFR_PLUS = 2 };
 enum { OR_SIMULTANEOUS = 0, OR_ALTERNATING = 1 };
 
-/* Runs iterations t0+1 .. t0+T of CFR (rule OR_CFR_PLUS or OR_CFR, linear
- * averaging w_t = t) from the state (R, sbar), both [A] and updated in place.
- * Zero state and t0 = 0 is a fresh solve. root_value (optional) receives the
- * chance-weighted root value of the last pass. Returns 0, or < 0 on error. */
+/* Runs iterations t0+1 .. t0+T of CFR (rule OR_CFR_PLUS, OR_CFR or
+ * OR_PCFR_PLUS) from the state (R, sbar), both [A] and updated in place.
+ * Zero state and t0 = 0 is a fresh solve. Averaging weight w_t = t, or t^2
+ * for PCFR+. PCFR+ (Section 3, "update rules"): the CFR+ regret update, and
+ * the strategy is regret matching of R + pred, where pred [A] holds each
+ * slot's last instantaneous regret (the prediction; zero at the start,
+ * updated in place; required for OR_PCFR_PLUS, ignored otherwise). root_value (optional)
+ * receives the chance-weighted root value of the last pass. Returns 0, or
+ * < 0 on error. */
 int or_cfr_run(const or_game *g, int64_t t0, int64_t T, int rule, int order, double *R, double *sbar,
-               double *root_value);
+               double *pred, double *root_value);
 
 /* Average strategy: sbar normalised per information set, uniform if zero. */
 void or_avg_strategy(const or_game *g, const double *sbar, double *out);
 
-/* Regret-matching strategy of the cumulative regrets R. */
-void or_current_strategy(const or_game *g, const double *R, double *out);
+/* Regret-matching strategy of the cumulative regrets R (plus the prediction
+ * pred [A] when it is not NULL: the PCFR+ strategy). */
+void or_current_strategy(const or_game *g, const double *R, const double *pred, double *out);
 
 /* Expected payoff to player 1 when both players follow sigma [A]. */
 double or_expected_value(const or_game *g, const double *sigma);
