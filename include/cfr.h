@@ -70,7 +70,8 @@ typedef struct cfr_game_spec {
 
 enum { CFR_P64 = 0, CFR_P32 = 1 };
 enum { CFR_EXEC_AUTO = 0, CFR_EXEC_LEVELS = 1, CFR_EXEC_GRAPH = 2, CFR_EXEC_PERSISTENT = 3 };
-enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1 };
+enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1, CFR_RULE_PCFR_PLUS = 2 };
+enum { CFR_ORDER_SIMULTANEOUS = 0, CFR_ORDER_ALTERNATING = 1 };
 
 typedef struct cfr_options {
   /* CFR_P64: every value in FP64 (the parity mode). CFR_P32: reach, values,
@@ -82,12 +83,23 @@ typedef struct cfr_options {
    * CFR_EXEC_PERSISTENT: one kernel per cfr_iterate call with a grid-wide
    * barrier between depth levels; CFR_EXEC_AUTO picks by game size. */
   int exec_form;
-  int rule;            /* CFR_RULE_CFR_PLUS (clamp) or CFR_RULE_CFR (no clamp) */
+  /* Update rule (Section 3, update rules): CFR_RULE_CFR_PLUS (regret clamped
+   * at zero, linear averaging w_t = t), CFR_RULE_CFR (no clamp, linear
+   * averaging) or CFR_RULE_PCFR_PLUS (clamp; the next strategy matches
+   * R + r, the iteration's instantaneous regret as the prediction; quadratic
+   * averaging w_t = t^2). */
+  int rule;
   int lanes_per_set;   /* 0 = by mean set size (see cfr_autotune); else 1, 2, 4, 8, 16 or 32 lanes per set,
                           or 256 = one thread block per set in the per-level kernels (sets of at most 8
                           actions; the persistent kernel then uses 32) */
   int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
   int64_t barrier_spin_limit; /* 0 = default; polls before a grid barrier reports CFR_ERR_TIMEOUT */
+  /* CFR_ORDER_SIMULTANEOUS: both players' regrets from one strategy profile;
+   * CFR_ORDER_ALTERNATING: each iteration is two half-iterations (forward and
+   * backward pass each), the first updating player 1's sets, the second
+   * player 2's with player 1's new strategy; each half accumulates only its
+   * player's average (Section 3; Section 4.2 runs the body twice). */
+  int order;
 } cfr_options;
 
 typedef struct cfr_counts {
@@ -158,7 +170,9 @@ int cfr_reset(cfr_handle *h, void *stream);
 int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream);
 
 /* Copies the solver state out / in, host arrays in spec slot order:
- * R[A] and avg[A] (un-normalised strategy sums) as doubles, and t. */
+ * R[A] and avg[A] (un-normalised strategy sums) as doubles, and t. Under
+ * PCFR+ the prediction is not part of the state: cfr_set_state restarts it
+ * at zero (the next strategy is regret matching of R alone). */
 int cfr_get_state(cfr_handle *h, double *R, double *avg, int64_t *t, void *stream);
 int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, void *stream);
 
@@ -198,10 +212,11 @@ int cfr_autotune(cfr_handle *h, int reps, void *stream);
 /* The launch floor of one iteration (no counterpart in the paper's API; its
  * Section 4.3 discusses the graph-launch floor): the mean time of one
  * iteration's launch structure with no work in it, over n iterations.
- * graph_ms: a CUDA graph of the same 2D launches with the same grid sizes
- * as the per-level form (depth-first forward, then backward), each an empty
- * kernel. persistent_ms: one cooperative launch of an empty kernel with the
- * persistent form's grid and its 2D grid barriers per iteration (bounded
+ * graph_ms: a CUDA graph of the same 2D launches (4D under alternating
+ * updates) with the same grid sizes as the per-level form (depth-first
+ * forward, then backward), each an empty kernel. persistent_ms: one
+ * cooperative launch of an empty kernel with the persistent form's grid and
+ * its 2D (4D) grid barriers per iteration (bounded
  * waits: CFR_ERR_TIMEOUT if one gives up). The handle must be bound; solver
  * state is untouched. Synchronises `stream`. */
 int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *graph_ms, double *persistent_ms);
@@ -237,7 +252,8 @@ int cfr_level_bytes(const cfr_handle *h, int level, int64_t *fwd_bytes, int64_t 
 /* Measurement: runs ONE iteration (t -> t+1) as per-level launches on
  * `stream` with a CUDA event pair around every launch, and writes each
  * launch's device time in milliseconds: fwd_ms[d] and bwd_ms[d] for
- * d = 0 .. D-1 (host arrays of D doubles). Synchronises `stream`. */
+ * d = 0 .. D-1 (host arrays of D doubles; under alternating updates the two
+ * halves' times of a depth are added). Synchronises `stream`. */
 int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *stream);
 
 /* Allocation-free variant of cfr_iterate, for callers that cannot allocate

@@ -35,6 +35,8 @@ struct InstDesc {
   int32_t rule;
   int32_t n_sets;
   int32_t root_vs;  // the root's value slot (N - 1)
+  int32_t order;    // 0 simultaneous, 1 alternating updates
+  int32_t pad;
 };
 
 template <int THREADS>
@@ -102,25 +104,29 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
   const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;
   constexpr int NG = THREADS / LANES;
   const unsigned mask = group_mask<LANES>();
+  const int halves = in.order ? 2 : 1;  // alternating: player 1's half, then player 2's
   for (long long it = 0; it < in.n_iter; ++it) {
-    for (int d = 0; d < in.D; ++d) {
-      const LevelWork w = in.lw[d];
-      for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
-        if (w.fan) fwd_int4<T, false, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
-        else fwd_int4<T, false, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
+    const double wt = avg_weight(t0 + it + 1, in.rule);
+    for (int hf = 0; hf < halves; ++hf) {
+      const int upd = in.order ? (1 << hf) : 3;
+      for (int d = 0; d < in.D; ++d) {
+        const LevelWork w = in.lw[d];
+        for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
+          if (w.fan) fwd_int4<T, false, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
+          else fwd_int4<T, false, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
+        }
+        for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, i);
+        __syncthreads();
       }
-      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, i);
-      __syncthreads();
-    }
-    const double wt = (double)(t0 + it + 1);
-    for (int d = in.D - 1; d >= 0; --d) {
-      const LevelWork w = in.lw[d];
-      for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS)
-        bwd_chance<T, false>(in.g, st.v, i);
-      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS>(in.g, st.v, i, sm);
-      for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-        bwd_set<T, MAXA, LANES, false>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule);
-      __syncthreads();
+      for (int d = in.D - 1; d >= 0; --d) {
+        const LevelWork w = in.lw[d];
+        for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS)
+          bwd_chance<T, false>(in.g, st.v, i);
+        for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS>(in.g, st.v, i, sm);
+        for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
+          bwd_set<T, MAXA, LANES, false>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
+        __syncthreads();
+      }
     }
   }
   if (threadIdx.x == 0) *in.t = t0 + in.n_iter;

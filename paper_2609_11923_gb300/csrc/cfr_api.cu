@@ -49,7 +49,7 @@ struct Buf {
 struct cfr_handle {
   Compiled c;
   cfr_options opt{};
-  int precision = CFR_P32, exec_form = CFR_EXEC_GRAPH, rule = 0;
+  int precision = CFR_P32, exec_form = CFR_EXEC_GRAPH, rule = 0, order = 0;
   int maxa_tier = 8;           // 4, 8 or 64: register arrays of the per-set code
   std::vector<int> level_lanes;  // lanes per information set, per depth
   int persist_lanes = 8;
@@ -133,7 +133,8 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   else { h->opt.precision = CFR_P32; h->opt.exec_form = CFR_EXEC_AUTO; }
   if (h->opt.precision != CFR_P64 && h->opt.precision != CFR_P32) { delete h; return set_err(CFR_ERR_ARG, "bad precision"); }
   if (h->opt.exec_form < 0 || h->opt.exec_form > 3) { delete h; return set_err(CFR_ERR_ARG, "bad exec_form"); }
-  if (h->opt.rule != CFR_RULE_CFR_PLUS && h->opt.rule != CFR_RULE_CFR) { delete h; return set_err(CFR_ERR_ARG, "bad rule"); }
+  if (h->opt.rule != CFR_RULE_CFR_PLUS && h->opt.rule != CFR_RULE_CFR && h->opt.rule != CFR_RULE_PCFR_PLUS) { delete h; return set_err(CFR_ERR_ARG, "bad rule"); }
+  if (h->opt.order != CFR_ORDER_SIMULTANEOUS && h->opt.order != CFR_ORDER_ALTERNATING) { delete h; return set_err(CFR_ERR_ARG, "bad order"); }
   const int lp = h->opt.lanes_per_set;
   if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32 or 256"); }
   std::string err;
@@ -143,6 +144,7 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (lp != 0 && (lp < 4 || lp == kThreads) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2 or 256 needs sets of at most 8 actions"); }
   h->precision = h->opt.precision;
   h->rule = h->opt.rule;
+  h->order = h->opt.order;
   h->maxa_tier = c.max_act <= 4 ? 4 : (c.max_act <= 8 ? 8 : 64);
   h->exec_form = h->opt.exec_form;
   if (h->exec_form == CFR_EXEC_AUTO) h->exec_form = c.N <= (1 << 16) ? CFR_EXEC_PERSISTENT : CFR_EXEC_GRAPH;
@@ -196,7 +198,7 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
   o->n_nodes = c.N; o->n_edges = c.E; o->n_infosets = c.I; o->n_slots = c.A;
   o->n_internal = c.n_int; o->n_decision = c.n_dec; o->n_chance = c.n_chance; o->n_terminal = c.n_term;
   o->depth_blocks = c.D; o->max_actions = c.max_act;
-  o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision);
+  o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision) * (h->order == CFR_ORDER_ALTERNATING ? 2 : 1);
   o->upload_bytes = (int64_t)(h->b_iset_slot.bytes + h->b_iset_mem.bytes + h->b_iset_vb.bytes + h->b_mem_vs.bytes +
                               h->b_ch_vb.bytes + h->b_ch_nch.bytes + h->b_ch_vs.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
                               h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes +
@@ -337,8 +339,10 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
 }
 
 // ------------------------------------------------------------ iteration
+// upd: the players whose sets update (bit 0 player 1, bit 1 player 2); the
+// depth-0 launch of the pass that updates player 2 advances t.
 template <typename T>
-static int launch_bwd(cfr_handle *h, int d, cudaStream_t s) {
+static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3) {
   const LevelWork &w = h->levels[d];
   const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
   const int lanes = h->level_lanes[d];
@@ -346,7 +350,7 @@ static int launch_bwd(cfr_handle *h, int d, cudaStream_t s) {
   const int nb_wide = w.wc1 - w.wc0;
   const int nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;
   CK(launch_bwd_level<T>(h->maxa_tier, lanes, nb_ch + nb_wide + nb_is, s, game_view(h), state_view<T>(h), w, nb_ch,
-                         h->rule, d == 0 ? 1 : 0));
+                         h->rule, upd, (d == 0 && (upd & 2)) ? 1 : 0));
   return CFR_OK;
 }
 
@@ -354,13 +358,17 @@ template <typename T>
 static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
   const Compiled &c = h->c;
   GameView g = game_view(h);
-  for (int64_t d = 0; d < c.D; ++d) {
-    int rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
-    if (rc) return rc;
-  }
-  for (int64_t d = c.D - 1; d >= 0; --d) {
-    int rc = launch_bwd<T>(h, (int)d, s);
-    if (rc) return rc;
+  const int halves = h->order == CFR_ORDER_ALTERNATING ? 2 : 1;
+  for (int hf = 0; hf < halves; ++hf) {
+    const int upd = halves == 2 ? (1 << hf) : 3;
+    for (int64_t d = 0; d < c.D; ++d) {
+      int rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
+      if (rc) return rc;
+    }
+    for (int64_t d = c.D - 1; d >= 0; --d) {
+      int rc = launch_bwd<T>(h, (int)d, s, upd);
+      if (rc) return rc;
+    }
   }
   return CFR_OK;
 }
@@ -398,6 +406,7 @@ static int launch_persistent_form(cfr_handle *h, int64_t n, cudaStream_t s) {
   a.lw = h->p<LevelWork>(h->b_levels);
   a.D = (int)h->c.D;
   a.rule = h->rule;
+  a.order = h->order;
   a.n_iter = n;
   unsigned *bar = h->p<unsigned>(h->b_bar);
   a.bar.count = bar;
@@ -706,30 +715,42 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   return CFR_OK;
 }
 
+// One iteration with an event pair around every launch; under alternating
+// updates the two halves' times of a launch are added.
 template <typename T>
 static int profile_t(cfr_handle *h, double *fwd_ms, double *bwd_ms, cudaStream_t s) {
   const Compiled &c = h->c;
-  std::vector<cudaEvent_t> ev(4 * c.D + 2, nullptr);
+  const int halves = h->order == CFR_ORDER_ALTERNATING ? 2 : 1;
+  std::vector<cudaEvent_t> ev(4 * c.D * halves + 2, nullptr);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   GameView g = game_view(h);
   int rc = CFR_OK;
-  for (int64_t d = 0; d < c.D && rc == CFR_OK; ++d) {
-    CK(cudaEventRecord(ev[2 * d], s));
-    rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
-    CK(cudaEventRecord(ev[2 * d + 1], s));
-  }
-  for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
-    CK(cudaEventRecord(ev[2 * c.D + 2 * d], s));
-    rc = launch_bwd<T>(h, (int)d, s);
-    CK(cudaEventRecord(ev[2 * c.D + 2 * d + 1], s));
+  for (int hf = 0; hf < halves && rc == CFR_OK; ++hf) {
+    const int upd = halves == 2 ? (1 << hf) : 3;
+    cudaEvent_t *e = ev.data() + 4 * c.D * hf;
+    for (int64_t d = 0; d < c.D && rc == CFR_OK; ++d) {
+      CK(cudaEventRecord(e[2 * d], s));
+      rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
+      CK(cudaEventRecord(e[2 * d + 1], s));
+    }
+    for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
+      CK(cudaEventRecord(e[2 * c.D + 2 * d], s));
+      rc = launch_bwd<T>(h, (int)d, s, upd);
+      CK(cudaEventRecord(e[2 * c.D + 2 * d + 1], s));
+    }
   }
   CK(cudaStreamSynchronize(s));
   for (int64_t d = 0; d < c.D; ++d) {
-    float a = 0.f, b = 0.f;
-    CK(cudaEventElapsedTime(&a, ev[2 * d], ev[2 * d + 1]));
-    CK(cudaEventElapsedTime(&b, ev[2 * c.D + 2 * d], ev[2 * c.D + 2 * d + 1]));
-    fwd_ms[d] = a;
-    bwd_ms[d] = b;
+    fwd_ms[d] = 0.0;
+    bwd_ms[d] = 0.0;
+    for (int hf = 0; hf < halves; ++hf) {
+      cudaEvent_t *e = ev.data() + 4 * c.D * hf;
+      float a = 0.f, b = 0.f;
+      CK(cudaEventElapsedTime(&a, e[2 * d], e[2 * d + 1]));
+      CK(cudaEventElapsedTime(&b, e[2 * c.D + 2 * d], e[2 * c.D + 2 * d + 1]));
+      fwd_ms[d] += a;
+      bwd_ms[d] += b;
+    }
   }
   for (auto &e : ev) cudaEventDestroy(e);
   if (rc == CFR_OK) h->iteration_host += 1;
@@ -821,6 +842,7 @@ static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   a.lw = h->p<LevelWork>(h->b_levels);
   a.D = (int)c.D;
   a.rule = h->rule;
+  a.order = h->order;
   a.n_iter = n;
   unsigned *bar = (unsigned *)(sb + off_bar);
   a.bar.count = bar;
@@ -907,8 +929,10 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t ge = nullptr;
+  const int halves = h->order == CFR_ORDER_ALTERNATING ? 2 : 1;
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int gsz : grids) empty_level_kernel<<<std::max(gsz, 1), kThreads, 0, h->cap_stream>>>();
+  for (int hf = 0; hf < halves; ++hf)
+    for (int gsz : grids) empty_level_kernel<<<std::max(gsz, 1), kThreads, 0, h->cap_stream>>>();
   CK(cudaStreamEndCapture(h->cap_stream, &graph));
   cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
   cudaGraphDestroy(graph);
@@ -940,7 +964,7 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
     b.err = h->p<int>(h->b_err);
     b.spin_limit = h->opt.barrier_spin_limit > 0 ? h->opt.barrier_spin_limit : (int64_t)20000000;
     b.expected = (unsigned)h->persist_grid;
-    int n_sync = (int)(2 * c.D);
+    int n_sync = (int)(2 * c.D * halves);
     long long iters = (long long)n;
     void *args[] = {&b, &n_sync, &iters};
     e = cudaMemsetAsync(bar, 0, 4, s);
@@ -1071,6 +1095,7 @@ static int batch_table(cfr_handle *const *hs, int n, const int64_t *iters, int64
     d.rule = h->rule;
     d.n_sets = (int32_t)h->c.I;
     d.root_vs = (int32_t)(h->c.N - 1);
+    d.order = h->order;
   }
   return CFR_OK;
 }

@@ -276,6 +276,33 @@ __device__ __forceinline__ X group_sum_butterfly(X x, unsigned mask) {
   return x;
 }
 
+// ------------------------------------------------------------- update rules
+// CFR+ clamps the cumulative regret at zero; vanilla CFR does not; PCFR+
+// clamps like CFR+ and matches the next strategy against R + r, the
+// iteration's instantaneous regret serving as the prediction (Section 3,
+// update rules).
+constexpr int kRuleCfrPlus = 0, kRuleCfr = 1, kRulePcfrPlus = 2;
+
+// Averaging weight of iteration t (1-based): t, or t^2 under PCFR+.
+__device__ __forceinline__ double avg_weight(long long t, int rule) {
+  const double x = (double)t;
+  return rule == kRulePcfrPlus ? x * x : x;
+}
+
+// One slot's update from its set's totals (instantaneous regret r, average
+// term m): R <- R + r (clamped at 0 except under vanilla CFR), avg += w * m.
+// Returns what regret matching takes the positive part of: the new R, or
+// R + r under PCFR+.
+__device__ __forceinline__ double slot_update(double *R, double *avg, int32_t q, double r, double m, double wt,
+                                              int rule) {
+  double Rn = R[q] + r;
+  if (rule != kRuleCfr) Rn = Rn > 0.0 ? Rn : 0.0;
+  R[q] = Rn;
+  avg[q] += wt * m;
+  const double x = rule == kRulePcfrPlus ? Rn + r : Rn;
+  return x > 0.0 ? x : 0.0;
+}
+
 // ------------------------------------------------------------- backward
 // Narrow chance node i: the sum of its children's values (left to right).
 template <typename T, bool PERSIST>
@@ -417,7 +444,7 @@ __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsign
 // the set's slots runs one lane per action.
 template <typename T, int MAXA, int LANES, bool PERSIST>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                        int lane, unsigned mask, double wt, int rule) {
+                                        int lane, unsigned mask, double wt, int rule, int upd) {
   const int32_t sb = __ldg(g.iset_slot + I);
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
@@ -468,6 +495,8 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
       ps = qs; ir = jr;
     }
   }
+  // alternating updates: the other player's sets only pass their values up
+  if (!(upd & (p2 ? 2 : 1))) return;
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int a = 0; a < MAXA; ++a) {
@@ -479,20 +508,14 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   }
   // every lane now holds the set's totals racc[a], macc[a]
   if (na <= LANES) {
-    // lane a updates slot a: R <- max(R + r, 0) (CFR+), avg += t * m, then
-    // sigma^{t+1} = RM(R); the sum of positive regrets runs in action order
+    // lane a updates slot a (slot_update), then sigma^{t+1} = RM; the sum of
+    // positive parts runs in action order
     T r = T(0), m = T(0);
 #pragma unroll
     for (int a = 0; a < MAXA; ++a)
       if (a == lane) { r = racc[a]; m = macc[a]; }
     double pos = 0.0;
-    if (lane < na) {
-      double Rn = st.R[sb + lane] + (double)r;
-      if (rule == 0) Rn = Rn > 0.0 ? Rn : 0.0;
-      st.R[sb + lane] = Rn;
-      st.avg[sb + lane] += wt * (double)m;
-      pos = Rn > 0.0 ? Rn : 0.0;
-    }
+    if (lane < na) pos = slot_update(st.R, st.avg, sb + lane, (double)r, (double)m, wt, rule);
     if constexpr (sizeof(T) == 8) {
       double tot = 0.0;
       for (int a = 0; a < na; ++a) tot += __shfl_sync(mask, pos, a, LANES);
@@ -509,11 +532,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
 #pragma unroll
     for (int a = 0; a < MAXA; ++a) {
       if (a < na) {
-        double Rn = st.R[sb + a] + (double)racc[a];
-        if (rule == 0) Rn = Rn > 0.0 ? Rn : 0.0;  // CFR+ clamp
-        st.R[sb + a] = Rn;
-        st.avg[sb + a] += wt * (double)macc[a];    // linear averaging, sigma^t
-        pos[a] = Rn > 0.0 ? Rn : 0.0;
+        pos[a] = slot_update(st.R, st.avg, sb + a, (double)racc[a], (double)macc[a], wt, rule);
         tot += pos[a];
       }
     }
@@ -541,7 +560,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
 // finished by a fixed-shape tree. The slot update runs one thread per action.
 template <typename T, int MAXA>
 __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                              double wt, int rule) {
+                                              double wt, int rule, int upd) {
   __shared__ T s_d[kThreads * MAXA], s_m[kThreads * MAXA];  // [member][action]
   __shared__ double s_pos[MAXA];
   const int tid = threadIdx.x;
@@ -589,6 +608,7 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
       }
     }
   }
+  if (!(upd & (p2 ? 2 : 1))) return;  // alternating updates: values only (uniform over the block)
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int a = 0; a < MAXA; ++a) {
@@ -611,15 +631,11 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
       m = s_m[tid];
     }
   }
-  // thread a updates slot a: R <- max(R + r, 0) (CFR+), avg += t * m, then
-  // sigma^{t+1} = RM(R) with the positive regrets summed in action order
+  // thread a updates slot a (slot_update), then sigma^{t+1} = RM with the
+  // positive parts summed in action order
   double pos = 0.0;
   if (tid < na) {
-    double Rn = st.R[sb + tid] + (double)r;
-    if (rule == 0) Rn = Rn > 0.0 ? Rn : 0.0;
-    st.R[sb + tid] = Rn;
-    st.avg[sb + tid] += wt * (double)m;
-    pos = Rn > 0.0 ? Rn : 0.0;
+    pos = slot_update(st.R, st.avg, sb + tid, (double)r, (double)m, wt, rule);
     s_pos[tid] = pos;
   }
   __syncthreads();
@@ -642,7 +658,7 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
 // block).
 template <typename T, int MAXA, int LANES>
 __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1)) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
-                                                            int nb_chance, int rule, int bump_t) {
+                                                            int nb_chance, int rule, int upd, int bump_t) {
   const int nb_wide = w.wc1 - w.wc0;
   if ((int)blockIdx.x < nb_chance) {
     const int32_t stride = nb_chance * blockDim.x;
@@ -652,9 +668,9 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     bwd_wide_chunk<T, false>(g, w, st.v, w.wc0 + (int32_t)blockIdx.x - nb_chance);
   } else if constexpr (LANES == kThreads) {
     const int first = nb_chance + nb_wide;
-    const double wt = (double)(*st.t + 1);
+    const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + ((int)blockIdx.x - first); I < w.is1; I += (int)gridDim.x - first)
-      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule);
+      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd);
   } else {
     constexpr int GPB = kThreads / LANES;
     const int first = nb_chance + nb_wide;
@@ -662,9 +678,9 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     const int ngroups = ((int)gridDim.x - first) * GPB;
     const int lane = threadIdx.x % LANES;
     const unsigned mask = group_mask<LANES>();
-    const double wt = (double)(*st.t + 1);
+    const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule);
+      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd);
   }
   if (bump_t) {  // depth 0 holds only the root: no other block reads t here
     __syncthreads();
@@ -732,12 +748,14 @@ template <typename T> struct PersistArgs {
   const LevelWork *lw;
   int D;
   int rule;
+  int order;  // 0 simultaneous, 1 alternating (two half-iterations)
   long long n_iter;
   Barrier bar;
 };
 
 // All n iterations in one launch; depth levels separated by grid barriers
-// (2D barriers per iteration). The grid is co-resident (cooperative launch).
+// (2D barriers per iteration, 4D under alternating updates). The grid is
+// co-resident (cooperative launch).
 template <typename T, int MAXA, int LANES>
 __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) {
   const long long t0 = __ldcg(a.st.t);
@@ -745,24 +763,28 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
   const int nthr = gridDim.x * blockDim.x;
   const int gid = tid / LANES, ngroups = nthr / LANES, lane = tid % LANES;
   const unsigned mask = group_mask<LANES>();
+  const int halves = a.order ? 2 : 1;  // alternating: player 1's half, then player 2's
   for (long long it = 0; it < a.n_iter; ++it) {
-    for (int d = 0; d < a.D; ++d) {
-      const LevelWork w = a.lw[d];
-      for (int32_t qw = w.ib + (tid & ~31); qw < w.ie; qw += 4 * nthr) {
-        if (w.fan) fwd_int4<T, true, true>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
-        else fwd_int4<T, true, false>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+    const double wt = avg_weight(t0 + it + 1, a.rule);
+    for (int hf = 0; hf < halves; ++hf) {
+      const int upd = a.order ? (1 << hf) : 3;
+      for (int d = 0; d < a.D; ++d) {
+        const LevelWork w = a.lw[d];
+        for (int32_t qw = w.ib + (tid & ~31); qw < w.ie; qw += 4 * nthr) {
+          if (w.fan) fwd_int4<T, true, true>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+          else fwd_int4<T, true, false>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+        }
+        for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
+        if (!grid_sync(a.bar)) return;
       }
-      for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
-      if (!grid_sync(a.bar)) return;
-    }
-    const double wt = (double)(t0 + it + 1);
-    for (int d = a.D - 1; d >= 0; --d) {
-      const LevelWork w = a.lw[d];
-      for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
-      for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
-      for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-        bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule);
-      if (!grid_sync(a.bar)) return;
+      for (int d = a.D - 1; d >= 0; --d) {
+        const LevelWork w = a.lw[d];
+        for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
+        for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
+        for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
+          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd);
+        if (!grid_sync(a.bar)) return;
+      }
     }
   }
   if (tid == 0) *a.st.t = t0 + a.n_iter;

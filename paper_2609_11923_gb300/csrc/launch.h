@@ -10,7 +10,7 @@ namespace cfr {
 
 template <typename T>
 cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, GameView g, StateView<T> st,
-                             LevelWork w, int nb_chance, int rule, int bump);
+                             LevelWork w, int nb_chance, int rule, int upd, int bump);
 
 // query_occupancy != nullptr: only report resident blocks per SM of the
 // chosen instance (nothing is launched).

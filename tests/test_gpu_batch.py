@@ -49,6 +49,27 @@ def test_batched_fp64_matches_oracle():
         cfr.cfr_destroy(h)
 
 
+@pytest.mark.parametrize("rule,orule", [(cfr.RULE_PCFR_PLUS, oracle.PCFR_PLUS), (cfr.RULE_CFR, oracle.CFR)])
+@pytest.mark.parametrize("order", [cfr.ORDER_SIMULTANEOUS, cfr.ORDER_ALTERNATING])
+def test_batched_rules_and_orders_match_oracle(rule, orule, order):
+    specs = [gg.tiny_card(), gg.endgame(5, 4000), gg.random_tree(3, depth=8)]
+    opts = cfr.make_options(precision=cfr.P64, rule=rule, order=order)
+    hs = [cfr.cfr_compile(sp, opts) for sp in specs]
+    pool = serve.DevicePool(sum(cfr.cfr_plan(h) + 512 for h in hs) + 4096)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    for h in hs:
+        n = cfr.cfr_plan(h)
+        cfr.cfr_bind(h, pool.ptr(pool.alloc(n)), n, s)
+    tb = cfr.cfr_batch_table_bytes(len(hs))
+    table = torch.empty(tb + 16, dtype=torch.uint8, device="cuda")
+    cfr.cfr_batch_iterate(hs, 200, (table.data_ptr() + 15) & ~15, tb, 256, 4, s)
+    for sp, h in zip(specs, hs):
+        out = np.empty(cfr.cfr_get_counts(h)["n_slots"])
+        cfr.cfr_avg_strategy(h, out, False, s)
+        np.testing.assert_array_equal(out, oracle.solve(sp, 200, rule=orule, order=order).avg_strategy())
+        cfr.cfr_destroy(h)
+
+
 @pytest.mark.parametrize("threads,lanes", [(256, 4), (1024, 8), (256, 32), (1024, 2)])
 def test_solve_alone_equals_solve_in_mix(threads, lanes):
     specs = mixed_specs(12)

@@ -317,3 +317,55 @@ def test_launch_floor_is_positive_and_leaves_the_state_alone():
     assert before[2] == after[2]
     s.iterate(10)  # the solver still works after the floor measurement
     s.synchronize()
+
+
+RULES = [(cfr.RULE_CFR_PLUS, oracle.CFR_PLUS), (cfr.RULE_CFR, oracle.CFR), (cfr.RULE_PCFR_PLUS, oracle.PCFR_PLUS)]
+
+
+@pytest.mark.parametrize("form", [cfr.EXEC_GRAPH, cfr.EXEC_LEVELS, cfr.EXEC_PERSISTENT])
+@pytest.mark.parametrize("rule,orule", RULES)
+@pytest.mark.parametrize("order", [cfr.ORDER_SIMULTANEOUS, cfr.ORDER_ALTERNATING])
+def test_p64_every_rule_and_order_matches_oracle_bitwise(form, rule, orule, order):
+    g = gg.tiny_card()
+    o = oracle.solve(g, 400, rule=orule, order=order)
+    s = solve_gpu(g, 400, form=form, rule=rule, order=order)
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    R, avg, t = s.get_state()
+    np.testing.assert_array_equal(R, o.R)
+    np.testing.assert_array_equal(avg, o.sbar)
+    assert t == 400
+    np.testing.assert_array_equal(s.current_strategy(), o.current_strategy())
+
+
+@pytest.mark.parametrize("rule,orule", RULES[::2])
+def test_p64_alternating_on_a_random_tree_and_split_calls(rule, orule):
+    g = gg.random_tree(6, depth=9)
+    o = oracle.solve(g, 150, rule=orule, order=oracle.ALTERNATING)
+    s = cfr.Solver(g, precision=cfr.P64, exec_form=cfr.EXEC_GRAPH, rule=rule, order=cfr.ORDER_ALTERNATING)
+    for n in (7, 100, 43):
+        s.iterate(n)
+    s.synchronize()
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    assert abs(s.exploitability() - o.exploitability()) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [cfr.ORDER_SIMULTANEOUS, cfr.ORDER_ALTERNATING])
+def test_p32_pcfr_plus_within_tolerance(order):
+    g = gg.large_card(3, 2, 1, 1)
+    o = oracle.solve(g, 300, rule=oracle.PCFR_PLUS, order=order)
+    s = solve_gpu(g, 300, precision=cfr.P32, rule=cfr.RULE_PCFR_PLUS, order=order)
+    assert abs(s.exploitability() - o.exploitability()) <= 1e-4 * g.pot
+
+
+def test_alternating_counts_twice_the_bytes_and_bad_options_are_rejected():
+    g = gg.tiny_card()
+    a = cfr.cfr_compile(g, cfr.make_options(order=cfr.ORDER_SIMULTANEOUS))
+    b = cfr.cfr_compile(g, cfr.make_options(order=cfr.ORDER_ALTERNATING))
+    try:
+        assert cfr.cfr_get_counts(b)["algo_bytes_per_iter"] == 2 * cfr.cfr_get_counts(a)["algo_bytes_per_iter"]
+    finally:
+        cfr.cfr_destroy(a)
+        cfr.cfr_destroy(b)
+    for kw in ({"order": 2}, {"rule": 3}):
+        with pytest.raises(cfr.CfrError):
+            cfr.cfr_compile(g, cfr.make_options(**kw))
