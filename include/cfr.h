@@ -169,6 +169,20 @@ int cfr_reset(cfr_handle *h, void *stream);
  * Synchronises `stream`. */
 int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream);
 
+/* Rewrites the root's chance distribution, the other input Appendix H
+ * marks mutable without recompilation: prob[n] (host doubles, the root's
+ * outcomes in the spec's order; n must equal the root's child count; each
+ * finite and >= 0). The root must be a chance node (else
+ * CFR_ERR_UNSUPPORTED). The chance products below the root are recomputed in
+ * path order from the retained edge probabilities, so the template is
+ * bitwise the one a fresh compile with these probabilities produces. Works
+ * before cfr_bind (host only; bind uploads it); after bind it also rewrites
+ * the device template and synchronises `stream`. Solver state (R, avg, t)
+ * is kept: call cfr_reset to start a new solve. Ranges over private hands
+ * compose into it: prob[k] = r1[hand1(k)] * r2[hand2(k)] / Z for a deal
+ * root. */
+int cfr_set_root_chance(cfr_handle *h, const double *prob, int64_t n, void *stream);
+
 /* Copies the solver state out / in, host arrays in spec slot order:
  * R[A] and avg[A] (un-normalised strategy sums) as doubles, and t. Under
  * PCFR+ the prediction is not part of the state: cfr_set_state restarts it

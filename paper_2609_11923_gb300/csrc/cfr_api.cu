@@ -583,12 +583,33 @@ extern "C" int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream
   if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_set_payoffs: not bound");
   Compiled &c = h->c;
   for (int64_t x = 0; x < c.N; ++x)
+    if (c.child_begin[x] == c.child_begin[x + 1] && !std::isfinite(payoff[c.spec_of_new[x]]))
+      return set_err(CFR_ERR_ARG, "cfr_set_payoffs: non-finite payoff");
+  for (int64_t x = 0; x < c.N; ++x)
     if (c.child_begin[x] == c.child_begin[x + 1]) {
-      const double u = payoff[c.spec_of_new[x]];
-      if (!std::isfinite(u)) return set_err(CFR_ERR_ARG, "cfr_set_payoffs: non-finite payoff");
-      c.tmpl[x] = c.pc[x] * u;
+      c.u[x] = payoff[c.spec_of_new[x]];
+      c.tmpl[x] = c.pc[x] * c.u[x];
       c.tmpl_vs[c.vslot[x]] = c.tmpl[x];
     }
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = h->precision == CFR_P64 ? init_values<double>(h, s) : init_values<float>(h, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return CFR_OK;
+}
+
+extern "C" int cfr_set_root_chance(cfr_handle *h, const double *prob, int64_t n, void *stream) {
+  if (!h || (!prob && n > 0)) return set_err(CFR_ERR_ARG, "cfr_set_root_chance: null argument");
+  Compiled &c = h->c;
+  if (c.N == 0 || c.child_begin[1] == c.child_begin[0] || c.node_slot[0] >= 0)
+    return set_err(CFR_ERR_UNSUPPORTED, "cfr_set_root_chance: the root is not a chance node");
+  const int64_t nch = c.child_begin[1] - c.child_begin[0];
+  if (n != nch) return set_err(CFR_ERR_ARG, "cfr_set_root_chance: the root has %lld children, got %lld", (long long)nch, (long long)n);
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(prob[k]) || prob[k] < 0.0) return set_err(CFR_ERR_ARG, "cfr_set_root_chance: probability %lld is negative or not finite", (long long)k);
+  for (int64_t k = 0; k < n; ++k) c.edge_p[c.child_begin[0] + k] = prob[k];
+  fold_chance(c);
+  if (!h->bound) return CFR_OK;  // cfr_bind uploads the new template
   cudaStream_t s = (cudaStream_t)stream;
   int rc = h->precision == CFR_P64 ? init_values<double>(h, s) : init_values<float>(h, s);
   if (rc) return rc;

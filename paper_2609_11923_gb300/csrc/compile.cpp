@@ -117,6 +117,8 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
     c.node_slot.assign(N, -1);
     c.pc.assign(N, 0.0);
     c.tmpl.assign(N, 0.0);
+    c.edge_p.assign(N, 1.0);
+    c.u.assign(N, 0.0);
     c.pc[0] = 1.0;
     int64_t next = 1;
     c.n_dec = c.n_chance = c.n_term = c.n_int = 0;
@@ -130,14 +132,16 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
       next += e - b;
       if (k == CFR_TERMINAL) {
         ++c.n_term;
-        c.tmpl[h] = c.pc[h] * s.payoff[sv];  // values template, eq. (template)
+        c.u[h] = s.payoff[sv];
+        c.tmpl[h] = c.pc[h] * c.u[h];  // values template, eq. (template)
         continue;
       }
       ++c.n_int;
       if (k != CFR_CHANCE) c.max_act = std::max<int64_t>(c.max_act, e - b);
       for (int64_t q = b; q < e; ++q) {
         const int32_t ch = c.new_of_spec[s.child[q]];
-        c.pc[ch] = (k == CFR_CHANCE) ? c.pc[h] * s.chance_prob[q] : c.pc[h];
+        if (k == CFR_CHANCE) c.edge_p[ch] = s.chance_prob[q];
+        c.pc[ch] = (k == CFR_CHANCE) ? c.pc[h] * c.edge_p[ch] : c.pc[h];
       }
       if (k == CFR_CHANCE) ++c.n_chance; else ++c.n_dec;
     }
@@ -332,6 +336,22 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
   } catch (const std::bad_alloc &) {
     err = "out of host memory while compiling";
     return CFR_ERR_HOST_MEMORY;
+  }
+}
+
+void fold_chance(Compiled &c) {
+  const int64_t N = c.N;
+  if (N == 0) return;
+  c.pc[0] = 1.0;
+  for (int64_t h = 0; h < N; ++h) {
+    const int32_t cb = c.child_begin[h], ce = c.child_begin[h + 1];
+    if (cb == ce) {  // terminal
+      c.tmpl[h] = c.pc[h] * c.u[h];
+      c.tmpl_vs[c.vslot[h]] = c.tmpl[h];
+      continue;
+    }
+    const bool chance = c.node_slot[h] < 0;
+    for (int32_t ch = cb; ch < ce; ++ch) c.pc[ch] = chance ? c.pc[h] * c.edge_p[ch] : c.pc[h];
   }
 }
 

@@ -75,6 +75,8 @@ struct Compiled {
   std::vector<int32_t> wide_vb, wide_nch, wide_vs;  // [n_wide] the same for wide chance nodes
   std::vector<double> tmpl_vs;       // [N] the values template in slot order
   std::vector<double> pc;            // [N] chance product root..h (retained for set_payoffs)
+  std::vector<double> edge_p;        // [N] probability of the chance edge into h (1 below decision nodes and at the root)
+  std::vector<double> u;             // [N] payoff to player 1 at terminals, 0 elsewhere
   std::vector<double> tmpl;          // [N] pi_c(z) * u(z) at terminals, else 0 (eq. (template))
   std::vector<int32_t> new_of_spec;  // [N] compiled id of each spec node
   std::vector<int32_t> spec_of_new;  // [N]
@@ -85,6 +87,13 @@ struct Compiled {
 
 // Returns CFR_OK or CFR_ERR_INVALID_SPEC / CFR_ERR_HOST_MEMORY with a message.
 int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err);
+
+// Chance folding from the retained edge probabilities and payoffs: the
+// products root..h in path order (pc), the template pi_c(z) u(z) (eq.
+// (template)) in node order and in value-slot order. The same arithmetic as
+// the compile pass, so a rewritten input gives bitwise the template of a
+// fresh compile.
+void fold_chance(Compiled &c);
 
 // Algorithmic device bytes of one iteration (each array element touched the
 // minimum number of times the layout allows; see the design notes).

@@ -3,6 +3,7 @@ compile invariants of the paper (tree coverage, parent depth < child depth,
 D = number of parent depths), validation errors, and the C-ABI surface.
 CPU only: nothing here launches a kernel."""
 import ctypes
+import dataclasses
 import os
 import re
 
@@ -178,3 +179,44 @@ def test_library_exports_every_declared_symbol():
     for n in sorted(names):
         assert hasattr(lib, n), n
     assert names <= set(cfr.EXPORTED)
+
+
+def with_root_chance(g, p):
+    """The same game with the root's outcome probabilities replaced."""
+    cp = np.array(g.chance_prob, dtype=np.float64, copy=True)
+    cp[g.child_begin[0]:g.child_begin[1]] = p
+    return dataclasses.replace(g, chance_prob=cp, _owner=None,
+                               **{f: np.array(getattr(g, f), copy=True) for f in
+                                  ("kind", "infoset", "child_begin", "child", "payoff", "iset_player", "iset_nact")})
+
+
+@pytest.mark.parametrize("name", ["endgame", "card_small", "tiny"])
+def test_set_root_chance_gives_the_template_of_a_fresh_compile(name):
+    g = GAMES[name]()
+    n = int(g.child_begin[1] - g.child_begin[0])
+    p = np.random.default_rng(3).dirichlet(np.ones(n))
+    h1, h2 = cfr.cfr_compile(g), cfr.cfr_compile(with_root_chance(g, p))
+    try:
+        cfr.cfr_set_root_chance(h1, p)
+        for key in ("tmpl", "tmpl_vs"):
+            np.testing.assert_array_equal(cfr.cfr_export_array(h1, key), cfr.cfr_export_array(h2, key))
+        with pytest.raises(cfr.CfrError):
+            cfr.cfr_set_root_chance(h1, p[:-1])  # wrong count
+        q = p.copy()
+        q[0] = -0.1
+        with pytest.raises(cfr.CfrError):
+            cfr.cfr_set_root_chance(h1, q)
+    finally:
+        cfr.cfr_destroy(h1)
+        cfr.cfr_destroy(h2)
+
+
+def test_set_root_chance_needs_a_chance_root():
+    g = gg.random_tree(11, depth=5, p_chance=0.0)  # decision root
+    h = cfr.cfr_compile(g)
+    try:
+        with pytest.raises(cfr.CfrError) as ei:
+            cfr.cfr_set_root_chance(h, np.ones(int(g.child_begin[1] - g.child_begin[0])))
+        assert "not a chance node" in str(ei.value)
+    finally:
+        cfr.cfr_destroy(h)

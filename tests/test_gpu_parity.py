@@ -369,3 +369,19 @@ def test_alternating_counts_twice_the_bytes_and_bad_options_are_rejected():
     for kw in ({"order": 2}, {"rule": 3}):
         with pytest.raises(cfr.CfrError):
             cfr.cfr_compile(g, cfr.make_options(**kw))
+
+
+@pytest.mark.parametrize("form", [cfr.EXEC_GRAPH, cfr.EXEC_PERSISTENT])
+def test_set_root_chance_then_solve_equals_the_oracle_on_the_new_game(form):
+    from tests.test_compiler import with_root_chance
+    g = gg.endgame(5, 4000)
+    n = int(g.child_begin[1] - g.child_begin[0])
+    p = np.random.default_rng(9).dirichlet(np.ones(n))
+    s = solve_gpu(g, 50, form=form)  # a solve under the old distribution first
+    s.set_root_chance(p)
+    s.reset()
+    s.iterate(300)
+    s.synchronize()
+    o = oracle.solve(with_root_chance(g, p), 300)
+    np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
+    assert abs(s.exploitability() - o.exploitability()) <= 1e-12
