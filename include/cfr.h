@@ -239,17 +239,21 @@ int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *graph_ms, d
  * be bound (each to its own arena) and use the same precision, with sets of
  * at most 8 actions. One CTA of `threads` threads (256 or 1024; 0 = 256)
  * runs all iterations of one instance with `lanes` lanes per information set
- * (2, 4, 8 or 32; 0 = 4). A solve's result depends only on its own data and
- * on (threads, lanes): it is bitwise the same alone and in any mix.
+ * (2, 4, 8 or 32; 0 = 4); cfr_batch_iterate can instead give every instance
+ * a thread-block cluster of `cluster` CTAs (2, 4 or 8) that share its work
+ * and meet at the hardware cluster barrier between depths (for large
+ * instances). A solve's result depends only on its own data and on
+ * (threads, lanes, cluster): it is bitwise the same alone and in any mix.
  * table_dev: caller-owned device buffer of at least cfr_batch_table_bytes(n)
  * bytes (16-byte aligned) for the instance descriptors; it must stay
  * untouched until the launch completes. */
 size_t cfr_batch_table_bytes(int n);
 
 /* Runs iters[i] iterations of instance i (iters may be NULL: every
- * instance runs n_iter), asynchronously on `stream`. */
+ * instance runs n_iter), asynchronously on `stream`. cluster: CTAs per
+ * instance (0 or 1 = one CTA; 2, 4 or 8 = a thread-block cluster). */
 int cfr_batch_iterate(cfr_handle *const *handles, int n, const int64_t *iters, int64_t n_iter, void *table_dev,
-                      size_t table_bytes, int threads, int lanes, void *stream);
+                      size_t table_bytes, int threads, int lanes, int cluster, void *stream);
 
 /* Exploitability of every instance's average strategy in one launch; out
  * (host, [4n]) receives per instance (NashConv/2, br1, br2, u). Synchronises

@@ -98,7 +98,7 @@ def _load():
         "cfr_launch_floor": [H, i64, vp, dp, dp],
         "cfr_set_root_chance": [H, dp, i64, vp],
         "cfr_batch_iterate": [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(i64), i64, vp, ctypes.c_size_t,
-                              ctypes.c_int, ctypes.c_int, vp],
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
         "cfr_batch_exploitability": [ctypes.POINTER(H), ctypes.c_int, dp, vp, ctypes.c_size_t, ctypes.c_int,
                                      ctypes.c_int, vp],
     }
@@ -301,13 +301,14 @@ def _handles(hs):
 
 
 def cfr_batch_iterate(hs, n_iter, table_ptr: int, table_bytes: int, threads: int = 0, lanes: int = 0,
-                      stream: int = 0, iters=None) -> None:
-    """n_iter iterations of every handle in one launch (or iters[i] each)."""
+                      stream: int = 0, iters=None, cluster: int = 1) -> None:
+    """n_iter iterations of every handle in one launch (or iters[i] each);
+    cluster > 1 gives every instance a thread-block cluster of that many CTAs."""
     it = None
     if iters is not None:
         it = (ctypes.c_int64 * len(hs))(*[int(x) for x in iters])
     _check(_lib.cfr_batch_iterate(_handles(hs), len(hs), it, n_iter, table_ptr, table_bytes, threads, lanes,
-                                  stream))
+                                  cluster, stream))
 
 
 def cfr_batch_exploitability(hs, table_ptr: int, table_bytes: int, threads: int = 0, lanes: int = 0,

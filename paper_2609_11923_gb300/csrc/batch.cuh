@@ -4,11 +4,16 @@
 // CFR+ iterations with __syncthreads() between depth levels (no grid
 // barrier, no cross-CTA traffic), so a batch of hundreds of uneven
 // subgames is one launch whose CTAs the hardware schedules as SMs free up.
+// Large instances instead get a thread-block cluster of several CTAs (the
+// clustered instances of the kernel, launched with a cluster dimension):
+// the cluster's CTAs share each depth's work and meet at the hardware
+// cluster barrier (barrier.cluster, release/acquire) between depths, and
+// read the state arrays through L2 because their L1s are not coherent.
 // Each instance's arithmetic depends only on its own arrays and on the
-// launch shape (THREADS, LANES): a solve gives bitwise the same result alone
-// and inside any mix run with the same shape. The per-level device
-// functions are the ones of kernels.cuh; wide chance nodes are summed by the
-// whole CTA in a fixed order.
+// launch shape (THREADS, LANES, cluster size): a solve gives bitwise the
+// same result alone and inside any mix run with the same shape. The
+// per-level device functions are the ones of kernels.cuh; wide chance nodes
+// are summed by one CTA in a fixed order.
 #pragma once
 #include "kernels.cuh"
 
@@ -54,14 +59,35 @@ __device__ __forceinline__ double cta_sum(double x, double *sm) {
   return r;
 }
 
-// Wide chance node inside one CTA: its internal children copy its reach.
-template <typename T>
-__device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach, int32_t wi) {
+// Cluster geometry (1 and 0 outside a cluster launch) and the barrier
+// between depths: the CTA barrier, or the cluster barrier whose release /
+// acquire makes each CTA's global writes visible to the others.
+__device__ __forceinline__ unsigned cluster_ncta() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+template <bool CLUSTERED>
+__device__ __forceinline__ void level_sync() {
+  if constexpr (CLUSTERED)
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  else
+    __syncthreads();
+}
+
+// Wide chance node: its internal children copy its reach (thread ct of NT).
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach, int32_t wi, int ct, int NT) {
   const int32_t ir = __ldg(g.wide_irank + wi);
   const int32_t off = __ldg(g.int_cirank + ir);
   const int32_t nch = __ldg(g.big_irank + off);
-  const vec2_t<T> r = reach[ir];
-  for (int32_t j = threadIdx.x; j < nch; j += blockDim.x) {
+  const vec2_t<T> r = ldm<PERSIST>(reach + ir);
+  for (int32_t j = ct; j < nch; j += NT) {
     const int32_t c = __ldg(g.big_irank + off + 1 + j);
     if (c >= 0) reach[c] = r;
   }
@@ -69,29 +95,32 @@ __device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach
 
 // Wide chance node wi inside one CTA: value = sum of the children's values.
 // P64 sums left to right (thread 0); P32 uses the fixed-shape CTA tree.
-template <typename T, int THREADS>
+template <typename T, int THREADS, bool PERSIST>
 __device__ __forceinline__ void cta_bwd_wide(const GameView &g, T *v, int32_t wi, double *sm) {
   const int32_t h = __ldg(g.wide_vs + wi);
   const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   if constexpr (sizeof(T) == 8) {
     if (threadIdx.x == 0) {
       T s = T(0);
-      for (int32_t c = cb; c < ce; ++c) s = s + v[c];
+      for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
       v[h] = s;
     }
   } else {
     double x = 0.0;
-    for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) x += (double)v[c];
+    for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) x += (double)ldm<PERSIST>(v + c);
     x = cta_sum<THREADS>(x, sm);
     if (threadIdx.x == 0) v[h] = (T)x;
   }
 }
 
-template <typename T, int MAXA, int LANES, int THREADS>
+template <typename T, int MAXA, int LANES, int THREADS, bool CLUSTERED>
 __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *table, int n_inst) {
   __shared__ double sm[THREADS];
-  const int inst = blockIdx.x;
-  if (inst >= n_inst) return;
+  const int ncta = CLUSTERED ? (int)cluster_ncta() : 1;   // CTAs sharing this instance
+  const int rank = CLUSTERED ? (int)cluster_rank() : 0;
+  const int inst = (int)blockIdx.x / ncta;
+  if (inst >= n_inst) return;  // the whole cluster leaves together
+  const int ct = rank * THREADS + (int)threadIdx.x, NT = ncta * THREADS;
   const InstDesc in = table[inst];
   StateView<T> st;
   st.reach = (vec2_t<T> *)in.reach;
@@ -101,8 +130,8 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
   st.avg = in.avg;
   st.t = in.t;
   const long long t0 = *in.t;
-  const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;
-  constexpr int NG = THREADS / LANES;
+  const int lane = threadIdx.x % LANES, gid = ct / LANES;
+  const int NG = NT / LANES;
   const unsigned mask = group_mask<LANES>();
   const int halves = in.order ? 2 : 1;  // alternating: player 1's half, then player 2's
   for (long long it = 0; it < in.n_iter; ++it) {
@@ -111,25 +140,26 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
       const int upd = in.order ? (1 << hf) : 3;
       for (int d = 0; d < in.D; ++d) {
         const LevelWork w = in.lw[d];
-        for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
-          if (w.fan) fwd_int4<T, false, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
-          else fwd_int4<T, false, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), THREADS, w.ie);
+        for (int32_t qw = w.ib + rank * THREADS + (threadIdx.x & ~31); qw < w.ie; qw += 4 * NT) {
+          if (w.fan) fwd_int4<T, CLUSTERED, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), NT, w.ie);
+          else fwd_int4<T, CLUSTERED, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), NT, w.ie);
         }
-        for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T>(in.g, st.reach, i);
-        __syncthreads();
+        for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T, CLUSTERED>(in.g, st.reach, i, ct, NT);
+        level_sync<CLUSTERED>();
       }
       for (int d = in.D - 1; d >= 0; --d) {
         const LevelWork w = in.lw[d];
-        for (int32_t i = w.ch0 + threadIdx.x; i < w.ch1; i += THREADS)
-          bwd_chance<T, false>(in.g, st.v, i);
-        for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS>(in.g, st.v, i, sm);
+        for (int32_t i = w.ch0 + ct; i < w.ch1; i += NT)
+          bwd_chance<T, CLUSTERED>(in.g, st.v, i);
+        if (rank == 0)
+          for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
         for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-          bwd_set<T, MAXA, LANES, false>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
-        __syncthreads();
+          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
+        level_sync<CLUSTERED>();
       }
     }
   }
-  if (threadIdx.x == 0) *in.t = t0 + in.n_iter;
+  if (ct == 0) *in.t = t0 + in.n_iter;
 }
 
 // Exploitability of every instance's average strategy (FP64), one CTA each:
@@ -156,7 +186,7 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
       if (w.fan) fwd_int4<double, false, true>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
       else fwd_int4<double, false, false>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
     }
-    for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double>(g, in.reach2, i);
+    for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double, false>(g, in.reach2, i, threadIdx.x, THREADS);
     __syncthreads();
   }
   const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;

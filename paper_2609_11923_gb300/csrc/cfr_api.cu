@@ -1124,7 +1124,7 @@ static int batch_table(cfr_handle *const *hs, int n, const int64_t *iters, int64
 extern "C" size_t cfr_batch_table_bytes(int n) { return n > 0 ? sizeof(InstDesc) * (size_t)n : 0; }
 
 extern "C" int cfr_batch_iterate(cfr_handle *const *hs, int n, const int64_t *iters, int64_t n_iter, void *table_dev,
-                                 size_t table_bytes, int threads, int lanes, void *stream) {
+                                 size_t table_bytes, int threads, int lanes, int cluster, void *stream) {
   std::vector<InstDesc> tab;
   int maxa = 4, prec = 0;
   int rc = batch_table(hs, n, iters, n_iter, table_dev, table_bytes, &maxa, &prec, tab);
@@ -1133,10 +1133,14 @@ extern "C" int cfr_batch_iterate(cfr_handle *const *hs, int n, const int64_t *it
   if (lanes == 0) lanes = 4;
   if ((threads != 256 && threads != 1024) || (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32))
     return set_err(CFR_ERR_ARG, "batch: threads must be 256 or 1024 and lanes 2, 4, 8 or 32");
+  if (cluster == 0) cluster = 1;
+  if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
+    return set_err(CFR_ERR_ARG, "batch: cluster must be 1, 2, 4 or 8 CTAs per instance");
+  if (n == 0) return CFR_OK;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(table_dev, tab.data(), sizeof(InstDesc) * (size_t)n, cudaMemcpyHostToDevice, s));
-  if (prec == CFR_P64) CK(launch_batch_iterate<double>(maxa, lanes, threads, n, s, (const InstDesc *)table_dev));
-  else CK(launch_batch_iterate<float>(maxa, lanes, threads, n, s, (const InstDesc *)table_dev));
+  if (prec == CFR_P64) CK(launch_batch_iterate<double>(maxa, lanes, threads, cluster, n, s, (const InstDesc *)table_dev));
+  else CK(launch_batch_iterate<float>(maxa, lanes, threads, cluster, n, s, (const InstDesc *)table_dev));
   for (int i = 0; i < n; ++i) hs[i]->iteration_host += tab[i].n_iter;
   return CFR_OK;
 }

@@ -27,6 +27,7 @@ cudaError_t launch_br_level(int maxa, int lanes, int grid, cudaStream_t s, GameV
 
 namespace cfr {
 template <typename T>
-cudaError_t launch_batch_iterate(int maxa, int lanes, int threads, int n, cudaStream_t s, const InstDesc *table);
+cudaError_t launch_batch_iterate(int maxa, int lanes, int threads, int cluster, int n, cudaStream_t s,
+                                 const InstDesc *table);
 cudaError_t launch_batch_br(int maxa, int lanes, int threads, int n, cudaStream_t s, const InstDesc *table);
 }  // namespace cfr

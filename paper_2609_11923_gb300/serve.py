@@ -8,7 +8,12 @@ active solve (one CTA per solve), followed by ONE batched exploitability
 launch. Solves that reach `target * pot` exploitability (or `max_iters`)
 retire, free their memory, and the next arrivals are admitted before the
 next round, so work that arrives while others are on the GPU overlaps with
-them. A solve's iterates do not depend on what else is in the batch.
+them. Requests of at least `big_edges` edges run as thread-block clusters of
+`cluster` CTAs (a second batched launch on a side stream, concurrent with
+the one-CTA launch of the rest), so one large subgame no longer holds every
+round to the speed of a single SM. Whether a request is large depends only
+on the request, so a solve's iterates do not depend on what else is in the
+batch.
 """
 from __future__ import annotations
 
@@ -101,13 +106,15 @@ class _Active:
     off: int
     nbytes: int
     admitted: float
+    big: bool = False
     done: int = 0
 
 
 class Server:
     def __init__(self, pool_bytes: int, max_active: int = 256, precision: int = cfr.P32, threads: int = 256,
                  lanes: int = 4, check_every: int = 50, max_iters: int = 5000, target: float = 1e-3,
-                 compile_workers: int = 8, keep_strategies: bool = False, device="cuda"):
+                 compile_workers: int = 8, keep_strategies: bool = False, device="cuda",
+                 big_edges: int = 200_000, cluster: int = 8, big_threads: int = 1024, big_lanes: int = 8):
         import torch
 
         self.torch = torch
@@ -115,13 +122,21 @@ class Server:
         self.max_active = max_active
         self.opts = cfr.make_options(precision=precision, exec_form=cfr.EXEC_LEVELS)
         self.threads, self.lanes = threads, lanes
+        self.big_edges, self.cluster = big_edges, cluster
+        self.big_threads, self.big_lanes = big_threads, big_lanes
         self.check_every, self.max_iters, self.target = check_every, max_iters, target
         self.keep = keep_strategies
         self.table_bytes = cfr.cfr_batch_table_bytes(max_active)
         self.table = torch.empty(self.table_bytes + 16, dtype=torch.uint8, device=device)
         self.table_ptr = (self.table.data_ptr() + 15) & ~15
+        self.table2 = torch.empty(self.table_bytes + 16, dtype=torch.uint8, device=device)
+        self.table2_ptr = (self.table2.data_ptr() + 15) & ~15
+        self.side = torch.cuda.Stream(device=device)
         self.workers = ThreadPoolExecutor(max_workers=compile_workers)
         self.rounds = 0
+
+    def is_big(self, spec) -> bool:
+        return self.cluster > 1 and int(spec.n_edges) >= self.big_edges
 
     def _stream(self) -> int:
         return int(self.torch.cuda.current_stream().cuda_stream)
@@ -157,14 +172,25 @@ class Server:
                 if got is None:
                     break  # memory full: wait for retirements
                 waiting.popleft()
-                active.append(_Active(r, h, got[0], got[1], time.perf_counter() - t0))
+                active.append(_Active(r, h, got[0], got[1], time.perf_counter() - t0, self.is_big(r.spec)))
             if not active:
                 nxt = pending[0].arrival if pending else now + 1e-3
                 time.sleep(max(0.0, min(nxt - (time.perf_counter() - t0), 2e-3)))
                 continue
+            active.sort(key=lambda a: a.big)  # one-CTA solves first, clusters after
             hs = [a.h for a in active]
             iters = [min(self.check_every, self.max_iters - a.done) for a in active]
-            cfr.cfr_batch_iterate(hs, 0, self.table_ptr, self.table_bytes, self.threads, self.lanes, s, iters=iters)
+            nb = sum(1 for a in active if a.big)
+            ns = len(active) - nb
+            if nb:  # the large solves as clusters on the side stream, concurrently
+                self.side.wait_stream(self.torch.cuda.current_stream())
+                cfr.cfr_batch_iterate(hs[ns:], 0, self.table2_ptr, self.table_bytes, self.big_threads, self.big_lanes,
+                                      int(self.side.cuda_stream), iters=iters[ns:], cluster=self.cluster)
+            if ns:
+                cfr.cfr_batch_iterate(hs[:ns], 0, self.table_ptr, self.table_bytes, self.threads, self.lanes, s,
+                                      iters=iters[:ns])
+            if nb:
+                self.torch.cuda.current_stream().wait_stream(self.side)
             ex = cfr.cfr_batch_exploitability(hs, self.table_ptr, self.table_bytes, self.threads, self.lanes, s)
             self.rounds += 1
             keep = []

@@ -121,19 +121,63 @@ def test_server_continuous_batching_results_equal_alone():
     sizes = sorted(cfr.cfr_plan(h) for h in hs0)
     for h in hs0:
         cfr.cfr_destroy(h)
+    # requests of 8,000 edges or more run as 4-CTA clusters on the side stream
     srv = serve.Server(pool_bytes=4 * sizes[-1] + 4096, max_active=64, check_every=50, max_iters=600,
-                       target=1e-3, keep_strategies=True)
+                       target=1e-3, keep_strategies=True, big_edges=8000, cluster=4)
     res = srv.serve(reqs)
     srv.close()
     assert sorted(r.rid for r in res) == list(range(len(specs)))
     assert srv.rounds > 1
+    assert 0 < sum(srv.is_big(sp) for sp in specs) < len(specs)  # both launch kinds ran
     for r in res:
         assert r.finished >= r.admitted >= r.arrival - 1e-9
         assert r.exploitability <= 1e-3 * r.pot or r.iterations == 600
         # the same solve alone, same iteration count and launch shape
         p2, h2, t2, tp2, tb2, s = bound([specs[r.rid]])
-        cfr.cfr_batch_iterate(h2, r.iterations, tp2, tb2, srv.threads, srv.lanes, s)
+        if srv.is_big(specs[r.rid]):
+            cfr.cfr_batch_iterate(h2, r.iterations, tp2, tb2, srv.big_threads, srv.big_lanes, s, cluster=srv.cluster)
+        else:
+            cfr.cfr_batch_iterate(h2, r.iterations, tp2, tb2, srv.threads, srv.lanes, s)
         alone = np.empty(len(r.strategy))
         cfr.cfr_avg_strategy(h2[0], alone, False, s)
         np.testing.assert_array_equal(r.strategy, alone)
         cfr.cfr_destroy(h2[0])
+
+
+@pytest.mark.parametrize("cluster", [2, 8])
+def test_clustered_fp64_matches_oracle(cluster):
+    # a wide deal root (summed by the cluster's first CTA), a deep random tree
+    # and card games, each instance shared by `cluster` CTAs
+    specs = [gg.endgame(2, 100000), gg.random_tree(3, depth=10), gg.large_card(3, 2, 1, 1), gg.tiny_card()]
+    pool, hs, table, tp, tb, s = bound(specs, cfr.P64)
+    cfr.cfr_batch_iterate(hs, 120, tp, tb, 1024, 8, s, cluster=cluster)
+    for sp, h in zip(specs, hs):
+        out = np.empty(cfr.cfr_get_counts(h)["n_slots"])
+        cfr.cfr_avg_strategy(h, out, False, s)
+        np.testing.assert_array_equal(out, oracle.solve(sp, 120).avg_strategy())
+        cfr.cfr_destroy(h)
+
+
+def test_clustered_fp32_alone_equals_in_mix():
+    specs = mixed_specs(9, seed0=300)
+    pool, hs, table, tp, tb, s = bound(specs)
+    iters = [80 + 11 * i for i in range(len(specs))]
+    cfr.cfr_batch_iterate(hs, 0, tp, tb, 256, 8, s, iters=iters, cluster=4)
+    for i in (0, 4, 8):
+        p2, h2, t2, tp2, tb2, _ = bound([specs[i]])
+        cfr.cfr_batch_iterate(h2, iters[i], tp2, tb2, 256, 8, s, cluster=4)
+        a = np.empty(cfr.cfr_get_counts(hs[i])["n_slots"])
+        b = np.empty_like(a)
+        cfr.cfr_avg_strategy(hs[i], a, False, s)
+        cfr.cfr_avg_strategy(h2[0], b, False, s)
+        np.testing.assert_array_equal(a, b)
+        cfr.cfr_destroy(h2[0])
+    for h in hs:
+        cfr.cfr_destroy(h)
+
+
+def test_cluster_size_is_checked():
+    pool, hs, table, tp, tb, s = bound([gg.tiny_card()])
+    with pytest.raises(cfr.CfrError):
+        cfr.cfr_batch_iterate(hs, 1, tp, tb, 256, 4, s, cluster=3)
+    cfr.cfr_destroy(hs[0])
