@@ -339,7 +339,6 @@ def run_ours(args):
                    "precision": args.precision + (" (FP64 regret/average accumulators)" if prec == cfr.P32 else ""),
                    "exec_form": args.exec_form, "pot": pot, "parallelism": "replicas x%d" % world,
                    "lanes_per_set_by_depth": [int(x) for x in lanes],
-                   "values_gathered_by_depth": [int(x) for x in cfr.cfr_export_array(solver.h, "value_modes")],
                    "autotuned": not args.no_autotune,
                    "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % (solver.arena_bytes / 1e9)},
         "iters_per_s": world * iters_per_s,

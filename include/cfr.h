@@ -72,7 +72,6 @@ enum { CFR_P64 = 0, CFR_P32 = 1 };
 enum { CFR_EXEC_AUTO = 0, CFR_EXEC_LEVELS = 1, CFR_EXEC_GRAPH = 2, CFR_EXEC_PERSISTENT = 3 };
 enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1, CFR_RULE_PCFR_PLUS = 2 };
 enum { CFR_ORDER_SIMULTANEOUS = 0, CFR_ORDER_ALTERNATING = 1 };
-enum { CFR_VALUES_AUTO = 0, CFR_VALUES_GATHER = 1, CFR_VALUES_IN_PLACE = 2 };
 
 typedef struct cfr_options {
   /* CFR_P64: every value in FP64 (the parity mode). CFR_P32: reach, values,
@@ -101,13 +100,6 @@ typedef struct cfr_options {
    * player 2's with player 1's new strategy; each half accumulates only its
    * player's average (Section 3; Section 4.2 runs the body twice). */
   int order;
-  /* How each depth's internal nodes pass their values to their parents
-   * (the same arithmetic either way): CFR_VALUES_GATHER writes them
-   * coalesced in the order they are computed and the parents gather them;
-   * CFR_VALUES_IN_PLACE writes each into the slot its parent reads (a
-   * scattered write); CFR_VALUES_AUTO starts with GATHER everywhere and lets
-   * cfr_autotune pick per depth by timing both. */
-  int value_mode;
 } cfr_options;
 
 typedef struct cfr_counts {
@@ -213,9 +205,7 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * 22 ch_vb, 23 ch_nch, 24 ch_vs (per chance node of list 6: first child
  * slot, child count, own slot), 25 wide_vb, 26 wide_nch, 27 wide_vs (the
  * same for chance nodes with more than 1024 children), 28 template values
- * in value-slot order [N] (doubles), 29 slot_int[ceil(N/32)] (bit s set:
- * value slot s belongs to an internal node), 30 the value mode of each
- * depth (1 through vm, 0 in place; a runtime choice).
+ * in value-slot order [N] (doubles).
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);
@@ -223,9 +213,7 @@ int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity
 /* Autotuner for the thread-to-work mapping: for every depth it times the
  * backward launch with each supported number of lanes per information set
  * (1, 2, 4, 8, 16, 32, and 256 = one block per set when sets have at most 8
- * actions; `reps` launches each) and keeps the fastest; with
- * CFR_VALUES_AUTO it then picks every depth's value mode by timing whole
- * iterations in both (three alternating samples each); in the
+ * actions; `reps` launches each) and keeps the fastest; in the
  * persistent form it also times whole persistent iterations per lane count.
  * Trial launches overwrite the solver state, so the call ends by resetting it
  * (as cfr_reset) and dropping a captured graph. The chosen counts are
@@ -234,15 +222,6 @@ int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity
  * iterates; pin it with cfr_options.lanes_per_set for bitwise repeatability
  * across processes. Synchronises `stream`. */
 int cfr_autotune(cfr_handle *h, int reps, void *stream);
-
-/* Manual form of what cfr_autotune chooses, for one depth: lanes per
- * information set of its backward launch (0 keeps the current count; else
- * as cfr_options.lanes_per_set) and how its nodes pass values up (gather:
- * 1 through the coalesced value array, 0 in place, -1 keeps the current
- * mode). Results do not depend on either in FP64; in FP32 the lane count
- * fixes the shape of the member sums. Drops a captured graph; synchronises
- * `stream`. */
-int cfr_tune_level(cfr_handle *h, int depth, int lanes, int gather, void *stream);
 
 /* The launch floor of one iteration (no counterpart in the paper's API; its
  * Section 4.3 discusses the graph-launch floor): the mean time of one
@@ -301,8 +280,7 @@ int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *s
  * The paper has no counterpart to this entry point.
  * It runs n iterations with the persistent kernel, exactly as the
  * CFR_EXEC_PERSISTENT form does, but takes the per-iteration scratch (reach
- * lanes and values of the internal nodes, wide-node partial sums,
- * grid-barrier words) from one
+ * lanes, node values, wide-node partial sums, grid-barrier words) from one
  * static 12 MiB device array compiled into the library (held on every GPU
  * that loads the library, until the process exits) instead of the arena.
  * The arena bound with cfr_bind still holds the inputs and outputs: the
@@ -311,10 +289,9 @@ int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *s
  * a device resolves the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
  * Limits: games whose scratch exceeds the array are rejected with
- * CFR_ERR_ARG; the scratch is both reach lanes and the value of every
- * internal node, at most 24 bytes per node in FP64 and 12 in FP32 (about
- * 524,000 and 1,048,000 nodes for any tree shape; the value slots, which do
- * not change while iterating, stay in the arena). Every call re-initialises the part of the array it uses.
+ * CFR_ERR_ARG; the scratch is both reach lanes of every internal node and
+ * every node's value, at most 24 bytes per node in FP64 and 12 in FP32
+ * (about 524,000 and 1,048,000 nodes for any tree shape). Every call re-initialises the part of the array it uses.
  * All calls share the one array, so calls that overlap on the GPU (other
  * streams, other threads, other handles) race: serialise them. Synchronises
  * `stream`; a barrier timeout returns CFR_ERR_TIMEOUT. */

@@ -27,14 +27,12 @@ P64, P32 = 0, 1
 EXEC_AUTO, EXEC_LEVELS, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2, 3
 RULE_CFR_PLUS, RULE_CFR, RULE_PCFR_PLUS = 0, 1, 2
 ORDER_SIMULTANEOUS, ORDER_ALTERNATING = 0, 1
-VALUES_AUTO, VALUES_GATHER, VALUES_IN_PLACE = 0, 1, 2
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
           "spec_slot_of": 11, "level_lanes": 12, "int_slot": 13, "int_mask": 14, "int_cirank": 15,
           "big_irank": 16, "mem_irank": 17, "level_int": 18, "vslot": 19, "iset_vb": 20, "mem_vs": 21,
-          "ch_vb": 22, "ch_nch": 23, "ch_vs": 24, "wide_vb": 25, "wide_nch": 26, "wide_vs": 27, "tmpl_vs": 28,
-          "slot_int": 29, "value_modes": 30}
+          "ch_vb": 22, "ch_nch": 23, "ch_vs": 24, "wide_vb": 25, "wide_nch": 26, "wide_vs": 27, "tmpl_vs": 28}
 
 
 class CfrError(RuntimeError):
@@ -56,7 +54,7 @@ class Options(ctypes.Structure):
     _fields_ = [
         ("precision", ctypes.c_int), ("exec_form", ctypes.c_int), ("rule", ctypes.c_int),
         ("lanes_per_set", ctypes.c_int), ("persistent_ctas", ctypes.c_int),
-        ("barrier_spin_limit", ctypes.c_int64), ("order", ctypes.c_int), ("value_mode", ctypes.c_int),
+        ("barrier_spin_limit", ctypes.c_int64), ("order", ctypes.c_int),
     ]
 
 
@@ -99,7 +97,6 @@ def _load():
         "cfr_autotune": [H, ctypes.c_int, vp],
         "cfr_launch_floor": [H, i64, vp, dp, dp],
         "cfr_set_root_chance": [H, dp, i64, vp],
-        "cfr_tune_level": [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
         "cfr_batch_iterate": [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(i64), i64, vp, ctypes.c_size_t,
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
         "cfr_batch_exploitability": [ctypes.POINTER(H), ctypes.c_int, dp, vp, ctypes.c_size_t, ctypes.c_int,
@@ -124,7 +121,7 @@ EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterat
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
             "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune",
             "cfr_batch_table_bytes", "cfr_batch_iterate", "cfr_batch_exploitability", "cfr_launch_floor",
-            "cfr_set_root_chance", "cfr_tune_level"]
+            "cfr_set_root_chance"]
 
 
 def _check(rc: int) -> None:
@@ -158,12 +155,11 @@ def spec_struct(spec) -> Tuple[GameSpecC, list]:
 
 
 def make_options(precision=P32, exec_form=EXEC_AUTO, rule=RULE_CFR_PLUS, lanes_per_set=0, persistent_ctas=0,
-                 barrier_spin_limit=0, order=ORDER_SIMULTANEOUS, value_mode=VALUES_AUTO) -> Options:
+                 barrier_spin_limit=0, order=ORDER_SIMULTANEOUS) -> Options:
     o = Options()
     o.precision, o.exec_form, o.rule = precision, exec_form, rule
     o.lanes_per_set, o.persistent_ctas, o.barrier_spin_limit = lanes_per_set, persistent_ctas, barrier_spin_limit
     o.order = order
-    o.value_mode = value_mode
     return o
 
 
@@ -273,10 +269,6 @@ def cfr_level_bytes(h: int, level: int) -> Tuple[int, int]:
     return f.value, b.value
 
 
-def cfr_tune_level(h: int, depth: int, lanes: int = 0, gather: int = -1, stream: int = 0) -> None:
-    _check(_lib.cfr_tune_level(h, depth, lanes, gather, stream))
-
-
 def cfr_set_root_chance(h: int, prob, stream: int = 0) -> None:
     p = np.ascontiguousarray(prob, dtype=np.float64)
     _check(_lib.cfr_set_root_chance(h, _dp(p), len(p), stream))
@@ -342,13 +334,12 @@ class Solver:
 
     def __init__(self, spec, precision: int = P32, exec_form: int = EXEC_AUTO, rule: int = RULE_CFR_PLUS,
                  lanes_per_set: int = 0, persistent_ctas: int = 0, barrier_spin_limit: int = 0,
-                 device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS,
-                 value_mode: int = VALUES_AUTO):
+                 device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS):
         import torch
 
         self.torch = torch
         self.opts = make_options(precision, exec_form, rule, lanes_per_set, persistent_ctas, barrier_spin_limit,
-                                 order, value_mode)
+                                 order)
         self.h = cfr_compile(spec, self.opts)
         self.counts = cfr_get_counts(self.h)
         self.n_slots = self.counts["n_slots"]

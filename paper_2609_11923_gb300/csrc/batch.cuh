@@ -25,7 +25,6 @@ struct InstDesc {
   GameView g;
   void *reach;
   void *v;
-  void *vm;
   void *sigma;
   double *R;
   double *avg;
@@ -97,21 +96,20 @@ __device__ __forceinline__ void cta_fwd_wide(const GameView &g, vec2_t<T> *reach
 // Wide chance node wi inside one CTA: value = sum of the children's values.
 // P64 sums left to right (thread 0); P32 uses the fixed-shape CTA tree.
 template <typename T, int THREADS, bool PERSIST>
-__device__ __forceinline__ void cta_bwd_wide(const GameView &g, const StateView<T> &st, int32_t wi, int gath,
-                                             double *sm) {
-  T *vh = gath ? st.vm + g.n_dec + g.n_narrow + wi : st.v + __ldg(g.wide_vs + wi);
+__device__ __forceinline__ void cta_bwd_wide(const GameView &g, T *v, int32_t wi, double *sm) {
+  const int32_t h = __ldg(g.wide_vs + wi);
   const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   if constexpr (sizeof(T) == 8) {
     if (threadIdx.x == 0) {
       T s = T(0);
-      for (int32_t c = cb; c < ce; ++c) s = s + slot_value<T, PERSIST>(g, st, c);
-      *vh = s;
+      for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
+      v[h] = s;
     }
   } else {
     double x = 0.0;
-    for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) x += (double)slot_value<T, PERSIST>(g, st, c);
+    for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) x += (double)ldm<PERSIST>(v + c);
     x = cta_sum<THREADS>(x, sm);
-    if (threadIdx.x == 0) *vh = (T)x;
+    if (threadIdx.x == 0) v[h] = (T)x;
   }
 }
 
@@ -127,7 +125,6 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
   StateView<T> st;
   st.reach = (vec2_t<T> *)in.reach;
   st.v = (T *)in.v;
-  st.vm = (T *)in.vm;
   st.sigma = (T *)in.sigma;
   st.R = in.R;
   st.avg = in.avg;
@@ -153,11 +150,11 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
       for (int d = in.D - 1; d >= 0; --d) {
         const LevelWork w = in.lw[d];
         for (int32_t i = w.ch0 + ct; i < w.ch1; i += NT)
-          bwd_chance<T, CLUSTERED>(in.g, st, i, w.gath);
+          bwd_chance<T, CLUSTERED>(in.g, st.v, i);
         if (rank == 0)
-          for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st, i, w.gath, sm);
+          for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
         for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd, w.gath);
+          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
         level_sync<CLUSTERED>();
       }
     }

@@ -56,7 +56,7 @@ struct cfr_handle {
   std::vector<LevelWork> levels;
   // arena layout
   Buf b_iset_slot, b_iset_mem, b_iset_vb, b_mem_vs, b_ch_vb, b_ch_nch, b_ch_vs, b_spec_slot, b_levels;
-  Buf b_wide_vb, b_wide_nch, b_wide_vs, b_wide_chunk, b_wide_part, b_wide_cnt, b_slot_int, b_slot_int_all, b_vm;
+  Buf b_wide_vb, b_wide_nch, b_wide_vs, b_wide_chunk, b_wide_part, b_wide_cnt;
   Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_mem_irank, b_wide_irank;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
   size_t plan_bytes = 0;
@@ -98,8 +98,6 @@ static void plan(cfr_handle *h) {
   take(h->b_wide_nch, 4 * c.n_wide);
   take(h->b_wide_vs, 4 * c.n_wide);
   take(h->b_wide_chunk, 4 * (c.n_wide + 1));
-  take(h->b_slot_int, 4 * c.slot_int.size());      // active internal-slot bits (per-depth modes applied)
-  take(h->b_slot_int_all, 4 * c.slot_int.size());  // every internal node's bit
   take(h->b_wide_part, 3 * 8 * (size_t)c.wide_chunk.back());
   take(h->b_wide_cnt, 4 * c.n_wide);
   take(h->b_int_slot, 4 * c.n_int);
@@ -110,7 +108,6 @@ static void plan(cfr_handle *h) {
   take(h->b_wide_irank, 4 * c.n_wide);
   take(h->b_reach, 2 * T * std::max<int64_t>(c.n_int, 1));  // internal nodes only
   take(h->b_v, T * c.N);  // value slots
-  take(h->b_vm, T * std::max<int64_t>(c.n_int, 1));  // internal nodes' values (members, chance nodes)
   take(h->b_sigma, T * (c.A + 1));
   take(h->b_R, 8 * c.A);
   take(h->b_avg, 8 * c.A);
@@ -145,7 +142,6 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
   if (lp != 0 && (lp < 4 || lp == kThreads) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2 or 256 needs sets of at most 8 actions"); }
-  if (h->opt.value_mode < CFR_VALUES_AUTO || h->opt.value_mode > CFR_VALUES_IN_PLACE) { delete h; return set_err(CFR_ERR_ARG, "bad value_mode"); }
   h->precision = h->opt.precision;
   h->rule = h->opt.rule;
   h->order = h->opt.order;
@@ -178,10 +174,6 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
     w.wd1 = c.level_wide[d + 1];
     w.wc0 = c.wide_chunk[w.wd0];
     w.wc1 = c.wide_chunk[w.wd1];
-    w.gath = h->opt.value_mode == CFR_VALUES_IN_PLACE ? 0 : 1;
-    w.vs0 = d == 0 ? (int32_t)(c.N - 1) : c.level_begin[d] - 1;  // value slots of the depth's nodes
-    w.vs1 = d == 0 ? (int32_t)c.N : c.level_begin[d + 1] - 1;
-    w.pad = 0;
     w.fan = 0;  // a chance node of this depth has its children written warp-wide
     for (int64_t q = c.level_int[d]; q < c.level_int[d + 1] && !w.fan; ++q) {
       const uint32_t m = c.int_mask[q];
@@ -200,18 +192,16 @@ extern "C" void cfr_destroy(cfr_handle *h) {
   delete h;
 }
 
-static int64_t iteration_bytes(const cfr_handle *h);
-
 extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
   if (!h || !o) return set_err(CFR_ERR_ARG, "cfr_get_counts: null argument");
   const Compiled &c = h->c;
   o->n_nodes = c.N; o->n_edges = c.E; o->n_infosets = c.I; o->n_slots = c.A;
   o->n_internal = c.n_int; o->n_decision = c.n_dec; o->n_chance = c.n_chance; o->n_terminal = c.n_term;
   o->depth_blocks = c.D; o->max_actions = c.max_act;
-  o->algo_bytes_per_iter = iteration_bytes(h);
+  o->algo_bytes_per_iter = algo_bytes_per_iter(c, h->precision) * (h->order == CFR_ORDER_ALTERNATING ? 2 : 1);
   o->upload_bytes = (int64_t)(h->b_iset_slot.bytes + h->b_iset_mem.bytes + h->b_iset_vb.bytes + h->b_mem_vs.bytes +
                               h->b_ch_vb.bytes + h->b_ch_nch.bytes + h->b_ch_vs.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
-                              h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes + h->b_slot_int.bytes +
+                              h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes +
                               h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
                               h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes +
                               h->b_mem_irank.bytes + h->b_wide_irank.bytes);
@@ -239,9 +229,6 @@ static GameView game_view(const cfr_handle *h) {
   g.wide_vb = h->p<int32_t>(h->b_wide_vb);
   g.wide_nch = h->p<int32_t>(h->b_wide_nch);
   g.wide_vs = h->p<int32_t>(h->b_wide_vs);
-  g.slot_int = h->p<uint32_t>(h->b_slot_int);
-  g.n_dec = (int32_t)h->c.n_dec;
-  g.n_narrow = (int32_t)h->c.ch_vb.size();
   g.wide_chunk = h->p<int32_t>(h->b_wide_chunk);
   g.wide_part = h->p<double>(h->b_wide_part);
   g.wide_cnt = h->p<unsigned>(h->b_wide_cnt);
@@ -258,7 +245,6 @@ template <typename T> static StateView<T> state_view(const cfr_handle *h) {
   StateView<T> s;
   s.reach = h->p<vec2_t<T>>(h->b_reach);
   s.v = h->p<T>(h->b_v);
-  s.vm = h->p<T>(h->b_vm);
   s.sigma = h->p<T>(h->b_sigma);
   s.R = h->p<double>(h->b_R);
   s.avg = h->p<double>(h->b_avg);
@@ -295,31 +281,6 @@ static int init_state(cfr_handle *h, cudaStream_t s) {
   return CFR_OK;
 }
 
-// Depth d's value mode on the device: its slots' internal bits (copied or
-// cleared) and, when its nodes pass values through vm, the vm indices in
-// their slots. The LevelWork copy in the arena is rewritten too (the
-// persistent and batched kernels read it there).
-template <typename T>
-static int apply_level_mode(cfr_handle *h, int64_t d, cudaStream_t s) {
-  const Compiled &c = h->c;
-  const LevelWork &w = h->levels[d];
-  if (w.vs1 > w.vs0) {
-    set_slot_bits_kernel<<<grid_for((w.vs1 - w.vs0) / 32 + 2, kThreads), kThreads, 0, s>>>(
-        h->p<uint32_t>(h->b_slot_int), h->p<uint32_t>(h->b_slot_int_all), w.vs0, w.vs1, w.gath);
-    CK(cudaGetLastError());
-  }
-  if (w.gath) {
-    const int32_t k0 = c.iset_mem[c.level_iset[2 * d]], k1 = c.iset_mem[c.level_iset[2 * d + 2]];
-    const int64_t work = std::max<int64_t>({(int64_t)(k1 - k0), (int64_t)(w.ch1 - w.ch0), (int64_t)(w.wd1 - w.wd0), 1});
-    init_codes_kernel<T><<<grid_for(work, kThreads), kThreads, 0, s>>>(
-        h->p<int32_t>(h->b_mem_vs), h->p<int32_t>(h->b_ch_vs), h->p<int32_t>(h->b_wide_vs), (int32_t)c.n_dec,
-        (int32_t)c.ch_vs.size(), k0, k1, w.ch0, w.ch1, w.wd0, w.wd1, h->p<T>(h->b_v));
-    CK(cudaGetLastError());
-  }
-  CK(cudaMemcpyAsync(h->p<LevelWork>(h->b_levels) + d, &w, sizeof(LevelWork), cudaMemcpyHostToDevice, s));
-  return CFR_OK;
-}
-
 template <typename T>
 static int init_values(cfr_handle *h, cudaStream_t s) {
   const Compiled &c = h->c;
@@ -327,10 +288,6 @@ static int init_values(cfr_handle *h, cudaStream_t s) {
   init_values_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
       h->p<double>(h->b_tmpl), (int32_t)c.N, h->p<T>(h->b_v), h->p<double2>(h->b_vb), h->p<double>(h->b_vavg));
   CK(cudaGetLastError());
-  for (int64_t d = 0; d < c.D; ++d) {
-    int rc = apply_level_mode<T>(h, d, s);
-    if (rc) return rc;
-  }
   return CFR_OK;
 }
 
@@ -360,8 +317,6 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_wide_nch, c.wide_nch.data(), 4 * c.n_wide))) return rc;
   if ((rc = up(h->b_wide_vs, c.wide_vs.data(), 4 * c.n_wide))) return rc;
   if ((rc = up(h->b_wide_chunk, c.wide_chunk.data(), 4 * (c.n_wide + 1)))) return rc;
-  if ((rc = up(h->b_slot_int, c.slot_int.data(), 4 * c.slot_int.size()))) return rc;
-  if ((rc = up(h->b_slot_int_all, c.slot_int.data(), 4 * c.slot_int.size()))) return rc;
   if ((rc = up(h->b_int_slot, c.int_slot.data(), 4 * c.n_int))) return rc;
   if ((rc = up(h->b_int_mask, c.int_mask.data(), 4 * c.n_int))) return rc;
   if ((rc = up(h->b_int_cirank, c.int_cirank.data(), 4 * c.n_int))) return rc;
@@ -725,14 +680,6 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 10: src = c.tmpl.data(); n = (int64_t)c.tmpl.size(); esz = 8; break;
     case 11: src = c.spec_slot_of.data(); n = (int64_t)c.spec_slot_of.size(); break;
     case 12: src = h->level_lanes.data(); n = (int64_t)h->level_lanes.size(); break;
-    case 30: {  // per-depth value modes (1 = through vm, 0 = in place), a runtime choice
-      static thread_local std::vector<int32_t> modes;
-      modes.assign(h->levels.size(), 0);
-      for (size_t d = 0; d < h->levels.size(); ++d) modes[d] = h->levels[d].gath;
-      src = modes.data();
-      n = (int64_t)modes.size();
-      break;
-    }
     case 13: src = c.int_slot.data(); n = (int64_t)c.int_slot.size(); break;
     case 14: src = c.int_mask.data(); n = (int64_t)c.int_mask.size(); break;
     case 15: src = c.int_cirank.data(); n = (int64_t)c.int_cirank.size(); break;
@@ -749,7 +696,6 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 26: src = c.wide_nch.data(); n = (int64_t)c.wide_nch.size(); break;
     case 27: src = c.wide_vs.data(); n = (int64_t)c.wide_vs.size(); break;
     case 28: src = c.tmpl_vs.data(); n = (int64_t)c.tmpl_vs.size(); esz = 8; break;
-    case 29: src = c.slot_int.data(); n = (int64_t)c.slot_int.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -769,9 +715,10 @@ extern "C" int cfr_debug_set(cfr_handle *h, int key, int64_t value) {
   return set_err(CFR_ERR_ARG, "cfr_debug_set: unknown key %d", key);
 }
 
-// Algorithmic bytes of depth d's forward and backward launches (one pass).
-static void level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t *bwd) {
+extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t *bwd) {
+  if (!h || !fwd || !bwd) return set_err(CFR_ERR_ARG, "cfr_level_bytes: null argument");
   const Compiled &c = h->c;
+  if (d < 0 || d >= c.D) return set_err(CFR_ERR_ARG, "cfr_level_bytes: level out of range");
   const int64_t T = h->precision == CFR_P64 ? 8 : 4;
   const int64_t e = c.level_begin[d + 2] - c.level_begin[d + 1];  // children = next level
   const int64_t nint = c.level_int[d + 1] - c.level_int[d];
@@ -785,32 +732,8 @@ static void level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t *bwd) 
   for (int64_t q = c.level_int[d]; q < c.level_int[d + 1]; ++q)
     if (c.int_mask[q] & kBigNode) big += 1 + c.big_irank[c.int_cirank[q]];
   *fwd = 12 * nint + 2 * T * nint + 2 * T * nint_kids + T * slots + 4 * big;
-  // per child slot its entry and bitmap bit; the children's values gathered
-  // from vm when their depth passes values that way; the depth's own values
-  // written (coalesced, or in place after reading the node's value slot)
-  const bool own_vm = h->levels[d].gath != 0;
-  const bool kids_vm = d + 1 < c.D && h->levels[d + 1].gath != 0;
-  *bwd = 12 * sets + (32 + 2 * T) * slots + (4 + 3 * T) * dec + (8 + T) * nch + T * e + 4 * ((e + 31) / 32) +
-         (kids_vm ? T * nint_kids : 0) + (own_vm ? 0 : 4 * (dec + nch));
-}
-
-extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t *bwd) {
-  if (!h || !fwd || !bwd) return set_err(CFR_ERR_ARG, "cfr_level_bytes: null argument");
-  if (d < 0 || d >= h->c.D) return set_err(CFR_ERR_ARG, "cfr_level_bytes: level out of range");
-  level_bytes(h, d, fwd, bwd);
+  *bwd = 12 * sets + (32 + 2 * T) * slots + (8 + 3 * T) * dec + (12 + T) * nch + T * e;
   return CFR_OK;
-}
-
-// One iteration's algorithmic bytes: every depth's forward and backward
-// (twice under alternating updates).
-static int64_t iteration_bytes(const cfr_handle *h) {
-  int64_t tot = 0;
-  for (int d = 0; d < (int)h->c.D; ++d) {
-    int64_t f = 0, b = 0;
-    level_bytes(h, d, &f, &b);
-    tot += f + b;
-  }
-  return tot * (h->order == CFR_ORDER_ALTERNATING ? 2 : 1);
 }
 
 // One iteration with an event pair around every launch; under alternating
@@ -870,9 +793,8 @@ extern "C" int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_
 // iterations: code that runs while a CUDA graph is being captured, real-time
 // serving loops whose memory budget is fixed at start-up, or host code that
 // does not own the device allocator. cfr_iterate_noalloc serves them: it runs
-// the persistent kernel with its per-iteration scratch (both reach lanes and
-// the values of the internal nodes, wide-node partial sums and the
-// grid-barrier words) placed in
+// the persistent kernel with its per-iteration scratch (both reach lanes, the
+// node values, wide-node partial sums and the grid-barrier words) placed in
 // one file-scope device array of fixed size, so the call itself allocates
 // nothing. The bound arena still holds the compiled game and the solver state
 // (regrets, average, strategy, t), which are this call's inputs and outputs.
@@ -898,13 +820,14 @@ static int noalloc_scratch(void **out) {
   return CFR_OK;
 }
 
-// Every call starts from a clean scratch: root reach (1, 1), wide-node
-// tickets and barrier words at zero. (The value slots are read only while
-// iterating, so the handle's own, written at bind, serve.)
+// Every call starts from a clean scratch: value slots from the template,
+// root reach (1, 1), wide-node tickets and barrier words at zero.
 template <typename T>
-__global__ void noalloc_init_kernel(vec2_t<T> *reach, unsigned *wide_cnt, int32_t n_wide, unsigned *bar) {
+__global__ void noalloc_init_kernel(const double *tmpl_vs, int32_t N, T *v, vec2_t<T> *reach, unsigned *wide_cnt,
+                                    int32_t n_wide, unsigned *bar) {
   const int32_t stride = gridDim.x * blockDim.x;
   const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int32_t h = tid; h < N; h += stride) v[h] = (T)tmpl_vs[h];
   for (int32_t i = tid; i < n_wide; i += stride) wide_cnt[i] = 0u;
   if (tid == 0) {
     vec2_t<T> one;
@@ -917,8 +840,8 @@ __global__ void noalloc_init_kernel(vec2_t<T> *reach, unsigned *wide_cnt, int32_
 template <typename T>
 static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   const Compiled &c = h->c;
-  size_t off_vm = align_up(2 * sizeof(T) * (size_t)std::max<int64_t>(c.n_int, 1));
-  size_t off_part = off_vm + align_up(sizeof(T) * (size_t)std::max<int64_t>(c.n_int, 1));
+  size_t off_v = align_up(2 * sizeof(T) * (size_t)std::max<int64_t>(c.n_int, 1));
+  size_t off_part = off_v + align_up(sizeof(T) * (size_t)c.N);
   size_t off_cnt = off_part + align_up(3 * 8 * (size_t)c.wide_chunk.back());
   size_t off_bar = off_cnt + align_up(4 * (size_t)c.n_wide);
   const size_t need = off_bar + 256;
@@ -936,7 +859,7 @@ static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   a.g.wide_cnt = (unsigned *)(sb + off_cnt);
   a.st = state_view<T>(h);
   a.st.reach = (vec2_t<T> *)sb;
-  a.st.vm = (T *)(sb + off_vm);
+  a.st.v = (T *)(sb + off_v);
   a.lw = h->p<LevelWork>(h->b_levels);
   a.D = (int)c.D;
   a.rule = h->rule;
@@ -963,8 +886,9 @@ static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   }
   const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
   a.bar.expected = (unsigned)grid;
-  noalloc_init_kernel<T><<<grid_for(std::max<int64_t>(c.n_wide, 1), kThreads), kThreads, 0, s>>>(
-      a.st.reach, a.g.wide_cnt, (int32_t)c.n_wide, bar);
+  noalloc_init_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
+      h->p<double>(h->b_tmpl), (int32_t)c.N, a.st.v, a.st.reach, a.g.wide_cnt,
+      (int32_t)c.n_wide, bar);
   CK(cudaGetLastError());
   CK(launch_persistent<T>(h->maxa_tier, L, grid, s, a, nullptr));
   int err = 0;
@@ -990,27 +914,6 @@ extern "C" int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream) {
 // action tier has kernels for and keep the fastest; for the persistent form,
 // time whole persistent iterations per lane count. Trial launches change the
 // state, so the call ends with the state reset (as cfr_reset).
-// ------------------------------------------------------------ manual tuning
-extern "C" int cfr_tune_level(cfr_handle *h, int depth, int lanes, int gather, void *stream) {
-  if (!h) return set_err(CFR_ERR_ARG, "cfr_tune_level: null handle");
-  if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_tune_level: call cfr_bind first");
-  if (depth < 0 || depth >= h->c.D) return set_err(CFR_ERR_ARG, "cfr_tune_level: depth out of range");
-  const bool ok_lanes = lanes == 0 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32 ||
-                        (h->maxa_tier <= 8 && (lanes == 1 || lanes == 2 || lanes == kThreads));
-  if (!ok_lanes) return set_err(CFR_ERR_ARG, "cfr_tune_level: unsupported lanes %d for this game", lanes);
-  if (gather < -1 || gather > 1) return set_err(CFR_ERR_ARG, "cfr_tune_level: gather must be -1, 0 or 1");
-  cudaStream_t s = (cudaStream_t)stream;
-  if (lanes) h->level_lanes[depth] = lanes;
-  if (gather >= 0 && h->levels[depth].gath != gather) {
-    h->levels[depth].gath = gather;
-    int rc = h->precision == CFR_P64 ? apply_level_mode<double>(h, depth, s) : apply_level_mode<float>(h, depth, s);
-    if (rc) return rc;
-  }
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->graph_arena = nullptr; }
-  CK(cudaStreamSynchronize(s));
-  return CFR_OK;
-}
-
 // ------------------------------------------------------------ launch floor
 // The iteration's launch structure with no work in it: the same 2D launches
 // (same grid sizes) of an empty kernel captured in one graph, and one
@@ -1124,68 +1027,24 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   auto run_iter = [&]() -> int {
     return h->precision == CFR_P64 ? enqueue_iteration<double>(h, s) : enqueue_iteration<float>(h, s);
   };
-  auto bwd = [&](int64_t d) -> int {
-    return h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
-  };
-  auto timed = [&](int64_t d, float *ms) -> int {  // reps launches of depth d's backward
-    int r = bwd(d);
-    if (r) return r;
-    CK(cudaEventRecord(e0, s));
-    for (int i = 0; i < reps && r == CFR_OK; ++i) r = bwd(d);
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
-    CK(cudaEventElapsedTime(ms, e0, e1));
-    return r;
-  };
-  auto set_mode = [&](int64_t d, int gath) -> int {
-    h->levels[d].gath = gath;
-    return h->precision == CFR_P64 ? apply_level_mode<double>(h, d, s) : apply_level_mode<float>(h, d, s);
-  };
   rc = run_iter();  // realistic reach and values for the trials
-  // lanes per set: per depth, the fastest backward launch
   for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
     int best = h->level_lanes[d];
     float best_ms = 1e30f;
     for (int L : cand) {
       h->level_lanes[d] = L;
+      rc = h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
+      if (rc) break;
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps && rc == CFR_OK; ++r)
+        rc = h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
       float ms = 0.f;
-      if ((rc = timed(d, &ms))) break;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms) { best_ms = ms; best = L; }
     }
     h->level_lanes[d] = best;
-  }
-  // value modes (CFR_VALUES_AUTO): per depth below the root, whole
-  // iterations with the depth's values gathered and written in place; a
-  // mode changes one depth's writes and the next depth up's reads, so only
-  // complete iterations see both with the real cache state
-  if (h->opt.value_mode == CFR_VALUES_AUTO) {
-    const int iters = std::max(reps, 10);
-    auto iter_ms = [&](float *ms) -> int {
-      int r = run_iter();
-      if (r) return r;
-      CK(cudaEventRecord(e0, s));
-      for (int i = 0; i < iters && r == CFR_OK; ++i) r = run_iter();
-      CK(cudaEventRecord(e1, s));
-      CK(cudaEventSynchronize(e1));
-      CK(cudaEventElapsedTime(ms, e0, e1));
-      return r;
-    };
-    // the two modes differ by a few percent of an iteration: alternate three
-    // samples of each and compare the fastest
-    for (int64_t d = c.D - 1; d >= 1 && rc == CFR_OK; --d) {
-      float best[2] = {1e30f, 1e30f};
-      const int keep = h->levels[d].gath;
-      for (int smp = 0; smp < 6 && rc == CFR_OK; ++smp) {
-        const int m = (smp & 1) ? 1 - keep : keep;
-        if (h->levels[d].gath != m && (rc = set_mode(d, m))) break;
-        float ms = 0.f;
-        if ((rc = iter_ms(&ms))) break;
-        best[m] = std::min(best[m], ms);
-      }
-      if (rc) break;
-      const int pick = best[1] <= best[0] ? 1 : 0;
-      if (h->levels[d].gath != pick) rc = set_mode(d, pick);
-    }
   }
   if (rc == CFR_OK && h->exec_form == CFR_EXEC_PERSISTENT) {
     int best = h->persist_lanes;
@@ -1241,7 +1100,6 @@ static int batch_table(cfr_handle *const *hs, int n, const int64_t *iters, int64
     d.g = game_view(h);
     d.reach = h->arena + h->b_reach.off;
     d.v = h->arena + h->b_v.off;
-    d.vm = h->arena + h->b_vm.off;
     d.sigma = h->arena + h->b_sigma.off;
     d.R = h->p<double>(h->b_R);
     d.avg = h->p<double>(h->b_avg);

@@ -318,9 +318,6 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
       }
       c.tmpl_vs.assign(N, 0.0);
       for (int64_t h = 0; h < N; ++h) c.tmpl_vs[c.vslot[h]] = c.tmpl[h];
-      c.slot_int.assign((N + 31) / 32, 0u);
-      for (int64_t h = 0; h < N; ++h)
-        if (c.child_begin[h + 1] > c.child_begin[h]) c.slot_int[c.vslot[h] >> 5] |= 1u << (c.vslot[h] & 31);
     }
     // per-depth member statistics (used to size the per-set lane groups)
     c.level_max_members.assign(D, 0);
@@ -358,5 +355,19 @@ void fold_chance(Compiled &c) {
   }
 }
 
+int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
+  // Forward: every internal node's record (slot word, child mask, first
+  // internal child: 12 B) and its two reach lanes read, every internal
+  // child's reach lanes written, the strategy read once. Backward: per set
+  // its slot, member and value-block offsets (12 B); per slot R and the
+  // average read and written (FP64) and the strategy read and written; per
+  // member its value slot and internal rank (8 B), its reach lanes read and
+  // its value written; per chance node its block, child count and value slot
+  // (12 B) and its value written; every edge's child value read once.
+  const int64_t T = precision == CFR_P64 ? 8 : 4;
+  const int64_t int_kids = c.n_int > 0 ? c.n_int - 1 : 0;  // every internal node but the root
+  return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 12 * c.I +
+         (32 + 3 * T) * c.A + (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
+}
 
 }  // namespace cfr

@@ -74,7 +74,6 @@ struct Compiled {
   std::vector<int32_t> ch_vb, ch_nch, ch_vs;        // [narrow chance nodes] block, children, own slot
   std::vector<int32_t> wide_vb, wide_nch, wide_vs;  // [n_wide] the same for wide chance nodes
   std::vector<double> tmpl_vs;       // [N] the values template in slot order
-  std::vector<uint32_t> slot_int;    // [ceil(N/32)] bit vslot[h] set for every internal node h
   std::vector<double> pc;            // [N] chance product root..h (retained for set_payoffs)
   std::vector<double> edge_p;        // [N] probability of the chance edge into h (1 below decision nodes and at the root)
   std::vector<double> u;             // [N] payoff to player 1 at terminals, 0 elsewhere
@@ -96,5 +95,8 @@ int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err);
 // fresh compile.
 void fold_chance(Compiled &c);
 
+// Algorithmic device bytes of one iteration (each array element touched the
+// minimum number of times the layout allows; see the design notes).
+int64_t algo_bytes_per_iter(const Compiled &c, int precision);
 
 }  // namespace cfr

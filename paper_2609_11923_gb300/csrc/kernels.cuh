@@ -28,8 +28,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 namespace cfr {
 
 template <typename T> struct Vec2;
@@ -66,11 +64,6 @@ struct GameView {
   const int32_t *__restrict__ wide_vb;     // wide chance nodes: the same
   const int32_t *__restrict__ wide_nch;
   const int32_t *__restrict__ wide_vs;
-  // bit s set: value slot s belongs to an internal node, and the value array
-  // holds there the index of that node's value in vm (not a value)
-  const uint32_t *__restrict__ slot_int;
-  int32_t n_dec;     // vm: members [0, n_dec), narrow chance nodes, then wide ones
-  int32_t n_narrow;
   const int32_t *__restrict__ wide_chunk;  // prefix of their chunk counts
   double *wide_part;                       // [3 * chunks] partial sums
   unsigned *wide_cnt;                      // [wide nodes] chunks finished (reset by the last one)
@@ -87,8 +80,7 @@ constexpr uint32_t kBigBit = 0x80000000u;
 
 template <typename T> struct StateView {
   vec2_t<T> *reach;
-  T *v;    // value slots: terminal template values and internal nodes' vm indices (constant while iterating)
-  T *vm;   // values of the internal nodes, in the order they are computed (coalesced writes)
+  T *v;
   T *sigma;
   double *R;
   double *avg;
@@ -103,13 +95,6 @@ struct LevelWork {
   int32_t wd0, wd1;       // wide chance nodes of depth d (wide_* arrays)
   int32_t wc0, wc1;       // their chunks
   int32_t fan;            // 1 if a chance node of depth d has more than kFanLight internal children
-  // How the internal nodes of depth d pass their values up: 1 = written
-  // coalesced to vm (their value slots hold vm indices, flagged in slot_int)
-  // for the parents to gather; 0 = written straight into their value slots
-  // (a scattered write). vs0 .. vs1: the value slots of the nodes of depth d.
-  int32_t gath;
-  int32_t vs0, vs1;
-  int32_t pad;
 };
 
 // The wide node owning chunk q (binary search over the level's prefix).
@@ -319,70 +304,13 @@ __device__ __forceinline__ double slot_update(double *R, double *avg, int32_t q,
 }
 
 // ------------------------------------------------------------- backward
-// Index of an internal node's value in vm, as stored in its value slot.
-template <typename T> __device__ __forceinline__ T vm_code(int32_t i);
-template <> __device__ __forceinline__ float vm_code<float>(int32_t i) { return __int_as_float(i); }
-template <> __device__ __forceinline__ double vm_code<double>(int32_t i) { return __longlong_as_double((long long)i); }
-__device__ __forceinline__ int32_t vm_index(float x) { return __float_as_int(x); }
-__device__ __forceinline__ int32_t vm_index(double x) { return (int32_t)__double_as_longlong(x); }
-
-// The value of the node in value slot s: a terminal's template value, read
-// in place, or an internal node's value, gathered from vm through the index
-// its slot holds. Each internal node thus writes its value once, coalesced,
-// in the order it is computed, and its parent gathers it (a scattered read
-// instead of a scattered write).
-// A value slot's entry. Slots of nodes that write their values in place
-// change between depths, so kernels that span depths read them through L2.
+// Narrow chance node i: the sum of its children's values (left to right).
 template <typename T, bool PERSIST>
-__device__ __forceinline__ T slot_entry(const StateView<T> &st, int32_t s) {
-  if constexpr (PERSIST) return __ldcg(st.v + s);
-  else return __ldg(st.v + s);
-}
-
-template <typename T, bool PERSIST>
-__device__ __forceinline__ T slot_value(const GameView &g, const StateView<T> &st, int32_t s) {
-  const T raw = slot_entry<T, PERSIST>(st, s);
-  if ((__ldg(g.slot_int + (s >> 5)) >> (s & 31)) & 1u) return ldm<PERSIST>(st.vm + vm_index(raw));
-  return raw;
-}
-
-// The values of U consecutive slots s0 .. s0+U-1 (those below s1 only):
-// every slot's entry and bit are loaded first, then every gather is issued,
-// so the U dependent loads overlap instead of running one after another.
-template <typename T, bool PERSIST, int U>
-__device__ __forceinline__ void slot_values(const GameView &g, const StateView<T> &st, int32_t s0, int32_t s1,
-                                            T (&out)[U]) {
-  bool in_[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int32_t s = s0 + u;
-    in_[u] = false;
-    out[u] = T(0);
-    if (s < s1) {
-      out[u] = slot_entry<T, PERSIST>(st, s);
-      in_[u] = (__ldg(g.slot_int + (s >> 5)) >> (s & 31)) & 1u;
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u)
-    if (in_[u]) out[u] = ldm<PERSIST>(st.vm + vm_index(out[u]));
-}
-
-// Narrow chance node i: the sum of its children's values (left to right),
-// passed up as its depth's mode says (gath).
-template <typename T, bool PERSIST>
-__device__ __forceinline__ void bwd_chance(const GameView &g, const StateView<T> &st, int32_t i, int gath) {
+__device__ __forceinline__ void bwd_chance(const GameView &g, T *v, int32_t i) {
   const int32_t cb = __ldg(g.ch_vb + i), ce = cb + __ldg(g.ch_nch + i);
   T s = T(0);
-  for (int32_t c = cb; c < ce; c += 8) {
-    T x[8];
-    slot_values<T, PERSIST, 8>(g, st, c, ce, x);
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (c + u < ce) s = s + x[u];
-  }
-  if (gath) st.vm[g.n_dec + i] = s;
-  else st.v[__ldg(g.ch_vs + i)] = s;
+  for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
+  v[__ldg(g.ch_vs + i)] = s;
 }
 
 // One chunk of a wide chance node's value sum. P32: every chunk block sums
@@ -391,23 +319,22 @@ __device__ __forceinline__ void bwd_chance(const GameView &g, const StateView<T>
 // float atomics). P64: the first chunk's block sums all children strictly
 // left to right, the order of the recursive definition.
 template <typename T, bool PERSIST>
-__device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWork &w, const StateView<T> &st,
-                                               int32_t q) {
+__device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWork &w, T *v, int32_t q) {
   const int32_t wi = wide_of_chunk(g, w, q);
-  T *vh = w.gath ? st.vm + g.n_dec + g.n_narrow + wi : st.v + __ldg(g.wide_vs + wi);  // where its value goes
+  const int32_t h = __ldg(g.wide_vs + wi);  // the node's own value slot
   const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   const int32_t q0 = __ldg(g.wide_chunk + wi), nq = __ldg(g.wide_chunk + wi + 1) - q0;
   if constexpr (sizeof(T) == 8) {
     if (q == q0 && threadIdx.x == 0) {
       T s = T(0);
-      for (int32_t c = cb; c < ce; ++c) s = s + slot_value<T, PERSIST>(g, st, c);
-      *vh = s;
+      for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
+      v[h] = s;
     }
     return;
   } else {
     const int32_t c0 = cb + (q - q0) * kWideChunkK, c1 = min(ce, c0 + kWideChunkK);
     double x = 0.0;
-    for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) x += (double)slot_value<T, PERSIST>(g, st, c);
+    for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) x += (double)ldm<PERSIST>(v + c);
     x = block_sum(x);
     __shared__ unsigned s_ticket;
     if (threadIdx.x == 0) {
@@ -422,109 +349,47 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
       for (int32_t k = threadIdx.x; k < nq; k += blockDim.x) y += __ldcg(g.wide_part + q0 + k);
       y = block_sum(y);
       if (threadIdx.x == 0) {
-        *vh = (T)y;
+        v[h] = (T)y;
         g.wide_cnt[wi] = 0u;
       }
     }
   }
 }
 
-// A member's index (member order: a coalesced read): its internal rank,
-// where its reach lives. Past the set's end: -1.
-__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, int32_t &ir) {
-  ir = k < m1 ? __ldg(g.mem_irank + k) : -1;
-}
-
-// What a step loads ahead for one member (k < m1): its internal rank and its
-// children's value-slot entries with their internal bits (constant data), so
-// the step itself issues the reach read and the child gathers at once.
-template <typename T, int MAXA>
-struct MemberPre {
-  using Bits = typename std::conditional<(MAXA > 32), unsigned long long, uint32_t>::type;  // one bit per action
-  int32_t ir;
-  int32_t ps;  // own value slot (read only when the depth writes values in place)
-  Bits bits;
-  T raw[MAXA];
-};
-
-template <typename T, int MAXA, bool PERSIST>
-__device__ __forceinline__ void member_pre(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
-                                           int32_t m1, int32_t vb, int32_t na, int gath, MemberPre<T, MAXA> &p) {
-  using Bits = typename MemberPre<T, MAXA>::Bits;
-  p.ir = -1;
-  p.ps = -1;
-  p.bits = 0;
-#pragma unroll
-  for (int a = 0; a < MAXA; ++a) p.raw[a] = T(0);
-  if (k >= m1) return;
-  p.ir = __ldg(g.mem_irank + k);
-  if (!gath) p.ps = __ldg(g.mem_vs + k);
-  const int32_t cb = vb + (k - m0) * na;
-#pragma unroll
-  for (int a = 0; a < MAXA; ++a) {
-    if (a < na) {
-      const int32_t s = cb + a;
-      p.raw[a] = slot_entry<T, PERSIST>(st, s);
-      p.bits |= (Bits)((__ldg(g.slot_int + (s >> 5)) >> (s & 31)) & 1u) << a;
-    }
+// A member's two indices (member order: coalesced reads): its own value slot
+// and its internal rank (where its reach lives). Past the set's end: -1.
+__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, int32_t &ps, int32_t &ir) {
+  ps = -1;
+  ir = -1;
+  if (k < m1) {
+    ps = __ldg(g.mem_vs + k);
+    ir = __ldg(g.mem_irank + k);
   }
 }
 
-// member_data with the loads of member_pre already done.
-template <typename T, int MAXA, bool PERSIST>
-__device__ __forceinline__ void member_data_pre(const StateView<T> &st, int32_t k, int32_t m1, int32_t na, bool p2,
-                                                const T (&sig)[MAXA], const MemberPre<T, MAXA> &p, T (&d)[MAXA],
-                                                T (&mm)[MAXA]) {
-#pragma unroll
-  for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
-  if (k >= m1) return;
-  const vec2_t<T> r = ldm<PERSIST>(st.reach + p.ir);
-  T vc[MAXA];
-#pragma unroll
-  for (int a = 0; a < MAXA; ++a) {
-    vc[a] = p.raw[a];
-    if ((p.bits >> a) & 1) vc[a] = ldm<PERSIST>(st.vm + vm_index(p.raw[a]));
-  }
-  T vh = T(0);
-#pragma unroll
-  for (int a = 0; a < MAXA; ++a)
-    if (a < na) vh = vh + sig[a] * vc[a];
-  if (p.ps < 0) st.vm[k] = vh;
-  else st.v[p.ps] = vh;
-  const T po = p2 ? r.x : r.y;  // opponent's reach (chance is inside v)
-  const T pw = p2 ? r.y : r.x;  // own reach
-  const T f = (p2 ? T(-1) : T(1)) * po;
-#pragma unroll
-  for (int a = 0; a < MAXA; ++a) {
-    if (a < na) {
-      d[a] = f * (vc[a] - vh);
-      mm[a] = pw * sig[a];
-    }
-  }
-}
-
-// Loads and per-member terms of one member (k < m1) whose internal rank is
+// Loads and per-member terms of one member (k < m1) whose indices are
 // already known, or zeros. The member's children are slots
 // vb + (k - m0) * na .. + na - 1 of the set's block: the group's lanes read
-// consecutive members' children as one run. The member's own value goes to
-// vm[k] (member order: a coalesced write).
+// consecutive members' children as one run.
 template <typename T, int MAXA, bool PERSIST>
 __device__ __forceinline__ void member_data(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
                                             int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
-                                            int32_t ir, int gath, T (&d)[MAXA], T (&mm)[MAXA]) {
+                                            int32_t h, int32_t ir, T (&d)[MAXA], T (&mm)[MAXA]) {
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
   if (k >= m1) return;
   const int32_t cb = vb + (k - m0) * na;
   const vec2_t<T> r = ldm<PERSIST>(st.reach + ir);
   T vc[MAXA];
-  slot_values<T, PERSIST, MAXA>(g, st, cb, cb + na, vc);
   T vh = T(0);
 #pragma unroll
-  for (int a = 0; a < MAXA; ++a)
-    if (a < na) vh = vh + sig[a] * vc[a];
-  if (gath) st.vm[k] = vh;
-  else st.v[__ldg(g.mem_vs + k)] = vh;
+  for (int a = 0; a < MAXA; ++a) {
+    if (a < na) {
+      vc[a] = ldm<PERSIST>(st.v + cb + a);
+      vh = vh + sig[a] * vc[a];
+    }
+  }
+  st.v[h] = vh;
   const T po = p2 ? r.x : r.y;  // opponent's reach (chance is inside v)
   const T pw = p2 ? r.y : r.x;  // own reach
   const T f = (p2 ? T(-1) : T(1)) * po;
@@ -541,10 +406,10 @@ __device__ __forceinline__ void member_data(const GameView &g, const StateView<T
 template <typename T, int MAXA, bool PERSIST>
 __device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
                                              int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
-                                             int gath, T (&d)[MAXA], T (&mm)[MAXA]) {
-  int32_t ir;
-  member_idx(g, k, m1, ir);
-  member_data<T, MAXA, PERSIST>(g, st, k, m0, m1, vb, na, p2, sig, ir, gath, d, mm);
+                                             T (&d)[MAXA], T (&mm)[MAXA]) {
+  int32_t h, ir;
+  member_idx(g, k, m1, h, ir);
+  member_data<T, MAXA, PERSIST>(g, st, k, m0, m1, vb, na, p2, sig, h, ir, d, mm);
 }
 
 // Adds one chunk's member terms to the group totals. P64: lane order (the
@@ -579,7 +444,7 @@ __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsign
 // the set's slots runs one lane per action.
 template <typename T, int MAXA, int LANES, bool PERSIST>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                        int lane, unsigned mask, double wt, int rule, int upd, int gath) {
+                                        int lane, unsigned mask, double wt, int rule, int upd) {
   const int32_t sb = __ldg(g.iset_slot + I);
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
@@ -595,40 +460,39 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   int32_t k0 = m0;
   if constexpr (TWO) {
     if (k0 + LANES < m1) {
-      MemberPre<T, MAXA> p0, p1;
-      member_pre<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, gath, p0);
-      member_pre<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, gath, p1);
+      int32_t ps0, ir0, ps1, ir1;
+      member_idx(g, k0 + lane, m1, ps0, ir0);
+      member_idx(g, k0 + LANES + lane, m1, ps1, ir1);
       for (; k0 + LANES < m1; k0 += 2 * LANES) {
-        MemberPre<T, MAXA> q0, q1;  // the next step's loads
-        member_pre<T, MAXA, PERSIST>(g, st, k0 + 2 * LANES + lane, m0, m1, vb, na, gath, q0);
-        member_pre<T, MAXA, PERSIST>(g, st, k0 + 3 * LANES + lane, m0, m1, vb, na, gath, q1);
+        int32_t qs0, jr0, qs1, jr1;  // the next step's indices
+        member_idx(g, k0 + 2 * LANES + lane, m1, qs0, jr0);
+        member_idx(g, k0 + 3 * LANES + lane, m1, qs1, jr1);
         T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
-        member_data_pre<T, MAXA, PERSIST>(st, k0 + lane, m1, na, p2, sig, p0, d0, mm0);
-        member_data_pre<T, MAXA, PERSIST>(st, k0 + LANES + lane, m1, na, p2, sig, p1, d1, mm1);
+        member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps0, ir0, d0, mm0);
+        member_data<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, ps1, ir1, d1, mm1);
         accumulate_chunk<T, MAXA, LANES>(LANES, na, mask, d0, mm0, racc, macc);
         const int32_t c1 = (m1 - k0 - LANES) < LANES ? (m1 - k0 - LANES) : LANES;
         accumulate_chunk<T, MAXA, LANES>(c1, na, mask, d1, mm1, racc, macc);
-        p0 = q0;
-        p1 = q1;
+        ps0 = qs0; ir0 = jr0; ps1 = qs1; ir1 = jr1;
       }
     }
     for (; k0 < m1; k0 += LANES) {
       T d[MAXA], mm[MAXA];
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, gath, d, mm);
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
       accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
     }
   } else {
-    MemberPre<T, MAXA> p;
-    member_pre<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, gath, p);
+    int32_t ps, ir;
+    member_idx(g, k0 + lane, m1, ps, ir);
     for (; k0 < m1; k0 += LANES) {
-      MemberPre<T, MAXA> q;  // the next step's loads
-      member_pre<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, gath, q);
+      int32_t qs, jr;  // the next step's indices
+      member_idx(g, k0 + LANES + lane, m1, qs, jr);
       T d[MAXA], mm[MAXA];
-      member_data_pre<T, MAXA, PERSIST>(st, k0 + lane, m1, na, p2, sig, p, d, mm);
+      member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
       accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
-      p = q;
+      ps = qs; ir = jr;
     }
   }
   // alternating updates: the other player's sets only pass their values up
@@ -696,7 +560,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
 // finished by a fixed-shape tree. The slot update runs one thread per action.
 template <typename T, int MAXA>
 __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                              double wt, int rule, int upd, int gath) {
+                                              double wt, int rule, int upd) {
   __shared__ T s_d[kThreads * MAXA], s_m[kThreads * MAXA];  // [member][action]
   __shared__ double s_pos[MAXA];
   const int tid = threadIdx.x;
@@ -712,13 +576,14 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
     macc[a] = T(0);
   }
   T r = T(0), m = T(0);  // P64: column tid's running sums (tid < na)
-  int32_t ir;
-  member_idx(g, m0 + tid, m1, ir);
+  int32_t ps, ir;
+  member_idx(g, m0 + tid, m1, ps, ir);
   for (int32_t k0 = m0; k0 < m1; k0 += kThreads) {
-    int32_t jr;  // the next chunk's index
-    member_idx(g, k0 + kThreads + tid, m1, jr);
+    int32_t qs, jr;  // the next chunk's indices
+    member_idx(g, k0 + kThreads + tid, m1, qs, jr);
     T d[MAXA], mm[MAXA];
-    member_data<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, ir, gath, d, mm);
+    member_data<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
+    ps = qs;
     ir = jr;
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
@@ -798,14 +663,14 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
   if ((int)blockIdx.x < nb_chance) {
     const int32_t stride = nb_chance * blockDim.x;
     for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride)
-      bwd_chance<T, false>(g, st, i, w.gath);
+      bwd_chance<T, false>(g, st.v, i);
   } else if ((int)blockIdx.x < nb_chance + nb_wide) {
-    bwd_wide_chunk<T, false>(g, w, st, w.wc0 + (int32_t)blockIdx.x - nb_chance);
+    bwd_wide_chunk<T, false>(g, w, st.v, w.wc0 + (int32_t)blockIdx.x - nb_chance);
   } else if constexpr (LANES == kThreads) {
     const int first = nb_chance + nb_wide;
     const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + ((int)blockIdx.x - first); I < w.is1; I += (int)gridDim.x - first)
-      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd, w.gath);
+      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd);
   } else {
     constexpr int GPB = kThreads / LANES;
     const int first = nb_chance + nb_wide;
@@ -815,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     const unsigned mask = group_mask<LANES>();
     const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd, w.gath);
+      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd);
   }
   if (bump_t) {  // depth 0 holds only the root: no other block reads t here
     __syncthreads();
@@ -914,10 +779,10 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
       }
       for (int d = a.D - 1; d >= 0; --d) {
         const LevelWork w = a.lw[d];
-        for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st, i, w.gath);
-        for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st, q);
+        for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
+        for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
         for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd, w.gath);
+          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd);
         if (!grid_sync(a.bar)) return;
       }
     }
@@ -960,32 +825,6 @@ __global__ void init_values_kernel(const double *tmpl_vs, int32_t N, T *v, doubl
 }
 
 // sigma from R by regret matching (used after a state upload)
-// Writes into the value slots of one depth's internal nodes the index of
-// their values in vm (members k -> k, narrow chance node i -> n_dec + i, wide
-// node w -> n_dec + n_narrow + w): members [k0, k1), chance nodes [i0, i1),
-// wide nodes [w0, w1).
-template <typename T>
-__global__ void init_codes_kernel(const int32_t *mem_vs, const int32_t *ch_vs, const int32_t *wide_vs, int32_t n_dec,
-                                  int32_t n_narrow, int32_t k0, int32_t k1, int32_t i0, int32_t i1, int32_t w0,
-                                  int32_t w1, T *v) {
-  const int32_t stride = gridDim.x * blockDim.x;
-  const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int32_t k = k0 + tid; k < k1; k += stride) v[mem_vs[k]] = vm_code<T>(k);
-  for (int32_t i = i0 + tid; i < i1; i += stride) v[ch_vs[i]] = vm_code<T>(n_dec + i);
-  for (int32_t w = w0 + tid; w < w1; w += stride) v[wide_vs[w]] = vm_code<T>(n_dec + n_narrow + w);
-}
-
-// The internal-slot bits of value slots [s0, s1): copied from the full
-// bitmap (the depth's nodes pass values through vm) or cleared (in place).
-static __global__ void set_slot_bits_kernel(uint32_t *active, const uint32_t *all, int32_t s0, int32_t s1, int gath) {
-  const int32_t w0 = s0 >> 5, w1 = (s1 + 31) >> 5;
-  for (int32_t wd = w0 + blockIdx.x * blockDim.x + threadIdx.x; wd < w1; wd += gridDim.x * blockDim.x) {
-    const int32_t lo = max(s0, wd * 32) - wd * 32, hi = min(s1, wd * 32 + 32) - wd * 32;  // bits [lo, hi)
-    const uint32_t m = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-    active[wd] = (active[wd] & ~m) | (gath ? (all[wd] & m) : 0u);
-  }
-}
-
 template <typename T>
 __global__ void rm_kernel(const int32_t *iset_slot, int32_t n_sets, const double *R, T *sigma) {
   const int32_t stride = gridDim.x * blockDim.x;

@@ -139,16 +139,13 @@ def flatten(g):
             return z, z, z
         return (vslot[child_begin[lst]].astype(np.int32), (child_begin[lst + 1] - child_begin[lst]).astype(np.int32),
                 vslot[lst].astype(np.int32))
-    slot_int = np.zeros((N + 31) // 32, dtype=np.uint32)
-    for h in np.nonzero(nch > 0)[0]:
-        slot_int[vslot[h] >> 5] |= np.uint32(1 << int(vslot[h] & 31))
     ch_vb, ch_nch, ch_vs = chance_arrays(chance_list)
     wide_vb, wide_nch, wide_vs = chance_arrays(wide_list)
     return {
         "vslot": vslot.astype(np.int32), "iset_vb": iset_vb.astype(np.int32),
         "mem_vs": (vslot[mem_node] if len(mem_node) else np.zeros(0, np.int64)).astype(np.int32),
         "ch_vb": ch_vb, "ch_nch": ch_nch, "ch_vs": ch_vs, "wide_vb": wide_vb, "wide_nch": wide_nch,
-        "wide_vs": wide_vs, "tmpl_vs": tmpl_vs, "slot_int": slot_int.view(np.int32),
+        "wide_vs": wide_vs, "tmpl_vs": tmpl_vs,
         "int_slot": np.array(int_slot, dtype=np.int32), "int_mask": np.array(int_mask, dtype=np.uint32).view(np.int32),
         "int_cirank": np.array(int_cirank, dtype=np.int32), "big_irank": np.array(big, dtype=np.int32),
         "mem_irank": mem_irank.astype(np.int32), "level_int": level_int,

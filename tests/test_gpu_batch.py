@@ -181,23 +181,3 @@ def test_cluster_size_is_checked():
     with pytest.raises(cfr.CfrError):
         cfr.cfr_batch_iterate(hs, 1, tp, tb, 256, 4, s, cluster=3)
     cfr.cfr_destroy(hs[0])
-
-
-@pytest.mark.parametrize("cluster", [1, 4])
-def test_batched_in_place_values_match_oracle(cluster):
-    specs = [gg.tiny_card(), gg.endgame(2, 100000), gg.random_tree(3, depth=9)]
-    opts = cfr.make_options(precision=cfr.P64, value_mode=cfr.VALUES_IN_PLACE)
-    hs = [cfr.cfr_compile(sp, opts) for sp in specs]
-    pool = serve.DevicePool(sum(cfr.cfr_plan(h) + 512 for h in hs) + 4096)
-    s = int(torch.cuda.current_stream().cuda_stream)
-    for h in hs:
-        n = cfr.cfr_plan(h)
-        cfr.cfr_bind(h, pool.ptr(pool.alloc(n)), n, s)
-    tb = cfr.cfr_batch_table_bytes(len(hs))
-    table = torch.empty(tb + 16, dtype=torch.uint8, device="cuda")
-    cfr.cfr_batch_iterate(hs, 100, (table.data_ptr() + 15) & ~15, tb, 1024, 8, s, cluster=cluster)
-    for sp, h in zip(specs, hs):
-        out = np.empty(cfr.cfr_get_counts(h)["n_slots"])
-        cfr.cfr_avg_strategy(h, out, False, s)
-        np.testing.assert_array_equal(out, oracle.solve(sp, 100).avg_strategy())
-        cfr.cfr_destroy(h)

@@ -268,7 +268,6 @@ def test_autotune_keeps_fp64_parity_and_picks_valid_lanes():
     lanes = s.autotune(reps=2)
     assert len(lanes) == s.counts["depth_blocks"]
     assert set(lanes) <= {1, 2, 4, 8, 16, 32, 256}
-    assert set(cfr.cfr_export_array(s.h, "value_modes")) <= {0, 1}
     assert s.get_state()[2] == 0  # the trials were reset
     s.iterate(300)
     np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 300).avg_strategy())
@@ -386,23 +385,3 @@ def test_set_root_chance_then_solve_equals_the_oracle_on_the_new_game(form):
     o = oracle.solve(with_root_chance(g, p), 300)
     np.testing.assert_array_equal(s.avg_strategy(), o.avg_strategy())
     assert abs(s.exploitability() - o.exploitability()) <= 1e-12
-
-
-@pytest.mark.parametrize("mode", [cfr.VALUES_GATHER, cfr.VALUES_IN_PLACE])
-@pytest.mark.parametrize("form", [cfr.EXEC_GRAPH, cfr.EXEC_LEVELS, cfr.EXEC_PERSISTENT])
-@pytest.mark.parametrize("name,iters", [("tiny", 400), ("rt", 150), ("wide", 60)])
-def test_p64_value_modes_match_oracle_bitwise(mode, form, name, iters):
-    g = {"tiny": gg.tiny_card, "rt": lambda: gg.random_tree(5, depth=9), "wide": lambda: gg.endgame(2, 100000)}[name]()
-    s = solve_gpu(g, iters, form=form, value_mode=mode)
-    assert set(cfr.cfr_export_array(s.h, "value_modes")) == {1 if mode == cfr.VALUES_GATHER else 0}
-    np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, iters).avg_strategy())
-
-
-def test_mixed_value_modes_after_autotune_match_the_oracle():
-    # autotune may leave some depths gathering and others writing in place
-    g = gg.large_card(4, 4, 1, 1)
-    s = cfr.Solver(g, precision=cfr.P64, exec_form=cfr.EXEC_GRAPH)
-    s.autotune(reps=2)
-    s.iterate(40)
-    s.synchronize()
-    np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 40).avg_strategy())
