@@ -146,8 +146,16 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
       if (k == CFR_CHANCE) ++c.n_chance; else ++c.n_dec;
     }
     c.child_begin[N] = (int32_t)next;
-    // ---- information sets: order by (depth, player, first member)
+    // ---- information sets and value slots, depth by depth. The sets of
+    // depth d go player 1 first, then player 2, each group ordered by the
+    // smallest value slot among a set's members: sets whose members pass
+    // their values into the same parent blocks come together, so the sets
+    // processed at the same time fill whole blocks. The members' children
+    // then take the next value slots (set by set, members in ascending id,
+    // children in action order), followed by the children of depth d's
+    // chance nodes (node order). The root's slot is N - 1.
     std::vector<int32_t> first(I, -1), cid_of_spec(I, -1);
+    std::vector<int64_t> smb(I + 1, 0);
     std::vector<int32_t> enc;  // spec sets in order of their first member
     enc.reserve(I);
     for (int64_t h = 0; h < N; ++h) {
@@ -158,24 +166,61 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
       if (first[is] < 0) { first[is] = (int32_t)h; enc.push_back(is); }
       else if (depth[first[is]] != depth[h])
         return fail(err, "information set with members at different depths");
+      smb[is + 1]++;
     }
     if ((int64_t)enc.size() != I) return fail(err, "information set without members");
+    for (int64_t is = 0; is < I; ++is) smb[is + 1] += smb[is];
+    std::vector<int32_t> smem(c.n_dec);  // members of each spec set, ascending node id
+    {
+      std::vector<int64_t> fill(smb.begin(), smb.end() - 1);
+      for (int64_t h = 0; h < N; ++h) {
+        const int k = s.kind[c.spec_of_new[h]];
+        if (k == CFR_PLAYER1 || k == CFR_PLAYER2) smem[fill[s.infoset[c.spec_of_new[h]]]++] = (int32_t)h;
+      }
+    }
     c.level_iset.assign(2 * D + 1, 0);
+    c.vslot.assign(N, -1);
+    c.vslot[0] = (int32_t)(N - 1);
+    c.iset_vb.assign(I, 0);
     {
       std::vector<int32_t> order;
       order.reserve(I);
+      std::vector<std::pair<int64_t, int32_t>> keyed;
+      int64_t next = 0;
       size_t i = 0;
       for (int64_t d = 0; d < D; ++d) {
         size_t j = i;
         while (j < enc.size() && depth[first[enc[j]]] == d) ++j;
-        c.level_iset[2 * d] = (int32_t)order.size();
-        for (size_t q = i; q < j; ++q) if (s.iset_player[enc[q]] == 0) order.push_back(enc[q]);
-        c.level_iset[2 * d + 1] = (int32_t)order.size();
-        for (size_t q = i; q < j; ++q) if (s.iset_player[enc[q]] == 1) order.push_back(enc[q]);
+        for (int pl = 0; pl < 2; ++pl) {
+          c.level_iset[2 * d + pl] = (int32_t)order.size();
+          keyed.clear();
+          for (size_t q = i; q < j; ++q) {
+            const int32_t is = enc[q];
+            if (s.iset_player[is] != pl) continue;
+            int64_t key = N;
+            for (int64_t m = smb[is]; m < smb[is + 1]; ++m) key = std::min<int64_t>(key, c.vslot[smem[m]]);
+            keyed.emplace_back(key * (int64_t)I + (int64_t)(q - i), is);  // ties: first-member order
+          }
+          std::sort(keyed.begin(), keyed.end());
+          for (const auto &kv : keyed) order.push_back(kv.second);
+        }
+        for (size_t q = c.level_iset[2 * d]; q < order.size(); ++q) {  // value slots of depth d + 1
+          const int32_t is = order[q];
+          c.iset_vb[q] = (int32_t)next;
+          for (int64_t m = smb[is]; m < smb[is + 1]; ++m) {
+            const int32_t h = smem[m];
+            for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
+          }
+        }
+        for (int64_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h) {
+          if (s.kind[c.spec_of_new[h]] != CFR_CHANCE) continue;
+          for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
+        }
         i = j;
       }
       c.level_iset[2 * D] = (int32_t)order.size();
       if (i != enc.size()) return fail(err, "internal: information set below the deepest parent");
+      if (next != N - 1) return fail(err, "internal error: value slots do not cover the tree");
       for (size_t q = 0; q < order.size(); ++q) cid_of_spec[order[q]] = (int32_t)q;
       c.iset_slot.assign(I + 1, 0);
       c.spec_slot_of.assign(A, 0);
@@ -275,26 +320,8 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
       for (int64_t w = 0; w < c.n_wide; ++w) c.wide_irank[w] = rank[c.wide_list[w]];
       if ((int64_t)c.big_irank.size() >= (int64_t(1) << 31)) return fail(err, "too many children of large nodes");
     }
-    // value slots (see Compiled::vslot)
+    // arrays read through the value slots (laid out with the set order above)
     {
-      c.vslot.assign(N, -1);
-      c.iset_vb.assign(c.I, 0);
-      int64_t next = 0;
-      for (int64_t d = 0; d < D; ++d) {
-        for (int32_t q = c.level_iset[2 * d]; q < c.level_iset[2 * d + 2]; ++q) {
-          c.iset_vb[q] = (int32_t)next;
-          for (int32_t k = c.iset_mem[q]; k < c.iset_mem[q + 1]; ++k) {
-            const int32_t h = c.mem_node[k];
-            for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
-          }
-        }
-        for (int64_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h) {
-          if (s.kind[c.spec_of_new[h]] != CFR_CHANCE) continue;
-          for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
-        }
-      }
-      if (next != N - 1) return fail(err, "internal error: value slots do not cover the tree");
-      c.vslot[0] = (int32_t)(N - 1);
       c.mem_vs.resize(c.n_dec);
       for (int64_t k = 0; k < c.n_dec; ++k) c.mem_vs[k] = c.vslot[c.mem_node[k]];
       const size_t nn = c.chance_list.size();

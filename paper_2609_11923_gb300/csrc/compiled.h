@@ -31,7 +31,8 @@ struct Compiled {
   std::vector<int32_t> node_slot;    // [N]
   std::vector<int32_t> level_begin;  // [D+2]: nodes of depth d are level_begin[d] .. level_begin[d+1]-1
   // Information sets in compiled order: by depth, player 1 before player 2,
-  // then by first member. Slots are contiguous per set in that order.
+  // then by the smallest value slot among the set's members (first member on
+  // ties; see compile_game). Slots are contiguous per set in that order.
   std::vector<int32_t> iset_slot;    // [I+1]
   std::vector<int32_t> iset_mem;     // [I+1] offsets into mem_node
   std::vector<int32_t> mem_node;     // [n_dec] members, ascending node id per set

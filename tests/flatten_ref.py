@@ -3,9 +3,10 @@
 Written from the definitions, not from the C++ compiler: breadth-first
 numbering (the paper's compile pass: parents before children, siblings in
 action order), depth blocks = distinct parent depths (eq. (blocks)),
-information sets ordered by (depth, player, first member), slots contiguous in
-that order, members ascending, chance product along the path and the values
-template pi_c(z) u(z) (eq. (template)).
+information sets ordered by depth, then player, then the smallest value slot
+among their members (first member on ties), slots contiguous in that order,
+members ascending, chance product along the path and the values template
+pi_c(z) u(z) (eq. (template)), value slots laid out depth by depth.
 """
 from collections import deque
 
@@ -37,12 +38,41 @@ def flatten(g):
     D = int(depth[internal].max()) + 1 if internal.any() else 0
     level_begin = np.array([int(np.searchsorted(depth, d)) for d in range(D + 1)] + [N], dtype=np.int32)
     kinds = np.array([g.kind[v] for v in order])
-    # information sets
-    first = {}
+    # information sets and value slots, depth by depth: the sets of a depth
+    # go player 1 first, then player 2, each group by the smallest value slot
+    # among its members (ties: first member); then the children of those
+    # sets' members take the next value slots (set, member, action order),
+    # then the children of the depth's chance nodes (node order); the root's
+    # value goes last
+    child_begin_l = child_begin.tolist()
+    first, mem_of = {}, {}
     for h, v in enumerate(order):
         if kinds[h] in (P1, P2):
             first.setdefault(int(g.infoset[v]), h)
-    sets = sorted(first, key=lambda s: (depth[first[s]], int(g.iset_player[s]), first[s]))
+            mem_of.setdefault(int(g.infoset[v]), []).append(h)
+    by_first = sorted(first, key=lambda s: first[s])
+    vslot = np.full(N, -1, dtype=np.int64)
+    vslot[0] = N - 1
+    sets, vb_of = [], {}
+    nxt = 0
+    for d in range(D):
+        here = [s_ for s_ in by_first if depth[first[s_]] == d]
+        start = len(sets)
+        for p in (0, 1):
+            grp = [s_ for s_ in here if int(g.iset_player[s_]) == p]
+            sets.extend(sorted(grp, key=lambda s_: (min(vslot[h] for h in mem_of[s_]), first[s_])))
+        for s_ in sets[start:]:
+            vb_of[s_] = nxt
+            for h in mem_of[s_]:
+                for x in range(child_begin_l[h], child_begin_l[h + 1]):
+                    vslot[x] = nxt
+                    nxt += 1
+        for h in range(level_begin[d], level_begin[d + 1]):
+            if kinds[h] == CHANCE:
+                for x in range(child_begin_l[h], child_begin_l[h + 1]):
+                    vslot[x] = nxt
+                    nxt += 1
+    assert nxt == N - 1 or N == 1
     cid = {s: i for i, s in enumerate(sets)}
     nact = np.array([g.iset_nact[s] for s in sets], dtype=np.int64)
     iset_slot = np.concatenate([[0], np.cumsum(nact)]).astype(np.int32)
@@ -107,28 +137,7 @@ def flatten(g):
             big.append(ce - cb)
             big.extend(int(r) for r in kids)
     mem_irank = rank[mem_node] if len(mem_node) else np.zeros(0, np.int64)
-    # value slots: per parent depth, the blocks of the sets' members' children
-    # (set order, member order, action order), then the chance nodes' children
-    # (node order); the root's value goes last
-    vslot = np.full(N, -1, dtype=np.int64)
-    iset_vb = np.zeros(len(sets), dtype=np.int64)
-    nxt = 0
-    for d in range(D):
-        for ci, s_ in enumerate(sets):
-            if depth[first[s_]] != d:
-                continue
-            iset_vb[ci] = nxt
-            for h in members[ci]:
-                for x in range(child_begin[h], child_begin[h + 1]):
-                    vslot[x] = nxt
-                    nxt += 1
-        for h in range(level_begin[d], level_begin[d + 1]):
-            if kinds[h] == CHANCE:
-                for x in range(child_begin[h], child_begin[h + 1]):
-                    vslot[x] = nxt
-                    nxt += 1
-    assert nxt == N - 1
-    vslot[0] = N - 1
+    iset_vb = np.array([vb_of[s_] for s_ in sets], dtype=np.int64)
     tmpl_vs = np.zeros(N)
     tmpl_vs[vslot] = tmpl
 
