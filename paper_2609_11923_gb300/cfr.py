@@ -27,6 +27,7 @@ P64, P32 = 0, 1
 EXEC_AUTO, EXEC_LEVELS, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2, 3
 RULE_CFR_PLUS, RULE_CFR, RULE_PCFR_PLUS = 0, 1, 2
 ORDER_SIMULTANEOUS, ORDER_ALTERNATING = 0, 1
+REACH_BFS, REACH_SLOTS = 0, 1
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
@@ -54,7 +55,7 @@ class Options(ctypes.Structure):
     _fields_ = [
         ("precision", ctypes.c_int), ("exec_form", ctypes.c_int), ("rule", ctypes.c_int),
         ("lanes_per_set", ctypes.c_int), ("persistent_ctas", ctypes.c_int),
-        ("barrier_spin_limit", ctypes.c_int64), ("order", ctypes.c_int),
+        ("barrier_spin_limit", ctypes.c_int64), ("order", ctypes.c_int), ("reach_order", ctypes.c_int),
     ]
 
 
@@ -155,11 +156,12 @@ def spec_struct(spec) -> Tuple[GameSpecC, list]:
 
 
 def make_options(precision=P32, exec_form=EXEC_AUTO, rule=RULE_CFR_PLUS, lanes_per_set=0, persistent_ctas=0,
-                 barrier_spin_limit=0, order=ORDER_SIMULTANEOUS) -> Options:
+                 barrier_spin_limit=0, order=ORDER_SIMULTANEOUS, reach_order=REACH_BFS) -> Options:
     o = Options()
     o.precision, o.exec_form, o.rule = precision, exec_form, rule
     o.lanes_per_set, o.persistent_ctas, o.barrier_spin_limit = lanes_per_set, persistent_ctas, barrier_spin_limit
     o.order = order
+    o.reach_order = reach_order
     return o
 
 
@@ -334,12 +336,13 @@ class Solver:
 
     def __init__(self, spec, precision: int = P32, exec_form: int = EXEC_AUTO, rule: int = RULE_CFR_PLUS,
                  lanes_per_set: int = 0, persistent_ctas: int = 0, barrier_spin_limit: int = 0,
-                 device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS):
+                 device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS,
+                 reach_order: int = REACH_BFS):
         import torch
 
         self.torch = torch
         self.opts = make_options(precision, exec_form, rule, lanes_per_set, persistent_ctas, barrier_spin_limit,
-                                 order)
+                                 order, reach_order)
         self.h = cfr_compile(spec, self.opts)
         self.counts = cfr_get_counts(self.h)
         self.n_slots = self.counts["n_slots"]

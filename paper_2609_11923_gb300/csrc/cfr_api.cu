@@ -138,7 +138,8 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   const int lp = h->opt.lanes_per_set;
   if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32 or 256"); }
   std::string err;
-  int rc = compile_game(*spec, h->c, err);
+  if (h->opt.reach_order != CFR_REACH_BFS && h->opt.reach_order != CFR_REACH_SLOTS) { delete h; return set_err(CFR_ERR_ARG, "bad reach_order"); }
+  int rc = compile_game(*spec, h->c, err, h->opt.reach_order);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
   if (lp != 0 && (lp < 4 || lp == kThreads) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2 or 256 needs sets of at most 8 actions"); }

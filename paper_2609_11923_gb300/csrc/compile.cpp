@@ -21,7 +21,7 @@ static int fail(std::string &err, const std::string &msg) {
   return CFR_ERR_INVALID_SPEC;
 }
 
-int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
+int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reach_order) {
   try {
     const int64_t N = s.n_nodes, I = s.n_infosets;
     if (N < 1 || N >= (int64_t(1) << 31) - 2) return fail(err, "n_nodes must be in [1, 2^31-2)");
@@ -276,12 +276,27 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err) {
     c.level_chance[D] = (int32_t)c.chance_list.size();
     c.level_wide[D] = (int32_t)c.wide_list.size();
     c.n_wide = (int64_t)c.wide_list.size();
-    // compact internal-node index space
+    // compact internal-node index space. Breadth-first order (default): the
+    // forward reads parents and writes children as two streams. Value-slot
+    // order (the root, then depth by depth in parents' block order): the
+    // members of the sets processed together have neighbouring ranks, which
+    // suits small latency-bound games; a parent's internal children have
+    // consecutive ranks in both.
     {
       std::vector<int32_t> rank(N, -1);
       int32_t r = 0;
-      for (int64_t h = 0; h < N; ++h)
-        if (c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;
+      if (reach_order == CFR_REACH_SLOTS) {
+        if (N > 0 && c.child_begin[1] > c.child_begin[0]) rank[0] = r++;
+        std::vector<int32_t> node_of_slot(N > 0 ? N - 1 : 0);
+        for (int64_t h = 1; h < N; ++h) node_of_slot[c.vslot[h]] = (int32_t)h;
+        for (int64_t q = 0; q + 1 < N; ++q) {
+          const int32_t h = node_of_slot[q];
+          if (c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;
+        }
+      } else {
+        for (int64_t h = 0; h < N; ++h)
+          if (c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;
+      }
       c.level_int.assign(D + 1, 0);
       for (int64_t h = 0; h < N; ++h)  // internal nodes sit at depths < D
         if (rank[h] >= 0 && depth[h] < D) c.level_int[depth[h] + 1]++;

@@ -87,7 +87,7 @@ struct Compiled {
 };
 
 // Returns CFR_OK or CFR_ERR_INVALID_SPEC / CFR_ERR_HOST_MEMORY with a message.
-int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err);
+int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err, int reach_order = CFR_REACH_BFS);
 
 // Chance folding from the retained edge probabilities and payoffs: the
 // products root..h in path order (pc), the template pi_c(z) u(z) (eq.

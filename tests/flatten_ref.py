@@ -18,7 +18,9 @@ WIDE = 1024
 WIDE_CHUNK = 2048
 
 
-def flatten(g):
+def flatten(g, reach_order=0):
+    """reach_order 0: internal ranks in breadth-first order; 1: the root,
+    then by (depth, value slot)."""
     N = g.n_nodes
     order = []
     depth_of = {}
@@ -113,13 +115,17 @@ def flatten(g):
             pc[new[c]] = pc[h] * g.chance_prob[q_] if kinds[h] == CHANCE else pc[h]
         if kinds[h] == TERMINAL:
             tmpl[h] = pc[h] * g.payoff[v]
-    # compact space of internal nodes (reach lives only there)
+    # compact space of internal nodes (reach lives only there): breadth-first,
+    # or the root then by (depth, value slot)
     internal = nch > 0
     rank = np.full(N, -1, dtype=np.int64)
-    rank[internal] = np.arange(int(internal.sum()))
+    int_nodes = np.nonzero(internal)[0].tolist()
+    if reach_order == 1:
+        int_nodes = sorted(int_nodes, key=lambda h: (depth[h], vslot[h]))
+    rank[int_nodes] = np.arange(len(int_nodes))
     level_int = np.array([int(internal[:level_begin[d]].sum()) for d in range(D + 1)], dtype=np.int32)
     int_slot, int_mask, int_cirank, big = [], [], [], []
-    for h in np.nonzero(internal)[0]:
+    for h in int_nodes:  # records in rank order
         cb, ce = child_begin[h], child_begin[h + 1]
         kids = rank[cb:ce]
         int_slot.append(node_slot[h])

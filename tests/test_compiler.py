@@ -27,11 +27,12 @@ GAMES = {
 }
 
 
+@pytest.mark.parametrize("reach_order", [cfr.REACH_BFS, cfr.REACH_SLOTS])
 @pytest.mark.parametrize("name", list(GAMES))
-def test_arrays_bit_exact(name):
+def test_arrays_bit_exact(name, reach_order):
     g = GAMES[name]()
-    ref = flatten(g)
-    h = cfr.cfr_compile(g)
+    ref = flatten(g, reach_order)
+    h = cfr.cfr_compile(g, cfr.make_options(reach_order=reach_order))
     try:
         for key in cfr.EXPORT:
             if key == "level_lanes":  # a runtime choice, not a compiled array
