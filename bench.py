@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--max-iters", type=int, default=5000, help="serving only: iteration cap per solve")
     p.add_argument("--baseline-sample", type=int, default=48, help="serving only: solves timed one by one")
     p.add_argument("--exec", dest="exec_form", default="graph", choices=["graph", "levels", "persistent", "auto"])
+    p.add_argument("--reach-order", default="members", choices=["members", "bfs", "slots"],
+                   help="layout of the internal nodes' reach (members: the forward pulls; bfs, slots: it pushes)")
     p.add_argument("--precision", default="p32", choices=["p32", "p64"])
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--deal-stride", type=int, default=1,
@@ -228,7 +230,9 @@ def run_ours(args):
     forms = {"graph": cfr.EXEC_GRAPH, "levels": cfr.EXEC_LEVELS, "persistent": cfr.EXEC_PERSISTENT,
              "auto": cfr.EXEC_AUTO}
     prec = cfr.P32 if args.precision == "p32" else cfr.P64
-    solver = cfr.Solver(spec, precision=prec, exec_form=forms[args.exec_form], device=str(dev))
+    orders = {"members": cfr.REACH_MEMBERS, "bfs": cfr.REACH_BFS, "slots": cfr.REACH_SLOTS}
+    solver = cfr.Solver(spec, precision=prec, exec_form=forms[args.exec_form], device=str(dev),
+                        reach_order=orders[args.reach_order])
     counts = solver.counts
     E, D = counts["n_edges"], counts["depth_blocks"]
     pot, n_nodes = spec.pot, spec.n_nodes
@@ -325,7 +329,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle(wl, args.cpu_seconds)
 
-    per_iter_launches = {cfr.EXEC_GRAPH: 2 * D, cfr.EXEC_LEVELS: 2 * D}.get(counts["exec_form"], 0)
+    # per depth one forward and one backward launch; in member order the
+    # deepest depth has no forward launch (no internal node below it pulls)
+    fwd_launches = D - 1 if args.reach_order == "members" else D
+    per_iter_launches = {cfr.EXEC_GRAPH: fwd_launches + D, cfr.EXEC_LEVELS: fwd_launches + D}.get(counts["exec_form"], 0)
     gpu_launches = args.steps * per_iter_launches if per_iter_launches else 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -337,7 +344,7 @@ def run_ours(args):
                    "description": wl["desc"], "nodes": n_nodes, "edges": E,
                    "infosets": counts["n_infosets"], "slots": counts["n_slots"], "depth_blocks": D,
                    "precision": args.precision + (" (FP64 regret/average accumulators)" if prec == cfr.P32 else ""),
-                   "exec_form": args.exec_form, "pot": pot, "parallelism": "replicas x%d" % world,
+                   "exec_form": args.exec_form, "reach_order": args.reach_order, "pot": pot, "parallelism": "replicas x%d" % world,
                    "lanes_per_set_by_depth": [int(x) for x in lanes],
                    "autotuned": not args.no_autotune,
                    "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % (solver.arena_bytes / 1e9)},

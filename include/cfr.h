@@ -72,7 +72,7 @@ enum { CFR_P64 = 0, CFR_P32 = 1 };
 enum { CFR_EXEC_AUTO = 0, CFR_EXEC_LEVELS = 1, CFR_EXEC_GRAPH = 2, CFR_EXEC_PERSISTENT = 3 };
 enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1, CFR_RULE_PCFR_PLUS = 2 };
 enum { CFR_ORDER_SIMULTANEOUS = 0, CFR_ORDER_ALTERNATING = 1 };
-enum { CFR_REACH_BFS = 0, CFR_REACH_SLOTS = 1 };
+enum { CFR_REACH_MEMBERS = 0, CFR_REACH_BFS = 1, CFR_REACH_SLOTS = 2 };
 
 typedef struct cfr_options {
   /* CFR_P64: every value in FP64 (the parity mode). CFR_P32: reach, values,
@@ -101,11 +101,15 @@ typedef struct cfr_options {
    * player 2's with player 1's new strategy; each half accumulates only its
    * player's average (Section 3; Section 4.2 runs the body twice). */
   int order;
-  /* Order of the internal nodes' reach (a layout choice; results are the
-   * same): CFR_REACH_BFS, breadth-first (the forward pass streams; best for
-   * large games), or CFR_REACH_SLOTS, the order of their value slots (the
-   * sets processed together read neighbouring reach; best for small
-   * latency-bound games such as batched subgames). */
+  /* Order of the internal nodes' reach (a layout choice; results are
+   * bitwise the same). CFR_REACH_MEMBERS (default): depth by depth, the
+   * members of the depth's information sets in set order, then the depth's
+   * chance nodes; the backward pass reads each set's reach as one run and
+   * needs no rank table, and the forward pass pulls (every internal node
+   * reads its parent's reach). CFR_REACH_BFS: breadth-first, and
+   * CFR_REACH_SLOTS: the order of the nodes' value slots; in both a parent's
+   * internal children have consecutive ranks and the forward pass pushes
+   * (every parent writes its children's reach). */
   int reach_order;
 } cfr_options;
 

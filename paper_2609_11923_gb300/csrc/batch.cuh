@@ -140,11 +140,19 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
       const int upd = in.order ? (1 << hf) : 3;
       for (int d = 0; d < in.D; ++d) {
         const LevelWork w = in.lw[d];
-        for (int32_t qw = w.ib + rank * THREADS + (threadIdx.x & ~31); qw < w.ie; qw += 4 * NT) {
-          if (w.fan) fwd_int4<T, CLUSTERED, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), NT, w.ie);
-          else fwd_int4<T, CLUSTERED, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), NT, w.ie);
+        if (in.g.int_edge) {  // member order: depth d + 1 pulls
+          if (d + 1 < in.D) {
+            const int32_t qe = in.lw[d + 1].ie;
+            for (int32_t q = in.lw[d + 1].ib + ct; q < qe; q += kPull * NT)
+              fwd_pull<T, CLUSTERED>(in.g, st.sigma, st.reach, q, NT, qe);
+          }
+        } else {
+          for (int32_t qw = w.ib + rank * THREADS + (threadIdx.x & ~31); qw < w.ie; qw += 4 * NT) {
+            if (w.fan) fwd_int4<T, CLUSTERED, true>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), NT, w.ie);
+            else fwd_int4<T, CLUSTERED, false>(in.g, st.sigma, st.reach, qw + (threadIdx.x & 31), NT, w.ie);
+          }
+          for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T, CLUSTERED>(in.g, st.reach, i, ct, NT);
         }
-        for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<T, CLUSTERED>(in.g, st.reach, i, ct, NT);
         level_sync<CLUSTERED>();
       }
       for (int d = in.D - 1; d >= 0; --d) {
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
         if (rank == 0)
           for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
         for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
+          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd, w.koff);
         level_sync<CLUSTERED>();
       }
     }
@@ -182,11 +190,19 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
   __syncthreads();
   for (int d = 0; d < in.D; ++d) {
     const LevelWork w = in.lw[d];
-    for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
-      if (w.fan) fwd_int4<double, false, true>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
-      else fwd_int4<double, false, false>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
+    if (g.int_edge) {  // member order: depth d + 1 pulls
+      if (d + 1 < in.D) {
+        const int32_t qe = in.lw[d + 1].ie;
+        for (int32_t q = in.lw[d + 1].ib + (int32_t)threadIdx.x; q < qe; q += kPull * THREADS)
+          fwd_pull<double, false>(g, in.sbs, in.reach2, q, THREADS, qe);
+      }
+    } else {
+      for (int32_t qw = w.ib + (threadIdx.x & ~31); qw < w.ie; qw += 4 * THREADS) {
+        if (w.fan) fwd_int4<double, false, true>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
+        else fwd_int4<double, false, false>(g, in.sbs, in.reach2, qw + (threadIdx.x & 31), THREADS, w.ie);
+      }
+      for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double, false>(g, in.reach2, i, threadIdx.x, THREADS);
     }
-    for (int32_t i = w.wd0; i < w.wd1; ++i) cta_fwd_wide<double, false>(g, in.reach2, i, threadIdx.x, THREADS);
     __syncthreads();
   }
   const int lane = threadIdx.x % LANES, gid = threadIdx.x / LANES;
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
         if (k < m1) {
           const int32_t h = __ldg(g.mem_vs + k);
           const int32_t cb = vb0 + (k - m0) * na;
-          const double2 r = in.reach2[__ldg(g.mem_irank + k)];
+          const double2 r = in.reach2[member_rank(g, k, w.koff)];
           const double po = p ? r.x : r.y;
           double oth = 0.0, va = 0.0;
 #pragma unroll

@@ -57,7 +57,7 @@ struct cfr_handle {
   // arena layout
   Buf b_iset_slot, b_iset_mem, b_iset_vb, b_mem_vs, b_ch_vb, b_ch_nch, b_ch_vs, b_spec_slot, b_levels;
   Buf b_wide_vb, b_wide_nch, b_wide_vs, b_wide_chunk, b_wide_part, b_wide_cnt;
-  Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_mem_irank, b_wide_irank;
+  Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_int_edge, b_mem_irank, b_wide_irank;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
   size_t plan_bytes = 0;
   char *arena = nullptr;
@@ -100,12 +100,14 @@ static void plan(cfr_handle *h) {
   take(h->b_wide_chunk, 4 * (c.n_wide + 1));
   take(h->b_wide_part, 3 * 8 * (size_t)c.wide_chunk.back());
   take(h->b_wide_cnt, 4 * c.n_wide);
-  take(h->b_int_slot, 4 * c.n_int);
-  take(h->b_int_mask, 4 * c.n_int);
-  take(h->b_int_cirank, 4 * c.n_int);
+  // push records (breadth-first or value-slot order) or pull edges (member order)
+  take(h->b_int_slot, 4 * c.int_slot.size());
+  take(h->b_int_mask, 4 * c.int_mask.size());
+  take(h->b_int_cirank, 4 * c.int_cirank.size());
   take(h->b_big_irank, 4 * c.big_irank.size());
-  take(h->b_mem_irank, 4 * c.n_dec);
-  take(h->b_wide_irank, 4 * c.n_wide);
+  take(h->b_int_edge, 4 * c.int_edge.size());
+  take(h->b_mem_irank, c.int_edge.empty() ? 4 * c.n_dec : 0);  // member order: ranks follow from k
+  take(h->b_wide_irank, 4 * c.wide_irank.size());
   take(h->b_reach, 2 * T * std::max<int64_t>(c.n_int, 1));  // internal nodes only
   take(h->b_v, T * c.N);  // value slots
   take(h->b_sigma, T * (c.A + 1));
@@ -138,7 +140,7 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   const int lp = h->opt.lanes_per_set;
   if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32 or 256"); }
   std::string err;
-  if (h->opt.reach_order != CFR_REACH_BFS && h->opt.reach_order != CFR_REACH_SLOTS) { delete h; return set_err(CFR_ERR_ARG, "bad reach_order"); }
+  if (h->opt.reach_order < CFR_REACH_MEMBERS || h->opt.reach_order > CFR_REACH_SLOTS) { delete h; return set_err(CFR_ERR_ARG, "bad reach_order"); }
   int rc = compile_game(*spec, h->c, err, h->opt.reach_order);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
@@ -175,8 +177,10 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
     w.wd1 = c.level_wide[d + 1];
     w.wc0 = c.wide_chunk[w.wd0];
     w.wc1 = c.wide_chunk[w.wd1];
+    // member order: member k of depth d has rank k + koff
+    w.koff = c.int_edge.empty() ? 0 : c.level_int[d] - c.iset_mem[c.level_iset[2 * d]];
     w.fan = 0;  // a chance node of this depth has its children written warp-wide
-    for (int64_t q = c.level_int[d]; q < c.level_int[d + 1] && !w.fan; ++q) {
+    for (int64_t q = c.level_int[d]; q < c.level_int[d + 1] && !w.fan && !c.int_mask.empty(); ++q) {
       const uint32_t m = c.int_mask[q];
       if (c.int_slot[q] < 0 && m != 0u && ((m & kBigNode) || __builtin_popcount(m) > kFanLight)) w.fan = 1;
     }
@@ -204,7 +208,7 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
                               h->b_ch_vb.bytes + h->b_ch_nch.bytes + h->b_ch_vs.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
                               h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes +
                               h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
-                              h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes +
+                              h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes + h->b_int_edge.bytes +
                               h->b_mem_irank.bytes + h->b_wide_irank.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
@@ -237,7 +241,8 @@ static GameView game_view(const cfr_handle *h) {
   g.int_mask = h->p<uint32_t>(h->b_int_mask);
   g.int_cirank = h->p<int32_t>(h->b_int_cirank);
   g.big_irank = h->p<int32_t>(h->b_big_irank);
-  g.mem_irank = h->p<int32_t>(h->b_mem_irank);
+  g.int_edge = h->c.int_edge.empty() ? nullptr : h->p<int2>(h->b_int_edge);
+  g.mem_irank = h->c.int_edge.empty() ? h->p<int32_t>(h->b_mem_irank) : nullptr;
   g.wide_irank = h->p<int32_t>(h->b_wide_irank);
   return g;
 }
@@ -262,7 +267,17 @@ static int grid_for(int64_t work, int per_block) {
 // block per wide chunk; depths with many-child chance nodes take the form
 // that writes those children warp-wide.
 template <typename T>
-static int launch_fwd(const LevelWork &w, cudaStream_t s, const GameView &g, const T *sigma, vec2_t<T> *reach) {
+static int launch_fwd(const cfr_handle *h, int64_t d, cudaStream_t s, const GameView &g, const T *sigma,
+                      vec2_t<T> *reach) {
+  const LevelWork &w = h->levels[d];
+  if (g.int_edge) {  // member order: the next depth's internal nodes pull their reach
+    if (d + 1 >= h->c.D) return CFR_OK;
+    const LevelWork &n = h->levels[d + 1];
+    const int nb = grid_for((n.ie - n.ib + kPull - 1) / kPull, kThreads);
+    fwd_pull_kernel<T><<<nb, kThreads, 0, s>>>(g, sigma, reach, n.ib, n.ie);
+    CK(cudaGetLastError());
+    return CFR_OK;
+  }
   const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
   if (w.fan) fwd_level_kernel<T, true><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, sigma, reach, w, nb);
   else fwd_level_kernel<T, false><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, sigma, reach, w, nb);
@@ -318,12 +333,13 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_wide_nch, c.wide_nch.data(), 4 * c.n_wide))) return rc;
   if ((rc = up(h->b_wide_vs, c.wide_vs.data(), 4 * c.n_wide))) return rc;
   if ((rc = up(h->b_wide_chunk, c.wide_chunk.data(), 4 * (c.n_wide + 1)))) return rc;
-  if ((rc = up(h->b_int_slot, c.int_slot.data(), 4 * c.n_int))) return rc;
-  if ((rc = up(h->b_int_mask, c.int_mask.data(), 4 * c.n_int))) return rc;
-  if ((rc = up(h->b_int_cirank, c.int_cirank.data(), 4 * c.n_int))) return rc;
+  if ((rc = up(h->b_int_slot, c.int_slot.data(), 4 * c.int_slot.size()))) return rc;
+  if ((rc = up(h->b_int_mask, c.int_mask.data(), 4 * c.int_mask.size()))) return rc;
+  if ((rc = up(h->b_int_cirank, c.int_cirank.data(), 4 * c.int_cirank.size()))) return rc;
   if ((rc = up(h->b_big_irank, c.big_irank.data(), 4 * c.big_irank.size()))) return rc;
-  if ((rc = up(h->b_mem_irank, c.mem_irank.data(), 4 * c.n_dec))) return rc;
-  if ((rc = up(h->b_wide_irank, c.wide_irank.data(), 4 * c.n_wide))) return rc;
+  if ((rc = up(h->b_int_edge, c.int_edge.data(), 4 * c.int_edge.size()))) return rc;
+  if ((rc = up(h->b_mem_irank, c.mem_irank.data(), h->b_mem_irank.bytes))) return rc;
+  if ((rc = up(h->b_wide_irank, c.wide_irank.data(), 4 * c.wide_irank.size()))) return rc;
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
   CK(cudaMemsetAsync(h->arena + h->b_bar.off, 0, 16, s));
   CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
@@ -363,7 +379,7 @@ static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
   for (int hf = 0; hf < halves; ++hf) {
     const int upd = halves == 2 ? (1 << hf) : 3;
     for (int64_t d = 0; d < c.D; ++d) {
-      int rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
+      int rc = launch_fwd<T>(h, d, s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
       if (rc) return rc;
     }
     for (int64_t d = c.D - 1; d >= 0; --d) {
@@ -552,7 +568,7 @@ extern "C" int cfr_exploitability(cfr_handle *h, double *out_expl, double *out_b
                                                                        h->p<double>(h->b_avg), h->p<double>(h->b_sbs));
   CK(cudaGetLastError());
   for (int64_t d = 0; d < c.D; ++d) {
-    int rc = launch_fwd<double>(h->levels[d], s, g, h->p<double>(h->b_sbs), h->p<double2>(h->b_reach2));
+    int rc = launch_fwd<double>(h, d, s, g, h->p<double>(h->b_sbs), h->p<double2>(h->b_reach2));
     if (rc) return rc;
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
@@ -697,6 +713,7 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 26: src = c.wide_nch.data(); n = (int64_t)c.wide_nch.size(); break;
     case 27: src = c.wide_vs.data(); n = (int64_t)c.wide_vs.size(); break;
     case 28: src = c.tmpl_vs.data(); n = (int64_t)c.tmpl_vs.size(); esz = 8; break;
+    case 29: src = c.int_edge.data(); n = (int64_t)c.int_edge.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -729,6 +746,11 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   const int64_t slots = c.iset_slot[i1] - c.iset_slot[i0];
   const int64_t dec = c.iset_mem[i1] - c.iset_mem[i0];
   const int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
+  if (!c.int_edge.empty()) {  // member order: the launch of depth d fills depth d + 1 by pulling
+    *fwd = 8 * nint_kids + 2 * T * nint + 2 * T * nint_kids + T * slots;
+    *bwd = 12 * sets + (32 + 2 * T) * slots + (4 + 3 * T) * dec + (12 + T) * nch + T * e;
+    return CFR_OK;
+  }
   int64_t big = 0;  // child lists of nodes with more than 31 children
   for (int64_t q = c.level_int[d]; q < c.level_int[d + 1]; ++q)
     if (c.int_mask[q] & kBigNode) big += 1 + c.big_irank[c.int_cirank[q]];
@@ -752,7 +774,7 @@ static int profile_t(cfr_handle *h, double *fwd_ms, double *bwd_ms, cudaStream_t
     cudaEvent_t *e = ev.data() + 4 * c.D * hf;
     for (int64_t d = 0; d < c.D && rc == CFR_OK; ++d) {
       CK(cudaEventRecord(e[2 * d], s));
-      rc = launch_fwd<T>(h->levels[d], s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
+      rc = launch_fwd<T>(h, d, s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
       CK(cudaEventRecord(e[2 * d + 1], s));
     }
     for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
@@ -940,7 +962,9 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
   std::vector<int> grids;
   for (int64_t d = 0; d < c.D; ++d) {
     const LevelWork &w = h->levels[d];
-    grids.push_back(grid_for((w.ie - w.ib + 3) / 4, kThreads) + (w.wc1 - w.wc0));
+    if (c.int_edge.empty()) grids.push_back(grid_for((w.ie - w.ib + 3) / 4, kThreads) + (w.wc1 - w.wc0));
+    else if (d + 1 < c.D)  // member order: the launch of depth d pulls depth d + 1
+      grids.push_back(grid_for((h->levels[d + 1].ie - h->levels[d + 1].ib + kPull - 1) / kPull, kThreads));
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
     const LevelWork &w = h->levels[d];

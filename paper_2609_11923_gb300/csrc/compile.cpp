@@ -279,13 +279,26 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
     // compact internal-node index space. Breadth-first order (default): the
     // forward reads parents and writes children as two streams. Value-slot
     // order (the root, then depth by depth in parents' block order): the
-    // members of the sets processed together have neighbouring ranks, which
-    // suits small latency-bound games; a parent's internal children have
-    // consecutive ranks in both.
+    // members of the sets processed together have neighbouring ranks; a
+    // parent's internal children have consecutive ranks in both, and the
+    // forward pushes each parent's reach to them. Member order (depth by
+    // depth: the members of the depth's sets in set order, then the depth's
+    // chance nodes): the backward reads every set's reach as one run and
+    // needs no rank table (member k of depth d has rank k + a per-depth
+    // offset); the forward pulls, each internal node reading its parent's
+    // reach through int_edge.
     {
       std::vector<int32_t> rank(N, -1);
       int32_t r = 0;
-      if (reach_order == CFR_REACH_SLOTS) {
+      const bool members = reach_order == CFR_REACH_MEMBERS;
+      if (members) {
+        for (int64_t d = 0; d < D; ++d) {
+          const int32_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
+          for (int32_t k = c.iset_mem[i0]; k < c.iset_mem[i1]; ++k) rank[c.mem_node[k]] = r++;
+          for (int32_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h)
+            if (c.node_slot[h] < 0 && c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;
+        }
+      } else if (reach_order == CFR_REACH_SLOTS) {
         if (N > 0 && c.child_begin[1] > c.child_begin[0]) rank[0] = r++;
         std::vector<int32_t> node_of_slot(N > 0 ? N - 1 : 0);
         for (int64_t h = 1; h < N; ++h) node_of_slot[c.vslot[h]] = (int32_t)h;
@@ -301,39 +314,58 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
       for (int64_t h = 0; h < N; ++h)  // internal nodes sit at depths < D
         if (rank[h] >= 0 && depth[h] < D) c.level_int[depth[h] + 1]++;
       for (int64_t d = 0; d < D; ++d) c.level_int[d + 1] += c.level_int[d];
-      c.int_slot.resize(r);
-      c.int_mask.resize(r);
-      c.int_cirank.resize(r);
+      c.int_slot.clear();
+      c.int_mask.clear();
+      c.int_cirank.clear();
       c.big_irank.clear();
-      for (int64_t h = 0; h < N; ++h) {
-        const int32_t q = rank[h];
-        if (q < 0) continue;
-        const int32_t cb = c.child_begin[h], ce = c.child_begin[h + 1];
-        const int32_t nch = ce - cb;
-        c.int_slot[q] = c.node_slot[h];
-        if (nch <= 31) {
-          uint32_t mask = 0;
-          int32_t first = 0;
-          bool got = false;
-          for (int32_t a = 0; a < nch; ++a)
-            if (rank[cb + a] >= 0) {
-              mask |= 1u << a;
-              if (!got) { first = rank[cb + a]; got = true; }
-            }
-          c.int_mask[q] = mask;
-          c.int_cirank[q] = first;
-        } else {
-          c.int_mask[q] = kBigNode;
-          c.int_cirank[q] = (int32_t)c.big_irank.size();
-          c.big_irank.push_back(nch);
-          for (int32_t a = 0; a < nch; ++a) c.big_irank.push_back(rank[cb + a]);
+      c.int_edge.clear();
+      c.wide_irank.clear();
+      if (members) {  // each internal node's parent rank and the slot word of its edge
+        c.int_edge.assign(2 * (size_t)r, -1);
+        for (int64_t h = 0; h < N; ++h) {
+          const int32_t q = rank[h];
+          if (q < 0) continue;
+          for (int32_t a = 0; a < c.child_begin[h + 1] - c.child_begin[h]; ++a) {
+            const int32_t k = rank[c.child_begin[h] + a];
+            if (k < 0) continue;
+            c.int_edge[2 * (size_t)k] = q;
+            c.int_edge[2 * (size_t)k + 1] = c.node_slot[h] < 0 ? -1 : c.node_slot[h] + a;
+          }
         }
+      } else {  // each internal node's record for the forward that pushes
+        c.int_slot.resize(r);
+        c.int_mask.resize(r);
+        c.int_cirank.resize(r);
+        for (int64_t h = 0; h < N; ++h) {
+          const int32_t q = rank[h];
+          if (q < 0) continue;
+          const int32_t cb = c.child_begin[h], ce = c.child_begin[h + 1];
+          const int32_t nch = ce - cb;
+          c.int_slot[q] = c.node_slot[h];
+          if (nch <= 31) {
+            uint32_t mask = 0;
+            int32_t first = 0;
+            bool got = false;
+            for (int32_t a = 0; a < nch; ++a)
+              if (rank[cb + a] >= 0) {
+                mask |= 1u << a;
+                if (!got) { first = rank[cb + a]; got = true; }
+              }
+            c.int_mask[q] = mask;
+            c.int_cirank[q] = first;
+          } else {
+            c.int_mask[q] = kBigNode;
+            c.int_cirank[q] = (int32_t)c.big_irank.size();
+            c.big_irank.push_back(nch);
+            for (int32_t a = 0; a < nch; ++a) c.big_irank.push_back(rank[cb + a]);
+          }
+        }
+        c.wide_irank.resize(c.n_wide);
+        for (int64_t w = 0; w < c.n_wide; ++w) c.wide_irank[w] = rank[c.wide_list[w]];
+        if ((int64_t)c.big_irank.size() >= (int64_t(1) << 31)) return fail(err, "too many children of large nodes");
       }
       c.mem_irank.resize(c.n_dec);
       for (int64_t k = 0; k < c.n_dec; ++k) c.mem_irank[k] = rank[c.mem_node[k]];
-      c.wide_irank.resize(c.n_wide);
-      for (int64_t w = 0; w < c.n_wide; ++w) c.wide_irank[w] = rank[c.wide_list[w]];
-      if ((int64_t)c.big_irank.size() >= (int64_t(1) << 31)) return fail(err, "too many children of large nodes");
     }
     // arrays read through the value slots (laid out with the set order above)
     {
@@ -406,8 +438,14 @@ int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
   // member its value slot and internal rank (8 B), its reach lanes read and
   // its value written; per chance node its block, child count and value slot
   // (12 B) and its value written; every edge's child value read once.
+  // Member order: the forward reads every internal node's edge (parent rank
+  // and slot word, 8 B) instead of the 12-byte records (each parent's reach
+  // counted once), and the backward reads no member rank.
   const int64_t T = precision == CFR_P64 ? 8 : 4;
   const int64_t int_kids = c.n_int > 0 ? c.n_int - 1 : 0;  // every internal node but the root
+  if (!c.int_edge.empty())
+    return 8 * int_kids + 2 * T * c.n_int + 2 * T * int_kids + 12 * c.I + (32 + 3 * T) * c.A +
+           (4 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
   return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 12 * c.I +
          (32 + 3 * T) * c.A + (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
 }

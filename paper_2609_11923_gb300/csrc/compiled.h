@@ -51,14 +51,19 @@ struct Compiled {
   //   int_slot  = node_slot (set's first slot | player-2 bit, or -1 for chance)
   //   int_mask  = bit a set if child a is internal (nodes with <= 31 children),
   //               or kBigNode for nodes with more children
-  //   int_cirank= rank of the first internal child (mask nodes), or the offset
-  //               of [nch, rank of child 0, rank of child 1, ...] in big_irank
-  //               (-1 for terminal children)
+  //   int_cirank= rank of the first internal child (mask nodes; the others
+  //               follow it), or the offset of [nch, rank of child 0, rank of
+  //               child 1, ...] in big_irank (-1 for terminal children)
   std::vector<int32_t> level_int;    // [D+1]
   std::vector<int32_t> int_slot;     // [n_int]
   std::vector<uint32_t> int_mask;    // [n_int]
   std::vector<int32_t> int_cirank;   // [n_int]
   std::vector<int32_t> big_irank;    // [...]
+  // member order only (the push records above and wide_irank stay empty):
+  //   int_edge  = [2 n_int] per internal node (rank order): its parent's rank
+  //               (root -1) and the slot word of the edge from the parent
+  //               (parent's slot word + action), or -1 under a chance node
+  std::vector<int32_t> int_edge;
   std::vector<int32_t> mem_irank;    // [n_dec] internal rank of each member
   std::vector<int32_t> wide_irank;   // [n_wide] internal rank of each wide node
   // Value slots. The value of node h lives in slot vslot[h] of the value
@@ -87,7 +92,7 @@ struct Compiled {
 };
 
 // Returns CFR_OK or CFR_ERR_INVALID_SPEC / CFR_ERR_HOST_MEMORY with a message.
-int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err, int reach_order = CFR_REACH_BFS);
+int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err, int reach_order = CFR_REACH_MEMBERS);
 
 // Chance folding from the retained edge probabilities and payoffs: the
 // products root..h in path order (pc), the template pi_c(z) u(z) (eq.

@@ -72,7 +72,10 @@ struct GameView {
   const uint32_t *__restrict__ int_mask;   // internal children (bit a), or kBigBit
   const int32_t *__restrict__ int_cirank;  // rank of the first internal child, or big_irank offset
   const int32_t *__restrict__ big_irank;   // [nch, child ranks...] of nodes with > 31 children
-  const int32_t *__restrict__ mem_irank;   // internal rank of each member (member order)
+  const int2 *__restrict__ int_edge;       // member order: each internal node's (parent rank, slot word of
+                                           //   its edge or -1 under chance); else null
+  const int32_t *__restrict__ mem_irank;   // internal rank of each member (null in member order:
+                                           //   member k of depth d has rank k + LevelWork::koff)
   const int32_t *__restrict__ wide_irank;  // internal rank of each wide node
 };
 
@@ -95,6 +98,7 @@ struct LevelWork {
   int32_t wd0, wd1;       // wide chance nodes of depth d (wide_* arrays)
   int32_t wc0, wc1;       // their chunks
   int32_t fan;            // 1 if a chance node of depth d has more than kFanLight internal children
+  int32_t koff;           // member order: rank - member index of depth d's members
 };
 
 // The wide node owning chunk q (binary search over the level's prefix).
@@ -262,6 +266,50 @@ __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T
     fwd_int4<T, false, FAN>(g, sigma, reach, qw + lane, stride, w.ie);
 }
 
+// Member order: each internal node of ranks [qb, qe) (one depth) pulls its
+// reach from its parent's, times the strategy of its edge in the acting
+// player's lane (a chance edge copies it). kPull nodes per thread in flight.
+constexpr int kPull = 4;
+template <typename T, bool PERSIST>
+__device__ __forceinline__ void fwd_pull(const GameView &g, const T *sigma, vec2_t<T> *reach, int32_t q,
+                                         int32_t stride, int32_t qe) {
+  int2 e[kPull];
+#pragma unroll
+  for (int u = 0; u < kPull; ++u) {
+    const int32_t x = q + u * stride;
+    e[u] = make_int2(-1, -1);
+    if (x < qe) e[u] = __ldg(g.int_edge + x);
+  }
+  vec2_t<T> r[kPull];
+  T sa[kPull];
+#pragma unroll
+  for (int u = 0; u < kPull; ++u) {
+    r[u].x = T(0); r[u].y = T(0);
+    sa[u] = T(1);
+    if (e[u].x >= 0) {
+      r[u] = ldm<PERSIST>(reach + e[u].x);
+      if (e[u].y >= 0) sa[u] = ldm<PERSIST>(sigma + (e[u].y & kMask));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kPull; ++u) {
+    if (e[u].x < 0) continue;
+    if (e[u].y >= 0) {
+      if (e[u].y & kP2Bit) r[u].y = r[u].y * sa[u];
+      else r[u].x = r[u].x * sa[u];
+    }
+    reach[q + u * stride] = r[u];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fwd_pull_kernel(GameView g, const T *sigma, vec2_t<T> *reach,
+                                                            int32_t qb, int32_t qe) {
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t q = qb + blockIdx.x * blockDim.x + threadIdx.x; q < qe; q += kPull * stride)
+    fwd_pull<T, false>(g, sigma, reach, q, stride, qe);
+}
+
 // ------------------------------------------------------------ group helpers
 template <int LANES>
 __device__ __forceinline__ unsigned group_mask() {
@@ -357,13 +405,19 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
 }
 
 // A member's two indices (member order: coalesced reads): its own value slot
-// and its internal rank (where its reach lives). Past the set's end: -1.
-__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, int32_t &ps, int32_t &ir) {
+// and its internal rank (where its reach lives; in member order the rank
+// follows from the member index). Past the set's end: -1.
+__device__ __forceinline__ int32_t member_rank(const GameView &g, int32_t k, int32_t koff) {
+  return g.mem_irank ? __ldg(g.mem_irank + k) : k + koff;
+}
+
+__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, int32_t koff, int32_t &ps,
+                                           int32_t &ir) {
   ps = -1;
   ir = -1;
   if (k < m1) {
     ps = __ldg(g.mem_vs + k);
-    ir = __ldg(g.mem_irank + k);
+    ir = member_rank(g, k, koff);
   }
 }
 
@@ -405,10 +459,10 @@ __device__ __forceinline__ void member_data(const GameView &g, const StateView<T
 // Indices, loads and per-member terms of one member (k < m1), or zeros.
 template <typename T, int MAXA, bool PERSIST>
 __device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
-                                             int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
-                                             T (&d)[MAXA], T (&mm)[MAXA]) {
+                                             int32_t m1, int32_t koff, int32_t vb, int32_t na, bool p2,
+                                             const T (&sig)[MAXA], T (&d)[MAXA], T (&mm)[MAXA]) {
   int32_t h, ir;
-  member_idx(g, k, m1, h, ir);
+  member_idx(g, k, m1, koff, h, ir);
   member_data<T, MAXA, PERSIST>(g, st, k, m0, m1, vb, na, p2, sig, h, ir, d, mm);
 }
 
@@ -444,7 +498,7 @@ __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsign
 // the set's slots runs one lane per action.
 template <typename T, int MAXA, int LANES, bool PERSIST>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                        int lane, unsigned mask, double wt, int rule, int upd) {
+                                        int lane, unsigned mask, double wt, int rule, int upd, int32_t koff) {
   const int32_t sb = __ldg(g.iset_slot + I);
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
@@ -461,12 +515,12 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   if constexpr (TWO) {
     if (k0 + LANES < m1) {
       int32_t ps0, ir0, ps1, ir1;
-      member_idx(g, k0 + lane, m1, ps0, ir0);
-      member_idx(g, k0 + LANES + lane, m1, ps1, ir1);
+      member_idx(g, k0 + lane, m1, koff, ps0, ir0);
+      member_idx(g, k0 + LANES + lane, m1, koff, ps1, ir1);
       for (; k0 + LANES < m1; k0 += 2 * LANES) {
         int32_t qs0, jr0, qs1, jr1;  // the next step's indices
-        member_idx(g, k0 + 2 * LANES + lane, m1, qs0, jr0);
-        member_idx(g, k0 + 3 * LANES + lane, m1, qs1, jr1);
+        member_idx(g, k0 + 2 * LANES + lane, m1, koff, qs0, jr0);
+        member_idx(g, k0 + 3 * LANES + lane, m1, koff, qs1, jr1);
         T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
         member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps0, ir0, d0, mm0);
         member_data<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, ps1, ir1, d1, mm1);
@@ -478,16 +532,16 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
     }
     for (; k0 < m1; k0 += LANES) {
       T d[MAXA], mm[MAXA];
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, d, mm);
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, koff, vb, na, p2, sig, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
       accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
     }
   } else {
     int32_t ps, ir;
-    member_idx(g, k0 + lane, m1, ps, ir);
+    member_idx(g, k0 + lane, m1, koff, ps, ir);
     for (; k0 < m1; k0 += LANES) {
       int32_t qs, jr;  // the next step's indices
-      member_idx(g, k0 + LANES + lane, m1, qs, jr);
+      member_idx(g, k0 + LANES + lane, m1, koff, qs, jr);
       T d[MAXA], mm[MAXA];
       member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
@@ -560,7 +614,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
 // finished by a fixed-shape tree. The slot update runs one thread per action.
 template <typename T, int MAXA>
 __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                              double wt, int rule, int upd) {
+                                              double wt, int rule, int upd, int32_t koff) {
   __shared__ T s_d[kThreads * MAXA], s_m[kThreads * MAXA];  // [member][action]
   __shared__ double s_pos[MAXA];
   const int tid = threadIdx.x;
@@ -577,10 +631,10 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
   }
   T r = T(0), m = T(0);  // P64: column tid's running sums (tid < na)
   int32_t ps, ir;
-  member_idx(g, m0 + tid, m1, ps, ir);
+  member_idx(g, m0 + tid, m1, koff, ps, ir);
   for (int32_t k0 = m0; k0 < m1; k0 += kThreads) {
     int32_t qs, jr;  // the next chunk's indices
-    member_idx(g, k0 + kThreads + tid, m1, qs, jr);
+    member_idx(g, k0 + kThreads + tid, m1, koff, qs, jr);
     T d[MAXA], mm[MAXA];
     member_data<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
     ps = qs;
@@ -670,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     const int first = nb_chance + nb_wide;
     const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + ((int)blockIdx.x - first); I < w.is1; I += (int)gridDim.x - first)
-      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd);
+      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd, w.koff);
   } else {
     constexpr int GPB = kThreads / LANES;
     const int first = nb_chance + nb_wide;
@@ -680,7 +734,7 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     const unsigned mask = group_mask<LANES>();
     const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd);
+      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd, w.koff);
   }
   if (bump_t) {  // depth 0 holds only the root: no other block reads t here
     __syncthreads();
@@ -770,11 +824,19 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
       const int upd = a.order ? (1 << hf) : 3;
       for (int d = 0; d < a.D; ++d) {
         const LevelWork w = a.lw[d];
-        for (int32_t qw = w.ib + (tid & ~31); qw < w.ie; qw += 4 * nthr) {
-          if (w.fan) fwd_int4<T, true, true>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
-          else fwd_int4<T, true, false>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+        if (a.g.int_edge) {  // member order: depth d + 1 pulls
+          if (d + 1 < a.D) {
+            const int32_t qe = a.lw[d + 1].ie;
+            for (int32_t q = a.lw[d + 1].ib + tid; q < qe; q += kPull * nthr)
+              fwd_pull<T, true>(a.g, a.st.sigma, a.st.reach, q, nthr, qe);
+          }
+        } else {
+          for (int32_t qw = w.ib + (tid & ~31); qw < w.ie; qw += 4 * nthr) {
+            if (w.fan) fwd_int4<T, true, true>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+            else fwd_int4<T, true, false>(a.g, a.st.sigma, a.st.reach, qw + (tid & 31), nthr, w.ie);
+          }
+          for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
         }
-        for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) fwd_wide_chunk<T, true>(a.g, w, a.st.reach, q);
         if (!grid_sync(a.bar)) return;
       }
       for (int d = a.D - 1; d >= 0; --d) {
@@ -782,7 +844,7 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
         for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
         for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
         for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd);
+          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd, w.koff);
         if (!grid_sync(a.bar)) return;
       }
     }
@@ -953,7 +1015,7 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
       if (k < m1) {
         const int32_t h = __ldg(g.mem_vs + k);
         const int32_t cb = vb0 + (k - m0) * na;
-        const double2 r = reach2[__ldg(g.mem_irank + k)];
+        const double2 r = reach2[member_rank(g, k, w.koff)];
         const double po = p ? r.x : r.y;
         double oth = 0.0, va = 0.0;
 #pragma unroll

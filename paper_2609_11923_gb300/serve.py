@@ -120,7 +120,7 @@ class Server:
         self.torch = torch
         self.pool = DevicePool(pool_bytes, device)
         self.max_active = max_active
-        self.opts = cfr.make_options(precision=precision, exec_form=cfr.EXEC_LEVELS, reach_order=cfr.REACH_SLOTS)
+        self.opts = cfr.make_options(precision=precision, exec_form=cfr.EXEC_LEVELS)
         self.threads, self.lanes = threads, lanes
         self.big_edges, self.cluster = big_edges, cluster
         self.big_threads, self.big_lanes = big_threads, big_lanes
@@ -220,7 +220,7 @@ def autotune_batch(specs, precision: int = cfr.P32, iters: int = 20, device="cud
     """Pick (threads, lanes) of the batched kernel by timing a sample batch."""
     import torch
 
-    opts = cfr.make_options(precision=precision, exec_form=cfr.EXEC_LEVELS, reach_order=cfr.REACH_SLOTS)
+    opts = cfr.make_options(precision=precision, exec_form=cfr.EXEC_LEVELS)
     hs = [cfr.cfr_compile(sp, opts) for sp in specs]
     sizes = [cfr.cfr_plan(h) for h in hs]
     pool = DevicePool(sum(((n + ALIGN - 1) & ~(ALIGN - 1)) for n in sizes) + ALIGN, device)

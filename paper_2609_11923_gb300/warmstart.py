@@ -166,7 +166,7 @@ def solve_batch(specs, iters: int, precision=cfr.P32, threads=1024, lanes=8, chu
 
     out = []
     s = int(torch.cuda.current_stream().cuda_stream)
-    opts = cfr.make_options(precision=precision, reach_order=cfr.REACH_SLOTS)
+    opts = cfr.make_options(precision=precision)
     for c0 in range(0, len(specs), chunk):
         part = specs[c0:c0 + chunk]
         hs = [cfr.cfr_compile(sp, opts) for sp in part]
@@ -253,7 +253,7 @@ def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iter
     import torch
 
     s = int(torch.cuda.current_stream().cuda_stream)
-    opts = cfr.make_options(precision=cfr.P32, reach_order=cfr.REACH_SLOTS)
+    opts = cfr.make_options(precision=cfr.P32)
     t0 = time.perf_counter()
     hs = [cfr.cfr_compile(sp, opts) for sp in specs]
     sizes = [cfr.cfr_plan(h) for h in hs]

@@ -18,9 +18,13 @@ WIDE = 1024
 WIDE_CHUNK = 2048
 
 
-def flatten(g, reach_order=0):
-    """reach_order 0: internal ranks in breadth-first order; 1: the root,
-    then by (depth, value slot)."""
+MEMBERS, BFS, SLOTS = 0, 1, 2  # internal-rank orders
+
+
+def flatten(g, reach_order=MEMBERS):
+    """Internal ranks: MEMBERS, depth by depth the members of the depth's
+    sets in member order, then its chance nodes; BFS, breadth-first; SLOTS,
+    the root, then by (depth, value slot)."""
     N = g.n_nodes
     order = []
     depth_of = {}
@@ -120,28 +124,41 @@ def flatten(g, reach_order=0):
     internal = nch > 0
     rank = np.full(N, -1, dtype=np.int64)
     int_nodes = np.nonzero(internal)[0].tolist()
-    if reach_order == 1:
+    if reach_order == SLOTS:
         int_nodes = sorted(int_nodes, key=lambda h: (depth[h], vslot[h]))
+    elif reach_order == MEMBERS:
+        mpos = {int(x): k for k, x in enumerate(mem_node)}
+        int_nodes = sorted(int_nodes, key=lambda h: (depth[h], 0, mpos[h]) if h in mpos else (depth[h], 1, h))
     rank[int_nodes] = np.arange(len(int_nodes))
     level_int = np.array([int(internal[:level_begin[d]].sum()) for d in range(D + 1)], dtype=np.int32)
-    int_slot, int_mask, int_cirank, big = [], [], [], []
-    for h in int_nodes:  # records in rank order
-        cb, ce = child_begin[h], child_begin[h + 1]
-        kids = rank[cb:ce]
-        int_slot.append(node_slot[h])
-        if ce - cb <= 31:
-            m = 0
-            for a, r in enumerate(kids):
-                if r >= 0:
-                    m |= 1 << a
-            int_mask.append(m)
-            firsts = [r for r in kids if r >= 0]
-            int_cirank.append(firsts[0] if firsts else 0)
-        else:
-            int_mask.append(1 << 31)
-            int_cirank.append(len(big))
-            big.append(ce - cb)
-            big.extend(int(r) for r in kids)
+    int_slot, int_mask, int_cirank, big, int_edge, wide_irank = [], [], [], [], [], []
+    if reach_order == MEMBERS:  # each internal node's parent rank and edge slot word (the forward pulls)
+        int_edge = [-1] * (2 * len(int_nodes))
+        for h in int_nodes:
+            for a in range(child_begin[h + 1] - child_begin[h]):
+                k = int(rank[child_begin[h] + a])
+                if k >= 0:
+                    int_edge[2 * k] = int(rank[h])
+                    int_edge[2 * k + 1] = -1 if node_slot[h] < 0 else int(node_slot[h]) + a
+    else:  # each internal node's record (the forward pushes)
+        for h in int_nodes:  # records in rank order
+            cb, ce = child_begin[h], child_begin[h + 1]
+            kids = rank[cb:ce]
+            int_slot.append(node_slot[h])
+            if ce - cb <= 31:
+                m = 0
+                for a, r in enumerate(kids):
+                    if r >= 0:
+                        m |= 1 << a
+                int_mask.append(m)
+                firsts = [r for r in kids if r >= 0]
+                int_cirank.append(firsts[0] if firsts else 0)
+            else:
+                int_mask.append(1 << 31)
+                int_cirank.append(len(big))
+                big.append(ce - cb)
+                big.extend(int(r) for r in kids)
+        wide_irank = [int(rank[h]) for h in wide_list]
     mem_irank = rank[mem_node] if len(mem_node) else np.zeros(0, np.int64)
     iset_vb = np.array([vb_of[s_] for s_ in sets], dtype=np.int64)
     tmpl_vs = np.zeros(N)
@@ -163,6 +180,7 @@ def flatten(g, reach_order=0):
         "wide_vs": wide_vs, "tmpl_vs": tmpl_vs,
         "int_slot": np.array(int_slot, dtype=np.int32), "int_mask": np.array(int_mask, dtype=np.uint32).view(np.int32),
         "int_cirank": np.array(int_cirank, dtype=np.int32), "big_irank": np.array(big, dtype=np.int32),
+        "int_edge": np.array(int_edge, dtype=np.int32), "wide_irank": np.array(wide_irank, dtype=np.int32),
         "mem_irank": mem_irank.astype(np.int32), "level_int": level_int,
         "child_begin": child_begin, "node_slot": node_slot, "level_begin": level_begin,
         "iset_slot": iset_slot, "iset_mem": iset_mem, "mem_node": mem_node,

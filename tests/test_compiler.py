@@ -27,7 +27,7 @@ GAMES = {
 }
 
 
-@pytest.mark.parametrize("reach_order", [cfr.REACH_BFS, cfr.REACH_SLOTS])
+@pytest.mark.parametrize("reach_order", [cfr.REACH_BFS, cfr.REACH_SLOTS, cfr.REACH_MEMBERS])
 @pytest.mark.parametrize("name", list(GAMES))
 def test_arrays_bit_exact(name, reach_order):
     g = GAMES[name]()
