@@ -276,27 +276,51 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
     c.level_chance[D] = (int32_t)c.chance_list.size();
     c.level_wide[D] = (int32_t)c.wide_list.size();
     c.n_wide = (int64_t)c.wide_list.size();
-    // compact internal-node index space. Breadth-first order (default): the
-    // forward reads parents and writes children as two streams. Value-slot
-    // order (the root, then depth by depth in parents' block order): the
-    // members of the sets processed together have neighbouring ranks; a
-    // parent's internal children have consecutive ranks in both, and the
-    // forward pushes each parent's reach to them. Member order (depth by
+    // compact internal-node index space. Member order (the default; depth by
     // depth: the members of the depth's sets in set order, then the depth's
-    // chance nodes): the backward reads every set's reach as one run and
+    // chance nodes in the order they are pulled from): the backward reads
+    // every set's reach as one run and
     // needs no rank table (member k of depth d has rank k + a per-depth
     // offset); the forward pulls, each internal node reading its parent's
-    // reach through int_edge.
+    // reach through int_edge. Breadth-first order: the forward reads parents
+    // and writes children as two streams. Value-slot order (the root, then
+    // depth by depth in parents' block order): the members of the sets
+    // processed together have neighbouring ranks. In both a parent's internal
+    // children have consecutive ranks and the forward pushes each parent's
+    // reach to them.
     {
       std::vector<int32_t> rank(N, -1);
       int32_t r = 0;
       const bool members = reach_order == CFR_REACH_MEMBERS;
       if (members) {
+        // A depth's chance nodes go in the order the next depth's internal
+        // nodes (in their rank order) first pull from them, so that a run of
+        // consecutive children reads neighbouring parents; chance nodes
+        // without internal children follow in node order. Found bottom-up.
+        std::vector<int32_t> parent(N, -1);
+        for (int64_t h = 0; h < N; ++h)
+          for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) parent[x] = (int32_t)h;
+        auto is_chance_int = [&](int32_t h) { return c.node_slot[h] < 0 && c.child_begin[h + 1] > c.child_begin[h]; };
+        std::vector<std::vector<int32_t>> chance_at(D);
+        std::vector<char> placed(N, 0);
+        for (int64_t d = D - 1; d >= 0; --d) {
+          std::vector<int32_t> &L = chance_at[d];
+          auto pull = [&](int32_t x) {
+            const int32_t p = parent[x];
+            if (p >= 0 && is_chance_int(p) && !placed[p]) { placed[p] = 1; L.push_back(p); }
+          };
+          if (d + 1 < D) {
+            const int32_t i0 = c.level_iset[2 * d + 2], i1 = c.level_iset[2 * d + 4];
+            for (int32_t k = c.iset_mem[i0]; k < c.iset_mem[i1]; ++k) pull(c.mem_node[k]);
+            for (int32_t x : chance_at[d + 1]) pull(x);
+          }
+          for (int32_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h)
+            if (is_chance_int(h) && !placed[h]) { placed[h] = 1; L.push_back(h); }
+        }
         for (int64_t d = 0; d < D; ++d) {
           const int32_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
           for (int32_t k = c.iset_mem[i0]; k < c.iset_mem[i1]; ++k) rank[c.mem_node[k]] = r++;
-          for (int32_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h)
-            if (c.node_slot[h] < 0 && c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;
+          for (int32_t h : chance_at[d]) rank[h] = r++;
         }
       } else if (reach_order == CFR_REACH_SLOTS) {
         if (N > 0 && c.child_begin[1] > c.child_begin[0]) rank[0] = r++;

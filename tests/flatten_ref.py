@@ -127,8 +127,28 @@ def flatten(g, reach_order=MEMBERS):
     if reach_order == SLOTS:
         int_nodes = sorted(int_nodes, key=lambda h: (depth[h], vslot[h]))
     elif reach_order == MEMBERS:
-        mpos = {int(x): k for k, x in enumerate(mem_node)}
-        int_nodes = sorted(int_nodes, key=lambda h: (depth[h], 0, mpos[h]) if h in mpos else (depth[h], 1, h))
+        # per depth: the members in member order, then the chance nodes in the
+        # order the next depth's internal nodes first pull from them (those
+        # with no internal child after, in node order), found bottom-up
+        parent = np.full(N, -1, dtype=np.int64)
+        for h in range(N):
+            parent[child_begin[h]:child_begin[h + 1]] = h
+        members_at = [[int(x) for x in mem_node[iset_mem[level_iset[2 * d]]:iset_mem[level_iset[2 * d + 2]]]]
+                      for d in range(D)]
+        chance_at = [[] for _ in range(D)]
+        placed = set()
+        for d in reversed(range(D)):
+            below = members_at[d + 1] + chance_at[d + 1] if d + 1 < D else []
+            for x in below:
+                p = int(parent[x])
+                if p >= 0 and kinds[p] == CHANCE and p not in placed:
+                    placed.add(p)
+                    chance_at[d].append(p)
+            for h in range(level_begin[d], level_begin[d + 1]):
+                if kinds[h] == CHANCE and internal[h] and h not in placed:
+                    placed.add(h)
+                    chance_at[d].append(h)
+        int_nodes = [h for d in range(D) for h in members_at[d] + chance_at[d]]
     rank[int_nodes] = np.arange(len(int_nodes))
     level_int = np.array([int(internal[:level_begin[d]].sum()) for d in range(D + 1)], dtype=np.int32)
     int_slot, int_mask, int_cirank, big, int_edge, wide_irank = [], [], [], [], [], []
