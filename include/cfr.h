@@ -73,6 +73,7 @@ enum { CFR_EXEC_AUTO = 0, CFR_EXEC_LEVELS = 1, CFR_EXEC_GRAPH = 2, CFR_EXEC_PERS
 enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1, CFR_RULE_PCFR_PLUS = 2 };
 enum { CFR_ORDER_SIMULTANEOUS = 0, CFR_ORDER_ALTERNATING = 1 };
 enum { CFR_REACH_MEMBERS = 0, CFR_REACH_BFS = 1, CFR_REACH_SLOTS = 2 };
+enum { CFR_TILES_AUTO = 0, CFR_TILES_OFF = 1, CFR_TILES_ON = 2 };
 
 typedef struct cfr_options {
   /* CFR_P64: every value in FP64 (the parity mode). CFR_P32: reach, values,
@@ -111,6 +112,17 @@ typedef struct cfr_options {
    * internal children have consecutive ranks and the forward pass pushes
    * (every parent writes its children's reach). */
   int reach_order;
+  /* Member order only: tiles of kTileSets consecutive information sets of
+   * equal size store their members' reach interleaved (member k of the
+   * tile's set j at tile base + k * kTileSets + j), so that a run of
+   * children in one set pulls from a compact block of parents when the
+   * parents' sets are tiled the same way (the two players' views of the
+   * same private-card pairs); lane groups at tiled depths take at most 8
+   * lanes. CFR_TILES_AUTO (default): tile the depths with at least 8192
+   * sets where tiles hold at least half the members; CFR_TILES_ON: every
+   * depth where tiles hold at least half the members (small games served
+   * in batches); CFR_TILES_OFF: none. */
+  int member_tiles;
 } cfr_options;
 
 typedef struct cfr_counts {

@@ -28,13 +28,14 @@ EXEC_AUTO, EXEC_LEVELS, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2, 3
 RULE_CFR_PLUS, RULE_CFR, RULE_PCFR_PLUS = 0, 1, 2
 ORDER_SIMULTANEOUS, ORDER_ALTERNATING = 0, 1
 REACH_MEMBERS, REACH_BFS, REACH_SLOTS = 0, 1, 2
+TILES_AUTO, TILES_OFF, TILES_ON = 0, 1, 2
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
           "spec_slot_of": 11, "level_lanes": 12, "int_slot": 13, "int_mask": 14, "int_cirank": 15,
           "big_irank": 16, "mem_irank": 17, "level_int": 18, "vslot": 19, "iset_vb": 20, "mem_vs": 21,
           "ch_vb": 22, "ch_nch": 23, "ch_vs": 24, "wide_vb": 25, "wide_nch": 26, "wide_vs": 27, "tmpl_vs": 28,
-          "int_edge": 29}
+          "int_edge": 29, "iset_rank": 30, "level_tiled": 31}
 
 
 class CfrError(RuntimeError):
@@ -57,6 +58,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("exec_form", ctypes.c_int), ("rule", ctypes.c_int),
         ("lanes_per_set", ctypes.c_int), ("persistent_ctas", ctypes.c_int),
         ("barrier_spin_limit", ctypes.c_int64), ("order", ctypes.c_int), ("reach_order", ctypes.c_int),
+        ("member_tiles", ctypes.c_int),
     ]
 
 
@@ -157,12 +159,14 @@ def spec_struct(spec) -> Tuple[GameSpecC, list]:
 
 
 def make_options(precision=P32, exec_form=EXEC_AUTO, rule=RULE_CFR_PLUS, lanes_per_set=0, persistent_ctas=0,
-                 barrier_spin_limit=0, order=ORDER_SIMULTANEOUS, reach_order=REACH_MEMBERS) -> Options:
+                 barrier_spin_limit=0, order=ORDER_SIMULTANEOUS, reach_order=REACH_MEMBERS,
+                 member_tiles=TILES_AUTO) -> Options:
     o = Options()
     o.precision, o.exec_form, o.rule = precision, exec_form, rule
     o.lanes_per_set, o.persistent_ctas, o.barrier_spin_limit = lanes_per_set, persistent_ctas, barrier_spin_limit
     o.order = order
     o.reach_order = reach_order
+    o.member_tiles = member_tiles
     return o
 
 
@@ -338,12 +342,12 @@ class Solver:
     def __init__(self, spec, precision: int = P32, exec_form: int = EXEC_AUTO, rule: int = RULE_CFR_PLUS,
                  lanes_per_set: int = 0, persistent_ctas: int = 0, barrier_spin_limit: int = 0,
                  device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS,
-                 reach_order: int = REACH_MEMBERS):
+                 reach_order: int = REACH_MEMBERS, member_tiles: int = TILES_AUTO):
         import torch
 
         self.torch = torch
         self.opts = make_options(precision, exec_form, rule, lanes_per_set, persistent_ctas, barrier_spin_limit,
-                                 order, reach_order)
+                                 order, reach_order, member_tiles)
         self.h = cfr_compile(spec, self.opts)
         self.counts = cfr_get_counts(self.h)
         self.n_slots = self.counts["n_slots"]

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
         if (rank == 0)
           for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
         for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd, w.koff);
+          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
         level_sync<CLUSTERED>();
       }
     }
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
       const int p = I >= w.is2 ? 1 : 0;
       const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
       const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+      const MemberRanks mr = member_ranks(g, I, m0);
       const int32_t vb0 = __ldg(g.iset_vb + I);
       double sg[MAXA], Q[MAXA];
 #pragma unroll
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
         if (k < m1) {
           const int32_t h = __ldg(g.mem_vs + k);
           const int32_t cb = vb0 + (k - m0) * na;
-          const double2 r = in.reach2[member_rank(g, k, w.koff)];
+          const double2 r = in.reach2[member_rank(g, k, mr)];
           const double po = p ? r.x : r.y;
           double oth = 0.0, va = 0.0;
 #pragma unroll

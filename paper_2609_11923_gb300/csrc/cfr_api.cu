@@ -46,6 +46,9 @@ struct Buf {
   size_t off = 0, bytes = 0;
 };
 
+// Largest lane group at depths whose sets are tiled (member order).
+constexpr int kTiledLanes = 32 / kTileSets;
+
 struct cfr_handle {
   Compiled c;
   cfr_options opt{};
@@ -57,7 +60,7 @@ struct cfr_handle {
   // arena layout
   Buf b_iset_slot, b_iset_mem, b_iset_vb, b_mem_vs, b_ch_vb, b_ch_nch, b_ch_vs, b_spec_slot, b_levels;
   Buf b_wide_vb, b_wide_nch, b_wide_vs, b_wide_chunk, b_wide_part, b_wide_cnt;
-  Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_int_edge, b_mem_irank, b_wide_irank;
+  Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_int_edge, b_iset_rank, b_mem_irank, b_wide_irank;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
   size_t plan_bytes = 0;
   char *arena = nullptr;
@@ -106,6 +109,7 @@ static void plan(cfr_handle *h) {
   take(h->b_int_cirank, 4 * c.int_cirank.size());
   take(h->b_big_irank, 4 * c.big_irank.size());
   take(h->b_int_edge, 4 * c.int_edge.size());
+  take(h->b_iset_rank, 4 * c.iset_rank.size());
   take(h->b_mem_irank, c.int_edge.empty() ? 4 * c.n_dec : 0);  // member order: ranks follow from k
   take(h->b_wide_irank, 4 * c.wide_irank.size());
   take(h->b_reach, 2 * T * std::max<int64_t>(c.n_int, 1));  // internal nodes only
@@ -141,7 +145,8 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32 or 256"); }
   std::string err;
   if (h->opt.reach_order < CFR_REACH_MEMBERS || h->opt.reach_order > CFR_REACH_SLOTS) { delete h; return set_err(CFR_ERR_ARG, "bad reach_order"); }
-  int rc = compile_game(*spec, h->c, err, h->opt.reach_order);
+  if (h->opt.member_tiles < CFR_TILES_AUTO || h->opt.member_tiles > CFR_TILES_ON) { delete h; return set_err(CFR_ERR_ARG, "bad member_tiles"); }
+  int rc = compile_game(*spec, h->c, err, h->opt.reach_order, h->opt.member_tiles);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
   if (lp != 0 && (lp < 4 || lp == kThreads) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2 or 256 needs sets of at most 8 actions"); }
@@ -153,14 +158,20 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (h->exec_form == CFR_EXEC_AUTO) h->exec_form = c.N <= (1 << 16) ? CFR_EXEC_PERSISTENT : CFR_EXEC_GRAPH;
   // lanes per information set: the smallest group that covers the mean set
   auto pick = [](double mean) { return mean <= 4.0 ? 4 : mean <= 8.0 ? 8 : mean <= 16.0 ? 16 : 32; };
+  // (tiled depths: at most one tile of sets per warp's worth of lanes, so a
+  // warp's member reads stay one run)
   h->level_lanes.assign(c.D, 8);
   double tot_mem = 0.0;
+  bool any_tiled = false;
   for (int64_t d = 0; d < c.D; ++d) {
     h->level_lanes[d] = lp ? lp : pick(c.level_mean_members[d]);
+    if (!lp && c.level_tiled[d]) h->level_lanes[d] = std::min(h->level_lanes[d], kTiledLanes);
+    any_tiled = any_tiled || c.level_tiled[d];
     tot_mem += c.level_mean_members[d] * (c.level_iset[2 * d + 2] - c.level_iset[2 * d]);
   }
   // the persistent kernel runs lane groups of at most a warp
   h->persist_lanes = lp ? std::min(lp, 32) : pick(c.I > 0 ? tot_mem / (double)c.I : 1.0);
+  if (!lp && any_tiled) h->persist_lanes = std::min(h->persist_lanes, kTiledLanes);
   h->levels.resize(c.D);
   for (int64_t d = 0; d < c.D; ++d) {
     LevelWork &w = h->levels[d];
@@ -177,8 +188,6 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
     w.wd1 = c.level_wide[d + 1];
     w.wc0 = c.wide_chunk[w.wd0];
     w.wc1 = c.wide_chunk[w.wd1];
-    // member order: member k of depth d has rank k + koff
-    w.koff = c.int_edge.empty() ? 0 : c.level_int[d] - c.iset_mem[c.level_iset[2 * d]];
     w.fan = 0;  // a chance node of this depth has its children written warp-wide
     for (int64_t q = c.level_int[d]; q < c.level_int[d + 1] && !w.fan && !c.int_mask.empty(); ++q) {
       const uint32_t m = c.int_mask[q];
@@ -208,7 +217,7 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
                               h->b_ch_vb.bytes + h->b_ch_nch.bytes + h->b_ch_vs.bytes + h->b_spec_slot.bytes + h->b_levels.bytes +
                               h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes +
                               h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
-                              h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes + h->b_int_edge.bytes +
+                              h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes + h->b_int_edge.bytes + h->b_iset_rank.bytes +
                               h->b_mem_irank.bytes + h->b_wide_irank.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
@@ -242,6 +251,7 @@ static GameView game_view(const cfr_handle *h) {
   g.int_cirank = h->p<int32_t>(h->b_int_cirank);
   g.big_irank = h->p<int32_t>(h->b_big_irank);
   g.int_edge = h->c.int_edge.empty() ? nullptr : h->p<int2>(h->b_int_edge);
+  g.iset_rank = h->c.iset_rank.empty() ? nullptr : h->p<int2>(h->b_iset_rank);
   g.mem_irank = h->c.int_edge.empty() ? h->p<int32_t>(h->b_mem_irank) : nullptr;
   g.wide_irank = h->p<int32_t>(h->b_wide_irank);
   return g;
@@ -338,6 +348,7 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_int_cirank, c.int_cirank.data(), 4 * c.int_cirank.size()))) return rc;
   if ((rc = up(h->b_big_irank, c.big_irank.data(), 4 * c.big_irank.size()))) return rc;
   if ((rc = up(h->b_int_edge, c.int_edge.data(), 4 * c.int_edge.size()))) return rc;
+  if ((rc = up(h->b_iset_rank, c.iset_rank.data(), 4 * c.iset_rank.size()))) return rc;
   if ((rc = up(h->b_mem_irank, c.mem_irank.data(), h->b_mem_irank.bytes))) return rc;
   if ((rc = up(h->b_wide_irank, c.wide_irank.data(), 4 * c.wide_irank.size()))) return rc;
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
@@ -714,6 +725,8 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 27: src = c.wide_vs.data(); n = (int64_t)c.wide_vs.size(); break;
     case 28: src = c.tmpl_vs.data(); n = (int64_t)c.tmpl_vs.size(); esz = 8; break;
     case 29: src = c.int_edge.data(); n = (int64_t)c.int_edge.size(); break;
+    case 30: src = c.iset_rank.data(); n = (int64_t)c.iset_rank.size(); break;
+    case 31: src = c.level_tiled.data(); n = (int64_t)c.level_tiled.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;

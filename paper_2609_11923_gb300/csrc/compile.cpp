@@ -21,7 +21,7 @@ static int fail(std::string &err, const std::string &msg) {
   return CFR_ERR_INVALID_SPEC;
 }
 
-int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reach_order) {
+int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reach_order, int member_tiles) {
   try {
     const int64_t N = s.n_nodes, I = s.n_infosets;
     if (N < 1 || N >= (int64_t(1) << 31) - 2) return fail(err, "n_nodes must be in [1, 2^31-2)");
@@ -294,9 +294,10 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
       const bool members = reach_order == CFR_REACH_MEMBERS;
       if (members) {
         // A depth's chance nodes go in the order the next depth's internal
-        // nodes (in their rank order) first pull from them, so that a run of
-        // consecutive children reads neighbouring parents; chance nodes
-        // without internal children follow in node order. Found bottom-up.
+        // nodes (its members in set order, then its chance nodes) first pull
+        // from them, so that a run of children reads neighbouring parents;
+        // chance nodes without internal children follow in node order.
+        // Found bottom-up.
         std::vector<int32_t> parent(N, -1);
         for (int64_t h = 0; h < N; ++h)
           for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) parent[x] = (int32_t)h;
@@ -317,9 +318,49 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
           for (int32_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h)
             if (is_chance_int(h) && !placed[h]) { placed[h] = 1; L.push_back(h); }
         }
+        // Tiles: kTileSets consecutive sets of one player and one size;
+        // member k of the tile's set j has rank base + k * kTileSets + j.
+        c.iset_rank.assign(2 * (size_t)c.I, 0);
+        c.level_tiled.assign(D, 0);
         for (int64_t d = 0; d < D; ++d) {
           const int32_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
-          for (int32_t k = c.iset_mem[i0]; k < c.iset_mem[i1]; ++k) rank[c.mem_node[k]] = r++;
+          auto size = [&](int32_t I) { return c.iset_mem[I + 1] - c.iset_mem[I]; };
+          auto tile_at = [&](int32_t I, int32_t end) {  // a tile starts at set I
+            if (I + kTileSets > end) return false;
+            for (int32_t j = 1; j < kTileSets; ++j)
+              if (size(I + j) != size(I)) return false;
+            return true;
+          };
+          bool tiled = false;
+          if (member_tiles != CFR_TILES_OFF && (member_tiles == CFR_TILES_ON || i1 - i0 >= kTileMinSets)) {
+            int64_t in_tiles = 0;
+            for (int pl = 0; pl < 2; ++pl) {
+              const int32_t b = c.level_iset[2 * d + pl], e = c.level_iset[2 * d + pl + 1];
+              for (int32_t I = b; I < e;)
+                if (tile_at(I, e)) { in_tiles += (int64_t)kTileSets * size(I); I += kTileSets; } else ++I;
+            }
+            tiled = 2 * in_tiles >= (int64_t)(c.iset_mem[i1] - c.iset_mem[i0]) && in_tiles > 0;
+          }
+          c.level_tiled[d] = tiled ? 1 : 0;
+          for (int pl = 0; pl < 2; ++pl) {
+            const int32_t b = c.level_iset[2 * d + pl], e = c.level_iset[2 * d + pl + 1];
+            for (int32_t I = b; I < e;) {
+              if (tiled && tile_at(I, e)) {
+                for (int32_t j = 0; j < kTileSets; ++j) {
+                  c.iset_rank[2 * (size_t)(I + j)] = r + j;
+                  c.iset_rank[2 * (size_t)(I + j) + 1] = kTileSets;
+                  for (int32_t k = 0; k < size(I); ++k) rank[c.mem_node[c.iset_mem[I + j] + k]] = r + k * kTileSets + j;
+                }
+                r += kTileSets * size(I);
+                I += kTileSets;
+              } else {
+                c.iset_rank[2 * (size_t)I] = r;
+                c.iset_rank[2 * (size_t)I + 1] = 1;
+                for (int32_t k = c.iset_mem[I]; k < c.iset_mem[I + 1]; ++k) rank[c.mem_node[k]] = r++;
+                ++I;
+              }
+            }
+          }
           for (int32_t h : chance_at[d]) rank[h] = r++;
         }
       } else if (reach_order == CFR_REACH_SLOTS) {
@@ -344,6 +385,10 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
       c.big_irank.clear();
       c.int_edge.clear();
       c.wide_irank.clear();
+      if (!members) {
+        c.iset_rank.clear();
+        c.level_tiled.assign(D, 0);
+      }
       if (members) {  // each internal node's parent rank and the slot word of its edge
         c.int_edge.assign(2 * (size_t)r, -1);
         for (int64_t h = 0; h < N; ++h) {

@@ -22,6 +22,12 @@ constexpr int kWide = 1024;
 constexpr int kWideChunk = 2048;
 constexpr uint32_t kBigNode = 0x80000000u;  // int_mask flag: children listed in big_irank
 
+// Member order: sets per reach tile, and the number of sets a depth needs
+// before it is tiled by default (tiled depths run lane groups of at most
+// 32 / kTileSets lanes, so they need many sets to fill the GPU).
+constexpr int32_t kTileSets = 4;
+constexpr int64_t kTileMinSets = 8192;
+
 struct Compiled {
   int64_t N = 0, E = 0, I = 0, A = 0, D = 0;
   int64_t n_dec = 0, n_chance = 0, n_term = 0, n_int = 0, max_act = 0;
@@ -64,6 +70,11 @@ struct Compiled {
   //               (root -1) and the slot word of the edge from the parent
   //               (parent's slot word + action), or -1 under a chance node
   std::vector<int32_t> int_edge;
+  //   iset_rank = [2 I] per set: rank of its member 0 and the rank stride of
+  //               its members (kTileSets inside a tile, else 1)
+  //   level_tiled = [D] 1 if depth d's sets are tiled
+  std::vector<int32_t> iset_rank;
+  std::vector<int32_t> level_tiled;
   std::vector<int32_t> mem_irank;    // [n_dec] internal rank of each member
   std::vector<int32_t> wide_irank;   // [n_wide] internal rank of each wide node
   // Value slots. The value of node h lives in slot vslot[h] of the value
@@ -92,7 +103,8 @@ struct Compiled {
 };
 
 // Returns CFR_OK or CFR_ERR_INVALID_SPEC / CFR_ERR_HOST_MEMORY with a message.
-int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err, int reach_order = CFR_REACH_MEMBERS);
+int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err, int reach_order = CFR_REACH_MEMBERS,
+                 int member_tiles = CFR_TILES_AUTO);
 
 // Chance folding from the retained edge probabilities and payoffs: the
 // products root..h in path order (pc), the template pi_c(z) u(z) (eq.

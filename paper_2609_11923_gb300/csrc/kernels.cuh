@@ -74,8 +74,9 @@ struct GameView {
   const int32_t *__restrict__ big_irank;   // [nch, child ranks...] of nodes with > 31 children
   const int2 *__restrict__ int_edge;       // member order: each internal node's (parent rank, slot word of
                                            //   its edge or -1 under chance); else null
-  const int32_t *__restrict__ mem_irank;   // internal rank of each member (null in member order:
-                                           //   member k of depth d has rank k + LevelWork::koff)
+  const int32_t *__restrict__ mem_irank;   // internal rank of each member (null in member order)
+  const int2 *__restrict__ iset_rank;      // member order: per set, rank of member 0 and the stride
+                                           //   of its members' ranks (else null)
   const int32_t *__restrict__ wide_irank;  // internal rank of each wide node
 };
 
@@ -98,8 +99,23 @@ struct LevelWork {
   int32_t wd0, wd1;       // wide chance nodes of depth d (wide_* arrays)
   int32_t wc0, wc1;       // their chunks
   int32_t fan;            // 1 if a chance node of depth d has more than kFanLight internal children
-  int32_t koff;           // member order: rank - member index of depth d's members
 };
+
+// Where set I's members keep their reach: member k (global member index) has
+// rank kb + k * rg (member order), or the rank table's entry (kb = rg = 0).
+struct MemberRanks {
+  int32_t kb, rg;
+};
+
+__device__ __forceinline__ MemberRanks member_ranks(const GameView &g, int32_t I, int32_t m0) {
+  MemberRanks mr{0, 0};
+  if (g.iset_rank) {
+    const int2 x = __ldg(g.iset_rank + I);
+    mr.rg = x.y;
+    mr.kb = x.x - m0 * x.y;
+  }
+  return mr;
+}
 
 // The wide node owning chunk q (binary search over the level's prefix).
 __device__ __forceinline__ int32_t wide_of_chunk(const GameView &g, const LevelWork &w, int32_t q) {
@@ -406,18 +422,19 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
 
 // A member's two indices (member order: coalesced reads): its own value slot
 // and its internal rank (where its reach lives; in member order the rank
-// follows from the member index). Past the set's end: -1.
-__device__ __forceinline__ int32_t member_rank(const GameView &g, int32_t k, int32_t koff) {
-  return g.mem_irank ? __ldg(g.mem_irank + k) : k + koff;
+// follows from the member index and the set's rank base and stride). Past
+// the set's end: -1.
+__device__ __forceinline__ int32_t member_rank(const GameView &g, int32_t k, MemberRanks mr) {
+  return g.mem_irank ? __ldg(g.mem_irank + k) : mr.kb + k * mr.rg;
 }
 
-__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, int32_t koff, int32_t &ps,
+__device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t m1, MemberRanks mr, int32_t &ps,
                                            int32_t &ir) {
   ps = -1;
   ir = -1;
   if (k < m1) {
     ps = __ldg(g.mem_vs + k);
-    ir = member_rank(g, k, koff);
+    ir = member_rank(g, k, mr);
   }
 }
 
@@ -459,10 +476,10 @@ __device__ __forceinline__ void member_data(const GameView &g, const StateView<T
 // Indices, loads and per-member terms of one member (k < m1), or zeros.
 template <typename T, int MAXA, bool PERSIST>
 __device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
-                                             int32_t m1, int32_t koff, int32_t vb, int32_t na, bool p2,
+                                             int32_t m1, MemberRanks mr, int32_t vb, int32_t na, bool p2,
                                              const T (&sig)[MAXA], T (&d)[MAXA], T (&mm)[MAXA]) {
   int32_t h, ir;
-  member_idx(g, k, m1, koff, h, ir);
+  member_idx(g, k, m1, mr, h, ir);
   member_data<T, MAXA, PERSIST>(g, st, k, m0, m1, vb, na, p2, sig, h, ir, d, mm);
 }
 
@@ -498,11 +515,12 @@ __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsign
 // the set's slots runs one lane per action.
 template <typename T, int MAXA, int LANES, bool PERSIST>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                        int lane, unsigned mask, double wt, int rule, int upd, int32_t koff) {
+                                        int lane, unsigned mask, double wt, int rule, int upd) {
   const int32_t sb = __ldg(g.iset_slot + I);
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
   const int32_t vb = __ldg(g.iset_vb + I);
+  const MemberRanks mr = member_ranks(g, I, m0);
   T sig[MAXA], racc[MAXA], macc[MAXA];
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) {
@@ -515,12 +533,12 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
   if constexpr (TWO) {
     if (k0 + LANES < m1) {
       int32_t ps0, ir0, ps1, ir1;
-      member_idx(g, k0 + lane, m1, koff, ps0, ir0);
-      member_idx(g, k0 + LANES + lane, m1, koff, ps1, ir1);
+      member_idx(g, k0 + lane, m1, mr, ps0, ir0);
+      member_idx(g, k0 + LANES + lane, m1, mr, ps1, ir1);
       for (; k0 + LANES < m1; k0 += 2 * LANES) {
         int32_t qs0, jr0, qs1, jr1;  // the next step's indices
-        member_idx(g, k0 + 2 * LANES + lane, m1, koff, qs0, jr0);
-        member_idx(g, k0 + 3 * LANES + lane, m1, koff, qs1, jr1);
+        member_idx(g, k0 + 2 * LANES + lane, m1, mr, qs0, jr0);
+        member_idx(g, k0 + 3 * LANES + lane, m1, mr, qs1, jr1);
         T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
         member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps0, ir0, d0, mm0);
         member_data<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, ps1, ir1, d1, mm1);
@@ -532,16 +550,16 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
     }
     for (; k0 < m1; k0 += LANES) {
       T d[MAXA], mm[MAXA];
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, koff, vb, na, p2, sig, d, mm);
+      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, mr, vb, na, p2, sig, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
       accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
     }
   } else {
     int32_t ps, ir;
-    member_idx(g, k0 + lane, m1, koff, ps, ir);
+    member_idx(g, k0 + lane, m1, mr, ps, ir);
     for (; k0 < m1; k0 += LANES) {
       int32_t qs, jr;  // the next step's indices
-      member_idx(g, k0 + LANES + lane, m1, koff, qs, jr);
+      member_idx(g, k0 + LANES + lane, m1, mr, qs, jr);
       T d[MAXA], mm[MAXA];
       member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
@@ -614,7 +632,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
 // finished by a fixed-shape tree. The slot update runs one thread per action.
 template <typename T, int MAXA>
 __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
-                                              double wt, int rule, int upd, int32_t koff) {
+                                              double wt, int rule, int upd) {
   __shared__ T s_d[kThreads * MAXA], s_m[kThreads * MAXA];  // [member][action]
   __shared__ double s_pos[MAXA];
   const int tid = threadIdx.x;
@@ -622,6 +640,7 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
   const int32_t na = __ldg(g.iset_slot + I + 1) - sb;
   const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
   const int32_t vb = __ldg(g.iset_vb + I);
+  const MemberRanks mr = member_ranks(g, I, m0);
   T sig[MAXA], racc[MAXA], macc[MAXA];
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) {
@@ -631,10 +650,10 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
   }
   T r = T(0), m = T(0);  // P64: column tid's running sums (tid < na)
   int32_t ps, ir;
-  member_idx(g, m0 + tid, m1, koff, ps, ir);
+  member_idx(g, m0 + tid, m1, mr, ps, ir);
   for (int32_t k0 = m0; k0 < m1; k0 += kThreads) {
     int32_t qs, jr;  // the next chunk's indices
-    member_idx(g, k0 + kThreads + tid, m1, koff, qs, jr);
+    member_idx(g, k0 + kThreads + tid, m1, mr, qs, jr);
     T d[MAXA], mm[MAXA];
     member_data<T, MAXA, false>(g, st, k0 + tid, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
     ps = qs;
@@ -724,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     const int first = nb_chance + nb_wide;
     const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + ((int)blockIdx.x - first); I < w.is1; I += (int)gridDim.x - first)
-      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd, w.koff);
+      bwd_set_block<T, MAXA>(g, st, I, I >= w.is2, wt, rule, upd);
   } else {
     constexpr int GPB = kThreads / LANES;
     const int first = nb_chance + nb_wide;
@@ -734,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1))
     const unsigned mask = group_mask<LANES>();
     const double wt = avg_weight(*st.t + 1, rule);
     for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd, w.koff);
+      bwd_set<T, MAXA, LANES, false>(g, st, I, I >= w.is2, lane, mask, wt, rule, upd);
   }
   if (bump_t) {  // depth 0 holds only the root: no other block reads t here
     __syncthreads();
@@ -844,7 +863,7 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
         for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
         for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
         for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
-          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd, w.koff);
+          bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd);
         if (!grid_sync(a.bar)) return;
       }
     }
@@ -1003,6 +1022,7 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
     const int p = I >= w.is2 ? 1 : 0;
     const int32_t sb = __ldg(g.iset_slot + I), na = __ldg(g.iset_slot + I + 1) - sb;
     const int32_t m0 = __ldg(g.iset_mem + I), m1 = __ldg(g.iset_mem + I + 1);
+    const MemberRanks mr = member_ranks(g, I, m0);
     const int32_t vb0 = __ldg(g.iset_vb + I);
     double sg[MAXA], Q[MAXA];
 #pragma unroll
@@ -1015,7 +1035,7 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
       if (k < m1) {
         const int32_t h = __ldg(g.mem_vs + k);
         const int32_t cb = vb0 + (k - m0) * na;
-        const double2 r = reach2[member_rank(g, k, w.koff)];
+        const double2 r = reach2[member_rank(g, k, mr)];
         const double po = p ? r.x : r.y;
         double oth = 0.0, va = 0.0;
 #pragma unroll

@@ -19,12 +19,15 @@ WIDE_CHUNK = 2048
 
 
 MEMBERS, BFS, SLOTS = 0, 1, 2  # internal-rank orders
+TILES_AUTO, TILES_OFF, TILES_ON = 0, 1, 2
+TILE, TILE_MIN_SETS = 4, 8192
 
 
-def flatten(g, reach_order=MEMBERS):
+def flatten(g, reach_order=MEMBERS, member_tiles=TILES_AUTO):
     """Internal ranks: MEMBERS, depth by depth the members of the depth's
-    sets in member order, then its chance nodes; BFS, breadth-first; SLOTS,
-    the root, then by (depth, value slot)."""
+    sets in member order (interleaved within tiles of TILE equal-size sets
+    at tiled depths), then its chance nodes; BFS, breadth-first; SLOTS, the
+    root, then by (depth, value slot)."""
     N = g.n_nodes
     order = []
     depth_of = {}
@@ -148,8 +151,53 @@ def flatten(g, reach_order=MEMBERS):
                 if kinds[h] == CHANCE and internal[h] and h not in placed:
                     placed.add(h)
                     chance_at[d].append(h)
-        int_nodes = [h for d in range(D) for h in members_at[d] + chance_at[d]]
-    rank[int_nodes] = np.arange(len(int_nodes))
+        # tiles: TILE consecutive sets of one player and one size; member k of
+        # the tile's set j at tile base + k * TILE + j
+        iset_rank = np.zeros(2 * len(sets), dtype=np.int32)
+        level_tiled = np.zeros(D, dtype=np.int32)
+        size = lambda s_: int(iset_mem[s_ + 1] - iset_mem[s_])
+        tile_at = lambda s_, e: s_ + TILE <= e and all(size(s_ + j) == size(s_) for j in range(1, TILE))
+        r = 0
+        for d in range(D):
+            ranges = [(int(level_iset[2 * d + pl]), int(level_iset[2 * d + pl + 1])) for pl in (0, 1)]
+            tiled = False
+            if member_tiles != TILES_OFF and (member_tiles == TILES_ON
+                                              or level_iset[2 * d + 2] - level_iset[2 * d] >= TILE_MIN_SETS):
+                in_tiles = 0
+                for b, e in ranges:
+                    s_ = b
+                    while s_ < e:
+                        if tile_at(s_, e):
+                            in_tiles += TILE * size(s_)
+                            s_ += TILE
+                        else:
+                            s_ += 1
+                tiled = in_tiles > 0 and 2 * in_tiles >= len(members_at[d])
+            level_tiled[d] = int(tiled)
+            for b, e in ranges:
+                s_ = b
+                while s_ < e:
+                    if tiled and tile_at(s_, e):
+                        for j in range(TILE):
+                            iset_rank[2 * (s_ + j)], iset_rank[2 * (s_ + j) + 1] = r + j, TILE
+                            for k in range(size(s_)):
+                                rank[mem_node[iset_mem[s_ + j] + k]] = r + k * TILE + j
+                        r += TILE * size(s_)
+                        s_ += TILE
+                    else:
+                        iset_rank[2 * s_], iset_rank[2 * s_ + 1] = r, 1
+                        for k in range(size(s_)):
+                            rank[mem_node[iset_mem[s_] + k]] = r + k
+                        r += size(s_)
+                        s_ += 1
+            for h in chance_at[d]:
+                rank[h] = r
+                r += 1
+        int_nodes = sorted(int_nodes, key=lambda h: rank[h])
+    if reach_order != MEMBERS:
+        rank[int_nodes] = np.arange(len(int_nodes))
+        iset_rank = np.zeros(0, dtype=np.int32)
+        level_tiled = np.zeros(D, dtype=np.int32)
     level_int = np.array([int(internal[:level_begin[d]].sum()) for d in range(D + 1)], dtype=np.int32)
     int_slot, int_mask, int_cirank, big, int_edge, wide_irank = [], [], [], [], [], []
     if reach_order == MEMBERS:  # each internal node's parent rank and edge slot word (the forward pulls)
@@ -201,6 +249,7 @@ def flatten(g, reach_order=MEMBERS):
         "int_slot": np.array(int_slot, dtype=np.int32), "int_mask": np.array(int_mask, dtype=np.uint32).view(np.int32),
         "int_cirank": np.array(int_cirank, dtype=np.int32), "big_irank": np.array(big, dtype=np.int32),
         "int_edge": np.array(int_edge, dtype=np.int32), "wide_irank": np.array(wide_irank, dtype=np.int32),
+        "iset_rank": iset_rank, "level_tiled": level_tiled,
         "mem_irank": mem_irank.astype(np.int32), "level_int": level_int,
         "child_begin": child_begin, "node_slot": node_slot, "level_begin": level_begin,
         "iset_slot": iset_slot, "iset_mem": iset_mem, "mem_node": mem_node,

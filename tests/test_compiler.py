@@ -27,12 +27,14 @@ GAMES = {
 }
 
 
-@pytest.mark.parametrize("reach_order", [cfr.REACH_BFS, cfr.REACH_SLOTS, cfr.REACH_MEMBERS])
+@pytest.mark.parametrize("reach_order,tiles", [(cfr.REACH_BFS, cfr.TILES_AUTO), (cfr.REACH_SLOTS, cfr.TILES_AUTO),
+                                               (cfr.REACH_MEMBERS, cfr.TILES_AUTO), (cfr.REACH_MEMBERS, cfr.TILES_ON),
+                                               (cfr.REACH_MEMBERS, cfr.TILES_OFF)])
 @pytest.mark.parametrize("name", list(GAMES))
-def test_arrays_bit_exact(name, reach_order):
+def test_arrays_bit_exact(name, reach_order, tiles):
     g = GAMES[name]()
-    ref = flatten(g, reach_order)
-    h = cfr.cfr_compile(g, cfr.make_options(reach_order=reach_order))
+    ref = flatten(g, reach_order, tiles)
+    h = cfr.cfr_compile(g, cfr.make_options(reach_order=reach_order, member_tiles=tiles))
     try:
         for key in cfr.EXPORT:
             if key == "level_lanes":  # a runtime choice, not a compiled array

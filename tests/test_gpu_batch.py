@@ -17,8 +17,8 @@ from paper_2609_11923_gb300 import cfr, serve
 pytestmark = pytest.mark.gpu
 
 
-def bound(specs, precision=cfr.P32, reach_order=cfr.REACH_MEMBERS):
-    opts = cfr.make_options(precision=precision, reach_order=reach_order)
+def bound(specs, precision=cfr.P32, reach_order=cfr.REACH_MEMBERS, tiles=cfr.TILES_AUTO):
+    opts = cfr.make_options(precision=precision, reach_order=reach_order, member_tiles=tiles)
     hs = [cfr.cfr_compile(sp, opts) for sp in specs]
     pool = serve.DevicePool(sum(cfr.cfr_plan(h) + 512 for h in hs) + 4096)
     s = int(torch.cuda.current_stream().cuda_stream)
@@ -37,11 +37,12 @@ def mixed_specs(n, seed0=100):
     return out
 
 
-@pytest.mark.parametrize("reach_order", [cfr.REACH_BFS, cfr.REACH_SLOTS, cfr.REACH_MEMBERS])
-def test_batched_fp64_matches_oracle(reach_order):
+@pytest.mark.parametrize("reach_order,tiles", [(cfr.REACH_BFS, cfr.TILES_AUTO), (cfr.REACH_SLOTS, cfr.TILES_AUTO),
+                                               (cfr.REACH_MEMBERS, cfr.TILES_AUTO), (cfr.REACH_MEMBERS, cfr.TILES_ON)])
+def test_batched_fp64_matches_oracle(reach_order, tiles):
     specs = [gg.tiny_card(), gg.kuhn(), gg.endgame(5, 4000), gg.endgame(2, 100000), gg.random_tree(3, depth=8),
              gg.large_card(3, 2, 1, 1)]
-    pool, hs, table, tp, tb, s = bound(specs, cfr.P64, reach_order)
+    pool, hs, table, tp, tb, s = bound(specs, cfr.P64, reach_order, tiles)
     cfr.cfr_batch_iterate(hs, 300, tp, tb, 256, 4, s)
     for sp, h in zip(specs, hs):
         out = np.empty(cfr.cfr_get_counts(h)["n_slots"])

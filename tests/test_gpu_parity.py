@@ -387,12 +387,13 @@ def test_set_root_chance_then_solve_equals_the_oracle_on_the_new_game(form):
     assert abs(s.exploitability() - o.exploitability()) <= 1e-12
 
 
-@pytest.mark.parametrize("reach_order", [cfr.REACH_BFS, cfr.REACH_SLOTS])
+@pytest.mark.parametrize("reach_order,tiles", [(cfr.REACH_BFS, cfr.TILES_AUTO), (cfr.REACH_SLOTS, cfr.TILES_AUTO),
+                                               (cfr.REACH_MEMBERS, cfr.TILES_ON), (cfr.REACH_MEMBERS, cfr.TILES_OFF)])
 @pytest.mark.parametrize("form", [cfr.EXEC_GRAPH, cfr.EXEC_PERSISTENT])
 @pytest.mark.parametrize("name,iters", [("tiny", 400), ("rt", 150), ("wide", 60), ("card", 40)])
-def test_p64_reach_in_other_orders_matches_oracle_bitwise(reach_order, form, name, iters):
+def test_p64_reach_layouts_match_oracle_bitwise(reach_order, tiles, form, name, iters):
     g = {"tiny": gg.tiny_card, "rt": lambda: gg.random_tree(5, depth=9), "wide": lambda: gg.endgame(2, 100000),
          "card": lambda: gg.large_card(3, 2, 1, 1)}[name]()
-    s = solve_gpu(g, iters, form=form, reach_order=reach_order)
+    s = solve_gpu(g, iters, form=form, reach_order=reach_order, member_tiles=tiles)
     np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, iters).avg_strategy())
     assert abs(s.exploitability() - oracle.solve(g, iters).exploitability()) <= 1e-12
