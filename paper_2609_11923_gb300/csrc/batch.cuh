@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
         if (rank == 0)
           for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
         for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-          bwd_set<T, MAXA, LANES, CLUSTERED>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
+// 1024-thread blocks leave 64 registers a thread: lean average terms
+          bwd_set<T, MAXA, LANES, CLUSTERED, (THREADS >= 1024)>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
         level_sync<CLUSTERED>();
       }
     }

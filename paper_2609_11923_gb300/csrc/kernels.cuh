@@ -441,8 +441,12 @@ __device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t
 // Loads and per-member terms of one member (k < m1) whose indices are
 // already known, or zeros. The member's children are slots
 // vb + (k - m0) * na .. + na - 1 of the set's block: the group's lanes read
-// consecutive members' children as one run.
-template <typename T, int MAXA, bool PERSIST>
+// consecutive members' children as one run. The average-strategy terms are
+// pw * sigma(a). LEAN (FP32 only): only pw is carried (mm[0]) and the set's
+// sum of pw is multiplied by sigma(a) once (avg_terms), which frees
+// registers where the budget is tight; otherwise each product is added, in
+// member order in FP64, as the definition does.
+template <typename T, int MAXA, bool PERSIST, bool LEAN = false>
 __device__ __forceinline__ void member_data(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
                                             int32_t m1, int32_t vb, int32_t na, bool p2, const T (&sig)[MAXA],
                                             int32_t h, int32_t ir, T (&d)[MAXA], T (&mm)[MAXA]) {
@@ -468,19 +472,29 @@ __device__ __forceinline__ void member_data(const GameView &g, const StateView<T
   for (int a = 0; a < MAXA; ++a) {
     if (a < na) {
       d[a] = f * (vc[a] - vh);
-      mm[a] = pw * sig[a];
+      if constexpr (!LEAN || sizeof(T) == 8) mm[a] = pw * sig[a];
     }
   }
+  if constexpr (LEAN && sizeof(T) == 4) mm[0] = pw;
+}
+
+// LEAN FP32: the set's average terms sigma(a) * (sum of the members' own
+// reach), from the sum carried in macc[0].
+template <typename T, int MAXA>
+__device__ __forceinline__ void avg_terms(const T (&sig)[MAXA], int32_t na, T (&macc)[MAXA]) {
+  const T spw = macc[0];
+#pragma unroll
+  for (int a = 0; a < MAXA; ++a) macc[a] = a < na ? sig[a] * spw : T(0);
 }
 
 // Indices, loads and per-member terms of one member (k < m1), or zeros.
-template <typename T, int MAXA, bool PERSIST>
+template <typename T, int MAXA, bool PERSIST, bool LEAN = false>
 __device__ __forceinline__ void member_terms(const GameView &g, const StateView<T> &st, int32_t k, int32_t m0,
                                              int32_t m1, MemberRanks mr, int32_t vb, int32_t na, bool p2,
                                              const T (&sig)[MAXA], T (&d)[MAXA], T (&mm)[MAXA]) {
   int32_t h, ir;
   member_idx(g, k, m1, mr, h, ir);
-  member_data<T, MAXA, PERSIST>(g, st, k, m0, m1, vb, na, p2, sig, h, ir, d, mm);
+  member_data<T, MAXA, PERSIST, LEAN>(g, st, k, m0, m1, vb, na, p2, sig, h, ir, d, mm);
 }
 
 // Adds one chunk's member terms to the group totals. P64: lane order (the
@@ -512,8 +526,8 @@ __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsign
 // in chunks of LANES (two chunks per step for narrow groups); each step loads
 // the next step's member indices while its own reach and child values are in
 // flight, so a step waits for one memory round trip, not two. The update of
-// the set's slots runs one lane per action.
-template <typename T, int MAXA, int LANES, bool PERSIST>
+// the set's slots runs one lane per action. LEAN: see member_data.
+template <typename T, int MAXA, int LANES, bool PERSIST, bool LEAN = false>
 __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &st, int32_t I, bool p2,
                                         int lane, unsigned mask, double wt, int rule, int upd) {
   const int32_t sb = __ldg(g.iset_slot + I);
@@ -529,8 +543,39 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
     macc[a] = T(0);
   }
   constexpr bool TWO = MAXA <= 8 && LANES <= 8;  // narrow groups keep two chunks in flight
+  constexpr int NCH = 2;
   int32_t k0 = m0;
-  if constexpr (TWO) {
+  // The two forms below compute the same; the one with chunk arrays
+  // compiles to fewer spills in LEAN kernels (64 registers a thread), the
+  // one with named chunks runs faster with a larger register budget.
+  if constexpr (TWO && LEAN) {
+    if (k0 + (NCH - 1) * LANES < m1) {
+      int32_t ps[NCH], ir[NCH];
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) member_idx(g, k0 + j * LANES + lane, m1, mr, ps[j], ir[j]);
+      for (; k0 + (NCH - 1) * LANES < m1; k0 += NCH * LANES) {
+        int32_t qs[NCH], jr[NCH];  // the next step's indices
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) member_idx(g, k0 + (NCH + j) * LANES + lane, m1, mr, qs[j], jr[j]);
+        T d[NCH][MAXA], mm[NCH][MAXA];
+#pragma unroll
+        for (int j = 0; j < NCH; ++j)
+          member_data<T, MAXA, PERSIST, LEAN>(g, st, k0 + j * LANES + lane, m0, m1, vb, na, p2, sig, ps[j], ir[j],
+                                              d[j], mm[j]);
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {  // chunks in member order
+          const int32_t left = m1 - k0 - j * LANES;
+          accumulate_chunk<T, MAXA, LANES>(left < 0 ? 0 : (left < LANES ? left : LANES), na, mask, d[j], mm[j], racc,
+                                           macc);
+        }
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          ps[j] = qs[j];
+          ir[j] = jr[j];
+        }
+      }
+    }
+  } else if constexpr (TWO) {
     if (k0 + LANES < m1) {
       int32_t ps0, ir0, ps1, ir1;
       member_idx(g, k0 + lane, m1, mr, ps0, ir0);
@@ -540,17 +585,19 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
         member_idx(g, k0 + 2 * LANES + lane, m1, mr, qs0, jr0);
         member_idx(g, k0 + 3 * LANES + lane, m1, mr, qs1, jr1);
         T d0[MAXA], mm0[MAXA], d1[MAXA], mm1[MAXA];
-        member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps0, ir0, d0, mm0);
-        member_data<T, MAXA, PERSIST>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, ps1, ir1, d1, mm1);
+        member_data<T, MAXA, PERSIST, LEAN>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps0, ir0, d0, mm0);
+        member_data<T, MAXA, PERSIST, LEAN>(g, st, k0 + LANES + lane, m0, m1, vb, na, p2, sig, ps1, ir1, d1, mm1);
         accumulate_chunk<T, MAXA, LANES>(LANES, na, mask, d0, mm0, racc, macc);
         const int32_t c1 = (m1 - k0 - LANES) < LANES ? (m1 - k0 - LANES) : LANES;
         accumulate_chunk<T, MAXA, LANES>(c1, na, mask, d1, mm1, racc, macc);
         ps0 = qs0; ir0 = jr0; ps1 = qs1; ir1 = jr1;
       }
     }
+  }
+  if constexpr (TWO) {  // the last chunk
     for (; k0 < m1; k0 += LANES) {
       T d[MAXA], mm[MAXA];
-      member_terms<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, mr, vb, na, p2, sig, d, mm);
+      member_terms<T, MAXA, PERSIST, LEAN>(g, st, k0 + lane, m0, m1, mr, vb, na, p2, sig, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
       accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
     }
@@ -561,7 +608,7 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
       int32_t qs, jr;  // the next step's indices
       member_idx(g, k0 + LANES + lane, m1, mr, qs, jr);
       T d[MAXA], mm[MAXA];
-      member_data<T, MAXA, PERSIST>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
+      member_data<T, MAXA, PERSIST, LEAN>(g, st, k0 + lane, m0, m1, vb, na, p2, sig, ps, ir, d, mm);
       const int32_t cnt = (m1 - k0) < LANES ? (m1 - k0) : LANES;
       accumulate_chunk<T, MAXA, LANES>(cnt, na, mask, d, mm, racc, macc);
       ps = qs; ir = jr;
@@ -574,8 +621,12 @@ __device__ __forceinline__ void bwd_set(const GameView &g, const StateView<T> &s
     for (int a = 0; a < MAXA; ++a) {
       if (a < na) {
         racc[a] = group_sum_butterfly<LANES>(racc[a], mask);
-        macc[a] = group_sum_butterfly<LANES>(macc[a], mask);
+        if constexpr (!LEAN) macc[a] = group_sum_butterfly<LANES>(macc[a], mask);
       }
+    }
+    if constexpr (LEAN) {
+      macc[0] = group_sum_butterfly<LANES>(macc[0], mask);
+      avg_terms<T, MAXA>(sig, na, macc);
     }
   }
   // every lane now holds the set's totals racc[a], macc[a]
