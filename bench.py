@@ -187,7 +187,7 @@ def run_reference(args):
 # ------------------------------------------------------------------ ours
 def kernel_source_hash() -> str:
     h = hashlib.sha1()
-    for f in ("kernels.cuh", "launch_impl.cuh", "cfr_api.cu"):
+    for f in ("kernels.cuh", "launch_impl.cuh", "cfr_api.cu", "compile.cpp", "compiled.h"):
         with open(os.path.join(ROOT, "paper_2609_11923_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

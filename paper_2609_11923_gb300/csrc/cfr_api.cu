@@ -760,7 +760,7 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   const int64_t dec = c.iset_mem[i1] - c.iset_mem[i0];
   const int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
   if (!c.int_edge.empty()) {  // member order: the launch of depth d fills depth d + 1 by pulling
-    *fwd = 8 * nint_kids + 2 * T * nint + 2 * T * nint_kids + T * slots;
+    *fwd = d + 1 < c.D ? 8 * nint_kids + 2 * T * nint + 2 * T * nint_kids + T * slots : 0;
     *bwd = 12 * sets + (32 + 2 * T) * slots + (4 + 3 * T) * dec + (12 + T) * nch + T * e;
     return CFR_OK;
   }

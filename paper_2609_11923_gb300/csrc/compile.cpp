@@ -508,13 +508,18 @@ int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
   // its value written; per chance node its block, child count and value slot
   // (12 B) and its value written; every edge's child value read once.
   // Member order: the forward reads every internal node's edge (parent rank
-  // and slot word, 8 B) instead of the 12-byte records (each parent's reach
-  // counted once), and the backward reads no member rank.
+  // and slot word, 8 B) instead of the 12-byte records, and each parent's
+  // reach and strategy once (the deepest depth's nodes and sets are nobody's
+  // parents: no launch reads them); the backward reads no member rank.
   const int64_t T = precision == CFR_P64 ? 8 : 4;
   const int64_t int_kids = c.n_int > 0 ? c.n_int - 1 : 0;  // every internal node but the root
-  if (!c.int_edge.empty())
-    return 8 * int_kids + 2 * T * c.n_int + 2 * T * int_kids + 12 * c.I + (32 + 3 * T) * c.A +
-           (4 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
+  if (!c.int_edge.empty()) {
+    const int64_t parents = c.D > 0 ? c.level_int[c.D - 1] : 0;  // internal nodes above the deepest depth
+    const int64_t last_slots =
+        c.D > 0 ? c.iset_slot[c.level_iset[2 * c.D]] - c.iset_slot[c.level_iset[2 * (c.D - 1)]] : 0;
+    return 8 * int_kids + 2 * T * parents + 2 * T * int_kids + T * (c.A - last_slots) + 12 * c.I +
+           (32 + 2 * T) * c.A + (4 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
+  }
   return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 12 * c.I +
          (32 + 3 * T) * c.A + (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
 }

@@ -223,3 +223,20 @@ def test_set_root_chance_needs_a_chance_root():
         assert "not a chance node" in str(ei.value)
     finally:
         cfr.cfr_destroy(h)
+
+
+@pytest.mark.parametrize("reach_order", [cfr.REACH_MEMBERS, cfr.REACH_BFS, cfr.REACH_SLOTS])
+@pytest.mark.parametrize("precision", [cfr.P32, cfr.P64])
+@pytest.mark.parametrize("name", ["tiny", "rt8", "card_small", "wide_root"])
+def test_iteration_bytes_are_the_sum_of_the_launches(name, reach_order, precision):
+    # the per-iteration algorithmic bytes (roofline numerator of the whole
+    # iteration) and the per-depth launch bytes count the same accesses
+    h = cfr.cfr_compile(GAMES[name](), cfr.make_options(precision=precision, reach_order=reach_order))
+    try:
+        c = cfr.cfr_get_counts(h)
+        per_launch = [cfr.cfr_level_bytes(h, d) for d in range(c["depth_blocks"])]
+        assert c["algo_bytes_per_iter"] == sum(f + b for f, b in per_launch)
+        if reach_order == cfr.REACH_MEMBERS:  # the deepest depth has no forward launch
+            assert per_launch[-1][0] == 0
+    finally:
+        cfr.cfr_destroy(h)
