@@ -280,9 +280,10 @@ def run_ours(args):
     fwd_ms = [statistics.median(p[0][d] for p in prof) for d in range(D)]
     bwd_ms = [statistics.median(p[1][d] for p in prof) for d in range(D)]
     launches = []
+    fwd_kernel = "fwd_pull_kernel" if args.reach_order == "members" else "fwd_level_kernel"
     for d in range(D):
         fb, bb = cfr.cfr_level_bytes(solver.h, d)
-        launches.append(("fwd_level_kernel", d, fwd_ms[d], fb))
+        launches.append((fwd_kernel, d, fwd_ms[d], fb))
         launches.append(("bwd_level_kernel", d, bwd_ms[d], bb))
     total_ms = sum(x[2] for x in launches)
     dom = max(launches, key=lambda x: x[2])
@@ -299,7 +300,8 @@ def run_ours(args):
     floor_graph, floor_pers = cfr.cfr_launch_floor(solver.h, 200, s)
     launch_floor = {"graph_ms": floor_graph, "persistent_ms": floor_pers,
                     "what": "per iteration: a graph of the same %d launches (same grids) of an empty kernel; one "
-                            "cooperative empty kernel with the persistent form's grid and %d grid barriers" % (2 * D, 2 * D)}
+                            "cooperative empty kernel with the persistent form's grid and %d grid barriers"
+                            % ((D - 1 if args.reach_order == "members" else D) + D, 2 * D)}
 
     # end to end through the public API: upload (bind) + K iterations + average strategy to host
     e2e = None
@@ -307,6 +309,7 @@ def run_ours(args):
         import numpy as np
 
         out = np.empty(counts["n_slots"])
+        cfr.cfr_pin_host(solver.h)  # the compiled game's host arrays, page-locked once
         torch.cuda.synchronize(dev)
         barrier()
         t0 = time.perf_counter()
@@ -322,7 +325,7 @@ def run_ours(args):
         e2e = {"value": world * E * args.steps / et, "unit": UNIT,
                "h2d_bytes_per_step": counts["upload_bytes"] / args.steps,
                "d2h_bytes_per_step": 8.0 * counts["n_slots"] / args.steps,
-               "what": "cfr_bind (upload of the compiled game from host memory) + cfr_iterate(K) + "
+               "what": "cfr_bind (upload of the compiled game from pinned host memory) + cfr_iterate(K) + "
                        "cfr_avg_strategy to host, wall clock"}
 
     cpu = None

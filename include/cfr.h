@@ -249,14 +249,24 @@ int cfr_autotune(cfr_handle *h, int reps, void *stream);
 /* The launch floor of one iteration (no counterpart in the paper's API; its
  * Section 4.3 discusses the graph-launch floor): the mean time of one
  * iteration's launch structure with no work in it, over n iterations.
- * graph_ms: a CUDA graph of the same 2D launches (4D under alternating
- * updates) with the same grid sizes as the per-level form (depth-first
- * forward, then backward), each an empty kernel. persistent_ms: one
+ * graph_ms: a CUDA graph of the same launches as the per-level form (2D,
+ * or 2D - 1 in member order, whose deepest depth has no forward launch;
+ * twice that under alternating updates) with the same grid sizes
+ * (depth-first forward, then backward), each an empty kernel. persistent_ms: one
  * cooperative launch of an empty kernel with the persistent form's grid and
  * its 2D (4D) grid barriers per iteration (bounded
  * waits: CFR_ERR_TIMEOUT if one gives up). The handle must be bound; solver
  * state is untouched. Synchronises `stream`. */
 int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *graph_ms, double *persistent_ms);
+
+/* Page-locks (pin != 0) or releases (pin == 0) the host memory that
+ * cfr_bind and the lifecycle calls copy to the device (the compiled arrays
+ * and the value template, owned by the handle), so those copies run at the
+ * pinned host-to-device rate. No counterpart in the paper's API. Ranges the
+ * driver reports as already page-locked (a page shared with another pinned
+ * range) stay as they are. cfr_destroy releases what is still pinned.
+ * Returns CFR_ERR_DEVICE if the driver refuses. */
+int cfr_pin_host(cfr_handle *h, int pin);
 
 /* Batched solves (many independent games in one launch). Every handle must
  * be bound (each to its own arena) and use the same precision, with sets of

@@ -100,6 +100,7 @@ def _load():
         "cfr_iterate_noalloc": [H, i64, vp],
         "cfr_autotune": [H, ctypes.c_int, vp],
         "cfr_launch_floor": [H, i64, vp, dp, dp],
+        "cfr_pin_host": [H, ctypes.c_int],
         "cfr_set_root_chance": [H, dp, i64, vp],
         "cfr_batch_iterate": [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(i64), i64, vp, ctypes.c_size_t,
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
@@ -125,7 +126,7 @@ EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterat
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
             "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune",
             "cfr_batch_table_bytes", "cfr_batch_iterate", "cfr_batch_exploitability", "cfr_launch_floor",
-            "cfr_set_root_chance"]
+            "cfr_set_root_chance", "cfr_pin_host"]
 
 
 def _check(rc: int) -> None:
@@ -281,6 +282,11 @@ def cfr_set_root_chance(h: int, prob, stream: int = 0) -> None:
     _check(_lib.cfr_set_root_chance(h, _dp(p), len(p), stream))
 
 
+def cfr_pin_host(h: int, pin: bool = True) -> None:
+    """Page-lock (or release) the handle's host arrays that cfr_bind uploads."""
+    _check(_lib.cfr_pin_host(h, 1 if pin else 0))
+
+
 def cfr_launch_floor(h: int, n: int, stream: int = 0) -> Tuple[float, float]:
     """Per-iteration ms of the launch structure alone: (graph of empty kernels, empty persistent kernel)."""
     g, p = ctypes.c_double(), ctypes.c_double()
@@ -400,6 +406,9 @@ class Solver:
 
     def set_payoffs(self, payoff) -> None:
         cfr_set_payoffs(self.h, payoff, self._s())
+
+    def pin_host(self, pin: bool = True) -> None:
+        cfr_pin_host(self.h, pin)
 
     def set_root_chance(self, prob) -> None:
         cfr_set_root_chance(self.h, prob, self._s())

@@ -65,6 +65,7 @@ struct cfr_handle {
   size_t plan_bytes = 0;
   char *arena = nullptr;
   bool bound = false;
+  std::vector<void *> pinned;  // host ranges page-locked by cfr_pin_host
   // graph form
   cudaGraphExec_t gexec = nullptr;
   char *graph_arena = nullptr;
@@ -201,6 +202,7 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
 
 extern "C" void cfr_destroy(cfr_handle *h) {
   if (!h) return;
+  for (void *p : h->pinned) cudaHostUnregister(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -314,6 +316,51 @@ static int init_values(cfr_handle *h, cudaStream_t s) {
   init_values_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
       h->p<double>(h->b_tmpl), (int32_t)c.N, h->p<T>(h->b_v), h->p<double2>(h->b_vb), h->p<double>(h->b_vavg));
   CK(cudaGetLastError());
+  return CFR_OK;
+}
+
+// The host ranges cfr_bind copies from, and the value template.
+static std::vector<std::pair<const void *, size_t>> host_ranges(const cfr_handle *h) {
+  const Compiled &c = h->c;
+  std::vector<std::pair<const void *, size_t>> r = {
+      {c.iset_slot.data(), 4 * c.iset_slot.size()},   {c.iset_mem.data(), 4 * c.iset_mem.size()},
+      {c.iset_vb.data(), 4 * c.iset_vb.size()},       {c.mem_vs.data(), 4 * c.mem_vs.size()},
+      {c.ch_vb.data(), 4 * c.ch_vb.size()},           {c.ch_nch.data(), 4 * c.ch_nch.size()},
+      {c.ch_vs.data(), 4 * c.ch_vs.size()},           {c.spec_slot_of.data(), 4 * c.spec_slot_of.size()},
+      {c.wide_vb.data(), 4 * c.wide_vb.size()},       {c.wide_nch.data(), 4 * c.wide_nch.size()},
+      {c.wide_vs.data(), 4 * c.wide_vs.size()},       {c.wide_chunk.data(), 4 * c.wide_chunk.size()},
+      {c.int_slot.data(), 4 * c.int_slot.size()},     {c.int_mask.data(), 4 * c.int_mask.size()},
+      {c.int_cirank.data(), 4 * c.int_cirank.size()}, {c.big_irank.data(), 4 * c.big_irank.size()},
+      {c.int_edge.data(), 4 * c.int_edge.size()},     {c.iset_rank.data(), 4 * c.iset_rank.size()},
+      {c.mem_irank.data(), 4 * c.mem_irank.size()},   {c.wide_irank.data(), 4 * c.wide_irank.size()},
+      {c.tmpl_vs.data(), 8 * c.tmpl_vs.size()}};
+  return r;
+}
+
+extern "C" int cfr_pin_host(cfr_handle *h, int pin) {
+  if (!h) return set_err(CFR_ERR_ARG, "cfr_pin_host: null handle");
+  if (!pin) {
+    for (void *p : h->pinned) cudaHostUnregister(p);
+    h->pinned.clear();
+    return CFR_OK;
+  }
+  if (!h->pinned.empty()) return CFR_OK;
+  for (const auto &r : host_ranges(h)) {
+    if (r.second == 0) continue;
+    void *p = const_cast<void *>(r.first);
+    const cudaError_t e = cudaHostRegister(p, r.second, cudaHostRegisterDefault);
+    if (e == cudaErrorHostMemoryAlreadyRegistered) {
+      cudaGetLastError();  // a page shared with a range pinned before: leave it
+      continue;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      for (void *q : h->pinned) cudaHostUnregister(q);
+      h->pinned.clear();
+      return set_err(CFR_ERR_DEVICE, "cfr_pin_host: %s", cudaGetErrorString(e));
+    }
+    h->pinned.push_back(p);
+  }
   return CFR_OK;
 }
 

@@ -397,3 +397,19 @@ def test_p64_reach_layouts_match_oracle_bitwise(reach_order, tiles, form, name, 
     s = solve_gpu(g, iters, form=form, reach_order=reach_order, member_tiles=tiles)
     np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, iters).avg_strategy())
     assert abs(s.exploitability() - oracle.solve(g, iters).exploitability()) <= 1e-12
+
+
+def test_pinned_host_arrays_bind_to_the_same_results():
+    # page-locking the compiled arrays changes how cfr_bind copies, not what
+    g = gg.large_card(3, 2, 1, 1)
+    a = cfr.Solver(g, precision=cfr.P64, exec_form=cfr.EXEC_GRAPH)
+    b = cfr.Solver(g, precision=cfr.P64, exec_form=cfr.EXEC_GRAPH)
+    b.pin_host()
+    b.pin_host()  # idempotent
+    cfr.cfr_bind(b.h, b.arena_ptr, b.arena_bytes, b._s())  # upload again from the pinned arrays
+    for s in (a, b):
+        s.iterate(30)
+        s.synchronize()
+    np.testing.assert_array_equal(a.avg_strategy(), b.avg_strategy())
+    b.pin_host(False)
+    b.pin_host(False)
