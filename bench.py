@@ -454,7 +454,7 @@ def run_warmstart(args):
     held = ws.endgame_family(list(range(20000, 20000 + args.heldout)), 1e3, 1e6)
     cold, cold_fin, cold_wall = ws.iterations_to_target(held, max_iters=args.max_iters)
     t2 = time.perf_counter()
-    init = [ws.warm_regrets(net, sp, kappa) for sp in held]
+    init = ws.warm_regrets_many(net, held, kappa)
     t_infer = time.perf_counter() - t2
     warm, warm_fin, warm_wall = ws.iterations_to_target(held, init=init, max_iters=args.max_iters)
     line = {

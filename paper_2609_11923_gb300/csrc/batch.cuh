@@ -100,11 +100,8 @@ __device__ __forceinline__ void cta_bwd_wide(const GameView &g, T *v, int32_t wi
   const int32_t h = __ldg(g.wide_vs + wi);
   const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   if constexpr (sizeof(T) == 8) {
-    if (threadIdx.x == 0) {
-      T s = T(0);
-      for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
-      v[h] = s;
-    }
+    const double s = ordered_sum<THREADS, PERSIST>(v, cb, ce);
+    if (threadIdx.x == 0) v[h] = s;
   } else {
     double x = 0.0;
     for (int32_t c = cb + threadIdx.x; c < ce; c += THREADS) x += (double)ldm<PERSIST>(v + c);
@@ -157,12 +154,14 @@ __global__ void __launch_bounds__(THREADS) batch_iterate_kernel(const InstDesc *
       }
       for (int d = in.D - 1; d >= 0; --d) {
         const LevelWork w = in.lw[d];
-        for (int32_t i = w.ch0 + ct; i < w.ch1; i += NT)
-          bwd_chance<T, CLUSTERED>(in.g, st.v, i);
-        if (rank == 0)
-          for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
+        if (d > 0) {  // a chance root's value has no reader in an iteration
+          for (int32_t i = w.ch0 + ct; i < w.ch1; i += NT)
+            bwd_chance<T, CLUSTERED>(in.g, st.v, i);
+          if (rank == 0)
+            for (int32_t i = w.wd0; i < w.wd1; ++i) cta_bwd_wide<T, THREADS, CLUSTERED>(in.g, st.v, i, sm);
+        }
+        // 1024-thread blocks leave 64 registers a thread: lean average terms
         for (int32_t I = w.is0 + gid; I < w.is1; I += NG)
-// 1024-thread blocks leave 64 registers a thread: lean average terms
           bwd_set<T, MAXA, LANES, CLUSTERED, (THREADS >= 1024)>(in.g, st, I, I >= w.is2, lane, mask, wt, in.rule, upd);
         level_sync<CLUSTERED>();
       }

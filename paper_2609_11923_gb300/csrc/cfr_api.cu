@@ -418,14 +418,19 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
 // depth-0 launch of the pass that updates player 2 advances t.
 template <typename T>
 static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3) {
-  const LevelWork &w = h->levels[d];
+  LevelWork w = h->levels[d];
+  if (d == 0) {  // a chance root's value has no reader in an iteration (the best response sums its own)
+    w.ch1 = w.ch0;
+    w.wc1 = w.wc0;
+  }
   const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
   const int lanes = h->level_lanes[d];
   const int nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
   const int nb_wide = w.wc1 - w.wc0;
   const int nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;
-  CK(launch_bwd_level<T>(h->maxa_tier, lanes, nb_ch + nb_wide + nb_is, s, game_view(h), state_view<T>(h), w, nb_ch,
-                         h->rule, upd, (d == 0 && (upd & 2)) ? 1 : 0));
+  // at least one block: the depth-0 launch also advances t
+  CK(launch_bwd_level<T>(h->maxa_tier, lanes, std::max(1, nb_ch + nb_wide + nb_is), s, game_view(h), state_view<T>(h),
+                         w, nb_ch, h->rule, upd, (d == 0 && (upd & 2)) ? 1 : 0));
   return CFR_OK;
 }
 
@@ -1028,9 +1033,9 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
     const LevelWork &w = h->levels[d];
-    const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
-    grids.push_back((nch > 0 ? grid_for(nch, kThreads) : 0) + (w.wc1 - w.wc0) +
-                    (nis > 0 ? grid_for(nis, kThreads / h->level_lanes[d]) : 0));
+    const int nch = d > 0 ? w.ch1 - w.ch0 : 0, nwide = d > 0 ? w.wc1 - w.wc0 : 0, nis = w.is1 - w.is0;
+    grids.push_back(std::max(1, (nch > 0 ? grid_for(nch, kThreads) : 0) + nwide +
+                                    (nis > 0 ? grid_for(nis, kThreads / h->level_lanes[d]) : 0)));
   }
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;

@@ -141,6 +141,30 @@ __device__ __forceinline__ double block_sum(double x) {
   return sm[0];
 }
 
+// The sum of v[cb, ce) strictly left to right (the FP64 parity order), for
+// one block of N threads that all call it: the block stages N values at a
+// time in shared memory, and thread 0 adds one batch while the others load
+// the next. The result is valid in thread 0.
+template <int N, bool PERSIST, typename T>
+__device__ __forceinline__ double ordered_sum(const T *v, int32_t cb, int32_t ce) {
+  __shared__ double buf[2 * N];
+  const int tid = threadIdx.x;
+  double s = 0.0;
+  if (cb + tid < ce) buf[tid] = (double)ldm<PERSIST>(v + cb + tid);
+  __syncthreads();
+  int b = 0;
+  for (int32_t c0 = cb; c0 < ce; c0 += N) {
+    if (c0 + N + tid < ce) buf[(b ^ 1) * N + tid] = (double)ldm<PERSIST>(v + c0 + N + tid);
+    if (tid == 0) {
+      const int n = ce - c0 < N ? ce - c0 : N;
+      for (int j = 0; j < n; ++j) s = s + buf[b * N + j];
+    }
+    __syncthreads();
+    b ^= 1;
+  }
+  return s;
+}
+
 // ------------------------------------------------------------ forward reach
 // reach of child a of an internal node with slot word s and reach r
 template <typename T, bool PERSIST>
@@ -389,10 +413,9 @@ __device__ __forceinline__ void bwd_wide_chunk(const GameView &g, const LevelWor
   const int32_t cb = __ldg(g.wide_vb + wi), ce = cb + __ldg(g.wide_nch + wi);
   const int32_t q0 = __ldg(g.wide_chunk + wi), nq = __ldg(g.wide_chunk + wi + 1) - q0;
   if constexpr (sizeof(T) == 8) {
-    if (q == q0 && threadIdx.x == 0) {
-      T s = T(0);
-      for (int32_t c = cb; c < ce; ++c) s = s + ldm<PERSIST>(v + c);
-      v[h] = s;
+    if (q == q0) {  // block-uniform: the whole block stages the children
+      const double s = ordered_sum<kThreads, PERSIST>(v, cb, ce);
+      if (threadIdx.x == 0) v[h] = s;
     }
     return;
   } else {
@@ -504,12 +527,27 @@ template <typename T, int MAXA, int LANES>
 __device__ __forceinline__ void accumulate_chunk(int32_t cnt, int32_t na, unsigned mask, const T (&d)[MAXA],
                                                  const T (&mm)[MAXA], T (&racc)[MAXA], T (&macc)[MAXA]) {
   if constexpr (sizeof(T) == 8) {
-    for (int j = 0; j < cnt; ++j) {
+    if constexpr (LANES <= 8) {  // unrolled: the shuffles issue ahead of the ordered adds
 #pragma unroll
-      for (int a = 0; a < MAXA; ++a) {
-        if (a < na) {
-          racc[a] = racc[a] + __shfl_sync(mask, d[a], j, LANES);
-          macc[a] = macc[a] + __shfl_sync(mask, mm[a], j, LANES);
+      for (int j = 0; j < LANES; ++j) {
+        if (j < cnt) {
+#pragma unroll
+          for (int a = 0; a < MAXA; ++a) {
+            if (a < na) {
+              racc[a] = racc[a] + __shfl_sync(mask, d[a], j, LANES);
+              macc[a] = macc[a] + __shfl_sync(mask, mm[a], j, LANES);
+            }
+          }
+        }
+      }
+    } else {  // wide groups keep the loop (registers)
+      for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) {
+          if (a < na) {
+            racc[a] = racc[a] + __shfl_sync(mask, d[a], j, LANES);
+            macc[a] = macc[a] + __shfl_sync(mask, mm[a], j, LANES);
+          }
         }
       }
     }
@@ -911,8 +949,10 @@ __global__ void __launch_bounds__(kThreads) persistent_kernel(PersistArgs<T> a) 
       }
       for (int d = a.D - 1; d >= 0; --d) {
         const LevelWork w = a.lw[d];
-        for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
-        for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
+        if (d > 0) {  // a chance root's value has no reader in an iteration
+          for (int32_t i = w.ch0 + tid; i < w.ch1; i += nthr) bwd_chance<T, true>(a.g, a.st.v, i);
+          for (int32_t q = w.wc0 + blockIdx.x; q < w.wc1; q += gridDim.x) bwd_wide_chunk<T, true>(a.g, w, a.st.v, q);
+        }
         for (int32_t I = w.is0 + gid; I < w.is1; I += ngroups)
           bwd_set<T, MAXA, LANES, true>(a.g, a.st, I, I >= w.is2, lane, mask, wt, a.rule, upd);
         if (!grid_sync(a.bar)) return;

@@ -19,7 +19,9 @@ deals that the acting player wins at the check-down showdown (value and a
 """
 from __future__ import annotations
 
+import os
 import time
+from concurrent.futures import ThreadPoolExecutor
 from typing import List, Optional
 
 import numpy as np
@@ -230,21 +232,43 @@ def train(X, nact, T, epochs: int = 3, batch: int = 4096, lr: float = 2e-3, seed
     return net
 
 
-def warm_regrets(net: MLP, spec, kappa: float) -> np.ndarray:
-    """R0 in spec slot order: kappa * pot * mass(I) * sigma_hat(I, a), i.e.
-    about kappa iterations' worth of regret pointing at the network's
-    strategy (mass(I) = chance probability of reaching I, the scale of one
-    iteration's regret increment at I)."""
-    import torch
-
-    X, na, mass = features(spec, return_mass=True)
-    prob = net.predict(torch.tensor(X, device=net.dev), torch.tensor(na, device=net.dev)).cpu().numpy()
+def _regrets_from(spec, prob: np.ndarray, mass: np.ndarray, kappa: float) -> np.ndarray:
     off = spec.slot_offsets()
     R0 = np.zeros(int(off[-1]))
     for a in range(N_OUT):
         ok = spec.iset_nact > a
         R0[off[:-1][ok] + a] = prob[ok, a] * mass[ok]
     return kappa * spec.pot * R0
+
+
+def warm_regrets(net: MLP, spec, kappa: float) -> np.ndarray:
+    """R0 in spec slot order: kappa * pot * mass(I) * sigma_hat(I, a), i.e.
+    about kappa iterations' worth of regret pointing at the network's
+    strategy (mass(I) = chance probability of reaching I, the scale of one
+    iteration's regret increment at I)."""
+    return warm_regrets_many(net, [spec], kappa, workers=1)[0]
+
+
+def warm_regrets_many(net: MLP, specs, kappa: float, workers: Optional[int] = None) -> List[np.ndarray]:
+    """warm_regrets for many games: their features computed on a thread pool
+    (NumPy's array loops release the interpreter lock), then one network
+    pass over every game's sets."""
+    import torch
+
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers > 1 and len(specs) > 1:
+        with ThreadPoolExecutor(workers) as ex:
+            feats = list(ex.map(lambda sp: features(sp, return_mass=True), specs))
+    else:
+        feats = [features(sp, return_mass=True) for sp in specs]
+    X = np.concatenate([f[0] for f in feats])
+    na = np.concatenate([f[1] for f in feats])
+    prob = net.predict(torch.tensor(X, device=net.dev), torch.tensor(na, device=net.dev)).cpu().numpy()
+    out, row = [], 0
+    for sp, (_, nag, mass) in zip(specs, feats):
+        out.append(_regrets_from(sp, prob[row:row + len(nag)], mass, kappa))
+        row += len(nag)
+    return out
 
 
 def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iters=5000, threads=1024, lanes=8):
@@ -298,8 +322,7 @@ def choose_kappa(net: MLP, specs, kappas=(4.0, 8.0, 16.0), max_iters: int = 3000
     """The kappa with the fewest mean iterations to 1e-3 pot on `specs`."""
     best, best_it, table = None, float("inf"), {}
     for k in kappas:
-        done, fin, _ = iterations_to_target(specs, init=[warm_regrets(net, sp, k) for sp in specs],
-                                            max_iters=max_iters)
+        done, fin, _ = iterations_to_target(specs, init=warm_regrets_many(net, specs, k), max_iters=max_iters)
         table[k] = float(np.mean(done))
         if table[k] < best_it:
             best, best_it = k, table[k]
