@@ -803,14 +803,15 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   const Compiled &c = h->c;
   if (d < 0 || d >= c.D) return set_err(CFR_ERR_ARG, "cfr_level_bytes: level out of range");
   const int64_t T = h->precision == CFR_P64 ? 8 : 4;
-  const int64_t e = c.level_begin[d + 2] - c.level_begin[d + 1];  // children = next level
+  int64_t e = c.level_begin[d + 2] - c.level_begin[d + 1];  // children = next level
   const int64_t nint = c.level_int[d + 1] - c.level_int[d];
   const int64_t nint_kids = (d + 1 < c.D) ? c.level_int[d + 2] - c.level_int[d + 1] : 0;
   const int64_t i0 = c.level_iset[2 * d], i1 = c.level_iset[2 * d + 2];
   const int64_t sets = i1 - i0;
   const int64_t slots = c.iset_slot[i1] - c.iset_slot[i0];
   const int64_t dec = c.iset_mem[i1] - c.iset_mem[i0];
-  const int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
+  int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
+  if (d == 0 && nch > 0) nch = e = 0;  // a chance root's sum is not done in an iteration
   if (!c.int_edge.empty()) {  // member order: the launch of depth d fills depth d + 1 by pulling
     *fwd = d + 1 < c.D ? 8 * nint_kids + 2 * T * nint + 2 * T * nint_kids + T * slots : 0;
     *bwd = 12 * sets + (32 + 2 * T) * slots + (4 + 3 * T) * dec + (12 + T) * nch + T * e;

@@ -511,17 +511,20 @@ int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
   // and slot word, 8 B) instead of the 12-byte records, and each parent's
   // reach and strategy once (the deepest depth's nodes and sets are nobody's
   // parents: no launch reads them); the backward reads no member rank.
+  // A chance root's sum is not done in an iteration (nothing reads it).
   const int64_t T = precision == CFR_P64 ? 8 : 4;
   const int64_t int_kids = c.n_int > 0 ? c.n_int - 1 : 0;  // every internal node but the root
+  const bool chance_root = c.N > 1 && c.node_slot[0] < 0;
+  const int64_t root_sum = chance_root ? (12 + T) + T * (c.child_begin[1] - c.child_begin[0]) : 0;
   if (!c.int_edge.empty()) {
     const int64_t parents = c.D > 0 ? c.level_int[c.D - 1] : 0;  // internal nodes above the deepest depth
     const int64_t last_slots =
         c.D > 0 ? c.iset_slot[c.level_iset[2 * c.D]] - c.iset_slot[c.level_iset[2 * (c.D - 1)]] : 0;
     return 8 * int_kids + 2 * T * parents + 2 * T * int_kids + T * (c.A - last_slots) + 12 * c.I +
-           (32 + 2 * T) * c.A + (4 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
+           (32 + 2 * T) * c.A + (4 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E - root_sum;
   }
   return 12 * c.n_int + 2 * T * c.n_int + 2 * T * int_kids + 4 * (int64_t)c.big_irank.size() + 12 * c.I +
-         (32 + 3 * T) * c.A + (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E;
+         (32 + 3 * T) * c.A + (8 + 3 * T) * c.n_dec + (12 + T) * c.n_chance + T * c.E - root_sum;
 }
 
 }  // namespace cfr
