@@ -221,14 +221,19 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * of each spec node [N], 10 template values [N] (doubles, node order),
  * 11 spec slot of each compiled slot [A], 12 lanes per set of each depth (a
  * runtime choice), 13 int_slot, 14 int_mask (bit pattern), 15 int_cirank
- * [N_int each: the internal-node records], 16 big_irank, 17 mem_irank
+ * [N_int each: the pushing forward's internal-node records; empty in
+ * member order], 16 big_irank (empty in member order), 17 mem_irank
  * [N_dec], 18 level_int[D+1], 19 vslot[N] (value slot of each node; the
  * root's is N-1), 20 iset_vb[I] (first slot of the block holding set I's
  * members' children), 21 mem_vs[N_dec] (value slot of each member),
  * 22 ch_vb, 23 ch_nch, 24 ch_vs (per chance node of list 6: first child
  * slot, child count, own slot), 25 wide_vb, 26 wide_nch, 27 wide_vs (the
  * same for chance nodes with more than 1024 children), 28 template values
- * in value-slot order [N] (doubles).
+ * in value-slot order [N] (doubles), 29 int_edge[2 N_int] (member order:
+ * per internal node in rank order, its parent's rank and the slot word of
+ * its edge, -1 under a chance node; the root's pair is -1, -1), 30
+ * iset_rank[2 I] (member order: rank of each set's first member and the
+ * stride of its members' ranks, 4 inside a tile), 31 level_tiled[D].
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);

@@ -240,3 +240,65 @@ def test_iteration_bytes_are_the_sum_of_the_launches(name, reach_order, precisio
             assert per_launch[-1][0] == 0
     finally:
         cfr.cfr_destroy(h)
+
+
+@pytest.mark.parametrize("tiles", [cfr.TILES_AUTO, cfr.TILES_ON])
+@pytest.mark.parametrize("name", ["tiny", "rt8", "card_small", "endgame", "wide_root"])
+def test_member_order_layout_properties(name, tiles):
+    # what the member-order kernels rely on, checked against the tree itself
+    # (not against a second flattener): a set's members sit at ranks
+    # base + k * stride (stride 4 inside a tile of four consecutive sets with
+    # equal member counts, else 1) within their depth's rank
+    # range; every internal node's edge names its parent's rank and the
+    # parent's slot + action (-1 under chance); ranks are one permutation
+    h = cfr.cfr_compile(GAMES[name](), cfr.make_options(member_tiles=tiles))
+    try:
+        ex = lambda k: cfr.cfr_export_array(h, k).astype(np.int64)
+        cb, ns, lb = ex("child_begin"), ex("node_slot"), ex("level_begin")
+        im, mn, li, lint = ex("iset_mem"), ex("mem_node"), ex("level_iset"), ex("level_int")
+        edge, irk = ex("int_edge").reshape(-1, 2), ex("iset_rank").reshape(-1, 2)
+        N, D = len(ns), len(lint) - 1
+        internal = np.nonzero(cb[1:] > cb[:-1])[0]
+        assert len(edge) == len(internal) == lint[D]
+        parent = np.full(N, -1)
+        for x in range(N):
+            parent[cb[x]:cb[x + 1]] = x
+        depth = np.searchsorted(lb, np.arange(N), side="right") - 1
+        rank = np.full(N, -1)
+        for I in range(len(im) - 1):
+            assert irk[I, 1] in (1, 4)
+            k = np.arange(im[I], im[I + 1])
+            rank[mn[k]] = irk[I, 0] + (k - im[I]) * irk[I, 1]
+            d = depth[mn[im[I]]]
+            assert np.all((rank[mn[k]] >= lint[d]) & (rank[mn[k]] < lint[d + 1]))
+        # chance nodes above a ranked node: their rank is that node's parent rank
+        for d in range(D - 1, 0, -1):
+            for x in internal[(depth[internal] == d) & (rank[internal] >= 0)]:
+                p = parent[x]
+                if rank[p] < 0:
+                    rank[p] = edge[rank[x], 0]
+                assert edge[rank[x], 0] == rank[p]
+        known = internal[rank[internal] >= 0]
+        assert len(set(rank[known].tolist())) == len(known)  # no two nodes share a rank
+        for x in known:
+            p = parent[x]
+            if p < 0:
+                assert tuple(edge[rank[x]]) == (-1, -1)
+            else:
+                assert edge[rank[x], 0] == rank[p]
+                assert edge[rank[x], 1] == (-1 if ns[p] < 0 else ns[p] + (x - cb[p]))
+        # the rest (chance nodes with no internal child) fill the free ranks
+        # of their depth, and those ranks' edges name their parents
+        rest = internal[rank[internal] < 0]
+        free = np.setdiff1d(np.arange(len(internal)), rank[known])
+        assert len(free) == len(rest)
+        assert sorted(depth[rest].tolist()) == sorted((np.searchsorted(lint, free, side="right") - 1).tolist())
+        assert sorted(edge[free, 0].tolist()) == sorted(rank[parent[rest]].tolist())
+        # tiles: four consecutive sets, consecutive bases, equal member counts
+        for I in range(len(im) - 1):
+            if irk[I, 1] == 4 and (I == 0 or irk[I - 1, 1] != 4 or irk[I, 0] != irk[I - 1, 0] + 1):
+                group = list(range(I, I + 4))
+                assert [irk[j, 0] for j in group] == [irk[I, 0] + j for j in range(4)]
+                assert len({im[j + 1] - im[j] for j in group}) == 1
+    finally:
+        cfr.cfr_destroy(h)
