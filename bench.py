@@ -185,6 +185,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
+def max_over_ranks(dist, seconds: float, device) -> float:
+    """The job's time: the slowest rank's, known to every rank (replicas)."""
+    if dist is None:
+        return seconds
+    import torch
+
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha1()
     for f in ("kernels.cuh", "launch_impl.cuh", "cfr_api.cu", "compile.cpp", "compiled.h"):
@@ -266,11 +277,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     solver.synchronize()
-    dt = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        t = torch.tensor([dt], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, dev)
     iters_per_s = args.steps / dt
     value = world * E * iters_per_s
     algo_gbps = counts["algo_bytes_per_iter"] * iters_per_s / 1e9
@@ -317,11 +324,7 @@ def run_ours(args):
         cfr.cfr_iterate(solver.h, args.steps, s)
         cfr.cfr_avg_strategy(solver.h, out, False, s)
         t1 = time.perf_counter()
-        et = t1 - t0
-        if dist is not None:
-            t = torch.tensor([et], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = max_over_ranks(dist, t1 - t0, dev)
         e2e = {"value": world * E * args.steps / et, "unit": UNIT,
                "h2d_bytes_per_step": counts["upload_bytes"] / args.steps,
                "d2h_bytes_per_step": 8.0 * counts["n_slots"] / args.steps,
