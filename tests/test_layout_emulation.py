@@ -1,0 +1,118 @@
+"""The compiled member-order layout computes CFR+ exactly (CPU only).
+
+A plain-Python FP64 run of the kernels' scheme over the exported arrays (the
+pulling forward over the internal nodes' edges, the backward over the sets'
+rank bases and strides, value blocks and value slots, with the kernels'
+summation order) must reach the oracle's cumulative regrets and average
+sums bitwise. This checks the layout (ranks, edges, tiles, value slots,
+chance blocks) without a GPU and independently of the kernels' code.
+"""
+import numpy as np
+import pytest
+
+import gamegen as gg
+import oracle
+from paper_2609_11923_gb300 import cfr
+
+P2BIT = 1 << 30
+MASK = P2BIT - 1
+
+GAMES = {
+    "kuhn": lambda: gg.kuhn(),
+    "tiny": lambda: gg.tiny_card(),
+    "rt6": lambda: gg.random_tree(1, depth=6),
+    "card_small": lambda: gg.large_card(3, 2, 1, 1),
+    "endgame": lambda: gg.endgame(3, 3000),
+}
+
+
+def emulate(h, iters):
+    ex = lambda k: cfr.cfr_export_array(h, k)
+    lint, edge = ex("level_int").astype(int), ex("int_edge").astype(int).reshape(-1, 2)
+    isl, im, ivb, li = ex("iset_slot").astype(int), ex("iset_mem").astype(int), ex("iset_vb").astype(int), \
+        ex("level_iset").astype(int)
+    irk, mvs = ex("iset_rank").astype(int).reshape(-1, 2), ex("mem_vs").astype(int)
+    chb, chn, chs, lch = ex("ch_vb").astype(int), ex("ch_nch").astype(int), ex("ch_vs").astype(int), \
+        ex("level_chance").astype(int)
+    wvb, wn, wvs = ex("wide_vb").astype(int), ex("wide_nch").astype(int), ex("wide_vs").astype(int)
+    lb, vslot = ex("level_begin").astype(int), ex("vslot").astype(int)
+    v = [float(x) for x in ex("tmpl_vs")]
+    D, I, A = len(lint) - 1, len(isl) - 1, int(isl[-1])
+    node_of_slot = np.empty(len(vslot), dtype=int)
+    node_of_slot[vslot] = np.arange(len(vslot))
+    wide_depth = np.searchsorted(lb, node_of_slot[wvs], side="right") - 1 if len(wvs) else []
+    sigma = [0.0] * A
+    for s in range(I):
+        for a in range(isl[s], isl[s + 1]):
+            sigma[a] = 1.0 / (isl[s + 1] - isl[s])
+    R, avg = [0.0] * A, [0.0] * A
+    reach = [[0.0, 0.0] for _ in range(len(edge))]
+    for t in range(1, iters + 1):
+        reach[0] = [1.0, 1.0]
+        for d in range(D - 1):  # the launch of depth d pulls depth d + 1
+            for q in range(lint[d + 1], lint[d + 2]):
+                p, s = edge[q]
+                r = list(reach[p])
+                if s >= 0:
+                    lane = 1 if s & P2BIT else 0
+                    r[lane] = r[lane] * sigma[s & MASK]
+                reach[q] = r
+        for d in range(D - 1, -1, -1):
+            if d > 0:  # chance nodes (the root's value is not needed)
+                for i in range(lch[d], lch[d + 1]):
+                    acc = 0.0
+                    for c in range(chb[i], chb[i] + chn[i]):
+                        acc = acc + v[c]
+                    v[chs[i]] = acc
+                for i in range(len(wvs)):
+                    if wide_depth[i] == d:
+                        acc = 0.0
+                        for c in range(wvb[i], wvb[i] + wn[i]):
+                            acc = acc + v[c]
+                        v[wvs[i]] = acc
+            for s in range(li[2 * d], li[2 * d + 2]):
+                p2 = s >= li[2 * d + 1]
+                sb, na = isl[s], isl[s + 1] - isl[s]
+                sig = sigma[sb:sb + na]
+                racc, macc = [0.0] * na, [0.0] * na
+                for k in range(im[s], im[s + 1]):
+                    r = reach[irk[s, 0] + (k - im[s]) * irk[s, 1]]
+                    cb = ivb[s] + (k - im[s]) * na
+                    vh = 0.0
+                    for a in range(na):
+                        vh = vh + sig[a] * v[cb + a]
+                    v[mvs[k]] = vh
+                    po, pw = (r[0], r[1]) if p2 else (r[1], r[0])
+                    f = (-1.0 if p2 else 1.0) * po
+                    for a in range(na):
+                        racc[a] = racc[a] + f * (v[cb + a] - vh)
+                        macc[a] = macc[a] + pw * sig[a]
+                pos = []
+                for a in range(na):
+                    rn = R[sb + a] + racc[a]
+                    R[sb + a] = rn if rn > 0.0 else 0.0
+                    avg[sb + a] = avg[sb + a] + float(t) * macc[a]
+                    pos.append(R[sb + a])
+                tot = 0.0
+                for a in range(na):
+                    tot = tot + pos[a]
+                for a in range(na):
+                    sigma[sb + a] = pos[a] / tot if tot > 0.0 else 1.0 / na
+    return np.array(R), np.array(avg)
+
+
+@pytest.mark.parametrize("tiles", [cfr.TILES_AUTO, cfr.TILES_ON])
+@pytest.mark.parametrize("name", list(GAMES))
+def test_member_layout_reaches_the_oracles_iterates(name, tiles):
+    g = GAMES[name]()
+    iters = 4
+    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P64, member_tiles=tiles))
+    try:
+        R, avg = emulate(h, iters)
+        spec_of = cfr.cfr_export_array(h, "spec_slot_of").astype(int)
+    finally:
+        cfr.cfr_destroy(h)
+    o = oracle.Oracle(g)
+    o.iterate(iters)
+    np.testing.assert_array_equal(R, o.R[spec_of])
+    np.testing.assert_array_equal(avg, o.sbar[spec_of])
