@@ -1,11 +1,13 @@
-"""The compiled member-order layout computes CFR+ exactly (CPU only).
+"""The compiled layouts compute CFR+ exactly (CPU only).
 
-A plain-Python FP64 run of the kernels' scheme over the exported arrays (the
-pulling forward over the internal nodes' edges, the backward over the sets'
-rank bases and strides, value blocks and value slots, with the kernels'
-summation order) must reach the oracle's cumulative regrets and average
-sums bitwise. This checks the layout (ranks, edges, tiles, value slots,
-chance blocks) without a GPU and independently of the kernels' code.
+A plain-Python FP64 run of the kernels' scheme over the exported arrays (in
+member order the pulling forward over the internal nodes' edges and the
+backward over the sets' rank bases and strides; in breadth-first and
+value-slot order the pushing forward over the internal-node records and the
+backward over the rank table; value blocks and value slots in all) with the
+kernels' summation order must reach the oracle's cumulative regrets and
+average sums bitwise. This checks the layouts without a GPU and
+independently of the kernels' code.
 """
 import numpy as np
 import pytest
@@ -23,6 +25,7 @@ GAMES = {
     "rt6": lambda: gg.random_tree(1, depth=6),
     "card_small": lambda: gg.large_card(3, 2, 1, 1),
     "endgame": lambda: gg.endgame(3, 3000),
+    "wide_root": lambda: gg.endgame(2, 100000),  # a deal root of more than 1,024 outcomes
 }
 
 
@@ -36,6 +39,11 @@ def emulate(h, iters):
         ex("level_chance").astype(int)
     wvb, wn, wvs = ex("wide_vb").astype(int), ex("wide_nch").astype(int), ex("wide_vs").astype(int)
     lb, vslot = ex("level_begin").astype(int), ex("vslot").astype(int)
+    members = len(ex("int_edge")) > 0
+    if not members:
+        islot, imask, icr = ex("int_slot").astype(int), ex("int_mask").view(np.uint32).astype(np.int64), \
+            ex("int_cirank").astype(int)
+        big, mirk = ex("big_irank").astype(int), ex("mem_irank").astype(int)
     v = [float(x) for x in ex("tmpl_vs")]
     D, I, A = len(lint) - 1, len(isl) - 1, int(isl[-1])
     node_of_slot = np.empty(len(vslot), dtype=int)
@@ -46,17 +54,37 @@ def emulate(h, iters):
         for a in range(isl[s], isl[s + 1]):
             sigma[a] = 1.0 / (isl[s + 1] - isl[s])
     R, avg = [0.0] * A, [0.0] * A
-    reach = [[0.0, 0.0] for _ in range(len(edge))]
+    reach = [[0.0, 0.0] for _ in range(lint[D])]
+
+    def child_reach(r, s, a):
+        r = list(r)
+        if s >= 0:
+            lane = 1 if s & P2BIT else 0
+            r[lane] = r[lane] * sigma[(s & MASK) + a]
+        return r
+
     for t in range(1, iters + 1):
         reach[0] = [1.0, 1.0]
-        for d in range(D - 1):  # the launch of depth d pulls depth d + 1
-            for q in range(lint[d + 1], lint[d + 2]):
-                p, s = edge[q]
-                r = list(reach[p])
-                if s >= 0:
-                    lane = 1 if s & P2BIT else 0
-                    r[lane] = r[lane] * sigma[s & MASK]
-                reach[q] = r
+        if members:
+            for d in range(D - 1):  # the launch of depth d pulls depth d + 1
+                for q in range(lint[d + 1], lint[d + 2]):
+                    p, s = edge[q]
+                    reach[q] = child_reach(reach[p], s, 0)
+        else:
+            for q in range(lint[D]):  # every parent pushes to its internal children
+                s, m, c = islot[q], int(imask[q]), icr[q]
+                if m & (1 << 31):  # listed children (-1: terminal)
+                    for a in range(big[c]):
+                        if big[c + 1 + a] >= 0:
+                            reach[big[c + 1 + a]] = child_reach(reach[q], s, a)
+                else:
+                    a = 0
+                    while m:
+                        if m & 1:
+                            reach[c] = child_reach(reach[q], s, a)
+                            c += 1
+                        m >>= 1
+                        a += 1
         for d in range(D - 1, -1, -1):
             if d > 0:  # chance nodes (the root's value is not needed)
                 for i in range(lch[d], lch[d + 1]):
@@ -76,7 +104,7 @@ def emulate(h, iters):
                 sig = sigma[sb:sb + na]
                 racc, macc = [0.0] * na, [0.0] * na
                 for k in range(im[s], im[s + 1]):
-                    r = reach[irk[s, 0] + (k - im[s]) * irk[s, 1]]
+                    r = reach[irk[s, 0] + (k - im[s]) * irk[s, 1]] if members else reach[mirk[k]]
                     cb = ivb[s] + (k - im[s]) * na
                     vh = 0.0
                     for a in range(na):
@@ -101,12 +129,13 @@ def emulate(h, iters):
     return np.array(R), np.array(avg)
 
 
-@pytest.mark.parametrize("tiles", [cfr.TILES_AUTO, cfr.TILES_ON])
+@pytest.mark.parametrize("order,tiles", [(cfr.REACH_MEMBERS, cfr.TILES_AUTO), (cfr.REACH_MEMBERS, cfr.TILES_ON),
+                                         (cfr.REACH_BFS, cfr.TILES_AUTO), (cfr.REACH_SLOTS, cfr.TILES_AUTO)])
 @pytest.mark.parametrize("name", list(GAMES))
-def test_member_layout_reaches_the_oracles_iterates(name, tiles):
+def test_layouts_reach_the_oracles_iterates(name, order, tiles):
     g = GAMES[name]()
     iters = 4
-    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P64, member_tiles=tiles))
+    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P64, reach_order=order, member_tiles=tiles))
     try:
         R, avg = emulate(h, iters)
         spec_of = cfr.cfr_export_array(h, "spec_slot_of").astype(int)
