@@ -196,11 +196,38 @@ def max_over_ranks(dist, seconds: float, device) -> float:
     return float(t.item())
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace collapsed (string
+    literals kept as they are): what the compiler sees of the code."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":  # literal
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            i = text.find("*/", i + 2)
+            i = n if i < 0 else i + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the kernels, the launch code and the compiler (which fixes
+    the layout), comments and whitespace left out: recorded DRAM traffic
+    applies while it matches."""
     h = hashlib.sha1()
     for f in ("kernels.cuh", "launch_impl.cuh", "cfr_api.cu", "compile.cpp", "compiled.h"):
-        with open(os.path.join(ROOT, "paper_2609_11923_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2609_11923_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

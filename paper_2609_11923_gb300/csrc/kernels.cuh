@@ -2,11 +2,14 @@
 //
 // Stage (a), forward reach (eq. (opfwd) on both lanes, eq. (lanes)): reach
 //   is stored for internal nodes only (terminal reach is never read), by
-//   internal rank; each thread takes four internal nodes of depth d and
-//   writes both reach lanes of their internal children. The acting player's
-//   lane is multiplied by sigma(I, a); the other lane and chance edges copy
-//   through (the paper's sentinel multiplier 1 becomes a branch on the node's
-//   slot word, uniform over the node's children).
+//   internal rank. Member order (the default): each thread takes four
+//   internal nodes of depth d + 1, and each reads its parent's reach through
+//   its edge record and writes its own (fwd_pull). Breadth-first and
+//   value-slot orders: each thread takes four internal nodes of depth d and
+//   writes both reach lanes of their internal children (fwd_int4). The
+//   acting player's lane is multiplied by sigma(I, a); the other lane and
+//   chance edges copy through (the paper's sentinel multiplier 1 becomes a
+//   branch on the edge's slot word).
 // Stage (b), terminal utility: the value array holds pi_c(z) u(z) in every
 //   terminal's value slot from bind time on (eq. (template)); no kernel
 //   writes it again, which removes the per-iteration template copy.
@@ -14,8 +17,9 @@
 //   values live in value slots: the children of one set's members form one
 //   contiguous block, and every node writes its own value into its parent's
 //   block. Per depth, chance nodes sum their children's values (one thread
-//   each) and every information set of that depth is handled by one group of
-//   LANES lanes: members' values v(h) = sum_a sigma(I,a) v(h.a), the regret terms
+//   each; a chance root is skipped, nothing reads its value) and every
+//   information set of that depth is handled by one group of LANES lanes,
+//   which reads its members' reach as one run in member order: members' values v(h) = sum_a sigma(I,a) v(h.a), the regret terms
 //   s * pi_{-i}(h) * (v(h.a) - v(h)) and the average terms pi_i(h) sigma(I,a)
 //   are summed over members in a fixed order (no atomics), then
 //   R <- max(R + r, 0) (CFR+), avg += t * m, and sigma^{t+1}(I,.) = RM(R) is
