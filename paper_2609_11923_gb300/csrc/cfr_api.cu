@@ -275,9 +275,11 @@ static int grid_for(int64_t work, int per_block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-// Forward launch of one depth: nb blocks over the internal nodes, then one
-// block per wide chunk; depths with many-child chance nodes take the form
-// that writes those children warp-wide.
+// Forward launch of depth d. Member order: the internal nodes of depth d + 1
+// pull their reach (no launch for the deepest depth). Breadth-first and
+// value-slot orders: nb blocks over depth d's internal nodes push to their
+// children, then one block per wide chunk; depths with many-child chance
+// nodes take the form that writes those children warp-wide.
 template <typename T>
 static int launch_fwd(const cfr_handle *h, int64_t d, cudaStream_t s, const GameView &g, const T *sigma,
                       vec2_t<T> *reach) {
@@ -1004,10 +1006,10 @@ extern "C" int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream) {
 // time whole persistent iterations per lane count. Trial launches change the
 // state, so the call ends with the state reset (as cfr_reset).
 // ------------------------------------------------------------ launch floor
-// The iteration's launch structure with no work in it: the same 2D launches
-// (same grid sizes) of an empty kernel captured in one graph, and one
-// cooperative launch of an empty kernel with the persistent form's grid and
-// its 2D grid barriers per iteration.
+// The iteration's launch structure with no work in it: the same launches
+// (2D, or 2D - 1 in member order; same grid sizes) of an empty kernel
+// captured in one graph, and one cooperative launch of an empty kernel with
+// the persistent form's grid and its 2D grid barriers per iteration.
 static __global__ void empty_level_kernel() {}
 
 static __global__ void __launch_bounds__(kThreads) empty_persistent_kernel(Barrier bar, int n_sync, long long n_iter) {
