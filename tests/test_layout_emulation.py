@@ -29,7 +29,7 @@ GAMES = {
 }
 
 
-def emulate(h, iters):
+def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS):
     ex = lambda k: cfr.cfr_export_array(h, k)
     lint, edge = ex("level_int").astype(int), ex("int_edge").astype(int).reshape(-1, 2)
     isl, im, ivb, li = ex("iset_slot").astype(int), ex("iset_mem").astype(int), ex("iset_vb").astype(int), \
@@ -63,69 +63,87 @@ def emulate(h, iters):
             r[lane] = r[lane] * sigma[(s & MASK) + a]
         return r
 
-    for t in range(1, iters + 1):
+    def forward():
         reach[0] = [1.0, 1.0]
         if members:
             for d in range(D - 1):  # the launch of depth d pulls depth d + 1
                 for q in range(lint[d + 1], lint[d + 2]):
                     p, s = edge[q]
                     reach[q] = child_reach(reach[p], s, 0)
-        else:
-            for q in range(lint[D]):  # every parent pushes to its internal children
-                s, m, c = islot[q], int(imask[q]), icr[q]
-                if m & (1 << 31):  # listed children (-1: terminal)
-                    for a in range(big[c]):
-                        if big[c + 1 + a] >= 0:
-                            reach[big[c + 1 + a]] = child_reach(reach[q], s, a)
-                else:
-                    a = 0
-                    while m:
-                        if m & 1:
-                            reach[c] = child_reach(reach[q], s, a)
-                            c += 1
-                        m >>= 1
-                        a += 1
-        for d in range(D - 1, -1, -1):
-            if d > 0:  # chance nodes (the root's value is not needed)
-                for i in range(lch[d], lch[d + 1]):
-                    acc = 0.0
-                    for c in range(chb[i], chb[i] + chn[i]):
-                        acc = acc + v[c]
-                    v[chs[i]] = acc
-                for i in range(len(wvs)):
-                    if wide_depth[i] == d:
-                        acc = 0.0
-                        for c in range(wvb[i], wvb[i] + wn[i]):
-                            acc = acc + v[c]
-                        v[wvs[i]] = acc
-            for s in range(li[2 * d], li[2 * d + 2]):
-                p2 = s >= li[2 * d + 1]
-                sb, na = isl[s], isl[s + 1] - isl[s]
-                sig = sigma[sb:sb + na]
-                racc, macc = [0.0] * na, [0.0] * na
-                for k in range(im[s], im[s + 1]):
-                    r = reach[irk[s, 0] + (k - im[s]) * irk[s, 1]] if members else reach[mirk[k]]
-                    cb = ivb[s] + (k - im[s]) * na
-                    vh = 0.0
-                    for a in range(na):
-                        vh = vh + sig[a] * v[cb + a]
-                    v[mvs[k]] = vh
-                    po, pw = (r[0], r[1]) if p2 else (r[1], r[0])
-                    f = (-1.0 if p2 else 1.0) * po
-                    for a in range(na):
-                        racc[a] = racc[a] + f * (v[cb + a] - vh)
-                        macc[a] = macc[a] + pw * sig[a]
-                pos = []
-                for a in range(na):
-                    rn = R[sb + a] + racc[a]
-                    R[sb + a] = rn if rn > 0.0 else 0.0
-                    avg[sb + a] = avg[sb + a] + float(t) * macc[a]
-                    pos.append(R[sb + a])
-                tot = 0.0
-                for a in range(na):
-                    tot = tot + pos[a]
-                for a in range(na):
-                    sigma[sb + a] = pos[a] / tot if tot > 0.0 else 1.0 / na
+            return
+        for q in range(lint[D]):  # every parent pushes to its internal children
+            s, m, c = islot[q], int(imask[q]), icr[q]
+            if m & (1 << 31):  # listed children (-1: terminal)
+                for a in range(big[c]):
+                    if big[c + 1 + a] >= 0:
+                        reach[big[c + 1 + a]] = child_reach(reach[q], s, a)
+                continue
+            a = 0
+            while m:
+                if m & 1:
+                    reach[c] = child_reach(reach[q], s, a)
+                    c += 1
+                m >>= 1
+                a += 1
+
+    def chance_sums(d):
+        if d == 0:  # the root's value is not needed
+            return
+        for i in range(lch[d], lch[d + 1]):
+            acc = 0.0
+            for c in range(chb[i], chb[i] + chn[i]):
+                acc = acc + v[c]
+            v[chs[i]] = acc
+        for i in range(len(wvs)):
+            if wide_depth[i] == d:
+                acc = 0.0
+                for c in range(wvb[i], wvb[i] + wn[i]):
+                    acc = acc + v[c]
+                v[wvs[i]] = acc
+
+    def set_pass(s, d, t, upd):
+        p2 = s >= li[2 * d + 1]
+        sb, na = isl[s], isl[s + 1] - isl[s]
+        sig = sigma[sb:sb + na]
+        racc, macc = [0.0] * na, [0.0] * na
+        for k in range(im[s], im[s + 1]):
+            r = reach[irk[s, 0] + (k - im[s]) * irk[s, 1]] if members else reach[mirk[k]]
+            cb = ivb[s] + (k - im[s]) * na
+            vh = 0.0
+            for a in range(na):
+                vh = vh + sig[a] * v[cb + a]
+            v[mvs[k]] = vh
+            po, pw = (r[0], r[1]) if p2 else (r[1], r[0])
+            f = (-1.0 if p2 else 1.0) * po
+            for a in range(na):
+                racc[a] = racc[a] + f * (v[cb + a] - vh)
+                macc[a] = macc[a] + pw * sig[a]
+        if (2 if p2 else 1) not in upd:  # the other player's sets only pass values up
+            return
+        w = float(t) * float(t) if rule == oracle.PCFR_PLUS else float(t)
+        pos = []
+        for a in range(na):
+            rn = R[sb + a] + racc[a]
+            if rule != oracle.CFR:
+                rn = rn if rn > 0.0 else 0.0
+            R[sb + a] = rn
+            avg[sb + a] = avg[sb + a] + w * macc[a]
+            x = rn + racc[a] if rule == oracle.PCFR_PLUS else rn
+            pos.append(x if x > 0.0 else 0.0)
+        tot = 0.0
+        for a in range(na):
+            tot = tot + pos[a]
+        for a in range(na):
+            sigma[sb + a] = pos[a] / tot if tot > 0.0 else 1.0 / na
+
+    halves = [(1, 2)] if order == oracle.SIMULTANEOUS else [(1,), (2,)]  # players whose sets update
+    for t in range(1, iters + 1):
+        for upd in halves:
+            forward()
+            for d in range(D - 1, -1, -1):
+                chance_sums(d)
+                for s in range(li[2 * d], li[2 * d + 2]):
+                    set_pass(s, d, t, upd)
     return np.array(R), np.array(avg)
 
 
@@ -142,6 +160,27 @@ def test_layouts_reach_the_oracles_iterates(name, order, tiles):
     finally:
         cfr.cfr_destroy(h)
     o = oracle.Oracle(g)
+    o.iterate(iters)
+    np.testing.assert_array_equal(R, o.R[spec_of])
+    np.testing.assert_array_equal(avg, o.sbar[spec_of])
+
+
+@pytest.mark.parametrize("rule", [oracle.CFR, oracle.PCFR_PLUS])
+@pytest.mark.parametrize("order", [oracle.SIMULTANEOUS, oracle.ALTERNATING])
+@pytest.mark.parametrize("name", ["tiny", "card_small"])
+def test_update_rules_and_orders_on_the_member_layout(name, rule, order):
+    # the update rules (vanilla CFR without the clamp; PCFR+ matching R + r,
+    # quadratic averaging weight) and alternating halves over the tiled
+    # member layout reach the oracle's iterates bitwise
+    g = GAMES[name]()
+    iters = 4
+    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P64, member_tiles=cfr.TILES_ON))
+    try:
+        R, avg = emulate(h, iters, rule, order)
+        spec_of = cfr.cfr_export_array(h, "spec_slot_of").astype(int)
+    finally:
+        cfr.cfr_destroy(h)
+    o = oracle.Oracle(g, rule=rule, order=order)
     o.iterate(iters)
     np.testing.assert_array_equal(R, o.R[spec_of])
     np.testing.assert_array_equal(avg, o.sbar[spec_of])
