@@ -154,10 +154,87 @@ def cpu_oracle(wl, seconds: float, min_iters: int = 3):
             "sample": "%s (%d edges), %d FP64 iterations in %.1f s, one thread" % (what, spec.n_edges, n, dt)}
 
 
+def run_reference_serving(args):
+    """The oracle solving the serving workload's requests one by one (same stop
+    rule), for about --cpu-seconds of host work: solves/s."""
+    import gamegen as gg
+    import oracle
+
+    t0 = time.perf_counter()
+    done, edges = 0, 0
+    for seed in range(args.requests):
+        sp = gg.endgame(seed)
+        o = oracle.Oracle(sp)
+        it = 0
+        while it < args.max_iters:
+            o.iterate(50)
+            it += 50
+            if o.exploitability() <= 1e-3 * sp.pot:
+                break
+        done, edges = done + 1, edges + sp.n_edges
+        if time.perf_counter() - t0 > args.cpu_seconds:
+            break
+    dt = time.perf_counter() - t0
+    value = done / dt
+    what = "endgame requests seeds 0-%d (%d edges), each solved alone to 1e-3 pot (checked every 50 iterations, " \
+           "cap %d), one thread" % (done - 1, edges, args.max_iters)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": done, "warmup": 0, "ms_per_step": 1e3 * dt / done, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serving: endgame subgames, edges log-uniform in [1e3, 1e6]", "sample": what},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_warmstart(args):
+    """The warm start's yardstick on the oracle: cold-start CFR+ iterations to
+    1e-3 pot on the held-out endgames, for about --cpu-seconds of host work."""
+    import oracle
+    from paper_2609_11923_gb300 import warmstart as ws
+
+    t0 = time.perf_counter()
+    iters = []
+    for sp in ws.iter_endgame_family(range(20000, 20000 + args.heldout), 1e3, 1e6):  # the bench's held-out games
+        o = oracle.Oracle(sp)
+        it = 0
+        while it < args.max_iters:
+            o.iterate(50)
+            it += 50
+            if o.exploitability() <= 1e-3 * sp.pot:
+                break
+        iters.append(it)
+        if time.perf_counter() - t0 > args.cpu_seconds:
+            break
+    dt = time.perf_counter() - t0
+    value = sum(iters) / len(iters)
+    what = "held-out endgames seeds 20000-%d, cold-start CFR+ to 1e-3 pot (checked every 50 iterations, cap %d), " \
+           "one thread, %.1f s" % (20000 + len(iters) - 1, args.max_iters, dt)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iterations to 1e-3 pot (mean, cold start)",
+        "n_gpus": args.gpus, "steps": len(iters), "warmup": 0, "ms_per_step": 1e3 * dt / len(iters),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "warm start yardstick: cold-start CFR+ on held-out endgames", "sample": what},
+        "cpu_baseline": {"value": value, "unit": "iterations to 1e-3 pot (mean, cold start)", "cores": 1,
+                         "kind": "oracle", "sample": what},
+        "e2e": {"value": value, "unit": "iterations to 1e-3 pot (mean, cold start)", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "serving":
+        return run_reference_serving(args)
+    if args.workload == "warmstart":
+        return run_reference_warmstart(args)
     import oracle
 
     wl = workloads()[args.workload]

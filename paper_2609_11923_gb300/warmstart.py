@@ -310,12 +310,20 @@ def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iter
     return done, finished, wall
 
 
-def endgame_family(seeds, lo: float = 1e3, hi: float = 1e6):
-    """Endgames with edge targets log-uniform in [lo, hi] (seeded per list)."""
+def iter_endgame_family(seeds, lo: float = 1e3, hi: float = 1e6):
+    """Endgames with edge targets log-uniform in [lo, hi] (seeded per list),
+    generated one at a time."""
     import gamegen as gg
 
+    seeds = list(seeds)
     rng = np.random.default_rng(int(seeds[0]) if len(seeds) else 0)
-    return [gg.endgame(int(s), int(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for s in seeds]
+    for s in seeds:
+        yield gg.endgame(int(s), int(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+
+
+def endgame_family(seeds, lo: float = 1e3, hi: float = 1e6):
+    """Endgames with edge targets log-uniform in [lo, hi] (seeded per list)."""
+    return list(iter_endgame_family(seeds, lo, hi))
 
 
 def choose_kappa(net: MLP, specs, kappas=(4.0, 8.0, 16.0), max_iters: int = 3000):

@@ -79,3 +79,33 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     assert d["steps"] == 3 and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_serving_reports_oracle_solves_per_second(monkeypatch, capsys):
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "serving", "--requests", "2",
+                                      "--max-iters", "100", "--cpu-seconds", "30"])
+    assert bench.main() == 0
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["steps"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_warmstart_reports_oracle_cold_iterations(monkeypatch, capsys):
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "warmstart", "--heldout", "1",
+                                      "--max-iters", "100", "--cpu-seconds", "30"])
+    assert bench.main() == 0
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["steps"] == 1 and 50 <= d["value"] <= 100
+    assert d["higher_is_better"] is False and d["cpu_baseline"]["kind"] == "oracle"
