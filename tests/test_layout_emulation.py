@@ -184,3 +184,24 @@ def test_update_rules_and_orders_on_the_member_layout(name, rule, order):
     o.iterate(iters)
     np.testing.assert_array_equal(R, o.R[spec_of])
     np.testing.assert_array_equal(avg, o.sbar[spec_of])
+
+
+@pytest.mark.parametrize("seed,depth,p_chance,max_group", [(7, 7, 0.1, 1), (8, 8, 0.4, 4), (9, 7, 0.6, 40),
+                                                           (10, 9, 0.2, 2), (11, 6, 0.0, 8)])
+@pytest.mark.parametrize("order,tiles", [(cfr.REACH_MEMBERS, cfr.TILES_ON), (cfr.REACH_MEMBERS, cfr.TILES_OFF),
+                                         (cfr.REACH_BFS, cfr.TILES_AUTO)])
+def test_random_shapes_reach_the_oracles_iterates(seed, depth, p_chance, max_group, order, tiles):
+    # random perfect-recall trees of several shapes (single-member sets tile
+    # everywhere; chance-heavy trees put chance nodes between sets)
+    g = gg.random_tree(seed, depth=depth, p_chance=p_chance, max_group=max_group)
+    iters = 3
+    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P64, reach_order=order, member_tiles=tiles))
+    try:
+        R, avg = emulate(h, iters)
+        spec_of = cfr.cfr_export_array(h, "spec_slot_of").astype(int)
+    finally:
+        cfr.cfr_destroy(h)
+    o = oracle.Oracle(g)
+    o.iterate(iters)
+    np.testing.assert_array_equal(R, o.R[spec_of])
+    np.testing.assert_array_equal(avg, o.sbar[spec_of])
