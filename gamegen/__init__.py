@@ -213,6 +213,79 @@ def endgame(seed: int, target_edges: int = 0) -> GameSpec:
     return _wrap(_load().gg_endgame(seed, target_edges))
 
 
+def leduc() -> GameSpec:
+    """Leduc poker: six cards (three ranks, two suits), ante 1 each, one
+    private card each (dealt to player 1, then to player 2), a betting round
+    with bets of 2, a public card, a betting round with bets of 4; at most
+    two bets per round, player 1 acts first in both; folding only facing a
+    bet. A private card pairing the public card wins, else the higher rank;
+    equal ranks split. Information sets hold the acting player's own card,
+    the public card and the betting so far: 936 sets, 1,093 sequences per
+    player, 9,457 nodes."""
+    n_cards, rank = 6, [0, 0, 1, 1, 2, 2]
+    nodes, isets, index = [], [], {}
+
+    def new_node():
+        nodes.append(None)
+        return len(nodes) - 1
+
+    def info_set(key, player, n_act):
+        if key not in index:
+            index[key] = len(isets)
+            isets.append((player, n_act))
+        return index[key]
+
+    def showdown(c1, c2, pub, put):
+        s1 = (int(rank[c1] == rank[pub]), rank[c1])
+        s2 = (int(rank[c2] == rank[pub]), rank[c2])
+        return float(put[1]) if s1 > s2 else (-float(put[0]) if s2 > s1 else 0.0)
+
+    def bet_round(c1, c2, pub, rnd, hist, put, me, bets, checks):
+        h = new_node()
+        owe = put[1 - me] - put[me]
+        acts = (["f"] if owe > 0 else []) + ["c"] + (["r"] if bets < 2 else [])
+        key = (me, c1 if me == 0 else c2, pub, hist)
+        kids = []
+        for a in acts:
+            if a == "f":  # the folder loses what it put in
+                kids.append(len(nodes))
+                nodes.append((TERMINAL, -1, [], None, -float(put[0]) if me == 0 else float(put[1])))
+            elif a == "c":
+                now = list(put)
+                now[me] = put[1 - me]
+                if owe > 0 or checks == 1:  # the round is over
+                    if rnd == 0:
+                        kids.append(public_card(c1, c2, hist + "c/", now))
+                    else:
+                        kids.append(len(nodes))
+                        nodes.append((TERMINAL, -1, [], None, showdown(c1, c2, pub, now)))
+                else:
+                    kids.append(bet_round(c1, c2, pub, rnd, hist + "c", now, 1 - me, bets, checks + 1))
+            else:
+                now = list(put)
+                now[me] = put[1 - me] + (2 if rnd == 0 else 4)
+                kids.append(bet_round(c1, c2, pub, rnd, hist + "r", now, 1 - me, bets + 1, 0))
+        nodes[h] = (P1 if me == 0 else P2, info_set(key, me, len(acts)), kids, None, 0.0)
+        return h
+
+    def public_card(c1, c2, hist, put):
+        h = new_node()
+        left = [c for c in range(n_cards) if c not in (c1, c2)]
+        kids = [bet_round(c1, c2, p, 1, hist, put, 0, 0, 0) for p in left]
+        nodes[h] = (CHANCE, -1, kids, [1.0 / len(left)] * len(left), 0.0)
+        return h
+
+    root = new_node()
+    firsts = []
+    for c1 in range(n_cards):
+        h = new_node()
+        seconds = [bet_round(c1, c2, -1, 0, "", [1, 1], 0, 0, 0) for c2 in range(n_cards) if c2 != c1]
+        nodes[h] = (CHANCE, -1, seconds, [1.0 / (n_cards - 1)] * (n_cards - 1), 0.0)
+        firsts.append(h)
+    nodes[root] = (CHANCE, -1, firsts, [1.0 / n_cards] * n_cards, 0.0)
+    return from_lists(nodes, isets, pot=2.0)
+
+
 def rand_u64(seed: int, stream: int, i: int) -> int:
     """The counter-based SplitMix64 word every generator draws from."""
     return int(_load().gg_rand(seed, stream, i))

@@ -18,6 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 GAMES = {
     "kuhn": lambda: gg.kuhn(),
+    "leduc": lambda: gg.leduc(),
     "tiny": lambda: gg.tiny_card(),
     "rt6": lambda: gg.random_tree(1, depth=6),
     "rt8": lambda: gg.random_tree(2, depth=8, max_group=16),

@@ -21,6 +21,7 @@ MASK = P2BIT - 1
 
 GAMES = {
     "kuhn": lambda: gg.kuhn(),
+    "leduc": lambda: gg.leduc(),
     "tiny": lambda: gg.tiny_card(),
     "rt6": lambda: gg.random_tree(1, depth=6),
     "card_small": lambda: gg.large_card(3, 2, 1, 1),
