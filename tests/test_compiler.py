@@ -185,6 +185,15 @@ def test_library_exports_every_declared_symbol():
     assert names <= set(cfr.EXPORTED)
 
 
+def test_library_exports_every_mlp_symbol():
+    header = open(os.path.join(ROOT, "include", "mlp.h")).read()
+    names = set(re.findall(r"^\s*(?:int|void)\s+(mlp_\w+)\s*\(", header, re.M))
+    assert {"mlp_gemm", "mlp_softmax_xent", "mlp_relu_grad", "mlp_colsum", "mlp_adam", "mlp_to_bf16"} <= names
+    lib = ctypes.CDLL(cfr.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
 def with_root_chance(g, p):
     """The same game with the root's outcome probabilities replaced."""
     cp = np.array(g.chance_prob, dtype=np.float64, copy=True)
