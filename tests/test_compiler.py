@@ -312,3 +312,28 @@ def test_member_order_layout_properties(name, tiles):
                 assert len({im[j + 1] - im[j] for j in group}) == 1
     finally:
         cfr.cfr_destroy(h)
+
+
+def test_binding_constants_mirror_the_header():
+    # every enumerator of include/cfr.h has the same value in the Python
+    # binding (options, node kinds, status codes), and the options struct has
+    # the header's fields in the header's order
+    header = open(os.path.join(ROOT, "include", "cfr.h")).read()
+    header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", header, re.S):
+        for name, val in re.findall(r"(CFR_\w+)\s*=\s*(-?\d+)", body):
+            values[name] = int(val)
+    py = {"CFR_P64": cfr.P64, "CFR_P32": cfr.P32, "CFR_OK": cfr.CFR_OK,
+          "CFR_DEBUG_BARRIER_MISSING_ARRIVALS": cfr.DEBUG_BARRIER_MISSING_ARRIVALS}
+    for prefix in ("EXEC_", "RULE_", "ORDER_", "REACH_", "TILES_"):
+        py.update({"CFR_" + n: getattr(cfr, n) for n in dir(cfr) if n.startswith(prefix)})
+    py.update({name: code for code, name in cfr.ERRORS.items()})
+    kinds = {"CFR_TERMINAL": gg.TERMINAL, "CFR_CHANCE": gg.CHANCE, "CFR_PLAYER1": gg.P1, "CFR_PLAYER2": gg.P2}
+    py.update(kinds)
+    assert set(values) == set(py), set(values) ^ set(py)
+    for name, v in values.items():
+        assert py[name] == v, name
+    struct = re.search(r"typedef struct cfr_options \{(.*?)\} cfr_options;", header, re.S).group(1)
+    fields = re.findall(r"\b(?:int|int64_t)\s+(\w+);", struct)
+    assert fields == [f[0] for f in cfr.Options._fields_]
