@@ -334,6 +334,13 @@ def test_binding_constants_mirror_the_header():
     assert set(values) == set(py), set(values) ^ set(py)
     for name, v in values.items():
         assert py[name] == v, name
-    struct = re.search(r"typedef struct cfr_options \{(.*?)\} cfr_options;", header, re.S).group(1)
-    fields = re.findall(r"\b(?:int|int64_t)\s+(\w+);", struct)
-    assert fields == [f[0] for f in cfr.Options._fields_]
+    for cname, pyclass in (("cfr_options", cfr.Options), ("cfr_counts", cfr.Counts), ("cfr_game_spec", cfr.GameSpecC)):
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (cname, cname), header, re.S).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:  # "type a, b" or "const type *a"
+                names = decl.split(None, 1)[1] if not decl.startswith("const") else decl.split(None, 2)[2]
+                fields += [n.strip(" *") for n in names.split(",")]
+        assert fields == [f[0] for f in pyclass._fields_], cname
+        assert ctypes.sizeof(pyclass) >= 4 * len(fields)
