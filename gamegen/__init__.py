@@ -181,6 +181,23 @@ def _wrap(ptr) -> GameSpec:
     )
 
 
+def spec_digest(g: GameSpec) -> str:
+    """SHA-256 of a game spec's arrays (dtype and bytes, in field order) and
+    its pot: the key under which stored expected values of a game are kept."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name, dt in (("kind", np.int8), ("infoset", np.int32), ("child_begin", np.int64), ("child", np.int32),
+                     ("chance_prob", np.float64), ("payoff", np.float64), ("iset_player", np.int8),
+                     ("iset_nact", np.int32)):
+        a = np.ascontiguousarray(getattr(g, name), dtype=dt)
+        h.update(name.encode())
+        h.update(str(a.shape[0]).encode())
+        h.update(memoryview(a).cast("B"))
+    h.update(repr(float(g.pot)).encode())
+    return h.hexdigest()
+
+
 def tiny_card(ranks: int = 5, cap: int = 2) -> GameSpec:
     """One-card poker (5 ranks, cap 2 bets: N=301, 30 infosets, 70 slots)."""
     return _wrap(_load().gg_tiny_card(ranks, cap))

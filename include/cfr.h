@@ -41,7 +41,7 @@ enum {
   CFR_ERR_ARG = -1,          /* null pointer, bad size or bad option */
   CFR_ERR_INVALID_SPEC = -2, /* the game fails a structural check (Algorithm "Compile", step 1) */
   CFR_ERR_NOT_BOUND = -3,    /* the call needs device memory: call cfr_bind first */
-  CFR_ERR_REBOUND = -4,      /* a captured graph refers to another arena */
+  CFR_ERR_REBOUND = -4,      /* reserved: cfr_bind drops a captured graph, so no call returns it */
   CFR_ERR_ARENA_SMALL = -5,  /* the arena is smaller than cfr_plan reported */
   CFR_ERR_TIMEOUT = -6,      /* a grid barrier of the persistent kernel gave up waiting */
   CFR_ERR_DEVICE = -7,       /* a CUDA call failed (message in cfr_last_error) */
@@ -93,7 +93,11 @@ typedef struct cfr_options {
   int rule;
   int lanes_per_set;   /* 0 = by mean set size (see cfr_autotune); else 1, 2, 4, 8, 16 or 32 lanes per set,
                           or 256 = one thread block per set in the per-level kernels (sets of at most 8
-                          actions; the persistent kernel then uses 32) */
+                          actions; the persistent kernel then uses 32), or 512 = the streaming backward
+                          (CFR_P32 in member order, sets of at most 8 actions): each depth's sets go in
+                          chunks whose reach, child values, member slots, set descriptors, strategy,
+                          regrets and averages are staged in shared memory by bulk asynchronous copies
+                          (depths where a group of sets exceeds one 48 KiB stage keep the default) */
   int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
   int64_t barrier_spin_limit; /* 0 = default; polls before a grid barrier reports CFR_ERR_TIMEOUT */
   /* CFR_ORDER_SIMULTANEOUS: both players' regrets from one strategy profile;
@@ -130,7 +134,9 @@ typedef struct cfr_counts {
   int64_t n_internal, n_decision, n_chance, n_terminal;
   int64_t depth_blocks;       /* D: number of distinct parent depths (eq. (blocks)) */
   int64_t max_actions;
-  int64_t algo_bytes_per_iter; /* algorithmic HBM bytes of one iteration (design notes) */
+  int64_t algo_bytes_per_iter; /* algorithmic HBM bytes of one iteration: every array element the
+                                  layout needs, touched once (the per-launch sums of cfr_level_bytes;
+                                  twice that under alternating updates) */
   int64_t upload_bytes;       /* host-to-device bytes cfr_bind copies */
   int64_t iteration;          /* t: iterations completed since bind/reset */
   int exec_form;              /* resolved execution form */
@@ -146,23 +152,47 @@ typedef struct cfr_handle cfr_handle;
  * opt may be NULL (P32, AUTO, CFR+). On success *out owns the result. */
 int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cfr_handle **out);
 
-/* Sizes of the compiled game. */
+/* Sizes of the compiled game in the paper's counts (Section 4.1 and
+ * Algorithm "Compile", steps 2-5: nodes, edges, information sets, slots, and
+ * D, the number of depth blocks of eq. (blocks)), the iteration counter t
+ * (Section 4.3) and the resolved options. Host only; never fails on a valid
+ * handle. */
 int cfr_get_counts(const cfr_handle *h, cfr_counts *out);
 
-/* Device bytes one solver needs (arrays + state + evaluation scratch). */
+/* The memory plan (Algorithm "Compile", step 8, and the memory-plan table
+ * of Appendix H): the device bytes one solver needs, sized from the game's
+ * counts and the precision: the compiled index arrays, the values template,
+ * the per-iteration buffers (reach lanes, values, strategy), the FP64
+ * accumulators (regrets, average-strategy sum) and the best-response
+ * scratch, each 256-byte aligned. Host only. Unlike the paper, the plan is
+ * binding, not an indicator: cfr_bind refuses a smaller arena. */
 int cfr_plan(const cfr_handle *h, size_t *device_bytes);
 
-/* Binds the caller's device arena (>= cfr_plan bytes, 256-byte aligned),
- * uploads the compiled arrays and initialises the state (R = 0, average = 0,
- * uniform strategy, t = 0). Synchronises `stream`. Binding again re-uploads
- * and drops any captured graph. */
+/* Binds the caller's device arena (>= cfr_plan bytes, 256-byte aligned;
+ * else CFR_ERR_ARENA_SMALL or CFR_ERR_ARG) and lays the memory plan out in it
+ * (the buffers of the memory-plan table, Appendix H), uploads the compiled
+ * arrays and the values template, and initialises the state (R = 0,
+ * average = 0, uniform strategy, t = 0). Synchronises `stream`. Section 4.3
+ * refuses to replay a captured graph whose buffers moved; here binding
+ * again re-uploads and drops any captured graph, so the next cfr_iterate
+ * captures against the new arena and a stale replay cannot happen. */
 int cfr_bind(cfr_handle *h, void *device_arena, size_t bytes, void *stream);
 
-/* Runs n CFR+ iterations (t+1 .. t+n), asynchronously on `stream`.
- * n = 0 is a no-op. Split calls give bitwise the same state as one call. */
+/* Runs n iterations t+1 .. t+n of the compiled iteration (Algorithm 1:
+ * forward reach, terminal values, backward values with the fused regret and
+ * average update, regret matching), asynchronously on `stream`, in the
+ * execution form the options chose: per-level launches, one CUDA graph of an
+ * iteration replayed n times (Section 4.3; captured on the first call), or
+ * one persistent kernel. The weight w_t of the average comes from a device
+ * counter the iteration itself advances (Section 4.3), so n = 0 is a no-op
+ * and split calls give bitwise the same state as one call. CFR_ERR_NOT_BOUND
+ * before cfr_bind. If capturing the graph fails, the call warns once on
+ * stderr and runs the same kernels in the same order as per-level launches
+ * from then on (Section 4.3): the results are bitwise the same. */
 int cfr_iterate(cfr_handle *h, int64_t n, void *stream);
 
-/* Waits for `stream` and reports a device-side failure of earlier calls:
+/* Waits for `stream` (the synchronisation point of Section 4.3's
+ * asynchronous replay) and reports a device-side failure of earlier calls:
  * CFR_ERR_TIMEOUT if a grid barrier of the persistent kernel gave up (the
  * state is then undefined until cfr_reset). */
 int cfr_synchronize(cfr_handle *h, void *stream);
@@ -183,13 +213,18 @@ int cfr_current_strategy(cfr_handle *h, double *out, int out_on_device, void *st
  * Synchronises `stream`. */
 int cfr_exploitability(cfr_handle *h, double *out_expl, double *out_br, void *stream);
 
-/* Zeroes regrets, averages and t and restores the uniform strategy, in place
- * (a captured graph stays valid). Asynchronous on `stream`. */
+/* reset() of Appendix H ("Mutable and immutable fields") and the lifecycle
+ * table: zeroes regrets, averages and t and restores the uniform strategy, in
+ * place; no buffer moves, so a captured graph stays valid and the next
+ * cfr_iterate runs from iteration one. Asynchronous on `stream`.
+ * CFR_ERR_NOT_BOUND before cfr_bind. */
 int cfr_reset(cfr_handle *h, void *stream);
 
-/* Rewrites the terminal payoffs (payoff[N] in spec node order, host) into
- * the values template from the retained chance products; no recompilation.
- * Synchronises `stream`. */
+/* set_payoffs of Appendix H ("Mutable and immutable fields") and the
+ * lifecycle table: rewrites the terminal payoffs (payoff[N] in spec node
+ * order, host; finite at terminals, else CFR_ERR_ARG) into the values
+ * template (eq. (template)) from the retained chance products; no
+ * recompilation. Solver state is kept. Synchronises `stream`. */
 int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream);
 
 /* Rewrites the root's chance distribution, the other input Appendix H
@@ -206,14 +241,20 @@ int cfr_set_payoffs(cfr_handle *h, const double *payoff, void *stream);
  * root. */
 int cfr_set_root_chance(cfr_handle *h, const double *prob, int64_t n, void *stream);
 
-/* Copies the solver state out / in, host arrays in spec slot order:
- * R[A] and avg[A] (un-normalised strategy sums) as doubles, and t. Under
+/* Copies the solver state out / in (the accumulators of the memory-plan
+ * table and the iteration counter that Section 4.3 carries across split
+ * solver calls), host arrays in spec slot order: R[A] and avg[A]
+ * (un-normalised strategy sums) as doubles, and t. Both synchronise
+ * `stream`; set_state recomputes the current strategy by regret matching
+ * (eq. (rm)). Under
  * PCFR+ the prediction is not part of the state: cfr_set_state restarts it
  * at zero (the next strategy is regret matching of R alone). */
 int cfr_get_state(cfr_handle *h, double *R, double *avg, int64_t *t, void *stream);
 int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, void *stream);
 
-/* Host copies of the compiled index arrays, for bit-exact checks.
+/* Host copies of the compiled index arrays that index emission produced
+ * (Algorithm "Compile", step 7, in this library's layout; Section 4.1), for
+ * bit-exact checks against an independent flattener. Host only.
  * which: 0 child_begin[N+1], 1 node_slot[N], 2 level_begin[D+2],
  * 3 iset_slot[I+1], 4 iset_mem[I+1], 5 mem_node[N_dec], 6 chance_list
  * (chance nodes with at most 1024 children), 7 level_chance[D+1],
@@ -233,7 +274,16 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * per internal node in rank order, its parent's rank and the slot word of
  * its edge, -1 under a chance node; the root's pair is -1, -1), 30
  * iset_rank[2 I] (member order: rank of each set's first member and the
- * stride of its members' ranks, 4 inside a tile), 31 level_tiled[D].
+ * stride of its members' ranks, 4 inside a tile), 31 level_tiled[D],
+ * 32 set descriptors of the streaming FP32 backward [8 I] (per set: first
+ * slot, actions, first member, members, first child value slot, reach rank
+ * of member 0, rank stride, flags: bits 0-2 the sets of the group it starts
+ * (1, 4 for a tile, 0 inside one), bit 8 player 2), 33 its chunks [16 per
+ * chunk: sets I0, I1, then the staged element ranges (start, count) of
+ * reach ranks, child value slots, members and slots, widened to 16-byte
+ * boundaries; 6 unused], 34 first chunk of each depth [D+1], 35 per depth
+ * whether it can stream [D] (all empty unless FP32 in member order with sets
+ * of at most 8 actions).
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);
@@ -241,7 +291,8 @@ int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity
 /* Autotuner for the thread-to-work mapping: for every depth it times the
  * backward launch with each supported number of lanes per information set
  * (1, 2, 4, 8, 16, 32, and 256 = one block per set when sets have at most 8
- * actions; `reps` launches each) and keeps the fastest; in the
+ * actions, and 512 = the streaming backward at depths that can stream;
+ * `reps` launches each) and keeps the fastest; in the
  * persistent form it also times whole persistent iterations per lane count.
  * Trial launches overwrite the solver state, so the call ends by resetting it
  * (as cfr_reset) and dropping a captured graph. The chosen counts are
@@ -301,8 +352,18 @@ int cfr_batch_exploitability(cfr_handle *const *handles, int n, double *out, voi
 
 /* Algorithmic device bytes of depth level d (0 <= d < D) for the forward
  * kernel and the backward kernel of one iteration: every array element the
- * layout needs, touched once (the design notes list the per-element terms).
- * Host only. */
+ * layout needs, touched once. With T the bytes of the compute type (4 or 8)
+ * and member-order reach, the launch of depth d < D-1 that fills depth d+1
+ * moves 8 per internal child (edge record) + 2T per internal parent and per
+ * internal child (reach read and written) + T per slot of depth d (sigma);
+ * the backward of depth d moves 12 per set (slot and member ranges, value
+ * block) + (32 + 2T) per slot (R and the average read and written in FP64,
+ * sigma read and written) + (4 + 3T) per member (value slot, reach lanes,
+ * value written) + (12 + T) per chance node + T per child value read. The
+ * other reach orders read an internal rank per member (4 more) and push
+ * records (12 per internal parent, 4 per long child list entry). Host only.
+ * The paper counts the same kind of bytes-moved lower bound (Appendix
+ * "Kernel-Level Profile"). */
 int cfr_level_bytes(const cfr_handle *h, int level, int64_t *fwd_bytes, int64_t *bwd_bytes);
 
 /* Measurement: runs ONE iteration (t -> t+1) as per-level launches on
@@ -313,11 +374,14 @@ int cfr_level_bytes(const cfr_handle *h, int level, int64_t *fwd_bytes, int64_t 
 int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *stream);
 
 /* Allocation-free variant of cfr_iterate, for callers that cannot allocate
- * device memory when they run iterations (for example code running during a
- * CUDA graph capture, or a serving loop whose memory is fixed at start-up).
- * The paper has no counterpart to this entry point.
+ * device memory while they run iterations: a serving loop whose device
+ * memory is carved out once at start-up (an allocation inside the loop could
+ * fail or stall the other solves sharing the GPU), or a host program that
+ * embeds the library without owning the device allocator. The paper has no
+ * counterpart to this entry point.
  * It runs n iterations with the persistent kernel, exactly as the
- * CFR_EXEC_PERSISTENT form does, but takes the per-iteration scratch (reach
+ * CFR_EXEC_PERSISTENT form does (same grid, same lane groups: the state it
+ * leaves is bitwise that form's), but takes the per-iteration scratch (reach
  * lanes, node values, wide-node partial sums, grid-barrier words) from one
  * static 12 MiB device array compiled into the library (held on every GPU
  * that loads the library, until the process exits) instead of the arena.
@@ -325,26 +389,41 @@ int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *s
  * compiled game and the solver state (regrets, average, strategy, t).
  * No cudaMalloc, cudaFree or other allocating call is made. The first call on
  * a device resolves the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current and keeps it for the life of the process; make that
+ * first call before any stream capture. The kept address is void after a
+ * cudaDeviceReset (or any teardown of the device's primary context): do not
+ * call this entry point after one.
  * Limits: games whose scratch exceeds the array are rejected with
  * CFR_ERR_ARG; the scratch is both reach lanes of every internal node and
  * every node's value, at most 24 bytes per node in FP64 and 12 in FP32
- * (about 524,000 and 1,048,000 nodes for any tree shape). Every call re-initialises the part of the array it uses.
+ * (about 524,000 and 1,048,000 nodes for any tree shape). Every call
+ * re-initialises the part of the array it uses (values from the template,
+ * root reach, counters and barrier words at zero).
  * All calls share the one array, so calls that overlap on the GPU (other
  * streams, other threads, other handles) race: serialise them. Synchronises
  * `stream`; a barrier timeout returns CFR_ERR_TIMEOUT. */
 int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream);
 
-/* Fault-injection hook for tests (no effect unless set).
+/* Fault-injection hooks for tests (no effect unless set; host-side only).
  * CFR_DEBUG_BARRIER_MISSING_ARRIVALS = k: the persistent kernel's grid
  * barriers wait for k blocks that do not exist, so every wait runs into its
  * spin limit (cfr_options.barrier_spin_limit) and the launch ends with
  * CFR_ERR_TIMEOUT reported by cfr_synchronize. Nothing faults or hangs: each
- * block stops after its bounded wait. */
-enum { CFR_DEBUG_BARRIER_MISSING_ARRIVALS = 1 };
+ * block stops after its bounded wait.
+ * CFR_DEBUG_FAIL_GRAPH_CAPTURE = 1: the next graph capture of the graph form
+ * is treated as refused after it ends (the captured graph is discarded), so
+ * cfr_iterate takes the capture-failure path of Section 4.3: one warning on
+ * stderr per handle, then per-level launches of the same kernels in the same
+ * order. */
+enum { CFR_DEBUG_BARRIER_MISSING_ARRIVALS = 1, CFR_DEBUG_FAIL_GRAPH_CAPTURE = 2 };
 int cfr_debug_set(cfr_handle *h, int key, int64_t value);
 
+/* Message of the calling thread's last failure (thread-local, valid until
+ * that thread's next failing call). No counterpart in the paper. */
 const char *cfr_last_error(void);
+/* Releases the handle's host memory, its captured graph and its page-locked
+ * ranges; the caller's arena is not freed. NULL is ignored. No counterpart in
+ * the paper. */
 void cfr_destroy(cfr_handle *h);
 
 #ifdef __cplusplus

@@ -22,7 +22,8 @@ ERRORS = {
     -5: "CFR_ERR_ARENA_SMALL", -6: "CFR_ERR_TIMEOUT", -7: "CFR_ERR_DEVICE", -8: "CFR_ERR_HOST_MEMORY",
     -9: "CFR_ERR_UNSUPPORTED",
 }
-CFR_ERR_TIMEOUT = -6
+CFR_ERR_ARG, CFR_ERR_INVALID_SPEC, CFR_ERR_NOT_BOUND, CFR_ERR_REBOUND = -1, -2, -3, -4
+CFR_ERR_ARENA_SMALL, CFR_ERR_TIMEOUT, CFR_ERR_DEVICE, CFR_ERR_HOST_MEMORY, CFR_ERR_UNSUPPORTED = -5, -6, -7, -8, -9
 P64, P32 = 0, 1
 EXEC_AUTO, EXEC_LEVELS, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2, 3
 RULE_CFR_PLUS, RULE_CFR, RULE_PCFR_PLUS = 0, 1, 2
@@ -30,12 +31,15 @@ ORDER_SIMULTANEOUS, ORDER_ALTERNATING = 0, 1
 REACH_MEMBERS, REACH_BFS, REACH_SLOTS = 0, 1, 2
 TILES_AUTO, TILES_OFF, TILES_ON = 0, 1, 2
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
+DEBUG_FAIL_GRAPH_CAPTURE = 2
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
           "spec_slot_of": 11, "level_lanes": 12, "int_slot": 13, "int_mask": 14, "int_cirank": 15,
           "big_irank": 16, "mem_irank": 17, "level_int": 18, "vslot": 19, "iset_vb": 20, "mem_vs": 21,
           "ch_vb": 22, "ch_nch": 23, "ch_vs": 24, "wide_vb": 25, "wide_nch": 26, "wide_vs": 27, "tmpl_vs": 28,
-          "int_edge": 29, "iset_rank": 30, "level_tiled": 31}
+          "int_edge": 29, "iset_rank": 30, "level_tiled": 31, "set_info": 32, "stream_chunks": 33, "stream_c0": 34,
+          "stream_ok": 35}
+STREAM_LANES = 512  # lanes_per_set code of the streaming FP32 backward
 
 
 class CfrError(RuntimeError):

@@ -62,17 +62,25 @@ struct cfr_handle {
   Buf b_wide_vb, b_wide_nch, b_wide_vs, b_wide_chunk, b_wide_part, b_wide_cnt;
   Buf b_int_slot, b_int_mask, b_int_cirank, b_big_irank, b_int_edge, b_iset_rank, b_mem_irank, b_wide_irank;
   Buf b_reach, b_v, b_sigma, b_R, b_avg, b_tmpl, b_sbs, b_reach2, b_vb, b_vavg, b_t, b_bar, b_err, b_out;
+  // streaming backward (FP32, member order): set descriptors, chunks, and per
+  // depth the chunk range (stream_c0[d] .. stream_c0[d+1]) and whether the
+  // depth can stream (every group fits one stage)
+  std::vector<SetInfo> set_info;
+  std::vector<StreamChunk> stream_chunks;
+  std::vector<int32_t> stream_c0, stream_ok;
+  Buf b_set_info, b_stream_chunks;
   size_t plan_bytes = 0;
   char *arena = nullptr;
   bool bound = false;
   std::vector<void *> pinned;  // host ranges page-locked by cfr_pin_host
   // graph form
   cudaGraphExec_t gexec = nullptr;
-  char *graph_arena = nullptr;
   cudaStream_t cap_stream = nullptr;
   // persistent form
   int persist_grid = 0;
   int test_missing_arrivals = 0;  // fault-injection hook: barriers wait for blocks that never come
+  int test_fail_capture = 0;      // test hook: treat the next graph capture as failed
+  bool capture_warned = false;    // the capture-failure warning is printed once per handle
   int64_t iteration_host = 0;  // iterations enqueued since bind/reset (bookkeeping)
   template <typename X> X *p(const Buf &b) const { return reinterpret_cast<X *>(arena + b.off); }
 };
@@ -127,7 +135,91 @@ static void plan(cfr_handle *h) {
   take(h->b_bar, 16);
   take(h->b_err, 16);
   take(h->b_out, 8 * std::max<int64_t>(c.A, 2) + 64);
+  take(h->b_set_info, sizeof(SetInfo) * h->set_info.size());
+  take(h->b_stream_chunks, sizeof(StreamChunk) * h->stream_chunks.size());
   h->plan_bytes = cur;
+}
+
+// Set descriptors and chunks of the streaming backward (FP32, member order,
+// sets of at most 8 actions). A group is a tile of kTileSets sets (members'
+// reach interleaved) or one untiled set; a chunk is a run of whole groups of
+// one depth whose staged bytes (stream_layout) fit one stage. A depth whose
+// largest group does not fit cannot stream.
+static void build_stream(cfr_handle *h) {
+  const Compiled &c = h->c;
+  h->set_info.clear();
+  h->stream_chunks.clear();
+  h->stream_c0.assign(c.D + 1, 0);
+  h->stream_ok.assign(c.D, 0);
+  if (h->precision != CFR_P32 || c.int_edge.empty() || c.max_act > 8 || c.I == 0) return;
+  h->set_info.resize(c.I);
+  for (int64_t d = 0; d < c.D; ++d) {
+    const int32_t p2 = c.level_iset[2 * d + 1];
+    for (int32_t I = c.level_iset[2 * d]; I < c.level_iset[2 * d + 2];) {
+      const bool tile = c.iset_rank[2 * I + 1] == kTileSets;
+      const int32_t G = tile ? kTileSets : 1;
+      for (int32_t j = 0; j < G; ++j) {
+        SetInfo &si = h->set_info[I + j];
+        si.sb = c.iset_slot[I + j];
+        si.na = c.iset_slot[I + j + 1] - si.sb;
+        si.m0 = c.iset_mem[I + j];
+        si.nm = c.iset_mem[I + j + 1] - si.m0;
+        si.vb = c.iset_vb[I + j];
+        si.rank0 = c.iset_rank[2 * (I + j)];
+        si.rstep = c.iset_rank[2 * (I + j) + 1];
+        si.flags = (j == 0 ? G : 0) | ((I + j) >= p2 ? 1 << 8 : 0);
+      }
+      I += G;
+    }
+  }
+  auto make = [&](int32_t I0, int32_t I1) {
+    StreamChunk k{};
+    int64_t rlo = INT64_MAX, rhi = 0, vlo = INT64_MAX, vhi = 0, mlo = INT64_MAX, mhi = 0, slo = INT64_MAX, shi = 0;
+    for (int32_t I = I0; I < I1; ++I) {
+      const SetInfo &si = h->set_info[I];
+      rlo = std::min<int64_t>(rlo, si.rank0);
+      rhi = std::max<int64_t>(rhi, (int64_t)si.rank0 + (int64_t)(si.nm - 1) * si.rstep + 1);
+      vlo = std::min<int64_t>(vlo, si.vb);
+      vhi = std::max<int64_t>(vhi, (int64_t)si.vb + (int64_t)si.nm * si.na);
+      mlo = std::min<int64_t>(mlo, si.m0);
+      mhi = std::max<int64_t>(mhi, (int64_t)si.m0 + si.nm);
+      slo = std::min<int64_t>(slo, si.sb);
+      shi = std::max<int64_t>(shi, (int64_t)si.sb + si.na);
+    }
+    k.I0 = I0;
+    k.I1 = I1;
+    k.ra = (int32_t)(rlo & ~int64_t(1));
+    k.nra = (int32_t)(((rhi + 1) & ~int64_t(1)) - k.ra);
+    k.va = (int32_t)(vlo & ~int64_t(3));
+    k.nva = (int32_t)(((vhi + 3) & ~int64_t(3)) - k.va);
+    k.ka = (int32_t)(mlo & ~int64_t(3));
+    k.nka = (int32_t)(((mhi + 3) & ~int64_t(3)) - k.ka);
+    k.sa = (int32_t)(slo & ~int64_t(3));
+    k.nsa = (int32_t)(((shi + 3) & ~int64_t(3)) - k.sa);
+    return k;
+  };
+  for (int64_t d = 0; d < c.D; ++d) {
+    h->stream_c0[d] = (int32_t)h->stream_chunks.size();
+    const int32_t is0 = c.level_iset[2 * d], is1 = c.level_iset[2 * d + 2];
+    bool ok = d > 0 && is1 > is0;  // depth 0 holds only the root (and advances t)
+    std::vector<StreamChunk> ch;
+    for (int32_t I = is0; ok && I < is1;) {
+      int32_t J = I + (h->set_info[I].flags & 7);
+      if (stream_layout(make(I, J)).total > (uint32_t)kStreamStageBytes) { ok = false; break; }
+      while (J < is1) {  // extend by whole groups while the stage holds them
+        const int32_t K = J + (h->set_info[J].flags & 7);
+        if (stream_layout(make(I, K)).total > (uint32_t)kStreamStageBytes) break;
+        J = K;
+      }
+      ch.push_back(make(I, J));
+      I = J;
+    }
+    if (ok) {
+      h->stream_ok[d] = 1;
+      h->stream_chunks.insert(h->stream_chunks.end(), ch.begin(), ch.end());
+    }
+  }
+  h->stream_c0[c.D] = (int32_t)h->stream_chunks.size();
 }
 
 // --------------------------------------------------------------- compile
@@ -143,14 +235,15 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   if (h->opt.rule != CFR_RULE_CFR_PLUS && h->opt.rule != CFR_RULE_CFR && h->opt.rule != CFR_RULE_PCFR_PLUS) { delete h; return set_err(CFR_ERR_ARG, "bad rule"); }
   if (h->opt.order != CFR_ORDER_SIMULTANEOUS && h->opt.order != CFR_ORDER_ALTERNATING) { delete h; return set_err(CFR_ERR_ARG, "bad order"); }
   const int lp = h->opt.lanes_per_set;
-  if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32 or 256"); }
+  if (lp != 0 && lp != 1 && lp != 2 && lp != 4 && lp != 8 && lp != 16 && lp != 32 && lp != kThreads && lp != kStreamLanes) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set must be 0, 1, 2, 4, 8, 16, 32, 256 or 512"); }
+  if (lp == kStreamLanes && (h->opt.precision != CFR_P32 || h->opt.reach_order != CFR_REACH_MEMBERS)) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 512 (streaming) needs CFR_P32 and CFR_REACH_MEMBERS"); }
   std::string err;
   if (h->opt.reach_order < CFR_REACH_MEMBERS || h->opt.reach_order > CFR_REACH_SLOTS) { delete h; return set_err(CFR_ERR_ARG, "bad reach_order"); }
   if (h->opt.member_tiles < CFR_TILES_AUTO || h->opt.member_tiles > CFR_TILES_ON) { delete h; return set_err(CFR_ERR_ARG, "bad member_tiles"); }
   int rc = compile_game(*spec, h->c, err, h->opt.reach_order, h->opt.member_tiles);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
-  if (lp != 0 && (lp < 4 || lp == kThreads) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2 or 256 needs sets of at most 8 actions"); }
+  if (lp != 0 && (lp < 4 || lp == kThreads || lp == kStreamLanes) && c.max_act > 8) { delete h; return set_err(CFR_ERR_ARG, "lanes_per_set 1, 2, 256 or 512 needs sets of at most 8 actions"); }
   h->precision = h->opt.precision;
   h->rule = h->opt.rule;
   h->order = h->opt.order;
@@ -164,9 +257,12 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   h->level_lanes.assign(c.D, 8);
   double tot_mem = 0.0;
   bool any_tiled = false;
+  build_stream(h);
   for (int64_t d = 0; d < c.D; ++d) {
-    h->level_lanes[d] = lp ? lp : pick(c.level_mean_members[d]);
-    if (!lp && c.level_tiled[d]) h->level_lanes[d] = std::min(h->level_lanes[d], kTiledLanes);
+    h->level_lanes[d] = (lp && lp != kStreamLanes) ? lp : pick(c.level_mean_members[d]);
+    if (lp == kStreamLanes && h->stream_ok[d]) h->level_lanes[d] = kStreamLanes;
+    if ((!lp || (lp == kStreamLanes && !h->stream_ok[d])) && c.level_tiled[d])
+      h->level_lanes[d] = std::min(h->level_lanes[d], kTiledLanes);
     any_tiled = any_tiled || c.level_tiled[d];
     tot_mem += c.level_mean_members[d] * (c.level_iset[2 * d + 2] - c.level_iset[2 * d]);
   }
@@ -220,7 +316,8 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
                               h->b_wide_vb.bytes + h->b_wide_nch.bytes + h->b_wide_vs.bytes +
                               h->b_wide_chunk.bytes + h->b_tmpl.bytes + h->b_int_slot.bytes +
                               h->b_int_mask.bytes + h->b_int_cirank.bytes + h->b_big_irank.bytes + h->b_int_edge.bytes + h->b_iset_rank.bytes +
-                              h->b_mem_irank.bytes + h->b_wide_irank.bytes);
+                              h->b_mem_irank.bytes + h->b_wide_irank.bytes + h->b_set_info.bytes +
+                              h->b_stream_chunks.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
   o->lanes_per_set = h->exec_form == CFR_EXEC_PERSISTENT ? h->persist_lanes : (c.D > 0 ? h->level_lanes[c.D - 1] : 0);
@@ -335,7 +432,9 @@ static std::vector<std::pair<const void *, size_t>> host_ranges(const cfr_handle
       {c.int_cirank.data(), 4 * c.int_cirank.size()}, {c.big_irank.data(), 4 * c.big_irank.size()},
       {c.int_edge.data(), 4 * c.int_edge.size()},     {c.iset_rank.data(), 4 * c.iset_rank.size()},
       {c.mem_irank.data(), 4 * c.mem_irank.size()},   {c.wide_irank.data(), 4 * c.wide_irank.size()},
-      {c.tmpl_vs.data(), 8 * c.tmpl_vs.size()}};
+      {c.tmpl_vs.data(), 8 * c.tmpl_vs.size()},
+      {h->set_info.data(), sizeof(SetInfo) * h->set_info.size()},
+      {h->stream_chunks.data(), sizeof(StreamChunk) * h->stream_chunks.size()}};
   return r;
 }
 
@@ -371,7 +470,7 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if (bytes < h->plan_bytes) return set_err(CFR_ERR_ARENA_SMALL, "cfr_bind: arena has %zu bytes, plan needs %zu", bytes, h->plan_bytes);
   if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return set_err(CFR_ERR_ARG, "cfr_bind: arena must be 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->graph_arena = nullptr; }
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   h->arena = (char *)arena;
   const Compiled &c = h->c;
   auto up = [&](const Buf &b, const void *src, size_t n) -> int {
@@ -400,6 +499,9 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_iset_rank, c.iset_rank.data(), 4 * c.iset_rank.size()))) return rc;
   if ((rc = up(h->b_mem_irank, c.mem_irank.data(), h->b_mem_irank.bytes))) return rc;
   if ((rc = up(h->b_wide_irank, c.wide_irank.data(), 4 * c.wide_irank.size()))) return rc;
+  if ((rc = up(h->b_set_info, h->set_info.data(), sizeof(SetInfo) * h->set_info.size()))) return rc;
+  if ((rc = up(h->b_stream_chunks, h->stream_chunks.data(), sizeof(StreamChunk) * h->stream_chunks.size()))) return rc;
+  if (!h->stream_chunks.empty()) CK(prepare_bwd_stream());
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
   CK(cudaMemsetAsync(h->arena + h->b_bar.off, 0, 16, s));
   CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
@@ -418,6 +520,33 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
 // ------------------------------------------------------------ iteration
 // upd: the players whose sets update (bit 0 player 1, bit 1 player 2); the
 // depth-0 launch of the pass that updates player 2 advances t.
+// Streaming CTAs of the streaming backward of depth d: two per SM, never
+// more than the depth has chunks.
+static int stream_ctas(const cfr_handle *h, int d) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 148;
+  }
+  const int n = h->stream_c0[d + 1] - h->stream_c0[d];
+  return std::max(1, std::min(n, 2 * nsm));
+}
+
+// Blocks of the backward launch of depth d (chance blocks, wide chunks, then
+// the information-set work).
+static void bwd_blocks(const cfr_handle *h, int d, int *nb_ch, int *nb_wide, int *nb_is) {
+  const LevelWork &w = h->levels[d];
+  const int nch = d > 0 ? w.ch1 - w.ch0 : 0, nis = w.is1 - w.is0;  // a chance root is skipped
+  const int lanes = h->level_lanes[d];
+  *nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
+  *nb_wide = d > 0 ? w.wc1 - w.wc0 : 0;
+  if (lanes == kStreamLanes) *nb_is = nis > 0 ? stream_ctas(h, d) : 0;
+  else *nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;
+}
+
+// upd: the players whose sets update (bit 0 player 1, bit 1 player 2); the
+// depth-0 launch of the pass that updates player 2 advances t.
 template <typename T>
 static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3) {
   LevelWork w = h->levels[d];
@@ -425,11 +554,15 @@ static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3) {
     w.ch1 = w.ch0;
     w.wc1 = w.wc0;
   }
-  const int nch = w.ch1 - w.ch0, nis = w.is1 - w.is0;
+  int nb_ch, nb_wide, nb_is;
+  bwd_blocks(h, d, &nb_ch, &nb_wide, &nb_is);
   const int lanes = h->level_lanes[d];
-  const int nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
-  const int nb_wide = w.wc1 - w.wc0;
-  const int nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;
+  if (lanes == kStreamLanes) {  // FP32 only (compile checks it)
+    CK(launch_bwd_stream(h->maxa_tier, nb_ch + nb_wide + nb_is, s, game_view(h), state_view<float>(h), w, nb_ch,
+                         h->p<SetInfo>(h->b_set_info), h->p<StreamChunk>(h->b_stream_chunks), h->stream_c0[d],
+                         h->stream_c0[d + 1], h->rule, upd, h->p<int>(h->b_err)));
+    return CFR_OK;
+  }
   // at least one block: the depth-0 launch also advances t
   CK(launch_bwd_level<T>(h->maxa_tier, lanes, std::max(1, nb_ch + nb_wide + nb_is), s, game_view(h), state_view<T>(h),
                          w, nb_ch, h->rule, upd, (d == 0 && (upd & 2)) ? 1 : 0));
@@ -518,9 +651,8 @@ static int iterate_t(cfr_handle *h, int64_t n, cudaStream_t s) {
     return CFR_OK;
   }
   if (h->exec_form == CFR_EXEC_PERSISTENT) return launch_persistent_form<T>(h, n, s);
-  // graph form: capture one iteration once, replay it n times
-  if (h->gexec && h->graph_arena != h->arena)
-    return set_err(CFR_ERR_REBOUND, "captured graph refers to another arena");
+  // graph form: capture one iteration once, replay it n times (cfr_bind drops
+  // the graph, so a replay always refers to the bound arena)
   if (!h->gexec) {
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -528,17 +660,25 @@ static int iterate_t(cfr_handle *h, int64_t n, cudaStream_t s) {
     int rc = enqueue_iteration<T>(h, h->cap_stream);
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
     if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e == cudaSuccess && h->test_fail_capture) {  // test hook: the same path as a refused capture
+      cudaGraphDestroy(graph);
+      graph = nullptr;
+      e = cudaErrorStreamCaptureUnsupported;
+    }
     if (e != cudaSuccess) {
       // capture failed: warn once, fall back to per-level launches (same kernels, same order)
-      static bool warned = false;
-      if (!warned) { fprintf(stderr, "cfr: graph capture failed (%s); using per-level launches\n", cudaGetErrorString(e)); warned = true; }
+      if (!h->capture_warned) {
+        fprintf(stderr, "cfr: graph capture failed (%s); using per-level launches\n", cudaGetErrorString(e));
+        fflush(stderr);
+        h->capture_warned = true;
+      }
+      if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
       h->exec_form = CFR_EXEC_LEVELS;
       return iterate_t<T>(h, n, s);
     }
     CK(cudaGraphInstantiate(&h->gexec, graph, 0));
     cudaGraphDestroy(graph);
-    h->graph_arena = h->arena;
   }
   for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(h->gexec, s));
   return CFR_OK;
@@ -564,7 +704,8 @@ extern "C" int cfr_synchronize(cfr_handle *h, void *stream) {
   CK(cudaMemcpy(&err, h->arena + h->b_err.off, 4, cudaMemcpyDeviceToHost));
   if (err) {
     CK(cudaMemset(h->arena + h->b_err.off, 0, 4));
-    return set_err(CFR_ERR_TIMEOUT, "persistent kernel: a grid barrier gave up waiting; the state is undefined until cfr_reset");
+    return set_err(CFR_ERR_TIMEOUT, "a bounded wait in a kernel gave up (a grid barrier of the persistent kernel, or a "
+                   "staged copy of the streaming backward); the state is undefined until cfr_reset");
   }
   return CFR_OK;
 }
@@ -781,6 +922,10 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 29: src = c.int_edge.data(); n = (int64_t)c.int_edge.size(); break;
     case 30: src = c.iset_rank.data(); n = (int64_t)c.iset_rank.size(); break;
     case 31: src = c.level_tiled.data(); n = (int64_t)c.level_tiled.size(); break;
+    case 32: src = h->set_info.data(); n = 8 * (int64_t)h->set_info.size(); break;
+    case 33: src = h->stream_chunks.data(); n = 16 * (int64_t)h->stream_chunks.size(); break;
+    case 34: src = h->stream_c0.data(); n = (int64_t)h->stream_c0.size(); break;
+    case 35: src = h->stream_ok.data(); n = (int64_t)h->stream_ok.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -795,6 +940,11 @@ extern "C" int cfr_debug_set(cfr_handle *h, int key, int64_t value) {
   if (key == CFR_DEBUG_BARRIER_MISSING_ARRIVALS) {
     if (value < 0 || value > 1024) return set_err(CFR_ERR_ARG, "cfr_debug_set: bad value");
     h->test_missing_arrivals = (int)value;
+    return CFR_OK;
+  }
+  if (key == CFR_DEBUG_FAIL_GRAPH_CAPTURE) {
+    if (value != 0 && value != 1) return set_err(CFR_ERR_ARG, "cfr_debug_set: bad value");
+    h->test_fail_capture = (int)value;
     return CFR_OK;
   }
   return set_err(CFR_ERR_ARG, "cfr_debug_set: unknown key %d", key);
@@ -881,9 +1031,9 @@ extern "C" int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_
 // Allocation-free iteration (no counterpart in the paper).
 //
 // Some callers cannot allocate device memory at the moment they want to run
-// iterations: code that runs while a CUDA graph is being captured, real-time
-// serving loops whose memory budget is fixed at start-up, or host code that
-// does not own the device allocator. cfr_iterate_noalloc serves them: it runs
+// iterations: serving loops whose device memory is carved out once at
+// start-up, or host code that embeds the library without owning the device
+// allocator. cfr_iterate_noalloc serves them: it runs
 // the persistent kernel with its per-iteration scratch (both reach lanes, the
 // node values, wide-node partial sums and the grid-barrier words) placed in
 // one file-scope device array of fixed size, so the call itself allocates
@@ -961,27 +1111,15 @@ static int iterate_noalloc_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   a.bar.gen = bar + 1;
   a.bar.err = (int *)(bar + 2);
   a.bar.spin_limit = h->opt.barrier_spin_limit > 0 ? h->opt.barrier_spin_limit : (int64_t)20000000;
-  const int L = h->persist_lanes;
-  int dev = 0, nsm = 0, per_sm = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK(launch_persistent<T>(h->maxa_tier, L, 0, s, a, &per_sm));
-  int64_t cap = (int64_t)nsm * std::max(per_sm, 1);
-  if (h->opt.persistent_ctas > 0) cap = std::min<int64_t>(cap, h->opt.persistent_ctas);
-  int64_t want = 1;
-  for (const LevelWork &w : h->levels) {
-    want = std::max<int64_t>(want, (w.ie - w.ib + 4 * kThreads - 1) / (4 * kThreads));
-    want = std::max<int64_t>(want, (w.ch1 - w.ch0 + kThreads - 1) / kThreads);
-    want = std::max<int64_t>(want, ((int64_t)(w.is1 - w.is0) * L + kThreads - 1) / kThreads);
-    want = std::max<int64_t>(want, w.wc1 - w.wc0);
-  }
-  const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
+  // the persistent form's grid (computed once per lane count; allocates nothing)
+  if ((rc = ensure_persist_grid<T>(h, s))) return rc;
+  const int grid = h->persist_grid;
   a.bar.expected = (unsigned)grid;
   noalloc_init_kernel<T><<<grid_for(c.N, kThreads), kThreads, 0, s>>>(
       h->p<double>(h->b_tmpl), (int32_t)c.N, a.st.v, a.st.reach, a.g.wide_cnt,
       (int32_t)c.n_wide, bar);
   CK(cudaGetLastError());
-  CK(launch_persistent<T>(h->maxa_tier, L, grid, s, a, nullptr));
+  CK(launch_persistent<T>(h->maxa_tier, h->persist_lanes, grid, s, a, nullptr));
   int err = 0;
   CK(cudaMemcpyAsync(&err, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1035,10 +1173,9 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
       grids.push_back(grid_for((h->levels[d + 1].ie - h->levels[d + 1].ib + kPull - 1) / kPull, kThreads));
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
-    const LevelWork &w = h->levels[d];
-    const int nch = d > 0 ? w.ch1 - w.ch0 : 0, nwide = d > 0 ? w.wc1 - w.wc0 : 0, nis = w.is1 - w.is0;
-    grids.push_back(std::max(1, (nch > 0 ? grid_for(nch, kThreads) : 0) + nwide +
-                                    (nis > 0 ? grid_for(nis, kThreads / h->level_lanes[d]) : 0)));
+    int nb_ch, nb_wide, nb_is;
+    bwd_blocks(h, (int)d, &nb_ch, &nb_wide, &nb_is);
+    grids.push_back(std::max(1, nb_ch + nb_wide + nb_is));
   }
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -1124,7 +1261,9 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   for (int64_t d = c.D - 1; d >= 0 && rc == CFR_OK; --d) {
     int best = h->level_lanes[d];
     float best_ms = 1e30f;
-    for (int L : cand) {
+    std::vector<int> cd = cand;
+    if (h->stream_ok[d]) cd.push_back(kStreamLanes);
+    for (int L : cd) {
       h->level_lanes[d] = L;
       rc = h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
       if (rc) break;
@@ -1161,7 +1300,7 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->graph_arena = nullptr; }
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
   rc = h->precision == CFR_P64 ? init_state<double>(h, s) : init_state<float>(h, s);

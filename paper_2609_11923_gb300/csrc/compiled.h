@@ -113,8 +113,14 @@ int compile_game(const cfr_game_spec &spec, Compiled &out, std::string &err, int
 // fresh compile.
 void fold_chance(Compiled &c);
 
-// Algorithmic device bytes of one iteration (each array element touched the
-// minimum number of times the layout allows; see the design notes).
+// Algorithmic device bytes of one iteration: each array element touched the
+// minimum number of times the layout allows, i.e. the sum over depths of the
+// forward and backward launch models (per internal child an 8-byte edge
+// record and both reach lanes written, per internal parent its reach read,
+// per slot sigma read; per set 12 bytes of ranges, per slot R and the
+// average read and written in FP64 plus sigma read and written, per member
+// its value slot, reach and value written, per chance node its ranges and
+// value, per child its value read).
 int64_t algo_bytes_per_iter(const Compiled &c, int precision);
 
 }  // namespace cfr

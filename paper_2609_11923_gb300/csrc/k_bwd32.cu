@@ -3,3 +3,30 @@
 namespace cfr {
 template cudaError_t launch_bwd_level<float>(int, int, int, cudaStream_t, GameView, StateView<float>, LevelWork, int, int, int, int);
 }
+
+namespace cfr {
+template <int MA>
+static cudaError_t stream_one(int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w, int nb_chance,
+                              const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
+                              int *err) {
+  bwd_stream_kernel<MA><<<grid, kThreads, kStreamStages * kStreamStageBytes, s>>>(g, st, w, nb_chance, info, chunks,
+                                                                                 c0, c1, rule, upd, err);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_bwd_stream() {
+  const int dyn = kStreamStages * kStreamStageBytes;
+  cudaError_t e = cudaFuncSetAttribute(bwd_stream_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bwd_stream_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  return e;
+}
+
+cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w,
+                              int nb_chance, const SetInfo *info, const StreamChunk *chunks, int c0, int c1,
+                              int rule, int upd, int *err) {
+  if (maxa == 4) return stream_one<4>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err);
+  if (maxa == 8) return stream_one<8>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err);
+  return cudaErrorInvalidValue;
+}
+}  // namespace cfr

@@ -5,8 +5,18 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "bwd_stream.cuh"
 
 namespace cfr {
+
+// The streaming FP32 backward of one depth (bwd_stream_kernel); grid =
+// nb_chance + nb_wide + the streaming CTAs over chunks [c0, c1).
+cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w,
+                              int nb_chance, const SetInfo *info, const StreamChunk *chunks, int c0, int c1,
+                              int rule, int upd, int *err);
+// Allows the streaming kernel its dynamic shared memory (call before the
+// first launch, outside any stream capture; idempotent).
+cudaError_t prepare_bwd_stream();
 
 template <typename T>
 cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, GameView g, StateView<T> st,

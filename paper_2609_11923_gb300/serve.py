@@ -14,10 +14,22 @@ the one-CTA launch of the rest), so one large subgame no longer holds every
 round to the speed of a single SM. Whether a request is large depends only
 on the request, so a solve's iterates do not depend on what else is in the
 batch.
+
+Admission (``admit``): requests are taken in arrival order. A request whose
+footprint exceeds the whole pool can never be admitted and is answered at
+once with a ``rejected`` result. When the request at the head of the queue
+does not fit the free memory yet, later requests that fit are admitted
+around it (backfill), but only for ``hol_rounds`` rounds: after that nothing
+passes the head until it fits, so a large request cannot starve behind a
+stream of small ones. ``cancel(rid)`` (thread-safe) drops a request that is
+still queued, or retires an active solve at the next round boundary, when
+none of its kernels is in flight; its result carries the iterations done.
+A spec the compiler refuses is answered with an ``error`` result.
 """
 from __future__ import annotations
 
 import bisect
+import threading
 import time
 from collections import deque
 from concurrent.futures import ThreadPoolExecutor
@@ -93,10 +105,46 @@ class Result:
     pot: float
     edges: int
     strategy: Optional[np.ndarray] = field(default=None, repr=False)
+    # "solved" (reached target * pot), "capped" (max_iters first), "rejected"
+    # (footprint larger than the pool), "cancelled" or "error" (compile failed)
+    status: str = "solved"
+    message: str = ""
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
+
+
+def admit(queue, n_free_slots: int, pool: DevicePool, footprint, head=(None, 0), hol_rounds: int = 8, key=id):
+    """One admission pass (host logic only). queue: entries in arrival order
+    whose compile has finished; footprint(entry) gives its device bytes.
+    Entries larger than the whole pool are rejected. The others are admitted
+    first-fit while slots last; once one does not fit (the blocked head),
+    later entries are still admitted around it unless that same head has
+    already waited hol_rounds passes. head = (key of the blocked head, passes
+    it has waited) from the previous pass. Returns (admitted [(entry, offset,
+    nbytes)], rejected [(entry, reason)], head for the next pass)."""
+    admitted, rejected = [], []
+    blocked = None
+    for ent in queue:
+        nbytes = int(footprint(ent))
+        if nbytes > pool.size:
+            rejected.append((ent, "footprint %d bytes exceeds the pool's %d bytes" % (nbytes, pool.size)))
+            continue
+        if len(admitted) >= n_free_slots:
+            break
+        if blocked is not None and head[0] == key(blocked) and head[1] >= hol_rounds:
+            break  # the head has waited long enough: nothing passes it
+        off = pool.alloc(nbytes)
+        if off is None:
+            if blocked is None:
+                blocked = ent
+            continue
+        admitted.append((ent, off, nbytes))
+    if blocked is None:
+        return admitted, rejected, (None, 0)
+    k = key(blocked)
+    return admitted, rejected, (k, head[1] + 1 if head[0] == k else 1)
 
 
 @dataclass
@@ -114,7 +162,8 @@ class Server:
     def __init__(self, pool_bytes: int, max_active: int = 256, precision: int = cfr.P32, threads: int = 256,
                  lanes: int = 4, check_every: int = 50, max_iters: int = 5000, target: float = 1e-3,
                  compile_workers: int = 8, keep_strategies: bool = False, device="cuda",
-                 big_edges: int = 200_000, cluster: int = 8, big_threads: int = 1024, big_lanes: int = 8):
+                 big_edges: int = 200_000, cluster: int = 8, big_threads: int = 1024, big_lanes: int = 8,
+                 hol_rounds: int = 8, on_round=None):
         import torch
 
         self.torch = torch
@@ -134,6 +183,21 @@ class Server:
         self.side = torch.cuda.Stream(device=device)
         self.workers = ThreadPoolExecutor(max_workers=compile_workers)
         self.rounds = 0
+        self.hol_rounds = hol_rounds
+        self.on_round = on_round  # called after every round with the active request ids
+        self._cancel_lock = threading.Lock()
+        self._cancelled = set()
+
+    def cancel(self, rid) -> None:
+        """Cancels request rid (any thread): dropped if still queued, retired
+        at the next round boundary if active."""
+        with self._cancel_lock:
+            self._cancelled.add(rid)
+
+    def _take_cancelled(self):
+        with self._cancel_lock:
+            out, self._cancelled = self._cancelled, set()
+        return out
 
     def is_big(self, spec) -> bool:
         return self.cluster > 1 and int(spec.n_edges) >= self.big_edges
@@ -144,35 +208,77 @@ class Server:
     def _compile(self, spec):
         return cfr.cfr_compile(spec, self.opts)
 
-    def bind(self, h: int):
-        nbytes = cfr.cfr_plan(h)
-        off = self.pool.alloc(nbytes)
-        if off is None:
-            return None
-        cfr.cfr_bind(h, self.pool.ptr(off), nbytes, self._stream())
-        return off, nbytes
+    def _compile_or_error(self, spec):
+        try:
+            return self._compile(spec)
+        except cfr.CfrError as e:
+            return e
 
     def serve(self, requests: List[Request]) -> List[Result]:
         s = self._stream()
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        waiting: deque = deque()  # (request, future) in arrival order
+        waiting: List = []  # (request, future) in arrival order
         active: List[_Active] = []
         results: List[Result] = []
+        head = (None, 0)  # the blocked head of the queue and the passes it has waited
         t0 = time.perf_counter()
+
+        def answer(r, status, msg="", h=None):
+            t = time.perf_counter() - t0
+            results.append(Result(r.rid, r.arrival, t, t, 0, float("nan"), float(getattr(r.spec, "pot", 1.0)),
+                                  int(r.spec.n_edges), None, status, msg))
+            if h is not None:
+                cfr.cfr_destroy(h)
+
         while pending or waiting or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
-                waiting.append((r, self.workers.submit(self._compile, r.spec)))
-            # admit in arrival order while a slot and pool memory are free
-            while waiting and len(active) < self.max_active and waiting[0][1].done():
-                r, fut = waiting[0]
+                waiting.append((r, self.workers.submit(self._compile_or_error, r.spec)))
+            cancelled = self._take_cancelled()
+            if cancelled:  # queued requests leave now; active ones at this round boundary
+                for r in [r for r in pending if r.rid in cancelled]:
+                    answer(r, "cancelled")
+                pending = deque(r for r in pending if r.rid not in cancelled)
+                keep_w = []
+                for r, fut in waiting:
+                    if r.rid in cancelled:
+                        h = fut.result()
+                        answer(r, "cancelled", h=h if not isinstance(h, Exception) else None)
+                    else:
+                        keep_w.append((r, fut))
+                waiting = keep_w
+                keep_a = []
+                for a in active:
+                    if a.req.rid in cancelled:
+                        self._retire(a, results, time.perf_counter() - t0, float("nan"), "cancelled", s)
+                    else:
+                        keep_a.append(a)
+                active = keep_a
+            # compile failures are answered; the rest is admitted in arrival order
+            ready = []
+            for i, (r, fut) in enumerate(waiting):
+                if not fut.done():
+                    break  # keep arrival order: later compiles wait for earlier ones
                 h = fut.result()
-                got = self.bind(h)
-                if got is None:
-                    break  # memory full: wait for retirements
-                waiting.popleft()
-                active.append(_Active(r, h, got[0], got[1], time.perf_counter() - t0, self.is_big(r.spec)))
+                if isinstance(h, Exception):
+                    answer(r, "error", str(h))
+                    continue
+                ready.append((r, fut, h))
+            errored = {id(r) for r, fut in waiting if fut.done() and isinstance(fut.result(), Exception)}
+            waiting = [(r, fut) for r, fut in waiting if id(r) not in errored]
+            if ready:
+                adm, rej, head = admit(ready, self.max_active - len(active), self.pool,
+                                       lambda e: cfr.cfr_plan(e[2]), head, self.hol_rounds, key=lambda e: e[0].rid)
+                gone = set()
+                for (r, fut, h), why in rej:
+                    answer(r, "rejected", why, h)
+                    gone.add(id(r))
+                for (r, fut, h), off, nbytes in adm:
+                    cfr.cfr_bind(h, self.pool.ptr(off), nbytes, s)
+                    active.append(_Active(r, h, off, nbytes, time.perf_counter() - t0, self.is_big(r.spec)))
+                    gone.add(id(r))
+                waiting = [(r, fut) for r, fut in waiting if id(r) not in gone]
             if not active:
                 nxt = pending[0].arrival if pending else now + 1e-3
                 time.sleep(max(0.0, min(nxt - (time.perf_counter() - t0), 2e-3)))
@@ -198,19 +304,29 @@ class Server:
             for a, n_it, row in zip(active, iters, ex):
                 a.done += n_it
                 pot = float(getattr(a.req.spec, "pot", 1.0))
-                if row[0] <= self.target * pot or a.done >= self.max_iters:
-                    strat = None
-                    if self.keep:
-                        strat = np.empty(cfr.cfr_get_counts(a.h)["n_slots"])
-                        cfr.cfr_avg_strategy(a.h, strat, False, s)
-                    results.append(Result(a.req.rid, a.req.arrival, a.admitted, t_now, a.done, float(row[0]), pot,
-                                          int(a.req.spec.n_edges), strat))
-                    self.pool.release(a.off, a.nbytes)
-                    cfr.cfr_destroy(a.h)
+                if row[0] <= self.target * pot:
+                    self._retire(a, results, t_now, float(row[0]), "solved", s)
+                elif a.done >= self.max_iters:
+                    self._retire(a, results, t_now, float(row[0]), "capped", s)
                 else:
                     keep.append(a)
             active = keep
+            if self.on_round is not None:
+                self.on_round(self, [a.req.rid for a in active])
         return results
+
+    def _retire(self, a: _Active, results: List[Result], t_now: float, expl: float, status: str, s: int) -> None:
+        """Result of an active solve, then its memory back to the pool (no
+        kernel of it is in flight between rounds)."""
+        pot = float(getattr(a.req.spec, "pot", 1.0))
+        strat = None
+        if self.keep:
+            strat = np.empty(cfr.cfr_get_counts(a.h)["n_slots"])
+            cfr.cfr_avg_strategy(a.h, strat, False, s)
+        results.append(Result(a.req.rid, a.req.arrival, a.admitted, t_now, a.done, expl, pot,
+                              int(a.req.spec.n_edges), strat, status))
+        self.pool.release(a.off, a.nbytes)
+        cfr.cfr_destroy(a.h)
 
     def close(self):
         self.workers.shutdown(wait=True)

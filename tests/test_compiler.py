@@ -40,6 +40,8 @@ def test_arrays_bit_exact(name, reach_order, tiles):
         for key in cfr.EXPORT:
             if key == "level_lanes":  # a runtime choice, not a compiled array
                 continue
+            if key == "set_info" or key.startswith("stream_"):  # derived from these arrays (test_stream_layout)
+                continue
             got = cfr.cfr_export_array(h, key)
             np.testing.assert_array_equal(got, ref[key], err_msg=key)
         assert cfr.cfr_get_counts(h)["depth_blocks"] == ref["D"]
@@ -155,15 +157,54 @@ def test_members_at_different_depths_are_rejected():
 
 
 def test_calls_before_bind_report_not_bound():
+    # every call that needs device memory refuses before cfr_bind, without
+    # touching the device (host-side check)
+    g = gg.kuhn()
+    h = cfr.cfr_compile(g)
+    A = cfr.cfr_get_counts(h)["n_slots"]
+    z = np.zeros(A)
+    calls = {
+        "iterate": lambda: cfr.cfr_iterate(h, 1, 0),
+        "iterate_noalloc": lambda: cfr.cfr_iterate_noalloc(h, 1, 0),
+        "synchronize": lambda: cfr.cfr_synchronize(h, 0),
+        "avg_strategy": lambda: cfr.cfr_avg_strategy(h, np.empty(A), False, 0),
+        "current_strategy": lambda: cfr.cfr_current_strategy(h, np.empty(A), False, 0),
+        "exploitability": lambda: cfr.cfr_exploitability(h, 0),
+        "reset": lambda: cfr.cfr_reset(h, 0),
+        "set_payoffs": lambda: cfr.cfr_set_payoffs(h, np.zeros(g.n_nodes), 0),
+        "get_state": lambda: cfr.cfr_get_state(h, A, 0),
+        "set_state": lambda: cfr.cfr_set_state(h, z, z, 0, 0),
+        "autotune": lambda: cfr.cfr_autotune(h, 1, 0),
+        "launch_floor": lambda: cfr.cfr_launch_floor(h, 1, 0),
+        "profile_iteration": lambda: cfr.cfr_profile_iteration(h, cfr.cfr_get_counts(h)["depth_blocks"], 0),
+        "batch_iterate": lambda: cfr.cfr_batch_iterate([h], 1, 4096, 4096),
+        "batch_exploitability": lambda: cfr.cfr_batch_exploitability([h], 4096, 4096),
+    }
+    try:
+        for name, call in calls.items():
+            with pytest.raises(cfr.CfrError) as ei:
+                call()
+            assert ei.value.code == cfr.CFR_ERR_NOT_BOUND, name
+        assert cfr.cfr_plan(h) > 0
+    finally:
+        cfr.cfr_destroy(h)
+
+
+def test_bind_refuses_a_small_or_misaligned_arena_before_touching_it():
+    # both checks come before any device access: the pointers below are
+    # never dereferenced
     h = cfr.cfr_compile(gg.kuhn())
     try:
+        need = cfr.cfr_plan(h)
         with pytest.raises(cfr.CfrError) as ei:
+            cfr.cfr_bind(h, 1 << 20, need - 1, 0)
+        assert ei.value.code == cfr.CFR_ERR_ARENA_SMALL and str(need) in str(ei.value)
+        with pytest.raises(cfr.CfrError) as ei:
+            cfr.cfr_bind(h, (1 << 20) + 16, need, 0)
+        assert ei.value.code == cfr.CFR_ERR_ARG and "aligned" in str(ei.value)
+        with pytest.raises(cfr.CfrError) as ei:  # still unbound afterwards
             cfr.cfr_iterate(h, 1, 0)
-        assert ei.value.code == -3
-        with pytest.raises(cfr.CfrError) as ei:
-            cfr.cfr_exploitability(h, 0)
-        assert ei.value.code == -3
-        assert cfr.cfr_plan(h) > 0
+        assert ei.value.code == cfr.CFR_ERR_NOT_BOUND
     finally:
         cfr.cfr_destroy(h)
 
@@ -325,7 +366,8 @@ def test_binding_constants_mirror_the_header():
         for name, val in re.findall(r"(CFR_\w+)\s*=\s*(-?\d+)", body):
             values[name] = int(val)
     py = {"CFR_P64": cfr.P64, "CFR_P32": cfr.P32, "CFR_OK": cfr.CFR_OK,
-          "CFR_DEBUG_BARRIER_MISSING_ARRIVALS": cfr.DEBUG_BARRIER_MISSING_ARRIVALS}
+          "CFR_DEBUG_BARRIER_MISSING_ARRIVALS": cfr.DEBUG_BARRIER_MISSING_ARRIVALS,
+          "CFR_DEBUG_FAIL_GRAPH_CAPTURE": cfr.DEBUG_FAIL_GRAPH_CAPTURE}
     for prefix in ("EXEC_", "RULE_", "ORDER_", "REACH_", "TILES_"):
         py.update({"CFR_" + n: getattr(cfr, n) for n in dir(cfr) if n.startswith(prefix)})
     py.update({name: code for code, name in cfr.ERRORS.items()})

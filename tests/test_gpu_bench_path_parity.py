@@ -1,0 +1,129 @@
+"""Parity of the configuration the benchmark times, at the workloads' sizes.
+
+The benchmark runs the FP32 mode (reach, values, strategy in FP32; regrets,
+average and best-response sums in FP64, Proposition 4) in member order with
+tiled sets, as per-level kernels replayed from a CUDA graph (Section 4.3),
+with the lanes per set chosen by the autotuner. The bar for that mode is the
+oracle's exploitability within 1e-4 of the pot at equal iteration counts
+(T = 1,000); the FP64 mode must reach the oracle's average strategy within
+1e-12 (here: bitwise, since it sums in the oracle's order).
+
+* games that really form tiles, checked against a live oracle run;
+* the two-round card game at stack 1 (68,395,921 nodes, tiled like the full
+  game) and at full size (264,306,001 nodes), checked against the oracle's
+  exploitability after 1,000 iterations stored in tests/golden/card_oracle.json
+  by tests/golden/make_card_oracle.py (calls only oracle/; keyed by the spec
+  digest, checked first);
+* the seeded random trees of depth 14 (about 2.8 million nodes), seeds 0-2,
+  both precisions, against live oracle runs (run concurrently in threads:
+  the oracle's C routine releases the interpreter lock).
+"""
+import ast
+import json
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+
+import gamegen as gg
+import oracle
+from paper_2609_11923_gb300 import cfr
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+T = 1000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+    torch.cuda.synchronize()
+
+
+def bench_solver(g, precision=cfr.P32, tiles=cfr.TILES_AUTO):
+    """The benchmark's set-up: member order, graph form, autotuned lanes."""
+    s = cfr.Solver(g, precision=precision, exec_form=cfr.EXEC_GRAPH, reach_order=cfr.REACH_MEMBERS,
+                   member_tiles=tiles)
+    s.autotune()
+    return s
+
+
+@pytest.mark.parametrize("name,make", [
+    ("card_4x4_stack1_cap1", lambda: gg.large_card(4, 4, 1, 1)),
+    ("card_3x2_stack1_cap1", lambda: gg.large_card(3, 2, 1, 1)),
+    ("card_4x2_stack2_cap2", lambda: gg.large_card(4, 2, 2, 2)),
+    ("tiny", lambda: gg.tiny_card()),
+])
+def test_p32_tiled_graph_autotuned_within_1e4_pot(name, make):
+    g = make()
+    s = bench_solver(g, tiles=cfr.TILES_ON)
+    tiled = cfr.cfr_export_array(s.h, "level_tiled")
+    assert tiled.any(), "no depth formed tiles"
+    s.iterate(T)
+    s.synchronize()
+    e_gpu = s.exploitability()
+    e_or = oracle.solve(g, T).exploitability()
+    assert abs(e_gpu - e_or) <= 1e-4 * g.pot, (e_gpu, e_or)
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", "card_oracle.json")
+    rec = json.load(open(path))[name]
+    return rec
+
+
+@pytest.mark.parametrize("name", ["stack1", "full"])
+def test_p32_card_game_bench_configuration_within_1e4_pot_of_stored_oracle(name):
+    rec = _golden(name)
+    head = "gamegen.large_card"
+    assert rec["generator"].startswith(head + "(")
+    g = gg.large_card(*ast.literal_eval(rec["generator"][len(head):]))  # the generator call the record names
+    assert gg.spec_digest(g) == rec["spec_digest"], "the generator produced another game than the stored one"
+    s = bench_solver(g)
+    assert cfr.cfr_export_array(s.h, "level_tiled")[4:].all()  # depths 4-7 tiled, as in the benchmark
+    del g
+    s.iterate(T)
+    s.synchronize()
+    e_gpu, b1, b2, u = cfr.cfr_exploitability(s.h, s._s())
+    ref = rec["by_iterations"][str(T)]
+    assert abs(e_gpu - ref["exploitability"]) <= 1e-4 * rec["pot"], (e_gpu, ref["exploitability"])
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def depth14_oracles():
+    """Oracle solves of the depth-14 random trees, T iterations each."""
+    def run(seed):
+        g = gg.random_tree(seed)
+        o = oracle.solve(g, T)
+        return seed, (g, o.avg_strategy(), o.exploitability())
+
+    with ThreadPoolExecutor(max_workers=3) as ex:
+        return dict(ex.map(run, [0, 1, 2]))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_depth14_random_tree_fp64_matches_oracle(seed, depth14_oracles):
+    g, avg, _ = depth14_oracles[seed]
+    assert g.n_edges > 2_000_000
+    s = bench_solver(g, precision=cfr.P64)
+    s.iterate(T)
+    s.synchronize()
+    got = s.avg_strategy()
+    d = np.abs(got - avg)
+    assert d.max() <= 1e-12, "max |diff| %.3e at slot %d" % (d.max(), int(d.argmax()))
+    np.testing.assert_array_equal(got, avg)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_depth14_random_tree_fp32_within_1e4_pot(seed, depth14_oracles):
+    g, _, e_or = depth14_oracles[seed]
+    s = bench_solver(g)
+    s.iterate(T)
+    s.synchronize()
+    e_gpu = s.exploitability()
+    assert abs(e_gpu - e_or) <= 1e-4 * g.pot, (e_gpu, e_or)

@@ -413,3 +413,45 @@ def test_pinned_host_arrays_bind_to_the_same_results():
     np.testing.assert_array_equal(a.avg_strategy(), b.avg_strategy())
     b.pin_host(False)
     b.pin_host(False)
+
+
+def test_capture_failure_falls_back_warns_once_and_gives_the_same_floats(capfd):
+    # Section 4.3: if capture fails the solver warns once and runs the same
+    # kernels in the same order eagerly, computing identical floats. The
+    # failure is injected on the host (the captured graph is discarded).
+    g = gg.random_tree(3, depth=9)
+    ref = solve_gpu(g, 30, precision=cfr.P32, form=cfr.EXEC_GRAPH, lanes_per_set=8)
+    s = cfr.Solver(g, precision=cfr.P32, exec_form=cfr.EXEC_GRAPH, lanes_per_set=8)
+    cfr.cfr_debug_set(s.h, cfr.DEBUG_FAIL_GRAPH_CAPTURE, 1)
+    capfd.readouterr()
+    for n in (10, 15, 5):
+        s.iterate(n)
+    s.synchronize()
+    err = capfd.readouterr().err
+    assert err.count("graph capture failed") == 1, err
+    assert s.counts_now()["exec_form"] == cfr.EXEC_LEVELS
+    for a, b in zip(s.get_state(), ref.get_state()):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_rebinding_recaptures_instead_of_replaying_a_stale_graph():
+    # Section 4.3 refuses to replay a graph whose buffers moved; here binding
+    # again drops the graph, so the next call captures against the new arena
+    # and the old arena is never written again.
+    g = gg.tiny_card()
+    s = solve_gpu(g, 20, precision=cfr.P64, form=cfr.EXEC_GRAPH)
+    old = s.arena
+    new = torch.empty_like(old)
+    new_ptr = (new.data_ptr() + 255) & ~255
+    cfr.cfr_bind(s.h, new_ptr, s.arena_bytes, s._s())  # fresh state in the new arena
+    s.arena, s.arena_ptr = new, new_ptr
+    torch.cuda.synchronize()
+    snapshot = old.clone()
+    s.iterate(30)
+    s.synchronize()
+    assert torch.equal(old, snapshot), "the old arena was written after rebinding"
+    R, avg, t = s.get_state()
+    o = oracle.solve(g, 30)
+    assert t == 30
+    np.testing.assert_array_equal(R, o.R)
+    np.testing.assert_array_equal(avg, o.sbar)

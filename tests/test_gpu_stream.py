@@ -1,0 +1,105 @@
+"""The streaming FP32 backward (lanes_per_set = 512) against the oracle.
+
+Its chunks and staged index arithmetic are checked on the CPU first
+(tests/test_stream_layout.py, tests/test_layout_emulation.py); here the
+kernel itself runs: FP32 exploitability within 1e-4 of the pot of the
+oracle's at T = 1,000 in every launch form that uses it, deterministic runs,
+split calls equal to one call, both update orders and every update rule.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gamegen as gg
+import oracle
+from paper_2609_11923_gb300 import cfr
+
+pytestmark = pytest.mark.gpu
+
+GAMES = {
+    "tiny": lambda: gg.tiny_card(),
+    "card_4x4": lambda: gg.large_card(4, 4, 1, 1),
+    "card_4x2_cap2": lambda: gg.large_card(4, 2, 2, 2),
+    "rt10": lambda: gg.random_tree(4, depth=10),
+    "endgame": lambda: gg.endgame(7, 200000),
+    "wide_root": lambda: gg.endgame(2, 100000),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+    torch.cuda.synchronize()
+
+
+def streaming(g, form=cfr.EXEC_GRAPH, tiles=cfr.TILES_AUTO, **kw):
+    s = cfr.Solver(g, precision=cfr.P32, exec_form=form, lanes_per_set=cfr.STREAM_LANES, member_tiles=tiles, **kw)
+    lanes = cfr.cfr_export_array(s.h, "level_lanes")
+    ok = cfr.cfr_export_array(s.h, "stream_ok")
+    assert (lanes[ok.astype(bool)] == cfr.STREAM_LANES).all() and ok.any()
+    return s
+
+
+@pytest.mark.parametrize("tiles", [cfr.TILES_AUTO, cfr.TILES_ON])
+@pytest.mark.parametrize("name", list(GAMES))
+def test_streaming_fp32_within_1e4_pot(name, tiles):
+    g = GAMES[name]()
+    s = streaming(g, tiles=tiles)
+    s.iterate(1000)
+    s.synchronize()
+    e_or = oracle.solve(g, 1000).exploitability()
+    assert abs(s.exploitability() - e_or) <= 1e-4 * g.pot, (s.exploitability(), e_or)
+
+
+def test_streaming_forms_agree_bitwise_runs_repeat_and_split_calls_equal_one_call():
+    g = gg.large_card(4, 4, 1, 1)
+    outs = []
+    for form, parts in ((cfr.EXEC_LEVELS, (60,)), (cfr.EXEC_GRAPH, (60,)), (cfr.EXEC_GRAPH, (7, 50, 0, 3))):
+        s = streaming(g, form=form, tiles=cfr.TILES_ON)
+        for n in parts:
+            s.iterate(n)
+        s.synchronize()
+        outs.append(s.get_state())
+    for R, avg, t in outs[1:]:
+        assert t == 60
+        np.testing.assert_array_equal(R, outs[0][0])
+        np.testing.assert_array_equal(avg, outs[0][1])
+
+
+@pytest.mark.parametrize("rule,orule", [(cfr.RULE_CFR_PLUS, oracle.CFR_PLUS), (cfr.RULE_CFR, oracle.CFR),
+                                        (cfr.RULE_PCFR_PLUS, oracle.PCFR_PLUS)])
+@pytest.mark.parametrize("order", [cfr.ORDER_SIMULTANEOUS, cfr.ORDER_ALTERNATING])
+def test_streaming_every_rule_and_order_within_tolerance(rule, orule, order):
+    g = gg.large_card(3, 2, 1, 1)
+    s = streaming(g, rule=rule, order=order, tiles=cfr.TILES_ON)
+    s.iterate(300)
+    s.synchronize()
+    e_or = oracle.solve(g, 300, rule=orule, order=order).exploitability()
+    assert abs(s.exploitability() - e_or) <= 1e-4 * g.pot, (s.exploitability(), e_or)
+
+
+def test_streaming_matches_the_lane_group_kernel_closely_after_one_iteration():
+    # one iteration from the uniform strategy: the two FP32 kernels sum the
+    # same terms in different fixed orders, so R agrees to FP32 rounding
+    g = gg.large_card(4, 4, 1, 1)
+    a = streaming(g, tiles=cfr.TILES_ON)
+    b = cfr.Solver(g, precision=cfr.P32, exec_form=cfr.EXEC_GRAPH, lanes_per_set=8, member_tiles=cfr.TILES_ON)
+    o = oracle.solve(g, 1)
+    for s in (a, b):
+        s.iterate(1)
+        s.synchronize()
+    Ra, Rb = a.get_state()[0], b.get_state()[0]
+    scale = np.abs(o.R).max()
+    assert np.abs(Ra - o.R).max() <= 1e-5 * scale
+    assert np.abs(Ra - Rb).max() <= 1e-5 * scale
+
+
+def test_autotune_may_pick_streaming_and_keeps_the_tolerance():
+    g = gg.large_card(4, 4, 1, 1)
+    s = cfr.Solver(g, precision=cfr.P32, exec_form=cfr.EXEC_GRAPH, member_tiles=cfr.TILES_ON)
+    lanes = s.autotune(reps=3)
+    assert set(lanes) <= {1, 2, 4, 8, 16, 32, 256, cfr.STREAM_LANES}
+    s.iterate(1000)
+    s.synchronize()
+    assert abs(s.exploitability() - oracle.solve(g, 1000).exploitability()) <= 1e-4 * g.pot

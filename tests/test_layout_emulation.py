@@ -30,7 +30,10 @@ GAMES = {
 }
 
 
-def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS):
+def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS, stream=False):
+    """stream: at the depths that can stream, the set passes read everything
+    from per-chunk copies of the staged ranges, with the streaming kernel's
+    index arithmetic (an index outside a staged range raises)."""
     ex = lambda k: cfr.cfr_export_array(h, k)
     lint, edge = ex("level_int").astype(int), ex("int_edge").astype(int).reshape(-1, 2)
     isl, im, ivb, li = ex("iset_slot").astype(int), ex("iset_mem").astype(int), ex("iset_vb").astype(int), \
@@ -50,6 +53,10 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS):
     node_of_slot = np.empty(len(vslot), dtype=int)
     node_of_slot[vslot] = np.arange(len(vslot))
     wide_depth = np.searchsorted(lb, node_of_slot[wvs], side="right") - 1 if len(wvs) else []
+    if stream:
+        sinfo = ex("set_info").astype(int).reshape(-1, 8)
+        chunks = ex("stream_chunks").astype(int).reshape(-1, 16)
+        sc0, sok = ex("stream_c0").astype(int), ex("stream_ok").astype(int)
     sigma = [0.0] * A
     for s in range(I):
         for a in range(isl[s], isl[s + 1]):
@@ -137,12 +144,78 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS):
         for a in range(na):
             sigma[sb + a] = pos[a] / tot if tot > 0.0 else 1.0 / na
 
+    def staged(arr, start, count, pad):
+        """A copy of arr[start:start+count], the part past the end filled
+        with pad (the padding of the device buffer, never used)."""
+        out = list(arr[start:start + count])
+        assert start >= 0 and len(out) <= count
+        return out + [pad] * (count - len(out))
+
+    def stream_set(k, st, s, t, upd):
+        """The set pass of set s from chunk k's staged copies st."""
+        I0, I1, ra, nra, va, nva, ka, nka, sa, nsa = k[:10]
+        sreach, sval, smem, ssig, sR, sA = st
+        get = lambda a, i: a[i] if 0 <= i < len(a) else (_ for _ in ()).throw(IndexError(i))
+        sb, na, m0, nm, vb, r0, rs, fl = sinfo[s]
+        p2 = (fl >> 8) & 1
+        sig = [get(ssig, sb - sa + a) for a in range(na)]
+        racc, macc = [0.0] * na, [0.0] * na
+        for q in range(nm):
+            r = get(sreach, r0 - ra + q * rs)
+            hh = get(smem, m0 - ka + q)
+            cb = vb - va + q * na
+            vc = [get(sval, cb + a) for a in range(na)]
+            vh = 0.0
+            for a in range(na):
+                vh = vh + sig[a] * vc[a]
+            v[hh] = vh
+            po, pw = (r[0], r[1]) if p2 else (r[1], r[0])
+            f = (-1.0 if p2 else 1.0) * po
+            for a in range(na):
+                racc[a] = racc[a] + f * (vc[a] - vh)
+                macc[a] = macc[a] + pw * sig[a]
+        if (2 if p2 else 1) not in upd:
+            return
+        w = float(t) * float(t) if rule == oracle.PCFR_PLUS else float(t)
+        pos = []
+        for a in range(na):
+            rn = get(sR, sb - sa + a) + racc[a]
+            if rule != oracle.CFR:
+                rn = rn if rn > 0.0 else 0.0
+            R[sb + a] = rn
+            avg[sb + a] = get(sA, sb - sa + a) + w * macc[a]
+            x = rn + racc[a] if rule == oracle.PCFR_PLUS else rn
+            pos.append(x if x > 0.0 else 0.0)
+        tot = 0.0
+        for a in range(na):
+            tot = tot + pos[a]
+        for a in range(na):
+            sigma[sb + a] = pos[a] / tot if tot > 0.0 else 1.0 / na
+
+    def stream_depth(d, t, upd):
+        nan2 = [float("nan"), float("nan")]
+        for k in chunks[sc0[d]:sc0[d + 1]]:
+            I0, I1, ra, nra, va, nva, ka, nka, sa, nsa = k[:10]
+            st = (staged(reach, ra, nra, nan2), staged(v, va, nva, float("nan")), staged(list(mvs), ka, nka, -1),
+                  staged(sigma, sa, nsa, float("nan")), staged(R, sa, nsa, float("nan")),
+                  staged(avg, sa, nsa, float("nan")))
+            I = I0
+            while I < I1:
+                G = sinfo[I, 7] & 7
+                assert G in (1, 4)
+                for s in range(I, I + G):
+                    stream_set(k, st, s, t, upd)
+                I += G
+
     halves = [(1, 2)] if order == oracle.SIMULTANEOUS else [(1,), (2,)]  # players whose sets update
     for t in range(1, iters + 1):
         for upd in halves:
             forward()
             for d in range(D - 1, -1, -1):
                 chance_sums(d)
+                if stream and sok[d]:
+                    stream_depth(d, t, upd)
+                    continue
                 for s in range(li[2 * d], li[2 * d + 2]):
                     set_pass(s, d, t, upd)
     return np.array(R), np.array(avg)
@@ -199,6 +272,29 @@ def test_random_shapes_reach_the_oracles_iterates(seed, depth, p_chance, max_gro
     h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P64, reach_order=order, member_tiles=tiles))
     try:
         R, avg = emulate(h, iters)
+        spec_of = cfr.cfr_export_array(h, "spec_slot_of").astype(int)
+    finally:
+        cfr.cfr_destroy(h)
+    o = oracle.Oracle(g)
+    o.iterate(iters)
+    np.testing.assert_array_equal(R, o.R[spec_of])
+    np.testing.assert_array_equal(avg, o.sbar[spec_of])
+
+
+@pytest.mark.parametrize("tiles", [cfr.TILES_AUTO, cfr.TILES_ON])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "rt6", "card_small", "endgame", "wide_root"])
+def test_streaming_chunks_reach_the_oracles_iterates(name, tiles):
+    # the streaming backward's data paths: every set pass reads its members'
+    # reach, children's values, own value slots and its slots' strategy,
+    # regret and average from the chunk's staged copies, with the kernel's
+    # index arithmetic; in FP64 and the oracle's member order this must give
+    # the oracle's iterates bitwise
+    g = GAMES[name]()
+    iters = 3
+    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P32, member_tiles=tiles))
+    try:
+        assert cfr.cfr_export_array(h, "stream_ok").any()
+        R, avg = emulate(h, iters, stream=True)
         spec_of = cfr.cfr_export_array(h, "spec_slot_of").astype(int)
     finally:
         cfr.cfr_destroy(h)
