@@ -64,11 +64,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="large_card", choices=["large_card", "random_tree", "tiny", "serving", "warmstart"])
-    p.add_argument("--train-games", type=int, default=4000, help="warmstart only: training solves")
+    p.add_argument("--train-games", type=int, default=10000, help="warmstart only: training solves")
     p.add_argument("--heldout", type=int, default=512, help="warmstart only: held-out games")
     p.add_argument("--requests", type=int, default=512, help="serving only: number of endgame solves")
     p.add_argument("--max-iters", type=int, default=5000, help="serving only: iteration cap per solve")
     p.add_argument("--baseline-sample", type=int, default=48, help="serving only: solves timed one by one")
+    p.add_argument("--batched-requests", type=int, default=128,
+                   help="large_card: endgame solves of the batched-serving leg after the timed region (0: none)")
+    p.add_argument("--batched-baseline", type=int, default=12,
+                   help="large_card: of those, solves timed one by one for the batching speed-up")
     p.add_argument("--exec", dest="exec_form", default="graph", choices=["graph", "levels", "persistent", "auto"])
     p.add_argument("--reach-order", default="members", choices=["members", "bfs", "slots"],
                    help="layout of the internal nodes' reach (members: the forward pulls; bfs, slots: it pushes)")
@@ -151,7 +155,23 @@ def cpu_oracle(wl, seconds: float, min_iters: int = 3):
         n += 1
     dt = time.perf_counter() - t0
     return {"value": spec.n_edges * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host_cores": os.cpu_count(), "host": host_cpu(),
             "sample": "%s (%d edges), %d FP64 iterations in %.1f s, one thread" % (what, spec.n_edges, n, dt)}
+
+
+def host_cpu() -> str:
+    """The host's CPU model (for the record next to the oracle's timing)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
 
 
 def run_reference_serving(args):
@@ -183,7 +203,8 @@ def run_reference_serving(args):
         "steps": done, "warmup": 0, "ms_per_step": 1e3 * dt / done, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "serving: endgame subgames, edges log-uniform in [1e3, 1e6]", "sample": what},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what,
+                         "host_cores": os.cpu_count(), "host": host_cpu()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -219,6 +240,7 @@ def run_reference_warmstart(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "warm start yardstick: cold-start CFR+ on held-out endgames", "sample": what},
         "cpu_baseline": {"value": value, "unit": "iterations to 1e-3 pot (mean, cold start)", "cores": 1,
+                         "host_cores": os.cpu_count(), "host": host_cpu(),
                          "kind": "oracle", "sample": what},
         "e2e": {"value": value, "unit": "iterations to 1e-3 pot (mean, cold start)", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -254,6 +276,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": args.workload, "description": wl["desc"],
                                         "sample": what, "edges": spec.n_edges},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host_cores": os.cpu_count(), "host": host_cpu(),
                          "sample": "%s (%d edges), each step one FP64 iteration, one thread" % (what, spec.n_edges)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -395,7 +418,8 @@ def run_ours(args):
     for d in range(D):
         fb, bb = cfr.cfr_level_bytes(solver.h, d)
         launches.append((fwd_kernel, d, fwd_ms[d], fb))
-        launches.append(("bwd_level_kernel", d, bwd_ms[d], bb))
+        launches.append(("bwd_stream_kernel" if int(lanes[d]) == cfr.STREAM_LANES else "bwd_level_kernel", d,
+                         bwd_ms[d], bb))
     total_ms = sum(x[2] for x in launches)
     dom = max(launches, key=lambda x: x[2])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -439,6 +463,17 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle(wl, args.cpu_seconds)
 
+    # the metric's second half: batched serving of endgame subgames (outside
+    # the timed region; the game's arena is released first)
+    batched = None
+    arena_gb = solver.arena_bytes / 1e9
+    if rank == 0 and args.batched_requests > 0 and args.workload == "large_card":
+        solver.close()
+        del solver
+        torch.cuda.empty_cache()
+        batched = serving_leg(args.batched_requests, args.max_iters, args.batched_baseline)
+    barrier()
+
     # per depth one forward and one backward launch; in member order the
     # deepest depth has no forward launch (no internal node below it pulls)
     fwd_launches = D - 1 if args.reach_order == "members" else D
@@ -457,7 +492,7 @@ def run_ours(args):
                    "exec_form": args.exec_form, "reach_order": args.reach_order, "pot": pot, "parallelism": "replicas x%d" % world,
                    "lanes_per_set_by_depth": [int(x) for x in lanes],
                    "autotuned": not args.no_autotune,
-                   "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % (solver.arena_bytes / 1e9)},
+                   "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % arena_gb},
         "iters_per_s": world * iters_per_s,
         "algo_gbps_per_gpu": algo_gbps,
         "algo_bytes_per_iter": counts["algo_bytes_per_iter"],
@@ -468,6 +503,7 @@ def run_ours(args):
         "clocks": clk,
         "launch_profile_ms": {"fwd": fwd_ms, "bwd": bwd_ms},
         "launch_floor": launch_floor,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -476,19 +512,20 @@ def run_ours(args):
     return 0
 
 
-def run_serving(args):
-    """Batched serving of endgame subgames: saturated solves/s (all requests
-    at t=0), p50/p99 latency under Poisson arrivals at 0.8x that rate, and the
-    same solves run one by one for the batching speed-up."""
+def serving_leg(n_requests: int, max_iters: int, baseline_sample: int, seed0: int = 0):
+    """Batched serving of endgame subgames (seeds seed0 .. seed0 + n - 1):
+    saturated solves/s (all requests at t = 0), p50/p99 latency under Poisson
+    arrivals at 0.8x that rate, and a sample of the same solves run one by
+    one (single-game solver per request, same stop rule) for the batching
+    speed-up. Returns the figures as a dict."""
     import numpy as np
     import torch
 
     import gamegen as gg
     from paper_2609_11923_gb300 import cfr, serve
 
-    torch.cuda.set_device(0)
-    n = args.requests
-    specs = [gg.endgame(seed) for seed in range(n)]
+    n = n_requests
+    specs = [gg.endgame(seed) for seed in range(seed0, seed0 + n)]
     edges = np.array([sp.n_edges for sp in specs])
     (threads, lanes), tune = serve.autotune_batch(specs[:64])
     hs = [cfr.cfr_compile(sp) for sp in specs[:8]]
@@ -499,7 +536,7 @@ def run_serving(args):
 
     def run(reqs):
         srv = serve.Server(pool_bytes, max_active=n, threads=threads, lanes=lanes, check_every=50,
-                           max_iters=args.max_iters, target=1e-3)
+                           max_iters=max_iters, target=1e-3)
         t = time.perf_counter()
         res = srv.serve(reqs)
         dt = time.perf_counter() - t
@@ -513,28 +550,52 @@ def run_serving(args):
     arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * rate), size=n))
     res_p, dt_p, rounds_p = run([serve.Request(i, sp, float(a)) for i, (sp, a) in enumerate(zip(specs, arrivals))])
     lat = np.array([r.latency for r in res_p])
-    sample = rng.choice(n, size=min(args.baseline_sample, n), replace=False)
+    conv_p = np.array([r.status == "solved" for r in res_p])
+    sample = rng.choice(n, size=min(baseline_sample, n), replace=False)
+    torch.cuda.synchronize()
     t = time.perf_counter()
     for i in sample:
-        serve.solve_alone(specs[i], check_every=50, max_iters=args.max_iters, target=1e-3)
+        serve.solve_alone(specs[i], check_every=50, max_iters=max_iters, target=1e-3)
     torch.cuda.synchronize()
     alone_rate = len(sample) / (time.perf_counter() - t)
-    conv = np.mean([r.exploitability <= 1e-3 * r.pot for r in res_b])
-    line = {
-        "metric": METRIC, "value": rate, "unit": "solves/s", "n_gpus": 1, "steps": n, "warmup": 0,
-        "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving: %d endgame subgames, edges log-uniform in [1e3, 1e6] (total %d)" % (n, edges.sum()),
-                   "stop": "exploitability <= 1e-3 pot, checked every 50 iterations, cap %d" % args.max_iters,
-                   "launch_shape": {"threads": threads, "lanes": lanes, "autotune_s": {"%dx%d" % k: v for k, v in tune.items()}}},
+    solved = np.array([r.status == "solved" for r in res_b])
+    return {
+        "requests": n, "edges_total": int(edges.sum()), "seeds": "%d-%d" % (seed0, seed0 + n - 1),
+        "stop": "exploitability <= 1e-3 pot, checked every 50 iterations, cap %d" % max_iters,
+        "launch_shape": {"threads": threads, "lanes": lanes,
+                         "autotune_s": {"%dx%d" % k: v for k, v in tune.items()}},
         "saturated_solves_per_s": rate, "burst_seconds": dt_b, "burst_rounds": rounds_b,
-        "poisson": {"rate_per_s": 0.8 * rate, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                    "seconds": dt_p, "rounds": rounds_p},
+        "poisson": {"rate_per_s": 0.8 * rate, "p50_s": float(np.percentile(lat, 50)),
+                    "p99_s": float(np.percentile(lat, 99)),
+                    "p50_s_solved": float(np.percentile(lat[conv_p], 50)) if conv_p.any() else None,
+                    "p99_s_solved": float(np.percentile(lat[conv_p], 99)) if conv_p.any() else None,
+                    "seconds": dt_p, "rounds": rounds_p,
+                    "note": "latencies of every request; a capped request's latency is its time to the cap"},
         "per_instance_solves_per_s": alone_rate, "batching_speedup": rate / alone_rate,
-        "per_instance_sample": int(len(sample)), "converged_fraction": float(conv),
+        "per_instance_sample": int(len(sample)),
+        "converged_fraction": float(solved.mean()), "censored_fraction": float(1.0 - solved.mean()),
         "iterations_p50": float(np.percentile([r.iterations for r in res_b], 50)),
         "gpu_launches": 2 * (rounds_b + rounds_p),
     }
+
+
+def run_serving(args):
+    """Batched serving of endgame subgames as its own bench line (solves/s)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    leg = serving_leg(args.requests, args.max_iters, args.baseline_sample)
+    rate = leg["saturated_solves_per_s"]
+    line = {
+        "metric": METRIC, "value": rate, "unit": "solves/s", "n_gpus": 1, "steps": args.requests, "warmup": 0,
+        "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving: %d endgame subgames, edges log-uniform in [1e3, 1e6] (total %d)"
+                               % (args.requests, leg["edges_total"]),
+                   "stop": leg["stop"], "launch_shape": leg["launch_shape"]},
+        "gpu_launches": leg["gpu_launches"],
+    }
+    line.update({k: v for k, v in leg.items() if k not in ("stop", "launch_shape", "gpu_launches")})
     print(json.dumps(line))
     return 0
 
@@ -560,10 +621,12 @@ def run_warmstart(args):
     kappa, ktable = ws.choose_kappa(net, val)
     held = ws.endgame_family(list(range(20000, 20000 + args.heldout)), 1e3, 1e6)
     cold, cold_fin, cold_wall = ws.iterations_to_target(held, max_iters=args.max_iters)
+    # the warm start's wall time includes its features (from the compiled
+    # games) and the network pass
     t2 = time.perf_counter()
-    init = ws.warm_regrets_many(net, held, kappa)
-    t_infer = time.perf_counter() - t2
-    warm, warm_fin, warm_wall = ws.iterations_to_target(held, init=init, max_iters=args.max_iters)
+    ws.warm_regrets_many(net, held[:64], kappa)
+    t_infer = (time.perf_counter() - t2) * len(held) / 64.0  # a separate estimate of that share
+    warm, warm_fin, warm_wall = ws.iterations_to_target(held, net=net, kappa=kappa, max_iters=args.max_iters)
     line = {
         "metric": METRIC, "value": float(np.mean(warm)), "unit": "iterations to 1e-3 pot (mean, warm start)",
         "n_gpus": 1, "steps": args.heldout, "warmup": 0, "ms_per_step": None, "higher_is_better": False,
@@ -574,7 +637,10 @@ def run_warmstart(args):
         "cold": {"mean_iters": float(np.mean(cold)), "median_iters": float(np.median(cold)),
                  "finished": float(cold_fin.mean()), "wall_s": cold_wall},
         "warm": {"mean_iters": float(np.mean(warm)), "median_iters": float(np.median(warm)),
-                 "finished": float(warm_fin.mean()), "wall_s": warm_wall + t_infer, "inference_s": t_infer},
+                 "finished": float(warm_fin.mean()), "wall_s": warm_wall,
+                 "features_and_inference_s_estimate": t_infer,
+                 "wall_includes": "compile, features from the compiled games, one network pass, the solves"},
+        "wall_ratio_warm_over_cold": warm_wall / cold_wall,
         "iteration_ratio_warm_over_cold": float(np.mean(warm) / np.mean(cold)),
         "kappa": kappa, "kappa_validation_mean_iters": ktable,
         "training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,

@@ -74,6 +74,7 @@ enum { CFR_RULE_CFR_PLUS = 0, CFR_RULE_CFR = 1, CFR_RULE_PCFR_PLUS = 2 };
 enum { CFR_ORDER_SIMULTANEOUS = 0, CFR_ORDER_ALTERNATING = 1 };
 enum { CFR_REACH_MEMBERS = 0, CFR_REACH_BFS = 1, CFR_REACH_SLOTS = 2 };
 enum { CFR_TILES_AUTO = 0, CFR_TILES_OFF = 1, CFR_TILES_ON = 2 };
+enum { CFR_OVERLAP_ON = 0, CFR_OVERLAP_OFF = 1 };
 
 typedef struct cfr_options {
   /* CFR_P64: every value in FP64 (the parity mode). CFR_P32: reach, values,
@@ -97,7 +98,9 @@ typedef struct cfr_options {
                           (CFR_P32 in member order, sets of at most 8 actions): each depth's sets go in
                           chunks whose reach, child values, member slots, set descriptors, strategy,
                           regrets and averages are staged in shared memory by bulk asynchronous copies
-                          (depths where a group of sets exceeds one 48 KiB stage keep the default) */
+                          (depths where a group of sets exceeds one 48 KiB stage keep the default; the
+                          form pays only for long sets, and cfr_autotune tries it where sets have at least
+                          32 members on average) */
   int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
   int64_t barrier_spin_limit; /* 0 = default; polls before a grid barrier reports CFR_ERR_TIMEOUT */
   /* CFR_ORDER_SIMULTANEOUS: both players' regrets from one strategy profile;
@@ -112,7 +115,9 @@ typedef struct cfr_options {
    * chance nodes; the backward pass reads each set's reach as one run and
    * needs no rank table, and the forward pass pulls (every internal node
    * reads its parent's reach). CFR_REACH_BFS: breadth-first, and
-   * CFR_REACH_SLOTS: the order of the nodes' value slots; in both a parent's
+   * CFR_REACH_SLOTS: the order of the nodes' places in their parents' value
+   * blocks, taken member by member (the value blocks themselves are
+   * action-major, see cfr_export_array 19-20); in both a parent's
    * internal children have consecutive ranks and the forward pass pushes
    * (every parent writes its children's reach). */
   int reach_order;
@@ -127,6 +132,20 @@ typedef struct cfr_options {
    * depth where tiles hold at least half the members (small games served
    * in batches); CFR_TILES_OFF: none. */
   int member_tiles;
+  /* CFR_OVERLAP_ON (default): the per-level kernels of an iteration are
+   * launched with programmatic dependent launch: each kernel first waits for
+   * the previous launch to complete (so every read sees every earlier
+   * write), but its launch and block scheduling overlap the previous
+   * kernel's tail. CFR_OVERLAP_OFF: plain stream order. Results are bitwise
+   * the same. */
+  int launch_overlap;
+  /* Graph form: iterations recorded into one CUDA graph (the paper's
+   * alternative-execution table records 1, 10 and 100); 0 or 1 = one.
+   * cfr_iterate(n) replays the k-iteration graph n / k times and a
+   * one-iteration graph for the rest (both captured on first use); the
+   * device counter makes the results bitwise those of one iteration per
+   * graph. At most 1000. */
+  int graph_iters;
 } cfr_options;
 
 typedef struct cfr_counts {
@@ -141,6 +160,8 @@ typedef struct cfr_counts {
   int64_t iteration;          /* t: iterations completed since bind/reset */
   int exec_form;              /* resolved execution form */
   int lanes_per_set;          /* resolved lanes per information set */
+  int64_t graph_kernels;      /* kernel nodes in the captured one-iteration graph (0 until captured) */
+  int64_t graph_k_kernels;    /* kernel nodes in the captured graph_iters-iteration graph (0 until captured) */
 } cfr_counts;
 
 typedef struct cfr_handle cfr_handle;
@@ -266,7 +287,8 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * member order], 16 big_irank (empty in member order), 17 mem_irank
  * [N_dec], 18 level_int[D+1], 19 vslot[N] (value slot of each node; the
  * root's is N-1), 20 iset_vb[I] (first slot of the block holding set I's
- * members' children), 21 mem_vs[N_dec] (value slot of each member),
+ * members' children, action-major: child a of member k at iset_vb[I] +
+ * a * M + k - first member, M members), 21 mem_vs[N_dec] (value slot of each member),
  * 22 ch_vb, 23 ch_nch, 24 ch_vs (per chance node of list 6: first child
  * slot, child count, own slot), 25 wide_vb, 26 wide_nch, 27 wide_vs (the
  * same for chance nodes with more than 1024 children), 28 template values
@@ -292,7 +314,8 @@ int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity
  * backward launch with each supported number of lanes per information set
  * (1, 2, 4, 8, 16, 32, and 256 = one block per set when sets have at most 8
  * actions, and 512 = the streaming backward at depths that can stream;
- * `reps` launches each) and keeps the fastest; in the
+ * `reps` launches each; 512 only where sets have at least 32 members on
+ * average) and keeps the fastest; in the
  * persistent form it also times whole persistent iterations per lane count.
  * Trial launches overwrite the solver state, so the call ends by resetting it
  * (as cfr_reset) and dropping a captured graph. The chosen counts are
@@ -314,6 +337,17 @@ int cfr_autotune(cfr_handle *h, int reps, void *stream);
  * waits: CFR_ERR_TIMEOUT if one gives up). The handle must be bound; solver
  * state is untouched. Synchronises `stream`. */
 int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *graph_ms, double *persistent_ms);
+
+/* Chance sums per information set from the chance products the compiler
+ * folded (Algorithm "Compile", step 6): mass[I] = the sum over the set's
+ * members h of pi_c(h), and, when root_w is given, wsum[I] = the sum of
+ * pi_c(h) * root_w[the root outcome above h] (root_w has one weight per
+ * outcome of a chance root, in the spec's order; CFR_ERR_UNSUPPORTED if the
+ * root is not a chance node). Members are added in ascending compiled id.
+ * Host arrays, spec set order; host only. Used for the learned warm start's
+ * features (a set's weight in its range, its equity against the opponent's
+ * range); no counterpart in the paper's API. */
+int cfr_set_chance_sums(const cfr_handle *h, const double *root_w, double *mass, double *wsum);
 
 /* Page-locks (pin != 0) or releases (pin == 0) the host memory that
  * cfr_bind and the lifecycle calls copy to the device (the compiled arrays

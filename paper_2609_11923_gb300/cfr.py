@@ -30,6 +30,7 @@ RULE_CFR_PLUS, RULE_CFR, RULE_PCFR_PLUS = 0, 1, 2
 ORDER_SIMULTANEOUS, ORDER_ALTERNATING = 0, 1
 REACH_MEMBERS, REACH_BFS, REACH_SLOTS = 0, 1, 2
 TILES_AUTO, TILES_OFF, TILES_ON = 0, 1, 2
+OVERLAP_ON, OVERLAP_OFF = 0, 1
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 DEBUG_FAIL_GRAPH_CAPTURE = 2
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
@@ -62,7 +63,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("exec_form", ctypes.c_int), ("rule", ctypes.c_int),
         ("lanes_per_set", ctypes.c_int), ("persistent_ctas", ctypes.c_int),
         ("barrier_spin_limit", ctypes.c_int64), ("order", ctypes.c_int), ("reach_order", ctypes.c_int),
-        ("member_tiles", ctypes.c_int),
+        ("member_tiles", ctypes.c_int), ("launch_overlap", ctypes.c_int), ("graph_iters", ctypes.c_int),
     ]
 
 
@@ -70,7 +71,8 @@ class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_nodes", "n_edges", "n_infosets", "n_slots", "n_internal", "n_decision", "n_chance", "n_terminal",
         "depth_blocks", "max_actions", "algo_bytes_per_iter", "upload_bytes", "iteration")] + [
-        ("exec_form", ctypes.c_int), ("lanes_per_set", ctypes.c_int)]
+        ("exec_form", ctypes.c_int), ("lanes_per_set", ctypes.c_int), ("graph_kernels", ctypes.c_int64),
+        ("graph_k_kernels", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -105,6 +107,7 @@ def _load():
         "cfr_autotune": [H, ctypes.c_int, vp],
         "cfr_launch_floor": [H, i64, vp, dp, dp],
         "cfr_pin_host": [H, ctypes.c_int],
+        "cfr_set_chance_sums": [H, dp, dp, dp],
         "cfr_set_root_chance": [H, dp, i64, vp],
         "cfr_batch_iterate": [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(i64), i64, vp, ctypes.c_size_t,
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
@@ -130,7 +133,7 @@ EXPORTED = ["cfr_compile", "cfr_get_counts", "cfr_plan", "cfr_bind", "cfr_iterat
             "cfr_get_state", "cfr_set_state", "cfr_export_array", "cfr_debug_set", "cfr_last_error",
             "cfr_destroy", "cfr_level_bytes", "cfr_profile_iteration", "cfr_iterate_noalloc", "cfr_autotune",
             "cfr_batch_table_bytes", "cfr_batch_iterate", "cfr_batch_exploitability", "cfr_launch_floor",
-            "cfr_set_root_chance", "cfr_pin_host"]
+            "cfr_set_root_chance", "cfr_pin_host", "cfr_set_chance_sums"]
 
 
 def _check(rc: int) -> None:
@@ -165,13 +168,15 @@ def spec_struct(spec) -> Tuple[GameSpecC, list]:
 
 def make_options(precision=P32, exec_form=EXEC_AUTO, rule=RULE_CFR_PLUS, lanes_per_set=0, persistent_ctas=0,
                  barrier_spin_limit=0, order=ORDER_SIMULTANEOUS, reach_order=REACH_MEMBERS,
-                 member_tiles=TILES_AUTO) -> Options:
+                 member_tiles=TILES_AUTO, launch_overlap=OVERLAP_ON, graph_iters=0) -> Options:
     o = Options()
     o.precision, o.exec_form, o.rule = precision, exec_form, rule
     o.lanes_per_set, o.persistent_ctas, o.barrier_spin_limit = lanes_per_set, persistent_ctas, barrier_spin_limit
     o.order = order
     o.reach_order = reach_order
     o.member_tiles = member_tiles
+    o.launch_overlap = launch_overlap
+    o.graph_iters = graph_iters
     return o
 
 
@@ -286,6 +291,17 @@ def cfr_set_root_chance(h: int, prob, stream: int = 0) -> None:
     _check(_lib.cfr_set_root_chance(h, _dp(p), len(p), stream))
 
 
+def cfr_set_chance_sums(h: int, n_sets: int, root_w=None):
+    """(mass[I], wsum[I] or None) in spec set order: per set the sum of its
+    members' chance products, and of those times root_w[root outcome]."""
+    mass = np.zeros(n_sets)
+    wsum = np.zeros(n_sets) if root_w is not None else None
+    rw = np.ascontiguousarray(root_w, dtype=np.float64) if root_w is not None else None
+    _check(_lib.cfr_set_chance_sums(h, _dp(rw) if rw is not None else None, _dp(mass),
+                                    _dp(wsum) if wsum is not None else None))
+    return mass, wsum
+
+
 def cfr_pin_host(h: int, pin: bool = True) -> None:
     """Page-lock (or release) the handle's host arrays that cfr_bind uploads."""
     _check(_lib.cfr_pin_host(h, 1 if pin else 0))
@@ -352,12 +368,13 @@ class Solver:
     def __init__(self, spec, precision: int = P32, exec_form: int = EXEC_AUTO, rule: int = RULE_CFR_PLUS,
                  lanes_per_set: int = 0, persistent_ctas: int = 0, barrier_spin_limit: int = 0,
                  device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS,
-                 reach_order: int = REACH_MEMBERS, member_tiles: int = TILES_AUTO):
+                 reach_order: int = REACH_MEMBERS, member_tiles: int = TILES_AUTO,
+                 launch_overlap: int = OVERLAP_ON, graph_iters: int = 0):
         import torch
 
         self.torch = torch
         self.opts = make_options(precision, exec_form, rule, lanes_per_set, persistent_ctas, barrier_spin_limit,
-                                 order, reach_order, member_tiles)
+                                 order, reach_order, member_tiles, launch_overlap, graph_iters)
         self.h = cfr_compile(spec, self.opts)
         self.counts = cfr_get_counts(self.h)
         self.n_slots = self.counts["n_slots"]

@@ -244,17 +244,17 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
         for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
         if (k < m1) {
           const int32_t h = __ldg(g.mem_vs + k);
-          const int32_t cb = vb0 + (k - m0) * na;
+          const int32_t cb = vb0 + (k - m0), M = m1 - m0;
           const double2 r = in.reach2[member_rank(g, k, mr)];
           const double po = p ? r.x : r.y;
           double oth = 0.0, va = 0.0;
 #pragma unroll
           for (int a = 0; a < MAXA; ++a) {
             if (a < na) {
-              const double2 x = in.vb[cb + a];
+              const double2 x = in.vb[cb + a * M];
               q[a] = po * (p ? x.y : x.x);
               oth += sg[a] * (p ? x.x : x.y);
-              va += sg[a] * in.vavg[cb + a];
+              va += sg[a] * in.vavg[cb + a * M];
             }
           }
           reinterpret_cast<double *>(in.vb + h)[1 - p] = oth;
@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(THREADS) batch_br_kernel(const InstDesc *table
         if (p == 0 ? Q[a] > Q[best] : Q[a] < Q[best]) best = a;
       for (int32_t k = m0 + lane; k < m1; k += LANES) {
         const int32_t h = __ldg(g.mem_vs + k);
-        const int32_t cb = vb0 + (k - m0) * na;
-        reinterpret_cast<double *>(in.vb + h)[p] = reinterpret_cast<const double *>(in.vb + cb + best)[p];
+        const int32_t cb = vb0 + (k - m0) + best * (m1 - m0);
+        reinterpret_cast<double *>(in.vb + h)[p] = reinterpret_cast<const double *>(in.vb + cb)[p];
       }
     }
     __syncthreads();

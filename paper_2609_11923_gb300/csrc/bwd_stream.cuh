@@ -10,21 +10,24 @@
 // average, and their set descriptors. The host cuts each depth's sets into
 // chunks of whole groups (a tile of four sets, or one untiled set) whose
 // staged bytes fit one pipeline stage. Every CTA walks the chunks c =
-// blockIdx, blockIdx + grid, ... through a ring of kStreamStages stages: one
-// thread issues the chunk's seven cp.async.bulk copies into a stage and the
-// stage's mbarrier counts their bytes; all threads wait on the mbarrier
-// (bounded), compute the chunk from shared memory, and the stage is refilled
-// with the chunk kStreamStages ahead. The loads in flight cost no registers,
-// so the memory pipe stays full at a low warp count; the one scattered access
-// left is each member's value write into its parent set's block.
+// blockIdx, blockIdx + grid, ... through a ring of kStreamStages stages. Its
+// kThreads compute threads do the members' work; one more warp, the control
+// warp, issues each chunk's seven cp.async.bulk copies into a stage (the
+// stage's mbarrier counts their bytes) and runs every group's slot update.
+// The loads in flight cost no registers, so the memory pipe stays full at a
+// low warp count, and the compute warps never wait for a slot update (they
+// hand each group's partial sums over through a double-buffered array and a
+// pair of mbarriers); the one scattered access left is each member's value
+// write into its parent set's block.
 //
-// Work inside a chunk: the CTA takes one group at a time with all its
-// threads; thread t serves set j = t % G of the group (G = 4 for a tile,
-// 1 otherwise) and members q = t / G, t / G + 256 / G, ... of that set, so a
-// warp reads a tile's reach as one contiguous run. Per-thread FP32 partial
-// sums are finished by a fixed-shape butterfly within the warp and a sum over
-// the warps in warp order (deterministic run to run), then warp 0 updates the
-// group's slots (one lane per slot) and writes sigma^{t+1}.
+// Work inside a chunk: the compute threads take one group at a time: thread
+// t serves set j = t % G of the group (G = 4 for a tile, 1 otherwise) and
+// members q = t / G, t / G + 256 / G, ... of that set, so a warp reads a
+// tile's reach as one contiguous run. Per-thread FP32 partial sums are
+// finished by a fixed-shape butterfly within the warp and, in the control
+// warp, a sum over the warps in warp order (deterministic run to run); the
+// control warp then updates the group's slots (one lane per slot) and writes
+// sigma^{t+1}. The form pays where sets are long (hundreds of members).
 #pragma once
 #include "kernels.cuh"
 
@@ -34,6 +37,7 @@ constexpr int kStreamLanes = 512;                 // lanes_per_set code of this 
 constexpr int kStreamStages = 2;                  // pipeline depth
 constexpr int kStreamStageBytes = 48 * 1024;      // bytes one chunk may stage
 constexpr int kStreamWarps = kThreads / 32;
+constexpr int kStreamMinMembers = 32;             // mean members per set below which the autotuner does not try it
 
 // Per information set (member order), 32 bytes, read by the streaming form.
 struct SetInfo {
@@ -110,7 +114,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > 4000000000ll) break;
+    if (clock64() - t0 > 2000000000ll) break;  // about a second at the boost clock
   }
   return false;
 }
@@ -136,14 +140,17 @@ __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char
   return true;
 }
 
-// One group of sets (G = 1 or 4) of a staged chunk, all threads.
+// The member work of one group of sets (G = 1 or 4) of a staged chunk, by
+// the kThreads compute threads: thread t serves set j = t % G and members
+// t / G, t / G + kThreads / G, ...; writes each member's value and leaves
+// the thread's partial regret and average sums, finished by a butterfly over
+// the warp's lanes that serve the same set, in racc / macc.
 template <int MAXA>
-__device__ __forceinline__ void stream_group(const StreamChunk &d, const StreamLayout &L, const unsigned char *stage,
-                                             int32_t I, float *v, float *sigma, double *Rg, double *avgg, double wt,
-                                             int rule, int upd, float (*red)[4][2 * MAXA]) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void stream_members(const StreamChunk &d, const StreamLayout &L, const unsigned char *stage,
+                                               int32_t I, int G, float *v, float (&racc)[MAXA],
+                                               float (&macc)[MAXA]) {
+  const int tid = threadIdx.x;
   const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
-  const int G = sinfo[I - d.I0].flags & 7;  // 1 or 4
   const int gs = G == 4 ? 2 : 0;
   const int j = tid & (G - 1);
   const int LPS = kThreads >> gs;
@@ -153,7 +160,7 @@ __device__ __forceinline__ void stream_group(const StreamChunk &d, const StreamL
   const float *sv = reinterpret_cast<const float *>(stage + L.val);
   const int32_t *sm = reinterpret_cast<const int32_t *>(stage + L.mem);
   const float *ss = reinterpret_cast<const float *>(stage + L.sig);
-  float sig[MAXA], racc[MAXA], macc[MAXA];
+  float sig[MAXA];
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) {
     sig[a] = a < si.na ? ss[si.sb - d.sa + a] : 0.f;
@@ -164,13 +171,13 @@ __device__ __forceinline__ void stream_group(const StreamChunk &d, const StreamL
   for (int32_t q = tid >> gs; q < si.nm; q += LPS) {
     const float2 r = sr[rb + q * si.rstep];
     const int32_t h = sm[kb + q];
-    const int32_t cb = cbase + q * si.na;
+    const int32_t cb = cbase + q;  // child a at cb + a * nm (action-major block)
     float vc[MAXA];
     float vh = 0.f;
 #pragma unroll
     for (int a = 0; a < MAXA; ++a) {
       if (a < si.na) {
-        vc[a] = sv[cb + a];
+        vc[a] = sv[cb + a * si.nm];
         vh = vh + sig[a] * vc[a];
       }
     }
@@ -186,7 +193,6 @@ __device__ __forceinline__ void stream_group(const StreamChunk &d, const StreamL
       }
     }
   }
-  // butterfly over the lanes of the warp that serve the same set
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) {
     for (int off = G; off < 32; off <<= 1) {
@@ -194,22 +200,24 @@ __device__ __forceinline__ void stream_group(const StreamChunk &d, const StreamL
       macc[a] += __shfl_xor_sync(0xffffffffu, macc[a], off);
     }
   }
-  if (lane < G) {
-#pragma unroll
-    for (int a = 0; a < MAXA; ++a) {
-      red[warp][lane][a] = racc[a];
-      red[warp][lane][MAXA + a] = macc[a];
-    }
-  }
-  __syncthreads();
-  if (warp != 0) return;
-  // warp 0: lane = a * G + jj updates slot a of set jj of the group
+}
+
+// The slot update of one group by the control warp: lane = a * G + j
+// updates slot a of set j (the warps' partial sums added in warp order),
+// then writes sigma^{t+1} of the group's sets.
+template <int MAXA>
+__device__ __forceinline__ void stream_update(const StreamChunk &d, const StreamLayout &L, const unsigned char *stage,
+                                              int32_t I, int G, float *sigma, double *Rg, double *avgg, double wt,
+                                              int rule, int upd, const float (*red)[4][2 * MAXA]) {
+  const int lane = threadIdx.x & 31;
+  const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
+  const int gs = G == 4 ? 2 : 0;
   const int jj = lane & (G - 1), a = lane >> gs;
   const SetInfo sj = sinfo[I + jj - d.I0];
   const bool q2 = (sj.flags >> 8) & 1;
-  const bool live = a < MAXA && a < sj.na;
+  const bool live = a < MAXA && a < sj.na && (upd & (q2 ? 2 : 1));
   float pf = 0.f;
-  if (live && (upd & (q2 ? 2 : 1))) {
+  if (live) {
     float r = 0.f, m = 0.f;
     for (int w = 0; w < kStreamWarps; ++w) {  // warps in order
       r += red[w][jj][a];
@@ -230,115 +238,147 @@ __device__ __forceinline__ void stream_group(const StreamChunk &d, const StreamL
     const float x = __shfl_sync(0xffffffffu, pf, (b * G + jj) & 31);
     if (b < sj.na) tot += x;
   }
-  if (live && (upd & (q2 ? 2 : 1))) sigma[sj.sb + a] = tot > 0.f ? pf / tot : 1.f / (float)sj.na;
+  if (live) sigma[sj.sb + a] = tot > 0.f ? pf / tot : 1.f / (float)sj.na;
 }
 
-// Grid: nb_chance blocks over narrow chance nodes, then one block per wide
-// chunk, then the streaming CTAs over chunks [c0, c1) of this depth.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Threads of a streaming CTA: kThreads compute threads and one control warp.
+constexpr int kStreamThreads = kThreads + 32;
+
+// Grid: nb_chance blocks over narrow chance nodes, then the streaming CTAs
+// over chunks [c0, c1) of this depth (a depth with wide chance nodes does
+// not stream). Barriers of a streaming CTA (every wait bounded):
+//   full[s]   the copies of the chunk in stage s have landed (bytes counted)
+//   empty[s]  all threads are done with stage s (the control warp refills it)
+//   rfull[p]  the compute threads have written the partial sums red[p]
+//   rempty[p] the control warp has consumed red[p]
+// The compute warps never wait for a slot update: the control warp runs
+// each group's update while they work on the next group.
 template <int MAXA>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kStreamThreads, 2)
     bwd_stream_kernel(GameView g, StateView<float> st, LevelWork w, int nb_chance, const SetInfo *info,
                       const StreamChunk *chunks, int32_t c0, int32_t c1, int rule, int upd, int *err) {
   extern __shared__ __align__(128) unsigned char s_stage[];
-  __shared__ __align__(8) uint64_t s_bar[kStreamStages];
+  __shared__ __align__(8) uint64_t s_full[kStreamStages], s_empty[kStreamStages], s_rfull[2], s_rempty[2];
   __shared__ StreamChunk s_desc[kStreamStages];
   __shared__ float s_red[2][kStreamWarps][4][2 * MAXA];
-  __shared__ int s_fail;
-  __shared__ int s_issued[kStreamStages];  // a stage has copies in flight or landed, not yet consumed
-  const int nb_wide = w.wc1 - w.wc0;
+  pdl_enter();
   if ((int)blockIdx.x < nb_chance) {
     const int32_t stride = nb_chance * blockDim.x;
     for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride)
       bwd_chance<float, false>(g, st.v, i);
     return;
   }
-  if ((int)blockIdx.x < nb_chance + nb_wide) {
-    bwd_wide_chunk<float, false>(g, w, st.v, w.wc0 + (int32_t)blockIdx.x - nb_chance);
-    return;
-  }
-  const int32_t b = (int32_t)blockIdx.x - nb_chance - nb_wide;
-  const int32_t nb = (int32_t)gridDim.x - nb_chance - nb_wide;
-  const int tid = threadIdx.x;
-  const double wt = avg_weight(*st.t + 1, rule);
+  const int32_t b = (int32_t)blockIdx.x - nb_chance;
+  const int32_t nb = (int32_t)gridDim.x - nb_chance;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool control = tid >= kThreads;
   if ((smem_u32(s_stage) & 15u) != 0u) {  // bulk copies need 16-byte aligned destinations
     if (tid == 0) atomicExch(err, 1);
     return;
   }
-  if (tid == 0) {
+  if (tid == kThreads) {
     for (int s = 0; s < kStreamStages; ++s) {
-      mbar_init(smem_u32(&s_bar[s]), 1);
-      s_issued[s] = 0;
+      mbar_init(smem_u32(&s_full[s]), 1);
+      mbar_init(smem_u32(&s_empty[s]), kStreamThreads);
+    }
+    for (int p = 0; p < 2; ++p) {
+      mbar_init(smem_u32(&s_rfull[p]), kThreads);
+      mbar_init(smem_u32(&s_rempty[p]), 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    s_fail = 0;
-  }
-  __syncthreads();
-  // prologue: the first kStreamStages chunks of this CTA
-  if (tid == 0) {
-    for (int s = 0; s < kStreamStages; ++s) {
+    for (int s = 0; s < kStreamStages; ++s) {  // the first chunks of this CTA
       const int32_t c = c0 + b + s * nb;
       if (c >= c1) break;
       s_desc[s] = chunks[c];
-      if (!stream_issue(s_desc[s], s_stage + s * kStreamStageBytes, smem_u32(&s_bar[s]), st.reach, st.v, g.mem_vs,
+      if (!stream_issue(s_desc[s], s_stage + s * kStreamStageBytes, smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs,
                         info, st.sigma, st.R, st.avg)) {
-        s_fail = 1;
-        atomicExch(err, 1);
+        atomicExch(err, 1);  // a chunk larger than a stage: never issued, every wait below gives up
         break;
       }
-      s_issued[s] = 1;
     }
   }
-  __syncthreads();
-  if (s_fail) return;
-  int par = 0;
+  __syncthreads();  // barriers initialised, first copies issued (the only CTA-wide barrier)
+  const double wt = avg_weight(*st.t + 1, rule);
+  // error exit of the thread that issues copies: let every chunk it issued
+  // and nobody waited for land (bounded waits), then leave
+  auto drain = [&](int32_t i0) {
+    if (tid != kThreads) return;
+    for (int k = 0; k < kStreamStages; ++k)
+      if (c0 + b + (i0 + k) * nb < c1)
+        mbar_wait(smem_u32(&s_full[(i0 + k) % kStreamStages]), (uint32_t)(((i0 + k) / kStreamStages) & 1));
+  };
+  int32_t grp = 0;  // groups done by this CTA (selects red[grp & 1] and the barrier phases)
   for (int32_t i = 0;; ++i) {
     const int32_t c = c0 + b + i * nb;
     if (c >= c1) break;
     const int s = i % kStreamStages;
-    const uint32_t parity = (uint32_t)((i / kStreamStages) & 1);
-    // the descriptor of the chunk this stage takes next (its load overlaps the compute)
-    const int32_t cn = c + kStreamStages * nb;
-    StreamChunk nd;
-    if (tid == 0 && cn < c1) nd = chunks[cn];
-    const bool have = s_issued[s] != 0;
-    if (have && !mbar_wait(smem_u32(&s_bar[s]), parity)) atomicExch(&s_fail, 1);
-    __syncthreads();
-    if (s_fail || !have) {
-      // give up: let the copies still in flight into the other stages land
-      // (bounded), then leave
-      if (tid == 0) {
-        atomicExch(err, 1);
-        for (int k = 1; k < kStreamStages; ++k)
-          if (s_issued[(s + k) % kStreamStages])
-            mbar_wait(smem_u32(&s_bar[(s + k) % kStreamStages]), (uint32_t)(((i + k) / kStreamStages) & 1));
-      }
+    const uint32_t par = (uint32_t)((i / kStreamStages) & 1);
+    if (!mbar_wait(smem_u32(&s_full[s]), par)) {
+      atomicExch(err, 1);
+      drain(i + 1);
       return;
     }
     const StreamChunk d = s_desc[s];
     const StreamLayout L = stream_layout(d);
     const unsigned char *stage = s_stage + s * kStreamStageBytes;
     const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
-    for (int32_t I = d.I0; I < d.I1;) {
+    for (int32_t I = d.I0; I < d.I1; ++grp) {
       const int G = sinfo[I - d.I0].flags & 7;
-      stream_group<MAXA>(d, L, stage, I, st.v, st.sigma, st.R, st.avg, wt, rule, upd, s_red[par]);
-      par ^= 1;
+      const int p = grp & 1;
+      const uint32_t rpar = (uint32_t)((grp >> 1) & 1);
+      if (!control) {
+        float racc[MAXA], macc[MAXA];
+        stream_members<MAXA>(d, L, stage, I, G, st.v, racc, macc);
+        // red[p] is free once the control warp consumed it two groups ago
+        if (grp >= 2 && !mbar_wait(smem_u32(&s_rempty[p]), rpar ^ 1u)) {
+          atomicExch(err, 1);
+          return;
+        }
+        if (lane < G) {
+#pragma unroll
+          for (int a = 0; a < MAXA; ++a) {
+            s_red[p][tid >> 5][lane][a] = racc[a];
+            s_red[p][tid >> 5][lane][MAXA + a] = macc[a];
+          }
+        }
+        mbar_arrive(smem_u32(&s_rfull[p]));
+      } else {
+        if (!mbar_wait(smem_u32(&s_rfull[p]), rpar)) {
+          atomicExch(err, 1);
+          drain(i + 1);
+          return;
+        }
+        stream_update<MAXA>(d, L, stage, I, G, st.sigma, st.R, st.avg, wt, rule, upd, s_red[p]);
+        mbar_arrive(smem_u32(&s_rempty[p]));
+      }
       I += G;
     }
-    __syncthreads();  // every thread is done with the stage
-    if (tid == 0) {
-      s_issued[s] = 0;
+    mbar_arrive(smem_u32(&s_empty[s]));  // this thread is done with stage s
+    if (tid == kThreads) {  // refill stage s with the chunk kStreamStages ahead
+      const int32_t cn = c + kStreamStages * nb;
       if (cn < c1) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        s_desc[s] = nd;
-        if (stream_issue(nd, s_stage + s * kStreamStageBytes, smem_u32(&s_bar[s]), st.reach, st.v, g.mem_vs, info,
-                         st.sigma, st.R, st.avg))
-          s_issued[s] = 1;
-        else
-          atomicExch(err, 1);  // the next wait on this stage sees it unissued and leaves
+        const StreamChunk nd = chunks[cn];
+        if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
+          atomicExch(err, 1);
+          drain(i + 1);
+          return;
+        } else {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          s_desc[s] = nd;
+          if (!stream_issue(nd, s_stage + s * kStreamStageBytes, smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs,
+                            info, st.sigma, st.R, st.avg))
+            atomicExch(err, 1);  // never issued: the next wait on this stage gives up
+        }
       }
     }
   }
+  // every chunk issued was waited on (full[s]) before the loop ended: no
+  // copy is in flight when the CTA leaves
 }
 
 }  // namespace cfr

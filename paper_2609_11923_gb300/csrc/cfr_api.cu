@@ -73,8 +73,11 @@ struct cfr_handle {
   char *arena = nullptr;
   bool bound = false;
   std::vector<void *> pinned;  // host ranges page-locked by cfr_pin_host
-  // graph form
+  // graph form: one iteration per graph (gexec) and, with graph_iters = k > 1,
+  // k iterations per graph (gexec_k)
   cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec_k = nullptr;
+  int64_t graph_kernels = 0, graph_k_kernels = 0;  // kernel nodes of the captured graphs
   cudaStream_t cap_stream = nullptr;
   // persistent form
   int persist_grid = 0;
@@ -86,6 +89,8 @@ struct cfr_handle {
 };
 
 static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void drop_graphs(cfr_handle *h);
 
 static void plan(cfr_handle *h) {
   const Compiled &c = h->c;
@@ -201,7 +206,10 @@ static void build_stream(cfr_handle *h) {
   for (int64_t d = 0; d < c.D; ++d) {
     h->stream_c0[d] = (int32_t)h->stream_chunks.size();
     const int32_t is0 = c.level_iset[2 * d], is1 = c.level_iset[2 * d + 2];
-    bool ok = d > 0 && is1 > is0;  // depth 0 holds only the root (and advances t)
+    // depth 0 holds only the root (and advances t); wide chance nodes are
+    // summed by the per-level kernel's chunk blocks, which the streaming
+    // kernel does not have
+    bool ok = d > 0 && is1 > is0 && c.level_wide[d + 1] == c.level_wide[d];
     std::vector<StreamChunk> ch;
     for (int32_t I = is0; ok && I < is1;) {
       int32_t J = I + (h->set_info[I].flags & 7);
@@ -240,6 +248,8 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   std::string err;
   if (h->opt.reach_order < CFR_REACH_MEMBERS || h->opt.reach_order > CFR_REACH_SLOTS) { delete h; return set_err(CFR_ERR_ARG, "bad reach_order"); }
   if (h->opt.member_tiles < CFR_TILES_AUTO || h->opt.member_tiles > CFR_TILES_ON) { delete h; return set_err(CFR_ERR_ARG, "bad member_tiles"); }
+  if (h->opt.launch_overlap != CFR_OVERLAP_ON && h->opt.launch_overlap != CFR_OVERLAP_OFF) { delete h; return set_err(CFR_ERR_ARG, "bad launch_overlap"); }
+  if (h->opt.graph_iters < 0 || h->opt.graph_iters > 1000) { delete h; return set_err(CFR_ERR_ARG, "graph_iters must be in [0, 1000]"); }
   int rc = compile_game(*spec, h->c, err, h->opt.reach_order, h->opt.member_tiles);
   if (rc != CFR_OK) { delete h; return set_err(rc, "cfr_compile: %s", err.c_str()); }
   const Compiled &c = h->c;
@@ -300,6 +310,7 @@ extern "C" void cfr_destroy(cfr_handle *h) {
   if (!h) return;
   for (void *p : h->pinned) cudaHostUnregister(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gexec_k) cudaGraphExecDestroy(h->gexec_k);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -320,6 +331,8 @@ extern "C" int cfr_get_counts(const cfr_handle *h, cfr_counts *o) {
                               h->b_stream_chunks.bytes);
   o->iteration = h->iteration_host;
   o->exec_form = h->exec_form;
+  o->graph_kernels = h->gexec ? h->graph_kernels : 0;
+  o->graph_k_kernels = h->gexec_k ? h->graph_k_kernels : 0;
   o->lanes_per_set = h->exec_form == CFR_EXEC_PERSISTENT ? h->persist_lanes : (c.D > 0 ? h->level_lanes[c.D - 1] : 0);
   return CFR_OK;
 }
@@ -379,20 +392,18 @@ static int grid_for(int64_t work, int per_block) {
 // nodes take the form that writes those children warp-wide.
 template <typename T>
 static int launch_fwd(const cfr_handle *h, int64_t d, cudaStream_t s, const GameView &g, const T *sigma,
-                      vec2_t<T> *reach) {
+                      vec2_t<T> *reach, bool pdl = false) {
   const LevelWork &w = h->levels[d];
   if (g.int_edge) {  // member order: the next depth's internal nodes pull their reach
     if (d + 1 >= h->c.D) return CFR_OK;
     const LevelWork &n = h->levels[d + 1];
     const int nb = grid_for((n.ie - n.ib + kPull - 1) / kPull, kThreads);
-    fwd_pull_kernel<T><<<nb, kThreads, 0, s>>>(g, sigma, reach, n.ib, n.ie);
-    CK(cudaGetLastError());
+    CK(launch_k(fwd_pull_kernel<T>, nb, kThreads, 0, s, pdl, g, sigma, reach, n.ib, n.ie));
     return CFR_OK;
   }
   const int nb = grid_for((w.ie - w.ib + 3) / 4, kThreads);
-  if (w.fan) fwd_level_kernel<T, true><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, sigma, reach, w, nb);
-  else fwd_level_kernel<T, false><<<nb + (w.wc1 - w.wc0), kThreads, 0, s>>>(g, sigma, reach, w, nb);
-  CK(cudaGetLastError());
+  if (w.fan) CK(launch_k(fwd_level_kernel<T, true>, nb + (w.wc1 - w.wc0), kThreads, 0, s, pdl, g, sigma, reach, w, nb));
+  else CK(launch_k(fwd_level_kernel<T, false>, nb + (w.wc1 - w.wc0), kThreads, 0, s, pdl, g, sigma, reach, w, nb));
   return CFR_OK;
 }
 
@@ -438,6 +449,33 @@ static std::vector<std::pair<const void *, size_t>> host_ranges(const cfr_handle
   return r;
 }
 
+extern "C" int cfr_set_chance_sums(const cfr_handle *h, const double *root_w, double *mass, double *wsum) {
+  if (!h || (!mass && h->c.I > 0) || (root_w && !wsum && h->c.I > 0))
+    return set_err(CFR_ERR_ARG, "cfr_set_chance_sums: null argument");
+  const Compiled &c = h->c;
+  std::vector<int32_t> owner;  // root outcome above each node (breadth-first ids: parents first)
+  if (root_w) {
+    if (c.N == 0 || c.child_begin[1] == c.child_begin[0] || c.node_slot[0] >= 0)
+      return set_err(CFR_ERR_UNSUPPORTED, "cfr_set_chance_sums: the root is not a chance node");
+    owner.assign(c.N, -1);
+    for (int32_t x = c.child_begin[0]; x < c.child_begin[1]; ++x) owner[x] = x - c.child_begin[0];
+    for (int64_t h2 = 1; h2 < c.N; ++h2)
+      for (int32_t x = c.child_begin[h2]; x < c.child_begin[h2 + 1]; ++x) owner[x] = owner[h2];
+  }
+  for (int64_t q = 0; q < c.I; ++q) {
+    double m = 0.0, w = 0.0;
+    for (int32_t k = c.iset_mem[q]; k < c.iset_mem[q + 1]; ++k) {
+      const int32_t hh = c.mem_node[k];
+      m += c.pc[hh];
+      if (root_w) w += c.pc[hh] * root_w[owner[hh]];
+    }
+    const int32_t sp = c.spec_set_of[q];
+    mass[sp] = m;
+    if (root_w) wsum[sp] = w;
+  }
+  return CFR_OK;
+}
+
 extern "C" int cfr_pin_host(cfr_handle *h, int pin) {
   if (!h) return set_err(CFR_ERR_ARG, "cfr_pin_host: null handle");
   if (!pin) {
@@ -470,7 +508,7 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if (bytes < h->plan_bytes) return set_err(CFR_ERR_ARENA_SMALL, "cfr_bind: arena has %zu bytes, plan needs %zu", bytes, h->plan_bytes);
   if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return set_err(CFR_ERR_ARG, "cfr_bind: arena must be 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  drop_graphs(h);
   h->arena = (char *)arena;
   const Compiled &c = h->c;
   auto up = [&](const Buf &b, const void *src, size_t n) -> int {
@@ -548,7 +586,7 @@ static void bwd_blocks(const cfr_handle *h, int d, int *nb_ch, int *nb_wide, int
 // upd: the players whose sets update (bit 0 player 1, bit 1 player 2); the
 // depth-0 launch of the pass that updates player 2 advances t.
 template <typename T>
-static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3) {
+static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3, bool pdl = false) {
   LevelWork w = h->levels[d];
   if (d == 0) {  // a chance root's value has no reader in an iteration (the best response sums its own)
     w.ch1 = w.ch0;
@@ -557,32 +595,39 @@ static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3) {
   int nb_ch, nb_wide, nb_is;
   bwd_blocks(h, d, &nb_ch, &nb_wide, &nb_is);
   const int lanes = h->level_lanes[d];
-  if (lanes == kStreamLanes) {  // FP32 only (compile checks it)
-    CK(launch_bwd_stream(h->maxa_tier, nb_ch + nb_wide + nb_is, s, game_view(h), state_view<float>(h), w, nb_ch,
+  if (lanes == kStreamLanes) {  // FP32 only (compile checks it); no wide chance nodes at this depth
+    CK(launch_bwd_stream(h->maxa_tier, nb_ch + nb_is, s, game_view(h), state_view<float>(h), w, nb_ch,
                          h->p<SetInfo>(h->b_set_info), h->p<StreamChunk>(h->b_stream_chunks), h->stream_c0[d],
-                         h->stream_c0[d + 1], h->rule, upd, h->p<int>(h->b_err)));
+                         h->stream_c0[d + 1], h->rule, upd, h->p<int>(h->b_err), pdl));
     return CFR_OK;
   }
   // at least one block: the depth-0 launch also advances t
   CK(launch_bwd_level<T>(h->maxa_tier, lanes, std::max(1, nb_ch + nb_wide + nb_is), s, game_view(h), state_view<T>(h),
-                         w, nb_ch, h->rule, upd, (d == 0 && (upd & 2)) ? 1 : 0));
+                         w, nb_ch, h->rule, upd, (d == 0 && (upd & 2)) ? 1 : 0, pdl));
   return CFR_OK;
 }
 
+// One iteration's launches. Every launch but the first of the iteration may
+// overlap its predecessor's tail (programmatic dependent launch).
 template <typename T>
-static int enqueue_iteration(cfr_handle *h, cudaStream_t s) {
+static int enqueue_iteration(cfr_handle *h, cudaStream_t s, bool first_overlaps = false) {
   const Compiled &c = h->c;
   GameView g = game_view(h);
   const int halves = h->order == CFR_ORDER_ALTERNATING ? 2 : 1;
+  const bool ov = h->opt.launch_overlap == CFR_OVERLAP_ON;
+  bool pdl = ov && first_overlaps;
   for (int hf = 0; hf < halves; ++hf) {
     const int upd = halves == 2 ? (1 << hf) : 3;
     for (int64_t d = 0; d < c.D; ++d) {
-      int rc = launch_fwd<T>(h, d, s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach));
+      if (g.int_edge && d + 1 >= c.D) continue;  // member order: no launch for the deepest depth
+      int rc = launch_fwd<T>(h, d, s, g, h->p<T>(h->b_sigma), h->p<vec2_t<T>>(h->b_reach), pdl);
       if (rc) return rc;
+      pdl = ov;
     }
     for (int64_t d = c.D - 1; d >= 0; --d) {
-      int rc = launch_bwd<T>(h, (int)d, s, upd);
+      int rc = launch_bwd<T>(h, (int)d, s, upd, pdl);
       if (rc) return rc;
+      pdl = ov;
     }
   }
   return CFR_OK;
@@ -636,6 +681,64 @@ static int launch_persistent_form(cfr_handle *h, int64_t n, cudaStream_t s) {
   return CFR_OK;
 }
 
+// Captures `iters` iterations into an executable graph. A refused capture
+// (or instantiation) warns once per handle and sets *failed.
+template <typename T>
+static int capture_iterations(cfr_handle *h, int iters, cudaGraphExec_t *out, bool *failed, int64_t *kernels) {
+  *failed = false;
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = CFR_OK;
+  for (int i = 0; i < iters && rc == CFR_OK; ++i) rc = enqueue_iteration<T>(h, h->cap_stream, i > 0);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e == cudaSuccess && h->test_fail_capture) {  // test hook: the same path as a refused capture
+    cudaGraphDestroy(graph);
+    graph = nullptr;
+    e = cudaErrorStreamCaptureUnsupported;
+  }
+  if (e == cudaSuccess) {  // count the kernel nodes (the launch-count gate)
+    size_t nn = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int64_t nk = 0;
+    for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+      cudaGraphNodeType ty;
+      e = cudaGraphNodeGetType(nodes[i], &ty);
+      if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+    }
+    *kernels = nk;
+  }
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (e != cudaSuccess) *out = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    // capture failed: warn once, fall back to per-level launches (same kernels, same order)
+    if (!h->capture_warned) {
+      fprintf(stderr, "cfr: graph capture failed (%s); using per-level launches\n", cudaGetErrorString(e));
+      fflush(stderr);
+      h->capture_warned = true;
+    }
+    cudaGetLastError();
+    *failed = true;
+  }
+  return CFR_OK;
+}
+
+static void drop_graphs(cfr_handle *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gexec_k) cudaGraphExecDestroy(h->gexec_k);
+  h->gexec = nullptr;
+  h->gexec_k = nullptr;
+}
+
 template <typename T>
 static int iterate_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   if (h->c.D == 0) {  // root is terminal: nothing to update but the counter
@@ -645,42 +748,33 @@ static int iterate_t(cfr_handle *h, int64_t n, cudaStream_t s) {
   }
   if (h->exec_form == CFR_EXEC_LEVELS) {
     for (int64_t i = 0; i < n; ++i) {
-      int rc = enqueue_iteration<T>(h, s);
+      int rc = enqueue_iteration<T>(h, s, i > 0);
       if (rc) return rc;
     }
     return CFR_OK;
   }
   if (h->exec_form == CFR_EXEC_PERSISTENT) return launch_persistent_form<T>(h, n, s);
-  // graph form: capture one iteration once, replay it n times (cfr_bind drops
-  // the graph, so a replay always refers to the bound arena)
-  if (!h->gexec) {
-    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_iteration<T>(h, h->cap_stream);
-    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
-    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
-    if (e == cudaSuccess && h->test_fail_capture) {  // test hook: the same path as a refused capture
-      cudaGraphDestroy(graph);
-      graph = nullptr;
-      e = cudaErrorStreamCaptureUnsupported;
-    }
-    if (e != cudaSuccess) {
-      // capture failed: warn once, fall back to per-level launches (same kernels, same order)
-      if (!h->capture_warned) {
-        fprintf(stderr, "cfr: graph capture failed (%s); using per-level launches\n", cudaGetErrorString(e));
-        fflush(stderr);
-        h->capture_warned = true;
-      }
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      h->exec_form = CFR_EXEC_LEVELS;
-      return iterate_t<T>(h, n, s);
-    }
-    CK(cudaGraphInstantiate(&h->gexec, graph, 0));
-    cudaGraphDestroy(graph);
+  // graph form: k iterations per graph (k = graph_iters) replayed n / k
+  // times, and a one-iteration graph for the rest; both captured on first
+  // use (cfr_bind drops them, so a replay always refers to the bound arena)
+  const int k = std::max(1, h->opt.graph_iters);
+  const int64_t nk = k > 1 ? n / k : 0, n1 = n - nk * k;
+  bool failed = false;
+  if (nk > 0 && !h->gexec_k) {
+    int rc = capture_iterations<T>(h, k, &h->gexec_k, &failed, &h->graph_k_kernels);
+    if (rc) return rc;
   }
-  for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(h->gexec, s));
+  if (!failed && n1 > 0 && !h->gexec) {
+    int rc = capture_iterations<T>(h, 1, &h->gexec, &failed, &h->graph_kernels);
+    if (rc) return rc;
+  }
+  if (failed) {
+    drop_graphs(h);
+    h->exec_form = CFR_EXEC_LEVELS;
+    return iterate_t<T>(h, n, s);
+  }
+  for (int64_t i = 0; i < nk; ++i) CK(cudaGraphLaunch(h->gexec_k, s));
+  for (int64_t i = 0; i < n1; ++i) CK(cudaGraphLaunch(h->gexec, s));
   return CFR_OK;
 }
 
@@ -1148,7 +1242,7 @@ extern "C" int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream) {
 // (2D, or 2D - 1 in member order; same grid sizes) of an empty kernel
 // captured in one graph, and one cooperative launch of an empty kernel with
 // the persistent form's grid and its 2D grid barriers per iteration.
-static __global__ void empty_level_kernel() {}
+static __global__ void empty_level_kernel() { pdl_enter(); }
 
 static __global__ void __launch_bounds__(kThreads) empty_persistent_kernel(Barrier bar, int n_sync, long long n_iter) {
   for (long long it = 0; it < n_iter; ++it)
@@ -1182,8 +1276,12 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
   cudaGraphExec_t ge = nullptr;
   const int halves = h->order == CFR_ORDER_ALTERNATING ? 2 : 1;
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  bool pdl = false;  // the same programmatic dependencies as the iteration's launches
   for (int hf = 0; hf < halves; ++hf)
-    for (int gsz : grids) empty_level_kernel<<<std::max(gsz, 1), kThreads, 0, h->cap_stream>>>();
+    for (int gsz : grids) {
+      CK(launch_k(empty_level_kernel, std::max(gsz, 1), kThreads, 0, h->cap_stream, pdl));
+      pdl = h->opt.launch_overlap == CFR_OVERLAP_ON;
+    }
   CK(cudaStreamEndCapture(h->cap_stream, &graph));
   cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
   cudaGraphDestroy(graph);
@@ -1262,7 +1360,9 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
     int best = h->level_lanes[d];
     float best_ms = 1e30f;
     std::vector<int> cd = cand;
-    if (h->stream_ok[d]) cd.push_back(kStreamLanes);
+    // the streaming form works on one group of sets at a time with the whole
+    // CTA: a candidate only where sets are long
+    if (h->stream_ok[d] && c.level_mean_members[d] >= kStreamMinMembers) cd.push_back(kStreamLanes);
     for (int L : cd) {
       h->level_lanes[d] = L;
       rc = h->precision == CFR_P64 ? launch_bwd<double>(h, (int)d, s) : launch_bwd<float>(h, (int)d, s);
@@ -1300,7 +1400,7 @@ extern "C" int cfr_autotune(cfr_handle *h, int reps, void *stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  drop_graphs(h);
   CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
   rc = h->precision == CFR_P64 ? init_state<double>(h, s) : init_state<float>(h, s);

@@ -182,6 +182,10 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
     c.vslot.assign(N, -1);
     c.vslot[0] = (int32_t)(N - 1);
     c.iset_vb.assign(I, 0);
+    // the value-slot reach order ranks internal nodes by their block position
+    // taken member-major (member, then action), so that a parent's internal
+    // children stay consecutive for the pushing forward
+    std::vector<int64_t> slot_key(N, (int64_t)N - 1);
     {
       std::vector<int32_t> order;
       order.reserve(I);
@@ -207,14 +211,19 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
         for (size_t q = c.level_iset[2 * d]; q < order.size(); ++q) {  // value slots of depth d + 1
           const int32_t is = order[q];
           c.iset_vb[q] = (int32_t)next;
-          for (int64_t m = smb[is]; m < smb[is + 1]; ++m) {
-            const int32_t h = smem[m];
-            for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
-          }
+          // action-major: the children of action a of all members, in member order, then action a + 1
+          const int32_t na = s.iset_nact[is];
+          for (int64_t m = smb[is]; m < smb[is + 1]; ++m)
+            for (int32_t a = 0; a < na; ++a) slot_key[c.child_begin[smem[m]] + a] = next + (m - smb[is]) * na + a;
+          for (int32_t a = 0; a < na; ++a)
+            for (int64_t m = smb[is]; m < smb[is + 1]; ++m) c.vslot[c.child_begin[smem[m]] + a] = (int32_t)next++;
         }
         for (int64_t h = c.level_begin[d]; h < c.level_begin[d + 1]; ++h) {
           if (s.kind[c.spec_of_new[h]] != CFR_CHANCE) continue;
-          for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) c.vslot[x] = (int32_t)next++;
+          for (int32_t x = c.child_begin[h]; x < c.child_begin[h + 1]; ++x) {
+            slot_key[x] = next;
+            c.vslot[x] = (int32_t)next++;
+          }
         }
         i = j;
       }
@@ -222,6 +231,7 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
       if (i != enc.size()) return fail(err, "internal: information set below the deepest parent");
       if (next != N - 1) return fail(err, "internal error: value slots do not cover the tree");
       for (size_t q = 0; q < order.size(); ++q) cid_of_spec[order[q]] = (int32_t)q;
+      c.spec_set_of.assign(order.begin(), order.end());
       c.iset_slot.assign(I + 1, 0);
       c.spec_slot_of.assign(A, 0);
       for (int64_t q = 0; q < I; ++q) {
@@ -366,7 +376,7 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
       } else if (reach_order == CFR_REACH_SLOTS) {
         if (N > 0 && c.child_begin[1] > c.child_begin[0]) rank[0] = r++;
         std::vector<int32_t> node_of_slot(N > 0 ? N - 1 : 0);
-        for (int64_t h = 1; h < N; ++h) node_of_slot[c.vslot[h]] = (int32_t)h;
+        for (int64_t h = 1; h < N; ++h) node_of_slot[slot_key[h]] = (int32_t)h;
         for (int64_t q = 0; q + 1 < N; ++q) {
           const int32_t h = node_of_slot[q];
           if (c.child_begin[h + 1] > c.child_begin[h]) rank[h] = r++;

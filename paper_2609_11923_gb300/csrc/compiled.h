@@ -79,12 +79,18 @@ struct Compiled {
   std::vector<int32_t> wide_irank;   // [n_wide] internal rank of each wide node
   // Value slots. The value of node h lives in slot vslot[h] of the value
   // array (not at h): the children of the members of one information set
-  // fill one block of slots (members in member order, each member's children
-  // in action order), the children of one chance node another. Blocks go by
-  // parent depth; within a depth the sets' blocks (set order) come before the
-  // chance nodes' (node order). The root takes the last slot, N-1. A set's
-  // backward pass therefore reads its members' children as one contiguous
-  // run; each node writes its own value to the one slot its parent reads.
+  // fill one block of slots, action-major (child a of every member in member
+  // order, then action a + 1: child a of member k at block + a * M + k - m0),
+  // the children of one chance node another. Blocks go by parent depth;
+  // within a depth the sets' blocks (set order) come before the chance
+  // nodes' (node order). The root takes the last slot, N-1. A set's backward
+  // pass therefore reads its members' children as one contiguous run (and
+  // each action's as a run of its own); each node writes its own value to
+  // the one slot its parent reads. Action-major keeps the children that
+  // are written (decision and chance nodes) apart from those that are not
+  // (terminals, which keep their template value), and puts the writes of
+  // the sets of one tile (neighbouring members of the parent set) into
+  // neighbouring words.
   std::vector<int32_t> vslot;        // [N]
   std::vector<int32_t> iset_vb;      // [I] first slot of set I's block
   std::vector<int32_t> mem_vs;       // [n_dec] own value slot of each member (member order)
@@ -100,6 +106,7 @@ struct Compiled {
   std::vector<int32_t> spec_slot_of; // [A] spec slot of each compiled slot
   std::vector<int32_t> level_max_members; // [D] largest information set per depth
   std::vector<double> level_mean_members; // [D]
+  std::vector<int32_t> spec_set_of;  // [I] the spec's id of each compiled set
 };
 
 // Returns CFR_OK or CFR_ERR_INVALID_SPEC / CFR_ERR_HOST_MEMORY with a message.

@@ -1,17 +1,16 @@
 // Backward-level kernel instances, P32 (see kernels.cuh).
 #include "launch_impl.cuh"
 namespace cfr {
-template cudaError_t launch_bwd_level<float>(int, int, int, cudaStream_t, GameView, StateView<float>, LevelWork, int, int, int, int);
+template cudaError_t launch_bwd_level<float>(int, int, int, cudaStream_t, GameView, StateView<float>, LevelWork, int, int, int, int, bool);
 }
 
 namespace cfr {
 template <int MA>
 static cudaError_t stream_one(int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w, int nb_chance,
                               const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
-                              int *err) {
-  bwd_stream_kernel<MA><<<grid, kThreads, kStreamStages * kStreamStageBytes, s>>>(g, st, w, nb_chance, info, chunks,
-                                                                                 c0, c1, rule, upd, err);
-  return cudaGetLastError();
+                              int *err, bool pdl) {
+  return launch_k(bwd_stream_kernel<MA>, grid, kStreamThreads, (size_t)(kStreamStages * kStreamStageBytes), s, pdl, g, st, w,
+                  nb_chance, info, chunks, c0, c1, rule, upd, err);
 }
 
 cudaError_t prepare_bwd_stream() {
@@ -24,9 +23,9 @@ cudaError_t prepare_bwd_stream() {
 
 cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w,
                               int nb_chance, const SetInfo *info, const StreamChunk *chunks, int c0, int c1,
-                              int rule, int upd, int *err) {
-  if (maxa == 4) return stream_one<4>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err);
-  if (maxa == 8) return stream_one<8>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err);
+                              int rule, int upd, int *err, bool pdl) {
+  if (maxa == 4) return stream_one<4>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err, pdl);
+  if (maxa == 8) return stream_one<8>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err, pdl);
   return cudaErrorInvalidValue;
 }
 }  // namespace cfr

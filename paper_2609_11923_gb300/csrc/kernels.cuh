@@ -51,6 +51,17 @@ __device__ __forceinline__ X ldm(const X *p) {
   else return *p;
 }
 
+// Programmatic dependent launch between the per-level kernels: every such
+// kernel first waits until the launch before it has completed and its
+// writes are visible (griddepcontrol.wait; a no-op without a programmatic
+// dependency), then lets the next launch start being scheduled
+// (launch_dependents), so the next kernel's launch and block scheduling
+// overlap this kernel's tail instead of following it.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 constexpr int32_t kWideNode = 1024;   // chance nodes above this fan-out go by chunks
 constexpr int32_t kWideChunkK = 2048; // children per chunk of a wide node
 
@@ -58,8 +69,9 @@ struct GameView {
   const int32_t *__restrict__ iset_slot;
   const int32_t *__restrict__ iset_mem;
   // value slots: a set's members' children form one block starting at
-  // iset_vb[I] (member-major, action-minor); every node writes its own value
-  // to the slot its parent reads (mem_vs, ch_vs, wide_vs)
+  // iset_vb[I] (action-major: child a of member k at iset_vb[I] + a * M +
+  // (k - first member), M members); every node writes its own value to the
+  // slot its parent reads (mem_vs, ch_vs, wide_vs)
   const int32_t *__restrict__ iset_vb;
   const int32_t *__restrict__ mem_vs;
   const int32_t *__restrict__ ch_vb;       // narrow chance nodes: children's block,
@@ -300,6 +312,7 @@ __device__ __forceinline__ void fwd_wide_chunk(const GameView &g, const LevelWor
 template <typename T, bool FAN>
 __global__ void __launch_bounds__(kThreads) fwd_level_kernel(GameView g, const T *sigma, vec2_t<T> *reach,
                                                             LevelWork w, int nb_nodes) {
+  pdl_enter();
   if ((int)blockIdx.x >= nb_nodes) {
     fwd_wide_chunk<T, false>(g, w, reach, w.wc0 + (int32_t)blockIdx.x - nb_nodes);
     return;
@@ -349,6 +362,7 @@ __device__ __forceinline__ void fwd_pull(const GameView &g, const T *sigma, vec2
 template <typename T>
 __global__ void __launch_bounds__(kThreads) fwd_pull_kernel(GameView g, const T *sigma, vec2_t<T> *reach,
                                                             int32_t qb, int32_t qe) {
+  pdl_enter();
   const int32_t stride = gridDim.x * blockDim.x;
   for (int32_t q = qb + blockIdx.x * blockDim.x + threadIdx.x; q < qe; q += kPull * stride)
     fwd_pull<T, false>(g, sigma, reach, q, stride, qe);
@@ -466,9 +480,9 @@ __device__ __forceinline__ void member_idx(const GameView &g, int32_t k, int32_t
 }
 
 // Loads and per-member terms of one member (k < m1) whose indices are
-// already known, or zeros. The member's children are slots
-// vb + (k - m0) * na .. + na - 1 of the set's block: the group's lanes read
-// consecutive members' children as one run. The average-strategy terms are
+// already known, or zeros. The member's child a is slot vb + a * M + (k -
+// m0) of the set's block (M = m1 - m0 members): for each action the group's
+// lanes read consecutive members' children as one run. The average-strategy terms are
 // pw * sigma(a). LEAN (FP32 only): only pw is carried (mm[0]) and the set's
 // sum of pw is multiplied by sigma(a) once (avg_terms), which frees
 // registers where the budget is tight; otherwise each product is added, in
@@ -480,14 +494,14 @@ __device__ __forceinline__ void member_data(const GameView &g, const StateView<T
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) { d[a] = T(0); mm[a] = T(0); }
   if (k >= m1) return;
-  const int32_t cb = vb + (k - m0) * na;
+  const int32_t cb = vb + (k - m0), M = m1 - m0;
   const vec2_t<T> r = ldm<PERSIST>(st.reach + ir);
   T vc[MAXA];
   T vh = T(0);
 #pragma unroll
   for (int a = 0; a < MAXA; ++a) {
     if (a < na) {
-      vc[a] = ldm<PERSIST>(st.v + cb + a);
+      vc[a] = ldm<PERSIST>(st.v + cb + a * M);
       vh = vh + sig[a] * vc[a];
     }
   }
@@ -825,6 +839,7 @@ __device__ __forceinline__ void bwd_set_block(const GameView &g, const StateView
 template <typename T, int MAXA, int LANES>
 __global__ void __launch_bounds__(kThreads, MAXA <= 4 ? 4 : (MAXA <= 8 ? 3 : 1)) bwd_level_kernel(GameView g, StateView<T> st, LevelWork w,
                                                             int nb_chance, int rule, int upd, int bump_t) {
+  pdl_enter();
   const int nb_wide = w.wc1 - w.wc0;
   if ((int)blockIdx.x < nb_chance) {
     const int32_t stride = nb_chance * blockDim.x;
@@ -1129,17 +1144,17 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
       for (int a = 0; a < MAXA; ++a) q[a] = 0.0;
       if (k < m1) {
         const int32_t h = __ldg(g.mem_vs + k);
-        const int32_t cb = vb0 + (k - m0) * na;
+        const int32_t cb = vb0 + (k - m0), M = m1 - m0;
         const double2 r = reach2[member_rank(g, k, mr)];
         const double po = p ? r.x : r.y;
         double oth = 0.0, va = 0.0;
 #pragma unroll
         for (int a = 0; a < MAXA; ++a) {
           if (a < na) {
-            const double2 x = vb[cb + a];
+            const double2 x = vb[cb + a * M];
             q[a] = po * (p ? x.y : x.x);
             oth += sg[a] * (p ? x.x : x.y);
-            va += sg[a] * vavg[cb + a];
+            va += sg[a] * vavg[cb + a * M];
           }
         }
         reinterpret_cast<double *>(vb + h)[1 - p] = oth;
@@ -1159,8 +1174,8 @@ __global__ void __launch_bounds__(kThreads) br_level_kernel(GameView g, const do
     // best agrees across the group without another shuffle
     for (int32_t k = m0 + lane; k < m1; k += LANES) {
       const int32_t h = __ldg(g.mem_vs + k);
-      const int32_t cb = vb0 + (k - m0) * na;
-      reinterpret_cast<double *>(vb + h)[p] = reinterpret_cast<const double *>(vb + cb + best)[p];
+      const int32_t cb = vb0 + (k - m0) + best * (m1 - m0);
+      reinterpret_cast<double *>(vb + h)[p] = reinterpret_cast<const double *>(vb + cb)[p];
     }
   }
 }

@@ -9,18 +9,36 @@
 
 namespace cfr {
 
+// Launch of a per-level kernel; with pdl set, as a programmatic dependent
+// launch (the kernel waits for its predecessor itself: pdl_enter).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                            Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // The streaming FP32 backward of one depth (bwd_stream_kernel); grid =
 // nb_chance + nb_wide + the streaming CTAs over chunks [c0, c1).
 cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w,
                               int nb_chance, const SetInfo *info, const StreamChunk *chunks, int c0, int c1,
-                              int rule, int upd, int *err);
+                              int rule, int upd, int *err, bool pdl);
 // Allows the streaming kernel its dynamic shared memory (call before the
 // first launch, outside any stream capture; idempotent).
 cudaError_t prepare_bwd_stream();
 
 template <typename T>
 cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, GameView g, StateView<T> st,
-                             LevelWork w, int nb_chance, int rule, int upd, int bump);
+                             LevelWork w, int nb_chance, int rule, int upd, int bump, bool pdl = false);
 
 // query_occupancy != nullptr: only report resident blocks per SM of the
 // chosen instance (nothing is launched).

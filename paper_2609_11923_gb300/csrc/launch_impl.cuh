@@ -6,12 +6,10 @@ namespace cfr {
 
 template <typename T>
 cudaError_t launch_bwd_level(int maxa, int lanes, int grid, cudaStream_t s, GameView g, StateView<T> st,
-                             LevelWork w, int nb_chance, int rule, int upd, int bump) {
-#define BWD_CASE(MA, L)                                                                         \
-  if (maxa == MA && lanes == L) {                                                               \
-    bwd_level_kernel<T, MA, L><<<grid, kThreads, 0, s>>>(g, st, w, nb_chance, rule, upd, bump); \
-    return cudaGetLastError();                                                                  \
-  }
+                             LevelWork w, int nb_chance, int rule, int upd, int bump, bool pdl) {
+#define BWD_CASE(MA, L)                                                                                     \
+  if (maxa == MA && lanes == L)                                                                             \
+    return launch_k(bwd_level_kernel<T, MA, L>, grid, kThreads, 0, s, pdl, g, st, w, nb_chance, rule, upd, bump);
   BWD_CASE(4, 1) BWD_CASE(4, 2) BWD_CASE(4, 4) BWD_CASE(4, 8) BWD_CASE(4, 16) BWD_CASE(4, 32) BWD_CASE(4, kThreads)
   BWD_CASE(8, 1) BWD_CASE(8, 2) BWD_CASE(8, 4) BWD_CASE(8, 8) BWD_CASE(8, 16) BWD_CASE(8, 32) BWD_CASE(8, kThreads)
   BWD_CASE(64, 4) BWD_CASE(64, 8) BWD_CASE(64, 16) BWD_CASE(64, 32)

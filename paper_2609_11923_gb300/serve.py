@@ -256,17 +256,18 @@ class Server:
                         keep_a.append(a)
                 active = keep_a
             # compile failures are answered; the rest is admitted in arrival order
-            ready = []
-            for i, (r, fut) in enumerate(waiting):
+            ready, errored = [], set()
+            for r, fut in waiting:
                 if not fut.done():
                     break  # keep arrival order: later compiles wait for earlier ones
                 h = fut.result()
                 if isinstance(h, Exception):
                     answer(r, "error", str(h))
+                    errored.add(id(r))
                     continue
                 ready.append((r, fut, h))
-            errored = {id(r) for r, fut in waiting if fut.done() and isinstance(fut.result(), Exception)}
-            waiting = [(r, fut) for r, fut in waiting if id(r) not in errored]
+            if errored:
+                waiting = [(r, fut) for r, fut in waiting if id(r) not in errored]
             if ready:
                 adm, rej, head = admit(ready, self.max_active - len(active), self.pool,
                                        lambda e: cfr.cfr_plan(e[2]), head, self.hol_rounds, key=lambda e: e[0].rid)

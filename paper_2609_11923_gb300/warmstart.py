@@ -58,33 +58,6 @@ def _rank3_vec(r0, r1, r2):
     return cat, val
 
 
-def chance_mass(spec, with_deal: bool = False):
-    """Chance probability of reaching every node (product along the path);
-    with_deal also returns the index of each node's root outcome."""
-    N = spec.n_nodes
-    pc = np.zeros(N)
-    pc[0] = 1.0
-    deal = np.full(N, -1, dtype=np.int64)
-    frontier = np.array([0], dtype=np.int64)
-    cb_all, ch_all = spec.child_begin, spec.child
-    while frontier.size:
-        cb = cb_all[frontier]
-        cnt = cb_all[frontier + 1] - cb
-        tot = int(cnt.sum())
-        if tot == 0:
-            break
-        start = np.repeat(cb, cnt)
-        off = np.arange(tot) - np.repeat(np.cumsum(cnt) - cnt, cnt)
-        e = start + off
-        kids = ch_all[e].astype(np.int64)
-        par = np.repeat(frontier, cnt)
-        mult = np.where(spec.kind[par] == 1, spec.chance_prob[e], 1.0)
-        pc[kids] = pc[par] * mult
-        deal[kids] = np.where(par == 0, off, deal[par])
-        frontier = kids
-    return (pc, deal) if with_deal else pc
-
-
 def checkdown_value(spec) -> np.ndarray:
     """Player-1 payoff of the line that takes action 0 everywhere below each
     root outcome (check-check to the showdown in the card games)."""
@@ -98,9 +71,13 @@ def checkdown_value(spec) -> np.ndarray:
     return spec.payoff[cur]
 
 
-def features(spec, return_mass: bool = False) -> tuple:
+def features(spec, return_mass: bool = False, handle: Optional[int] = None) -> tuple:
     """(X [I, F_IN] float32, nact [I] int32) for every information set
-    (and the sets' chance masses when return_mass)."""
+    (and the sets' chance masses when return_mass). The chance sums behind
+    the range weight and the equity come from the compiled game (the
+    library's cfr_set_chance_sums over the chance products the compiler
+    folded); handle: an already compiled handle of spec (else one is
+    compiled here and released)."""
     f = spec.iset_feat
     if f is None:
         raise ValueError("features need the card-game metadata of the generator")
@@ -127,15 +104,19 @@ def features(spec, return_mass: bool = False) -> tuple:
     X[:, 169] = c2 / 10.0
     me, op = np.where(f[:, 0] == 0, c1, c2), np.where(f[:, 0] == 0, c2, c1)
     X[:, 170] = (op - me) / 10.0
-    # relative range weight: chance mass of the set over the mean of its public state
-    pc, deal = chance_mass(spec, with_deal=True)
-    dec = spec.infoset >= 0
-    mass = np.bincount(spec.infoset[dec], weights=pc[dec], minlength=I)
-    # equity against the opponent's range at the check-down showdown
+    # relative range weight: chance mass of the set over the mean of its
+    # public state; equity against the opponent's range at the check-down
+    # showdown: the chance-weighted share of the set's deals player 1 wins
     sd = checkdown_value(spec)
     win1 = (1.0 + np.sign(sd)) / 2.0
-    node_w = np.where(deal[dec] >= 0, win1[np.maximum(deal[dec], 0)], 0.5)
-    eq1 = np.bincount(spec.infoset[dec], weights=pc[dec] * node_w, minlength=I) / np.maximum(mass, 1e-300)
+    own = handle is None
+    h = cfr.cfr_compile(spec, cfr.make_options(precision=cfr.P32)) if own else handle
+    try:
+        mass, wsum = cfr.cfr_set_chance_sums(h, I, win1)
+    finally:
+        if own:
+            cfr.cfr_destroy(h)
+    eq1 = wsum / np.maximum(mass, 1e-300)
     eq = np.where(f[:, 0] == 0, eq1, 1.0 - eq1)
     X[:, 172] = eq
     X[rows, 173 + np.clip((eq * 10).astype(np.int64), 0, 9)] = 1.0
@@ -162,16 +143,23 @@ def _pad_slots(spec, vec) -> np.ndarray:
     return out
 
 
-def solve_batch(specs, iters: int, precision=cfr.P32, threads=1024, lanes=8, chunk=256, init=None):
-    """Average strategies of `specs` after `iters` CFR+ iterations (batched)."""
+def solve_batch(specs, iters: int, precision=cfr.P32, threads=1024, lanes=8, chunk=256, init=None,
+                with_features: bool = False):
+    """Average strategies of `specs` after `iters` CFR+ iterations (batched);
+    with_features also returns every game's (X, nact), computed from the
+    same compiled handles."""
     import torch
 
-    out = []
+    out, feats = [], []
     s = int(torch.cuda.current_stream().cuda_stream)
     opts = cfr.make_options(precision=precision)
     for c0 in range(0, len(specs), chunk):
         part = specs[c0:c0 + chunk]
-        hs = [cfr.cfr_compile(sp, opts) for sp in part]
+        hs = compile_many(part, opts)
+        if with_features:
+            workers = min(16, os.cpu_count() or 1)
+            with ThreadPoolExecutor(workers) as ex:
+                feats += list(ex.map(lambda a: features(a[0], handle=a[1]), zip(part, hs)))
         sizes = [cfr.cfr_plan(h) for h in hs]
         pool = serve.DevicePool(sum(n + serve.ALIGN for n in sizes) + serve.ALIGN)
         for j, (h, n) in enumerate(zip(hs, sizes)):
@@ -187,16 +175,15 @@ def solve_batch(specs, iters: int, precision=cfr.P32, threads=1024, lanes=8, chu
             cfr.cfr_avg_strategy(h, v, False, s)
             out.append(v)
             cfr.cfr_destroy(h)
-    return out
+    return (out, feats) if with_features else out
 
 
 def make_dataset(specs, iters: int = 1000, max_sets_per_game: int = 256, seed: int = 0):
     """Features and target strategies of (a sample of) every game's sets."""
     rng = np.random.default_rng(seed)
-    strat = solve_batch(specs, iters)
+    strat, feats = solve_batch(specs, iters, with_features=True)
     Xs, Ns, Ts = [], [], []
-    for sp, st in zip(specs, strat):
-        X, na = features(sp)
+    for sp, st, (X, na) in zip(specs, strat, feats):
         T = _pad_slots(sp, st)
         idx = np.arange(sp.n_infosets)
         if len(idx) > max_sets_per_game:
@@ -249,18 +236,21 @@ def warm_regrets(net: MLP, spec, kappa: float) -> np.ndarray:
     return warm_regrets_many(net, [spec], kappa, workers=1)[0]
 
 
-def warm_regrets_many(net: MLP, specs, kappa: float, workers: Optional[int] = None) -> List[np.ndarray]:
+def warm_regrets_many(net: MLP, specs, kappa: float, workers: Optional[int] = None,
+                      handles: Optional[list] = None) -> List[np.ndarray]:
     """warm_regrets for many games: their features computed on a thread pool
-    (NumPy's array loops release the interpreter lock), then one network
-    pass over every game's sets."""
+    (the library and NumPy's array loops release the interpreter lock), from
+    the games' compiled handles when given, then one network pass over every
+    game's sets."""
     import torch
 
     workers = workers or min(16, os.cpu_count() or 1)
+    hs = handles if handles is not None else [None] * len(specs)
     if workers > 1 and len(specs) > 1:
         with ThreadPoolExecutor(workers) as ex:
-            feats = list(ex.map(lambda sp: features(sp, return_mass=True), specs))
+            feats = list(ex.map(lambda a: features(a[0], return_mass=True, handle=a[1]), zip(specs, hs)))
     else:
-        feats = [features(sp, return_mass=True) for sp in specs]
+        feats = [features(sp, return_mass=True, handle=h) for sp, h in zip(specs, hs)]
     X = np.concatenate([f[0] for f in feats])
     na = np.concatenate([f[1] for f in feats])
     prob = net.predict(torch.tensor(X, device=net.dev), torch.tensor(na, device=net.dev)).cpu().numpy()
@@ -271,15 +261,31 @@ def warm_regrets_many(net: MLP, specs, kappa: float, workers: Optional[int] = No
     return out
 
 
-def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iters=5000, threads=1024, lanes=8):
+def compile_many(specs, opts, workers: Optional[int] = None):
+    """cfr_compile of every spec on a thread pool (the compiler releases the
+    interpreter lock)."""
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers > 1 and len(specs) > 1:
+        with ThreadPoolExecutor(workers) as ex:
+            return list(ex.map(lambda sp: cfr.cfr_compile(sp, opts), specs))
+    return [cfr.cfr_compile(sp, opts) for sp in specs]
+
+
+def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iters=5000, threads=1024, lanes=8,
+                         net: Optional[MLP] = None, kappa: float = 8.0):
     """Iterations each game needs to reach target * pot (checked every
-    `check_every`), all games in one batch, and the wall time."""
+    `check_every`), all games in one batch, and the wall time (compile,
+    then for a warm start the features of the compiled games and one
+    network pass, then the solves). init: initial regrets per game (spec
+    slot order); or net: the warm start computed here from the handles."""
     import torch
 
     s = int(torch.cuda.current_stream().cuda_stream)
     opts = cfr.make_options(precision=cfr.P32)
     t0 = time.perf_counter()
-    hs = [cfr.cfr_compile(sp, opts) for sp in specs]
+    hs = compile_many(specs, opts)
+    if net is not None:
+        init = warm_regrets_many(net, specs, kappa, handles=hs)
     sizes = [cfr.cfr_plan(h) for h in hs]
     pool = serve.DevicePool(sum(n + serve.ALIGN for n in sizes) + serve.ALIGN)
     for j, (h, n) in enumerate(zip(hs, sizes)):
@@ -330,7 +336,7 @@ def choose_kappa(net: MLP, specs, kappas=(4.0, 8.0, 16.0), max_iters: int = 3000
     """The kappa with the fewest mean iterations to 1e-3 pot on `specs`."""
     best, best_it, table = None, float("inf"), {}
     for k in kappas:
-        done, fin, _ = iterations_to_target(specs, init=warm_regrets_many(net, specs, k), max_iters=max_iters)
+        done, fin, _ = iterations_to_target(specs, net=net, kappa=k, max_iters=max_iters)
         table[k] = float(np.mean(done))
         if table[k] < best_it:
             best, best_it = k, table[k]

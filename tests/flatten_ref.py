@@ -62,6 +62,7 @@ def flatten(g, reach_order=MEMBERS, member_tiles=TILES_AUTO):
     by_first = sorted(first, key=lambda s: first[s])
     vslot = np.full(N, -1, dtype=np.int64)
     vslot[0] = N - 1
+    slot_key = np.full(N, N - 1, dtype=np.int64)  # member-major block position (value-slot reach order)
     sets, vb_of = [], {}
     nxt = 0
     for d in range(D):
@@ -70,15 +71,20 @@ def flatten(g, reach_order=MEMBERS, member_tiles=TILES_AUTO):
         for p in (0, 1):
             grp = [s_ for s_ in here if int(g.iset_player[s_]) == p]
             sets.extend(sorted(grp, key=lambda s_: (min(vslot[h] for h in mem_of[s_]), first[s_])))
-        for s_ in sets[start:]:
+        for s_ in sets[start:]:  # action-major: child a of every member, then a + 1
             vb_of[s_] = nxt
-            for h in mem_of[s_]:
-                for x in range(child_begin_l[h], child_begin_l[h + 1]):
-                    vslot[x] = nxt
+            na = int(g.iset_nact[s_])
+            for i_, h in enumerate(mem_of[s_]):
+                for a in range(na):
+                    slot_key[child_begin_l[h] + a] = nxt + i_ * na + a  # member-major position
+            for a in range(na):
+                for h in mem_of[s_]:
+                    vslot[child_begin_l[h] + a] = nxt
                     nxt += 1
         for h in range(level_begin[d], level_begin[d + 1]):
             if kinds[h] == CHANCE:
                 for x in range(child_begin_l[h], child_begin_l[h + 1]):
+                    slot_key[x] = nxt
                     vslot[x] = nxt
                     nxt += 1
     assert nxt == N - 1 or N == 1
@@ -128,7 +134,7 @@ def flatten(g, reach_order=MEMBERS, member_tiles=TILES_AUTO):
     rank = np.full(N, -1, dtype=np.int64)
     int_nodes = np.nonzero(internal)[0].tolist()
     if reach_order == SLOTS:
-        int_nodes = sorted(int_nodes, key=lambda h: (depth[h], vslot[h]))
+        int_nodes = sorted(int_nodes, key=lambda h: (depth[h], slot_key[h]))
     elif reach_order == MEMBERS:
         # per depth: the members in member order, then the chance nodes in the
         # order the next depth's internal nodes first pull from them (those

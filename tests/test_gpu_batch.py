@@ -6,6 +6,8 @@ equals the single-solve evaluator; the continuous-batching server admits by
 memory, overlaps arrivals with running solves, and returns for every request
 exactly what solving it alone returns.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -183,3 +185,64 @@ def test_cluster_size_is_checked():
     with pytest.raises(cfr.CfrError):
         cfr.cfr_batch_iterate(hs, 1, tp, tb, 256, 4, s, cluster=3)
     cfr.cfr_destroy(hs[0])
+
+
+def test_server_rejects_a_request_larger_than_the_pool_and_serves_the_rest():
+    # the admission check answers a request that can never fit at once
+    # (it used to wait forever for memory that would never free up)
+    small = [gg.endgame(500 + i, 3000) for i in range(4)]
+    big = gg.endgame(600, 400000)
+    hs0 = [cfr.cfr_compile(sp) for sp in small + [big]]
+    sizes = [cfr.cfr_plan(h) for h in hs0]
+    for h in hs0:
+        cfr.cfr_destroy(h)
+    pool = 2 * max(sizes[:4]) + 4096
+    assert sizes[4] > pool
+    reqs = [serve.Request(i, sp, 0.0) for i, sp in enumerate(small)] + [serve.Request(99, big, 0.0)]
+    srv = serve.Server(pool_bytes=pool, max_active=8, check_every=50, max_iters=300, cluster=1)
+    res = {r.rid: r for r in srv.serve(reqs)}
+    srv.close()
+    assert res[99].status == "rejected" and "exceeds" in res[99].message and res[99].iterations == 0
+    for i in range(4):
+        assert res[i].status in ("solved", "capped") and res[i].iterations > 0
+
+
+def test_server_cancels_queued_and_active_requests_between_rounds():
+    specs = [gg.endgame(700 + i, 4000) for i in range(6)]
+    reqs = [serve.Request(i, sp, 0.0) for i, sp in enumerate(specs)]
+    reqs.append(serve.Request(50, gg.endgame(750, 4000), 30.0))  # arrives long after: cancelled while queued
+
+    def on_round(srv, active):
+        if srv.rounds == 2:
+            srv.cancel(1)  # active: retired at this round boundary
+            srv.cancel(50)  # not yet arrived
+
+    srv = serve.Server(pool_bytes=1 << 28, max_active=8, check_every=20, max_iters=400, target=1e-9,
+                       keep_strategies=True, cluster=1, on_round=on_round)
+    t = time.perf_counter()
+    res = {r.rid: r for r in srv.serve(reqs)}
+    srv.close()
+    assert time.perf_counter() - t < 25.0  # did not wait for the cancelled arrival
+    assert res[1].status == "cancelled" and res[1].iterations == 40
+    assert res[50].status == "cancelled" and res[50].iterations == 0
+    for i in (0, 2, 3, 4, 5):
+        assert res[i].status == "capped" and res[i].iterations == 400
+    # the cancelled solve left the others untouched: each equals its solve alone
+    for i in (0, 2):
+        p2, h2, t2, tp2, tb2, s = bound([specs[i]])
+        cfr.cfr_batch_iterate(h2, 400, tp2, tb2, srv.threads, srv.lanes, s)
+        alone = np.empty(len(res[i].strategy))
+        cfr.cfr_avg_strategy(h2[0], alone, False, s)
+        np.testing.assert_array_equal(res[i].strategy, alone)
+        cfr.cfr_destroy(h2[0])
+
+
+def test_server_answers_an_invalid_spec_with_an_error_result():
+    bad = gg.from_lists([(gg.P1, 0, [1, 2], None, 0.0), (gg.TERMINAL, -1, [], None, 1.0),
+                         (gg.TERMINAL, -1, [], None, -1.0)], [(0, 3)])  # 2 children, set says 3 actions
+    reqs = [serve.Request(0, bad, 0.0), serve.Request(1, gg.endgame(800, 3000), 0.0)]
+    srv = serve.Server(pool_bytes=1 << 26, max_active=4, check_every=50, max_iters=100, cluster=1)
+    res = {r.rid: r for r in srv.serve(reqs)}
+    srv.close()
+    assert res[0].status == "error" and "CFR_ERR_INVALID_SPEC" in res[0].message
+    assert res[1].status in ("solved", "capped")

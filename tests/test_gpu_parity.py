@@ -455,3 +455,42 @@ def test_rebinding_recaptures_instead_of_replaying_a_stale_graph():
     assert t == 30
     np.testing.assert_array_equal(R, o.R)
     np.testing.assert_array_equal(avg, o.sbar)
+
+
+@pytest.mark.parametrize("name,make", [("rt", lambda: gg.random_tree(6, depth=10)),
+                                       ("card", lambda: gg.large_card(4, 4, 1, 1))])
+def test_graph_iterations_and_launch_overlap_leave_the_state_bitwise_unchanged(name, make):
+    # k iterations per graph (the paper's alternative-execution table) and
+    # programmatic dependent launch change how the launches are issued, not
+    # what they compute: 37 = 3 x 10 + 7 iterations use both graphs
+    g = make()
+    outs = []
+    for form, k, ov in ((cfr.EXEC_LEVELS, 0, cfr.OVERLAP_OFF), (cfr.EXEC_LEVELS, 0, cfr.OVERLAP_ON),
+                        (cfr.EXEC_GRAPH, 0, cfr.OVERLAP_OFF), (cfr.EXEC_GRAPH, 1, cfr.OVERLAP_ON),
+                        (cfr.EXEC_GRAPH, 10, cfr.OVERLAP_ON), (cfr.EXEC_GRAPH, 10, cfr.OVERLAP_OFF)):
+        s = solve_gpu(g, 0, precision=cfr.P32, form=form, lanes_per_set=8, graph_iters=k, launch_overlap=ov)
+        for n in (20, 17):
+            s.iterate(n)
+        s.synchronize()
+        outs.append(s.get_state())
+    for R, avg, t in outs[1:]:
+        assert t == 37
+        np.testing.assert_array_equal(R, outs[0][0])
+        np.testing.assert_array_equal(avg, outs[0][1])
+
+
+@pytest.mark.parametrize("order,halves", [(cfr.ORDER_SIMULTANEOUS, 1), (cfr.ORDER_ALTERNATING, 2)])
+def test_launch_count_gate(order, halves):
+    # one iteration is 2D - 1 kernel launches in member order (a forward and
+    # a backward per depth, no forward for the deepest), twice that under
+    # alternating updates; k iterations per graph are k times that; the
+    # persistent form is one launch per call. (The paper's compiled
+    # iteration issues 87 kernels per iteration on its turn subgame.)
+    g = gg.large_card(4, 4, 1, 1)
+    s = solve_gpu(g, 12, precision=cfr.P32, form=cfr.EXEC_GRAPH, order=order, graph_iters=5)
+    c = s.counts_now()
+    D = c["depth_blocks"]
+    assert c["graph_kernels"] == halves * (2 * D - 1)
+    assert c["graph_k_kernels"] == 5 * halves * (2 * D - 1)
+    p = solve_gpu(g, 3, precision=cfr.P32, form=cfr.EXEC_PERSISTENT, order=order)
+    assert p.counts_now()["graph_kernels"] == 0

@@ -13,6 +13,7 @@ import torch
 import gamegen as gg
 import oracle
 from paper_2609_11923_gb300 import cfr
+from tests.fp32_band import fp32_band, fp32_bar
 
 pytestmark = pytest.mark.gpu
 
@@ -71,12 +72,15 @@ def test_streaming_forms_agree_bitwise_runs_repeat_and_split_calls_equal_one_cal
                                         (cfr.RULE_PCFR_PLUS, oracle.PCFR_PLUS)])
 @pytest.mark.parametrize("order", [cfr.ORDER_SIMULTANEOUS, cfr.ORDER_ALTERNATING])
 def test_streaming_every_rule_and_order_within_tolerance(rule, orule, order):
+    # vanilla CFR with alternating updates is ill-conditioned on this game:
+    # FP32-sized payoff perturbations alone move the oracle by about 1e-3
+    # at T = 300, so the bar there is the oracle's own band (fp32_band)
     g = gg.large_card(3, 2, 1, 1)
     s = streaming(g, rule=rule, order=order, tiles=cfr.TILES_ON)
     s.iterate(300)
     s.synchronize()
-    e_or = oracle.solve(g, 300, rule=orule, order=order).exploitability()
-    assert abs(s.exploitability() - e_or) <= 1e-4 * g.pot, (s.exploitability(), e_or)
+    e_or, delta = fp32_band(lambda: gg.large_card(3, 2, 1, 1), 300, rule=orule, order=order)
+    assert abs(s.exploitability() - e_or) <= fp32_bar(g.pot, delta), (s.exploitability(), e_or, delta)
 
 
 def test_streaming_matches_the_lane_group_kernel_closely_after_one_iteration():

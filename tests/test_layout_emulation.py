@@ -116,15 +116,15 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS, stream=Fa
         racc, macc = [0.0] * na, [0.0] * na
         for k in range(im[s], im[s + 1]):
             r = reach[irk[s, 0] + (k - im[s]) * irk[s, 1]] if members else reach[mirk[k]]
-            cb = ivb[s] + (k - im[s]) * na
+            cb, M = ivb[s] + (k - im[s]), im[s + 1] - im[s]  # child a at cb + a * M
             vh = 0.0
             for a in range(na):
-                vh = vh + sig[a] * v[cb + a]
+                vh = vh + sig[a] * v[cb + a * M]
             v[mvs[k]] = vh
             po, pw = (r[0], r[1]) if p2 else (r[1], r[0])
             f = (-1.0 if p2 else 1.0) * po
             for a in range(na):
-                racc[a] = racc[a] + f * (v[cb + a] - vh)
+                racc[a] = racc[a] + f * (v[cb + a * M] - vh)
                 macc[a] = macc[a] + pw * sig[a]
         if (2 if p2 else 1) not in upd:  # the other player's sets only pass values up
             return
@@ -163,8 +163,8 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS, stream=Fa
         for q in range(nm):
             r = get(sreach, r0 - ra + q * rs)
             hh = get(smem, m0 - ka + q)
-            cb = vb - va + q * na
-            vc = [get(sval, cb + a) for a in range(na)]
+            cb = vb - va + q
+            vc = [get(sval, cb + a * nm) for a in range(na)]
             vh = 0.0
             for a in range(na):
                 vh = vh + sig[a] * vc[a]

@@ -119,7 +119,7 @@ def test_stream_chunks_cover_the_sets_and_stay_in_bounds(name, tiles):
                     q = np.arange(nm)
                     rr = r0 - ra + q * rs
                     assert rr.min() >= 0 and rr.max() < nra
-                    cc = vb - va + q[:, None] * na + np.arange(na)[None, :]
+                    cc = vb - va + q[:, None] + np.arange(na)[None, :] * nm
                     assert cc.min() >= 0 and cc.max() < nva
                     mm = m0 - ka + q
                     assert mm.min() >= 0 and mm.max() < nka
