@@ -85,6 +85,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the lane counts picked from mean set sizes")
+    p.add_argument("--lanes", type=int, default=0,
+                   help="pin cfr_options.lanes_per_set (512: the streaming backward wherever it can run) and skip "
+                        "the autotuner (for profiling runs whose launch shapes must not depend on timing)")
     p.add_argument("--profile-iteration", action="store_true",
                    help="set up and warm up as usual, then run exactly one iteration between profiler start and "
                         "stop (for ncu --profile-from-start off) and exit without timing")
@@ -370,14 +373,15 @@ def run_ours(args):
     prec = cfr.P32 if args.precision == "p32" else cfr.P64
     orders = {"members": cfr.REACH_MEMBERS, "bfs": cfr.REACH_BFS, "slots": cfr.REACH_SLOTS}
     solver = cfr.Solver(spec, precision=prec, exec_form=forms[args.exec_form], device=str(dev),
-                        reach_order=orders[args.reach_order])
+                        reach_order=orders[args.reach_order], lanes_per_set=args.lanes)
     counts = solver.counts
     E, D = counts["n_edges"], counts["depth_blocks"]
     pot, n_nodes = spec.pot, spec.n_nodes
     del spec  # the compiled copy lives in the handle
     stream = torch.cuda.current_stream(dev)
     s = int(stream.cuda_stream)
-    lanes = solver.autotune() if not args.no_autotune else list(cfr.cfr_export_array(solver.h, "level_lanes"))
+    tune = not args.no_autotune and args.lanes == 0
+    lanes = solver.autotune() if tune else list(cfr.cfr_export_array(solver.h, "level_lanes"))
 
     # warm-up (graph capture happens on the first call)
     solver.iterate(args.warmup)
@@ -491,7 +495,7 @@ def run_ours(args):
                    "precision": args.precision + (" (FP64 regret/average accumulators)" if prec == cfr.P32 else ""),
                    "exec_form": args.exec_form, "reach_order": args.reach_order, "pot": pot, "parallelism": "replicas x%d" % world,
                    "lanes_per_set_by_depth": [int(x) for x in lanes],
-                   "autotuned": not args.no_autotune,
+                   "autotuned": tune,
                    "l2": "inputs larger than L2 (arena %.1f GB vs 129 MB L2)" % arena_gb},
         "iters_per_s": world * iters_per_s,
         "algo_gbps_per_gpu": algo_gbps,

@@ -84,7 +84,9 @@ typedef struct cfr_options {
   /* CFR_EXEC_LEVELS: per-level kernels launched eagerly; CFR_EXEC_GRAPH: the
    * same kernels captured once into a CUDA graph and replayed (Section 4.3);
    * CFR_EXEC_PERSISTENT: one kernel per cfr_iterate call with a grid-wide
-   * barrier between depth levels; CFR_EXEC_AUTO picks by game size. */
+   * barrier between depth levels; CFR_EXEC_AUTO picks by game size: the
+   * persistent form up to 768 nodes in CFR_P32 and 350 in CFR_P64 (where
+   * it was measured faster than graph replay), the graph form above. */
   int exec_form;
   /* Update rule (Section 3, update rules): CFR_RULE_CFR_PLUS (regret clamped
    * at zero, linear averaging w_t = t), CFR_RULE_CFR (no clamp, linear

@@ -11,7 +11,7 @@
 // chunks of whole groups (a tile of four sets, or one untiled set) whose
 // staged bytes fit one pipeline stage. Every CTA walks the chunks c =
 // blockIdx, blockIdx + grid, ... through a ring of kStreamStages stages. Its
-// kThreads compute threads do the members' work; one more warp, the control
+// kStreamCompute compute threads do the members' work; one more warp, the control
 // warp, issues each chunk's seven cp.async.bulk copies into a stage (the
 // stage's mbarrier counts their bytes) and runs every group's slot update.
 // The loads in flight cost no registers, so the memory pipe stays full at a
@@ -36,7 +36,8 @@ namespace cfr {
 constexpr int kStreamLanes = 512;                 // lanes_per_set code of this form
 constexpr int kStreamStages = 2;                  // pipeline depth
 constexpr int kStreamStageBytes = 48 * 1024;      // bytes one chunk may stage
-constexpr int kStreamWarps = kThreads / 32;
+constexpr int kStreamCompute = 256;               // compute threads of a streaming CTA (two CTAs per SM)
+constexpr int kStreamWarps = kStreamCompute / 32;
 constexpr int kStreamMinMembers = 32;             // mean members per set below which the autotuner does not try it
 
 // Per information set (member order), 32 bytes, read by the streaming form.
@@ -141,8 +142,8 @@ __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char
 }
 
 // The member work of one group of sets (G = 1 or 4) of a staged chunk, by
-// the kThreads compute threads: thread t serves set j = t % G and members
-// t / G, t / G + kThreads / G, ...; writes each member's value and leaves
+// the kStreamCompute compute threads: thread t serves set j = t % G and
+// members t / G, t / G + kStreamCompute / G, ...; writes each member's value and leaves
 // the thread's partial regret and average sums, finished by a butterfly over
 // the warp's lanes that serve the same set, in racc / macc.
 template <int MAXA>
@@ -153,7 +154,7 @@ __device__ __forceinline__ void stream_members(const StreamChunk &d, const Strea
   const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
   const int gs = G == 4 ? 2 : 0;
   const int j = tid & (G - 1);
-  const int LPS = kThreads >> gs;
+  const int LPS = kStreamCompute >> gs;
   const SetInfo si = sinfo[I + j - d.I0];
   const bool p2 = (si.flags >> 8) & 1;
   const float2 *sr = reinterpret_cast<const float2 *>(stage + L.reach);
@@ -245,8 +246,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Threads of a streaming CTA: kThreads compute threads and one control warp.
-constexpr int kStreamThreads = kThreads + 32;
+// Threads of a streaming CTA: kStreamCompute compute threads and one control warp.
+constexpr int kStreamThreads = kStreamCompute + 32;
 
 // Grid: nb_chance blocks over narrow chance nodes, then the streaming CTAs
 // over chunks [c0, c1) of this depth (a depth with wide chance nodes does
@@ -275,18 +276,18 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const int32_t b = (int32_t)blockIdx.x - nb_chance;
   const int32_t nb = (int32_t)gridDim.x - nb_chance;
   const int tid = threadIdx.x, lane = tid & 31;
-  const bool control = tid >= kThreads;
+  const bool control = tid >= kStreamCompute;
   if ((smem_u32(s_stage) & 15u) != 0u) {  // bulk copies need 16-byte aligned destinations
     if (tid == 0) atomicExch(err, 1);
     return;
   }
-  if (tid == kThreads) {
+  if (tid == kStreamCompute) {
     for (int s = 0; s < kStreamStages; ++s) {
       mbar_init(smem_u32(&s_full[s]), 1);
       mbar_init(smem_u32(&s_empty[s]), kStreamThreads);
     }
     for (int p = 0; p < 2; ++p) {
-      mbar_init(smem_u32(&s_rfull[p]), kThreads);
+      mbar_init(smem_u32(&s_rfull[p]), kStreamCompute);
       mbar_init(smem_u32(&s_rempty[p]), 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   // error exit of the thread that issues copies: let every chunk it issued
   // and nobody waited for land (bounded waits), then leave
   auto drain = [&](int32_t i0) {
-    if (tid != kThreads) return;
+    if (tid != kStreamCompute) return;
     for (int k = 0; k < kStreamStages; ++k)
       if (c0 + b + (i0 + k) * nb < c1)
         mbar_wait(smem_u32(&s_full[(i0 + k) % kStreamStages]), (uint32_t)(((i0 + k) / kStreamStages) & 1));
@@ -326,6 +327,11 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     const StreamChunk d = s_desc[s];
     const StreamLayout L = stream_layout(d);
     const unsigned char *stage = s_stage + s * kStreamStageBytes;
+    // the descriptor of the chunk that refills this stage, loaded now so that
+    // its latency overlaps this chunk's work
+    const int32_t cn = c + kStreamStages * nb;
+    StreamChunk nd;
+    if (tid == kStreamCompute && cn < c1) nd = chunks[cn];
     const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
     for (int32_t I = d.I0; I < d.I1; ++grp) {
       const int G = sinfo[I - d.I0].flags & 7;
@@ -359,10 +365,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
       I += G;
     }
     mbar_arrive(smem_u32(&s_empty[s]));  // this thread is done with stage s
-    if (tid == kThreads) {  // refill stage s with the chunk kStreamStages ahead
-      const int32_t cn = c + kStreamStages * nb;
+    if (tid == kStreamCompute) {  // refill stage s with the chunk kStreamStages ahead
       if (cn < c1) {
-        const StreamChunk nd = chunks[cn];
         if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
           atomicExch(err, 1);
           drain(i + 1);

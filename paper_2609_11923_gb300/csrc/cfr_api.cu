@@ -259,7 +259,11 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   h->order = h->opt.order;
   h->maxa_tier = c.max_act <= 4 ? 4 : (c.max_act <= 8 ? 8 : 64);
   h->exec_form = h->opt.exec_form;
-  if (h->exec_form == CFR_EXEC_AUTO) h->exec_form = c.N <= (1 << 16) ? CFR_EXEC_PERSISTENT : CFR_EXEC_GRAPH;
+  // AUTO: the persistent kernel only where it was measured faster than graph
+  // replay per iteration (one GB300: P32 up to about 400 nodes, graph from
+  // about 1,200; P64 up to about 300, graph from about 400)
+  if (h->exec_form == CFR_EXEC_AUTO)
+    h->exec_form = c.N <= (h->opt.precision == CFR_P32 ? 768 : 350) ? CFR_EXEC_PERSISTENT : CFR_EXEC_GRAPH;
   // lanes per information set: the smallest group that covers the mean set
   auto pick = [](double mean) { return mean <= 4.0 ? 4 : mean <= 8.0 ? 8 : mean <= 16.0 ? 16 : 32; };
   // (tiled depths: at most one tile of sets per warp's worth of lanes, so a

@@ -120,8 +120,15 @@ def features(spec, return_mass: bool = False, handle: Optional[int] = None) -> t
     eq = np.where(f[:, 0] == 0, eq1, 1.0 - eq1)
     X[:, 172] = eq
     X[rows, 173 + np.clip((eq * 10).astype(np.int64), 0, 9)] = 1.0
-    key = np.concatenate([f[:, [0, 3, 4]], f[:, 6:14]], axis=1)
-    _, grp = np.unique(key, axis=0, return_inverse=True)
+    # the public state: acting player, board card, round, betting history
+    # (small integers, each shifted to be >= 0), packed into one int64 key
+    key = np.zeros(I, dtype=np.int64)
+    for col, width in ((0, 3), (3, 33), (4, 3)) + tuple((6 + p, 12) for p in range(8)):
+        v = f[:, col].astype(np.int64) + 1
+        if I and (v.min() < 0 or v.max() >= width):  # the packing is one-to-one only within these ranges
+            raise ValueError("set feature %d outside the range the public-state key packs" % col)
+        key = key * width + v
+    _, grp = np.unique(key, return_inverse=True)
     grp = grp.reshape(-1)
     gmean = np.bincount(grp, weights=mass) / np.maximum(np.bincount(grp), 1)
     rel = mass / np.maximum(gmean[grp], 1e-300)

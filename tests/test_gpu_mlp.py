@@ -47,8 +47,12 @@ def test_network_gradients_match_fp64_reference():
     gW, gb = net.numpy_grads()
     rl, rW, rb = mlp_ref.loss_and_grads(W, b, X.astype(np.float64), nact, T.astype(np.float64), bf16=True)
     assert loss == pytest.approx(rl, rel=1e-4)
+    # element by element: both sides round the same operands to BF16; what
+    # is left is FP32 against FP64 accumulation and activations whose BF16
+    # rounding flips on the last bit (2^-8 of one term), so each entry must
+    # agree to 2% of itself or 0.5% of the tensor's largest entry
     for g, r in zip(gW + gb, rW + rb):
-        assert np.linalg.norm(g - r) <= 2e-3 * np.linalg.norm(r) + 1e-9
+        np.testing.assert_allclose(g, r, rtol=2e-2, atol=5e-3 * np.abs(r).max())
 
 
 def test_training_lowers_the_loss_on_a_fixed_task():
