@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--workload", default="large_card", choices=["large_card", "random_tree", "tiny", "serving", "warmstart"])
     p.add_argument("--train-games", type=int, default=10000, help="warmstart only: training solves")
     p.add_argument("--heldout", type=int, default=512, help="warmstart only: held-out games")
+    p.add_argument("--alone-sample", type=int, default=128,
+                   help="warmstart only: held-out games also solved one at a time, cold and warm")
     p.add_argument("--requests", type=int, default=512, help="serving only: number of endgame solves")
     p.add_argument("--max-iters", type=int, default=5000, help="serving only: iteration cap per solve")
     p.add_argument("--baseline-sample", type=int, default=48, help="serving only: solves timed one by one")
@@ -328,7 +330,8 @@ def kernel_source_hash() -> str:
     the layout), comments and whitespace left out: recorded DRAM traffic
     applies while it matches."""
     h = hashlib.sha1()
-    for f in ("kernels.cuh", "launch_impl.cuh", "cfr_api.cu", "compile.cpp", "compiled.h"):
+    for f in ("kernels.cuh", "bwd_stream.cuh", "launch.h", "launch_impl.cuh", "k_bwd32.cu", "cfr_api.cu", "compile.cpp",
+              "compiled.h"):
         with open(os.path.join(ROOT, "paper_2609_11923_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -624,13 +627,24 @@ def run_warmstart(args):
     val = ws.endgame_family(list(range(15000, 15064)), 1e3, 1e5)
     kappa, ktable = ws.choose_kappa(net, val)
     held = ws.endgame_family(list(range(20000, 20000 + args.heldout)), 1e3, 1e6)
-    cold, cold_fin, cold_wall = ws.iterations_to_target(held, max_iters=args.max_iters)
+    # each game on its own (a single real-time re-solve): iterations and wall
+    # time to the target, on a sample of the held-out games
+    alone = {"cold": [], "warm": []}
+    for sp in held[:args.alone_sample]:
+        alone["cold"].append(ws.time_to_target_alone(sp, max_iters=args.max_iters))
+        alone["warm"].append(ws.time_to_target_alone(sp, net=net, kappa=kappa, max_iters=args.max_iters))
+    alone_stats = {}
+    for arm, rows in alone.items():
+        it = np.array([r[0] for r in rows])
+        sec = np.array([r[1] for r in rows])
+        alone_stats[arm] = {"mean_iters": float(it.mean()), "mean_s": float(sec.mean()),
+                            "median_s": float(np.median(sec)), "reached": float(np.mean([r[2] for r in rows]))}
+    cold_t, warm_t = {}, {}
+    cold, cold_fin, cold_wall = ws.iterations_to_target(held, max_iters=args.max_iters, timings=cold_t)
     # the warm start's wall time includes its features (from the compiled
     # games) and the network pass
-    t2 = time.perf_counter()
-    ws.warm_regrets_many(net, held[:64], kappa)
-    t_infer = (time.perf_counter() - t2) * len(held) / 64.0  # a separate estimate of that share
-    warm, warm_fin, warm_wall = ws.iterations_to_target(held, net=net, kappa=kappa, max_iters=args.max_iters)
+    warm, warm_fin, warm_wall = ws.iterations_to_target(held, net=net, kappa=kappa, max_iters=args.max_iters,
+                                                        timings=warm_t)
     line = {
         "metric": METRIC, "value": float(np.mean(warm)), "unit": "iterations to 1e-3 pot (mean, warm start)",
         "n_gpus": 1, "steps": args.heldout, "warmup": 0, "ms_per_step": None, "higher_is_better": False,
@@ -639,13 +653,17 @@ def run_warmstart(args):
                                "%d held-out endgames (1e3-1e6 edges)" % (args.train_games, args.heldout),
                    "stop": "exploitability <= 1e-3 pot, checked every 50 iterations, cap %d" % args.max_iters},
         "cold": {"mean_iters": float(np.mean(cold)), "median_iters": float(np.median(cold)),
-                 "finished": float(cold_fin.mean()), "wall_s": cold_wall},
+                 "finished": float(cold_fin.mean()), "wall_s": cold_wall, "breakdown_s": cold_t},
         "warm": {"mean_iters": float(np.mean(warm)), "median_iters": float(np.median(warm)),
-                 "finished": float(warm_fin.mean()), "wall_s": warm_wall,
-                 "features_and_inference_s_estimate": t_infer,
+                 "finished": float(warm_fin.mean()), "wall_s": warm_wall, "breakdown_s": warm_t,
                  "wall_includes": "compile, features from the compiled games, one network pass, the solves"},
         "wall_ratio_warm_over_cold": warm_wall / cold_wall,
         "iteration_ratio_warm_over_cold": float(np.mean(warm) / np.mean(cold)),
+        "alone": dict(alone_stats, games=len(alone["cold"]),
+                      what="each game solved on its own (single-game form chosen by size), warm start = "
+                           "features from its compiled game + one network pass + initial regrets; wall time "
+                           "from compile to the target",
+                      wall_ratio_warm_over_cold=alone_stats["warm"]["mean_s"] / alone_stats["cold"]["mean_s"]),
         "kappa": kappa, "kappa_validation_mean_iters": ktable,
         "training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
                      "loss_by_epoch": [float(x) for x in net.history]},

@@ -244,13 +244,14 @@ def warm_regrets(net: MLP, spec, kappa: float) -> np.ndarray:
 
 
 def warm_regrets_many(net: MLP, specs, kappa: float, workers: Optional[int] = None,
-                      handles: Optional[list] = None) -> List[np.ndarray]:
+                      handles: Optional[list] = None, timings: Optional[dict] = None) -> List[np.ndarray]:
     """warm_regrets for many games: their features computed on a thread pool
     (the library and NumPy's array loops release the interpreter lock), from
     the games' compiled handles when given, then one network pass over every
-    game's sets."""
+    game's sets. timings (optional) receives the seconds of each part."""
     import torch
 
+    t0 = time.perf_counter()
     workers = workers or min(16, os.cpu_count() or 1)
     hs = handles if handles is not None else [None] * len(specs)
     if workers > 1 and len(specs) > 1:
@@ -258,13 +259,18 @@ def warm_regrets_many(net: MLP, specs, kappa: float, workers: Optional[int] = No
             feats = list(ex.map(lambda a: features(a[0], return_mass=True, handle=a[1]), zip(specs, hs)))
     else:
         feats = [features(sp, return_mass=True, handle=h) for sp, h in zip(specs, hs)]
+    t1 = time.perf_counter()
     X = np.concatenate([f[0] for f in feats])
     na = np.concatenate([f[1] for f in feats])
     prob = net.predict(torch.tensor(X, device=net.dev), torch.tensor(na, device=net.dev)).cpu().numpy()
+    t2 = time.perf_counter()
     out, row = [], 0
     for sp, (_, nag, mass) in zip(specs, feats):
         out.append(_regrets_from(sp, prob[row:row + len(nag)], mass, kappa))
         row += len(nag)
+    if timings is not None:
+        timings.update(features_s=t1 - t0, inference_s=t2 - t1, regrets_s=time.perf_counter() - t2,
+                       sets=int(X.shape[0]))
     return out
 
 
@@ -279,7 +285,7 @@ def compile_many(specs, opts, workers: Optional[int] = None):
 
 
 def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iters=5000, threads=1024, lanes=8,
-                         net: Optional[MLP] = None, kappa: float = 8.0):
+                         net: Optional[MLP] = None, kappa: float = 8.0, timings: Optional[dict] = None):
     """Iterations each game needs to reach target * pot (checked every
     `check_every`), all games in one batch, and the wall time (compile,
     then for a warm start the features of the compiled games and one
@@ -291,8 +297,11 @@ def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iter
     opts = cfr.make_options(precision=cfr.P32)
     t0 = time.perf_counter()
     hs = compile_many(specs, opts)
+    tc = time.perf_counter()
+    tw = {}
     if net is not None:
-        init = warm_regrets_many(net, specs, kappa, handles=hs)
+        init = warm_regrets_many(net, specs, kappa, handles=hs, timings=tw)
+    t_warm = time.perf_counter()
     sizes = [cfr.cfr_plan(h) for h in hs]
     pool = serve.DevicePool(sum(n + serve.ALIGN for n in sizes) + serve.ALIGN)
     for j, (h, n) in enumerate(zip(hs, sizes)):
@@ -302,6 +311,7 @@ def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iter
     tb = cfr.cfr_batch_table_bytes(len(hs))
     table = torch.empty(tb + 16, dtype=torch.uint8, device="cuda")
     tp = (table.data_ptr() + 15) & ~15
+    t_bind = time.perf_counter()
     done = np.zeros(len(hs), dtype=np.int64)
     finished = np.zeros(len(hs), dtype=bool)
     active = list(range(len(hs)))
@@ -317,10 +327,43 @@ def iterations_to_target(specs, init=None, target=1e-3, check_every=50, max_iter
             elif done[i] < max_iters:
                 keep.append(i)
         active = keep
-    wall = time.perf_counter() - t0
+    t_end = time.perf_counter()
+    wall = t_end - t0
+    if timings is not None:
+        timings.update(compile_s=tc - t0, warm_start_s=t_warm - tc, bind_s=t_bind - t_warm, solve_s=t_end - t_bind, **tw)
     for h in hs:
         cfr.cfr_destroy(h)
     return done, finished, wall
+
+
+def time_to_target_alone(spec, net: Optional[MLP] = None, kappa: float = 8.0, target: float = 1e-3,
+                         check_every: int = 50, max_iters: int = 5000):
+    """One game solved on its own, the way a single real-time re-solve runs:
+    compile, bind, (warm start: features from the compiled game, one
+    network pass, the initial regrets), then CFR+ in the single-game form
+    chosen by size (cfr EXEC_AUTO) with the exploitability checked every
+    `check_every` iterations. Returns (iterations, seconds, reached)."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = cfr.Solver(spec, precision=cfr.P32, exec_form=cfr.EXEC_AUTO)
+    if net is not None:
+        R0 = warm_regrets_many(net, [spec], kappa, workers=1, handles=[s.h])[0]
+        s.set_state(R0, np.zeros(len(R0)), 0)
+    done, reached = 0, False
+    pot = float(getattr(spec, "pot", 1.0))
+    while done < max_iters:
+        n = min(check_every, max_iters - done)
+        s.iterate(n)
+        done += n
+        if s.exploitability() <= target * pot:
+            reached = True
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return done, dt, reached
 
 
 def iter_endgame_family(seeds, lo: float = 1e3, hi: float = 1e6):
