@@ -35,7 +35,10 @@ namespace cfr {
 
 constexpr int kStreamLanes = 512;                 // lanes_per_set code of this form
 constexpr int kStreamStages = 2;                  // pipeline depth
-constexpr int kStreamStageBytes = 48 * 1024;      // bytes one chunk may stage
+constexpr int kStreamStageBytes = 48 * 1024;      // bytes one chunk may stage for the compute threads
+constexpr int kStreamSideSlots = 4;               // ring of the control warp's per-chunk data
+constexpr int kStreamSideBytes = 2048;            // bytes of one side slot
+constexpr int kStreamDynSmem = kStreamStages * kStreamStageBytes + kStreamSideSlots * kStreamSideBytes;
 constexpr int kStreamCompute = 256;               // compute threads of a streaming CTA (two CTAs per SM)
 constexpr int kStreamWarps = kStreamCompute / 32;
 constexpr int kStreamMinMembers = 32;             // mean members per set below which the autotuner does not try it
@@ -65,22 +68,32 @@ struct StreamChunk {
 static_assert(sizeof(SetInfo) == 32, "SetInfo is staged in 32-byte records");
 static_assert(sizeof(StreamChunk) == 64, "StreamChunk is 64 bytes");
 
-// Byte offsets of the staged arrays inside one stage.
+// Byte offsets of the staged arrays: in a stage (what the compute threads
+// read) and in a side slot (what the control warp reads for the slot
+// updates, so that the stage can be refilled while it still works).
 struct StreamLayout {
-  uint32_t reach, val, mem, info, sig, R, avg, total;
+  uint32_t reach, val, mem, info, sig, total;  // stage
+  uint32_t s_info, s_R, s_avg, s_total;        // side slot
 };
 
 __host__ __device__ inline StreamLayout stream_layout(const StreamChunk &c) {
   StreamLayout L;
+  const uint32_t nset = (uint32_t)sizeof(SetInfo) * (uint32_t)(c.I1 - c.I0);
   L.reach = 0;
   L.val = L.reach + 8u * (uint32_t)c.nra;
   L.mem = L.val + 4u * (uint32_t)c.nva;
   L.info = L.mem + 4u * (uint32_t)c.nka;
-  L.sig = L.info + (uint32_t)sizeof(SetInfo) * (uint32_t)(c.I1 - c.I0);
-  L.R = L.sig + 4u * (uint32_t)c.nsa;
-  L.avg = L.R + 8u * (uint32_t)c.nsa;
-  L.total = L.avg + 8u * (uint32_t)c.nsa;
+  L.sig = L.info + nset;
+  L.total = L.sig + 4u * (uint32_t)c.nsa;
+  L.s_info = 0;
+  L.s_R = nset;
+  L.s_avg = L.s_R + 8u * (uint32_t)c.nsa;
+  L.s_total = L.s_avg + 8u * (uint32_t)c.nsa;
   return L;
+}
+
+__host__ __device__ inline bool stream_fits(const StreamLayout &L) {
+  return L.total <= (uint32_t)kStreamStageBytes && L.s_total <= (uint32_t)kStreamSideBytes;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -120,24 +133,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// Issues the copies of chunk d into a stage (one thread). Returns false (and
-// issues nothing) if the chunk does not fit the stage.
-__device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char *stage, uint32_t bar,
-                                             const float2 *reach, const float *v, const int32_t *mem_vs,
-                                             const SetInfo *info, const float *sigma, const double *R,
-                                             const double *avg) {
+// Issues the copies of chunk d into a stage and a side slot (one thread),
+// all counted on the stage's mbarrier. Returns false (and issues nothing) if
+// the chunk does not fit.
+__device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char *stage, unsigned char *side,
+                                             uint32_t bar, const float2 *reach, const float *v,
+                                             const int32_t *mem_vs, const SetInfo *info, const float *sigma,
+                                             const double *R, const double *avg) {
   const StreamLayout L = stream_layout(d);
-  if (L.total > (uint32_t)kStreamStageBytes || d.nra <= 0 || d.nva <= 0 || d.nka <= 0 || d.I1 <= d.I0 || d.nsa <= 0)
-    return false;
-  const uint32_t s = smem_u32(stage);
-  mbar_expect_tx(bar, L.total);  // the seven sizes below add up to L.total
+  if (!stream_fits(L) || d.nra <= 0 || d.nva <= 0 || d.nka <= 0 || d.I1 <= d.I0 || d.nsa <= 0) return false;
+  const uint32_t s = smem_u32(stage), t = smem_u32(side);
+  mbar_expect_tx(bar, L.total + L.s_total);  // the eight sizes below add up to this
   bulk_g2s(s + L.reach, reach + d.ra, L.val - L.reach, bar);
   bulk_g2s(s + L.val, v + d.va, L.mem - L.val, bar);
   bulk_g2s(s + L.mem, mem_vs + d.ka, L.info - L.mem, bar);
   bulk_g2s(s + L.info, info + d.I0, L.sig - L.info, bar);
-  bulk_g2s(s + L.sig, sigma + d.sa, L.R - L.sig, bar);
-  bulk_g2s(s + L.R, R + d.sa, L.avg - L.R, bar);
-  bulk_g2s(s + L.avg, avg + d.sa, L.total - L.avg, bar);
+  bulk_g2s(s + L.sig, sigma + d.sa, L.total - L.sig, bar);
+  bulk_g2s(t + L.s_info, info + d.I0, L.s_R - L.s_info, bar);
+  bulk_g2s(t + L.s_R, R + d.sa, L.s_avg - L.s_R, bar);
+  bulk_g2s(t + L.s_avg, avg + d.sa, L.s_total - L.s_avg, bar);
   return true;
 }
 
@@ -207,11 +221,11 @@ __device__ __forceinline__ void stream_members(const StreamChunk &d, const Strea
 // updates slot a of set j (the warps' partial sums added in warp order),
 // then writes sigma^{t+1} of the group's sets.
 template <int MAXA>
-__device__ __forceinline__ void stream_update(const StreamChunk &d, const StreamLayout &L, const unsigned char *stage,
+__device__ __forceinline__ void stream_update(const StreamChunk &d, const StreamLayout &L, const unsigned char *side,
                                               int32_t I, int G, float *sigma, double *Rg, double *avgg, double wt,
                                               int rule, int upd, const float (*red)[4][2 * MAXA]) {
   const int lane = threadIdx.x & 31;
-  const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
+  const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(side + L.s_info);
   const int gs = G == 4 ? 2 : 0;
   const int jj = lane & (G - 1), a = lane >> gs;
   const SetInfo sj = sinfo[I + jj - d.I0];
@@ -225,8 +239,8 @@ __device__ __forceinline__ void stream_update(const StreamChunk &d, const Stream
       m += red[w][jj][MAXA + a];
     }
     const int32_t qs = sj.sb + a;
-    const double *sR = reinterpret_cast<const double *>(stage + L.R);
-    const double *sA = reinterpret_cast<const double *>(stage + L.avg);
+    const double *sR = reinterpret_cast<const double *>(side + L.s_R);
+    const double *sA = reinterpret_cast<const double *>(side + L.s_avg);
     double Rn = sR[qs - d.sa] + (double)r;
     if (rule != kRuleCfr) Rn = Rn > 0.0 ? Rn : 0.0;
     Rg[qs] = Rn;
@@ -251,18 +265,27 @@ constexpr int kStreamThreads = kStreamCompute + 32;
 
 // Grid: nb_chance blocks over narrow chance nodes, then the streaming CTAs
 // over chunks [c0, c1) of this depth (a depth with wide chance nodes does
-// not stream). Barriers of a streaming CTA (every wait bounded):
-//   full[s]   the copies of the chunk in stage s have landed (bytes counted)
-//   empty[s]  all threads are done with stage s (the control warp refills it)
+// not stream). Chunk i of a CTA uses stage i % kStreamStages (the compute
+// threads' data) and side slot i % kStreamSideSlots (set records, R and
+// average for the control warp's slot updates). Barriers of a streaming CTA
+// (every wait bounded):
+//   full[s]   the copies of the chunk in stage s and its side slot have
+//             landed (bytes counted)
+//   empty[s]  the compute threads are done with stage s
 //   rfull[p]  the compute threads have written the partial sums red[p]
 //   rempty[p] the control warp has consumed red[p]
-// The compute warps never wait for a slot update: the control warp runs
-// each group's update while they work on the next group.
+// The compute warps never wait for a slot update, and a stage is refilled as
+// soon as the compute threads are done with it: the control warp issues the
+// refill when the chunk's last group has been handed over, before it updates
+// that group's slots (from the side slot, which the refill does not touch:
+// the side ring is two chunks deeper than the stages, and the control warp
+// works through chunks in order).
 template <int MAXA>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     bwd_stream_kernel(GameView g, StateView<float> st, LevelWork w, int nb_chance, const SetInfo *info,
                       const StreamChunk *chunks, int32_t c0, int32_t c1, int rule, int upd, int *err) {
-  extern __shared__ __align__(128) unsigned char s_stage[];
+  static_assert(kStreamSideSlots >= 2 * kStreamStages, "side slots must outlast the stages by a full ring");
+  extern __shared__ __align__(128) unsigned char s_stage[];  // stages, then side slots
   __shared__ __align__(8) uint64_t s_full[kStreamStages], s_empty[kStreamStages], s_rfull[2], s_rempty[2];
   __shared__ StreamChunk s_desc[kStreamStages];
   __shared__ float s_red[2][kStreamWarps][4][2 * MAXA];
@@ -277,14 +300,22 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const int32_t nb = (int32_t)gridDim.x - nb_chance;
   const int tid = threadIdx.x, lane = tid & 31;
   const bool control = tid >= kStreamCompute;
+  const bool producer = tid == kStreamCompute;
+  unsigned char *s_side = s_stage + kStreamStages * kStreamStageBytes;
   if ((smem_u32(s_stage) & 15u) != 0u) {  // bulk copies need 16-byte aligned destinations
     if (tid == 0) atomicExch(err, 1);
     return;
   }
-  if (tid == kStreamCompute) {
+  auto issue = [&](int32_t i, const StreamChunk &dsc) {
+    const int s = i % kStreamStages;
+    s_desc[s] = dsc;
+    return stream_issue(dsc, s_stage + s * kStreamStageBytes, s_side + (i % kStreamSideSlots) * kStreamSideBytes,
+                        smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg);
+  };
+  if (producer) {
     for (int s = 0; s < kStreamStages; ++s) {
       mbar_init(smem_u32(&s_full[s]), 1);
-      mbar_init(smem_u32(&s_empty[s]), kStreamThreads);
+      mbar_init(smem_u32(&s_empty[s]), kStreamCompute);
     }
     for (int p = 0; p < 2; ++p) {
       mbar_init(smem_u32(&s_rfull[p]), kStreamCompute);
@@ -292,12 +323,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int s = 0; s < kStreamStages; ++s) {  // the first chunks of this CTA
-      const int32_t c = c0 + b + s * nb;
+    for (int i = 0; i < kStreamStages; ++i) {  // the first chunks of this CTA
+      const int32_t c = c0 + b + i * nb;
       if (c >= c1) break;
-      s_desc[s] = chunks[c];
-      if (!stream_issue(s_desc[s], s_stage + s * kStreamStageBytes, smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs,
-                        info, st.sigma, st.R, st.avg)) {
+      if (!issue(i, chunks[c])) {
         atomicExch(err, 1);  // a chunk larger than a stage: never issued, every wait below gives up
         break;
       }
@@ -308,7 +337,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   // error exit of the thread that issues copies: let every chunk it issued
   // and nobody waited for land (bounded waits), then leave
   auto drain = [&](int32_t i0) {
-    if (tid != kStreamCompute) return;
+    if (!producer) return;
     for (int k = 0; k < kStreamStages; ++k)
       if (c0 + b + (i0 + k) * nb < c1)
         mbar_wait(smem_u32(&s_full[(i0 + k) % kStreamStages]), (uint32_t)(((i0 + k) / kStreamStages) & 1));
@@ -327,12 +356,13 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     const StreamChunk d = s_desc[s];
     const StreamLayout L = stream_layout(d);
     const unsigned char *stage = s_stage + s * kStreamStageBytes;
+    const unsigned char *side = s_side + (i % kStreamSideSlots) * kStreamSideBytes;
+    const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(control ? side + L.s_info : stage + L.info);
     // the descriptor of the chunk that refills this stage, loaded now so that
     // its latency overlaps this chunk's work
     const int32_t cn = c + kStreamStages * nb;
     StreamChunk nd;
-    if (tid == kStreamCompute && cn < c1) nd = chunks[cn];
-    const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
+    if (producer && cn < c1) nd = chunks[cn];
     for (int32_t I = d.I0; I < d.I1; ++grp) {
       const int G = sinfo[I - d.I0].flags & 7;
       const int p = grp & 1;
@@ -353,32 +383,32 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
           }
         }
         mbar_arrive(smem_u32(&s_rfull[p]));
+        if (I + G >= d.I1) mbar_arrive(smem_u32(&s_empty[s]));  // this thread is done with stage s
       } else {
         if (!mbar_wait(smem_u32(&s_rfull[p]), rpar)) {
           atomicExch(err, 1);
           drain(i + 1);
           return;
         }
-        stream_update<MAXA>(d, L, stage, I, G, st.sigma, st.R, st.avg, wt, rule, upd, s_red[p]);
+        if (I + G >= d.I1) {
+          // the chunk's last group is handed over: the compute threads are
+          // about done with stage s, so refill it (with the chunk
+          // kStreamStages ahead) before updating this group's slots
+          __syncwarp();  // every control lane has read this chunk's descriptor
+          if (producer && cn < c1) {
+            if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
+              atomicExch(err, 1);
+              drain(i + 1);
+              return;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (!issue(i + kStreamStages, nd)) atomicExch(err, 1);  // never issued: the next wait gives up
+          }
+        }
+        stream_update<MAXA>(d, L, side, I, G, st.sigma, st.R, st.avg, wt, rule, upd, s_red[p]);
         mbar_arrive(smem_u32(&s_rempty[p]));
       }
       I += G;
-    }
-    mbar_arrive(smem_u32(&s_empty[s]));  // this thread is done with stage s
-    if (tid == kStreamCompute) {  // refill stage s with the chunk kStreamStages ahead
-      if (cn < c1) {
-        if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
-          atomicExch(err, 1);
-          drain(i + 1);
-          return;
-        } else {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          s_desc[s] = nd;
-          if (!stream_issue(nd, s_stage + s * kStreamStageBytes, smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs,
-                            info, st.sigma, st.R, st.avg))
-            atomicExch(err, 1);  // never issued: the next wait on this stage gives up
-        }
-      }
     }
   }
   // every chunk issued was waited on (full[s]) before the loop ended: no

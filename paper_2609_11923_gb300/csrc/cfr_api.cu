@@ -213,10 +213,10 @@ static void build_stream(cfr_handle *h) {
     std::vector<StreamChunk> ch;
     for (int32_t I = is0; ok && I < is1;) {
       int32_t J = I + (h->set_info[I].flags & 7);
-      if (stream_layout(make(I, J)).total > (uint32_t)kStreamStageBytes) { ok = false; break; }
+      if (!stream_fits(stream_layout(make(I, J)))) { ok = false; break; }
       while (J < is1) {  // extend by whole groups while the stage holds them
         const int32_t K = J + (h->set_info[J].flags & 7);
-        if (stream_layout(make(I, K)).total > (uint32_t)kStreamStageBytes) break;
+        if (!stream_fits(stream_layout(make(I, K)))) break;
         J = K;
       }
       ch.push_back(make(I, J));

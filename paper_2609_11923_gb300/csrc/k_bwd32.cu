@@ -9,12 +9,12 @@ template <int MA>
 static cudaError_t stream_one(int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w, int nb_chance,
                               const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
                               int *err, bool pdl) {
-  return launch_k(bwd_stream_kernel<MA>, grid, kStreamThreads, (size_t)(kStreamStages * kStreamStageBytes), s, pdl, g, st, w,
+  return launch_k(bwd_stream_kernel<MA>, grid, kStreamThreads, (size_t)kStreamDynSmem, s, pdl, g, st, w,
                   nb_chance, info, chunks, c0, c1, rule, upd, err);
 }
 
 cudaError_t prepare_bwd_stream() {
-  const int dyn = kStreamStages * kStreamStageBytes;
+  const int dyn = kStreamDynSmem;
   cudaError_t e = cudaFuncSetAttribute(bwd_stream_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(bwd_stream_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);

@@ -16,7 +16,8 @@ import pytest
 import gamegen as gg
 from paper_2609_11923_gb300 import cfr
 
-STAGE = 48 * 1024
+STAGE = 48 * 1024  # bytes of a stage (the compute threads' data)
+SIDE = 2048  # bytes of a side slot (the control warp's data)
 
 GAMES = {
     "tiny": lambda: gg.tiny_card(),
@@ -32,16 +33,19 @@ GAMES = {
 
 
 def layout(k):
-    """Byte offsets of the staged arrays (the kernel's stream_layout)."""
+    """Byte offsets of the staged arrays (the kernel's stream_layout): the
+    stage the compute threads read, and the side slot the control warp reads
+    (set records, R, average)."""
     I0, I1, ra, nra, va, nva, ka, nka, sa, nsa = k[:10]
     off = {"reach": 0}
     off["val"] = off["reach"] + 8 * nra
     off["mem"] = off["val"] + 4 * nva
     off["info"] = off["mem"] + 4 * nka
     off["sig"] = off["info"] + 32 * (I1 - I0)
-    off["R"] = off["sig"] + 4 * nsa
-    off["avg"] = off["R"] + 8 * nsa
-    off["total"] = off["avg"] + 8 * nsa
+    off["total"] = off["sig"] + 4 * nsa
+    off["s_R"] = 32 * (I1 - I0)
+    off["s_avg"] = off["s_R"] + 8 * nsa
+    off["s_total"] = off["s_avg"] + 8 * nsa
     return off
 
 
@@ -103,8 +107,8 @@ def test_stream_chunks_cover_the_sets_and_stay_in_bounds(name, tiles):
                     I += G
                 assert I == I1
                 off = layout(k)
-                assert off["total"] <= STAGE
-                for key in ("val", "mem", "info", "sig", "R", "avg", "total"):
+                assert off["total"] <= STAGE and off["s_total"] <= SIDE
+                for key in ("val", "mem", "info", "sig", "total", "s_R", "s_avg", "s_total"):
                     assert off[key] % 16 == 0
                 # copies: 16-byte aligned starts, inside the padded buffers
                 assert ra % 2 == 0 and nra % 2 == 0 and va % 4 == 0 and nva % 4 == 0
