@@ -387,3 +387,18 @@ def test_binding_constants_mirror_the_header():
                 fields += [n.strip(" *") for n in names.split(",")]
         assert fields == [f[0] for f in pyclass._fields_], cname
         assert ctypes.sizeof(pyclass) >= 4 * len(fields)
+
+
+def test_auto_picks_the_form_by_the_measured_crossover():
+    # the persistent form up to 768 nodes in FP32 and 350 in FP64 (where it
+    # was measured faster than graph replay), graph replay above
+    cases = [(gg.tiny_card(), cfr.P32, cfr.EXEC_PERSISTENT), (gg.tiny_card(), cfr.P64, cfr.EXEC_PERSISTENT),
+             (gg.random_tree(3, depth=6), cfr.P32, cfr.EXEC_PERSISTENT),
+             (gg.random_tree(3, depth=6), cfr.P64, cfr.EXEC_GRAPH),
+             (gg.random_tree(3, depth=7), cfr.P32, cfr.EXEC_GRAPH)]
+    for g, prec, form in cases:
+        h = cfr.cfr_compile(g, cfr.make_options(precision=prec, exec_form=cfr.EXEC_AUTO))
+        try:
+            assert cfr.cfr_get_counts(h)["exec_form"] == form, (g.n_nodes, prec)
+        finally:
+            cfr.cfr_destroy(h)
