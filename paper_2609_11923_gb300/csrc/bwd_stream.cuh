@@ -260,10 +260,65 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// The narrow chance nodes of a streaming depth, by the grid's first
+// nb_chance blocks: block b takes ranges of kStreamThreads consecutive nodes
+// (b, b + nb_chance, ...). Consecutive chance nodes of a depth have their
+// children in consecutive value slots, so a range's children form one run,
+// which all threads load into shared memory with independent 16-byte loads
+// (many in flight per thread) before thread t sums node t's children from
+// there. Each node's children are added left to right, as in bwd_chance: the
+// same value bit for bit. A node whose children lie outside the staged run,
+// or a run longer than the buffer, is summed from global memory.
+constexpr int kChanceUnroll = 8;
+__device__ __forceinline__ void stream_chance(const GameView &g, float *v, const LevelWork &w, int nb_chance,
+                                              float *buf, int32_t cap) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int32_t i0 = w.ch0 + (int32_t)blockIdx.x * NT; i0 < w.ch1; i0 += nb_chance * NT) {
+    const int32_t i1 = min(i0 + NT, w.ch1);
+    const int32_t lo = __ldg(g.ch_vb + i0) & ~3;  // 16-byte aligned start (the value array is 256-byte aligned)
+    const int32_t hi = __ldg(g.ch_vb + i1 - 1) + __ldg(g.ch_nch + i1 - 1);
+    const bool staged = hi >= lo && hi - lo <= cap;  // uniform over the block
+    if (staged) {
+      const int32_t n4 = (hi - lo) >> 2;  // whole 16-byte words inside [lo, hi)
+      const float4 *v4 = reinterpret_cast<const float4 *>(v + lo);
+      float4 *b4 = reinterpret_cast<float4 *>(buf);
+      for (int32_t k0 = 0; k0 < n4; k0 += kChanceUnroll * NT) {
+        float4 r[kChanceUnroll];
+#pragma unroll
+        for (int u = 0; u < kChanceUnroll; ++u) {
+          const int32_t k = k0 + u * NT + tid;
+          if (k < n4) r[u] = v4[k];
+        }
+#pragma unroll
+        for (int u = 0; u < kChanceUnroll; ++u) {
+          const int32_t k = k0 + u * NT + tid;
+          if (k < n4) b4[k] = r[u];
+        }
+      }
+      const int32_t t = 4 * n4 + tid;  // the last 0-3 values
+      if (t < hi - lo) buf[t] = v[lo + t];
+      __syncthreads();
+    }
+    const int32_t i = i0 + tid;
+    if (i < i1) {
+      const int32_t cb = __ldg(g.ch_vb + i), n = __ldg(g.ch_nch + i);
+      float sum = 0.f;
+      if (staged && cb >= lo && cb + n <= hi) {
+        const float *p = buf + (cb - lo);
+        for (int32_t c = 0; c < n; ++c) sum = sum + p[c];
+      } else {
+        for (int32_t c = 0; c < n; ++c) sum = sum + v[cb + c];
+      }
+      v[__ldg(g.ch_vs + i)] = sum;
+    }
+    if (staged) __syncthreads();  // the buffer is reused by the next range
+  }
+}
+
 // Threads of a streaming CTA: kStreamCompute compute threads and one control warp.
 constexpr int kStreamThreads = kStreamCompute + 32;
 
-// Grid: nb_chance blocks over narrow chance nodes, then the streaming CTAs
+// Grid: nb_chance blocks over narrow chance nodes (stream_chance), then the streaming CTAs
 // over chunks [c0, c1) of this depth (a depth with wide chance nodes does
 // not stream). Chunk i of a CTA uses stage i % kStreamStages (the compute
 // threads' data) and side slot i % kStreamSideSlots (set records, R and
@@ -291,9 +346,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   __shared__ float s_red[2][kStreamWarps][4][2 * MAXA];
   pdl_enter();
   if ((int)blockIdx.x < nb_chance) {
-    const int32_t stride = nb_chance * blockDim.x;
-    for (int32_t i = w.ch0 + blockIdx.x * blockDim.x + threadIdx.x; i < w.ch1; i += stride)
-      bwd_chance<float, false>(g, st.v, i);
+    stream_chance(g, st.v, w, nb_chance, reinterpret_cast<float *>(s_stage), kStreamDynSmem / 4);
     return;
   }
   const int32_t b = (int32_t)blockIdx.x - nb_chance;

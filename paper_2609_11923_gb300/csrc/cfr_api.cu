@@ -581,7 +581,8 @@ static void bwd_blocks(const cfr_handle *h, int d, int *nb_ch, int *nb_wide, int
   const LevelWork &w = h->levels[d];
   const int nch = d > 0 ? w.ch1 - w.ch0 : 0, nis = w.is1 - w.is0;  // a chance root is skipped
   const int lanes = h->level_lanes[d];
-  *nb_ch = nch > 0 ? grid_for(nch, kThreads) : 0;
+  // the streaming form's chance blocks take ranges of kStreamThreads nodes
+  *nb_ch = nch > 0 ? grid_for(nch, lanes == kStreamLanes ? kStreamThreads : kThreads) : 0;
   *nb_wide = d > 0 ? w.wc1 - w.wc0 : 0;
   if (lanes == kStreamLanes) *nb_is = nis > 0 ? stream_ctas(h, d) : 0;
   else *nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;

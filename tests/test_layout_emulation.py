@@ -97,11 +97,28 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS, stream=Fa
     def chance_sums(d):
         if d == 0:  # the root's value is not needed
             return
-        for i in range(lch[d], lch[d + 1]):
-            acc = 0.0
-            for c in range(chb[i], chb[i] + chn[i]):
-                acc = acc + v[c]
-            v[chs[i]] = acc
+        if stream and sok[d]:
+            # the streaming kernel's chance blocks: ranges of 288 nodes, each
+            # range's children staged as one run [lo, hi) from a 16-byte
+            # boundary, every node summed from the staged copy
+            for i0 in range(lch[d], lch[d + 1], 288):
+                i1 = min(i0 + 288, lch[d + 1])
+                lo = chb[i0] & ~3
+                hi = chb[i1 - 1] + chn[i1 - 1]
+                assert hi >= lo and hi - lo <= (2 * 48 * 1024 + 4 * 2048) // 4
+                buf = staged(v, lo, hi - lo, float("nan"))
+                for i in range(i0, i1):
+                    assert chb[i] >= lo and chb[i] + chn[i] <= hi
+                    acc = 0.0
+                    for c in range(chb[i] - lo, chb[i] - lo + chn[i]):
+                        acc = acc + buf[c]
+                    v[chs[i]] = acc
+        else:
+            for i in range(lch[d], lch[d + 1]):
+                acc = 0.0
+                for c in range(chb[i], chb[i] + chn[i]):
+                    acc = acc + v[c]
+                v[chs[i]] = acc
         for i in range(len(wvs)):
             if wide_depth[i] == d:
                 acc = 0.0

@@ -137,6 +137,55 @@ def test_stream_chunks_cover_the_sets_and_stay_in_bounds(name, tiles):
         cfr.cfr_destroy(h)
 
 
+STREAM_THREADS = 288  # threads of a streaming CTA: a chance block's range of nodes
+CHANCE_CAP = (2 * STAGE + 4 * SIDE) // 4  # floats of a chance block's buffer (the whole dynamic shared memory)
+
+
+def chance_ranges(chb, chn, lo_i, hi_i):
+    """The chance blocks' ranges of the kernel (stream_chance): per range of
+    STREAM_THREADS consecutive nodes, the staged run [lo, hi) of value slots,
+    whether it is staged, the whole 16-byte words it loads and its tail."""
+    for i0 in range(lo_i, hi_i, STREAM_THREADS):
+        i1 = min(i0 + STREAM_THREADS, hi_i)
+        lo = chb[i0] & ~3
+        hi = chb[i1 - 1] + chn[i1 - 1]
+        staged = hi >= lo and hi - lo <= CHANCE_CAP
+        yield i0, i1, lo, hi, staged, (hi - lo) >> 2
+
+
+@pytest.mark.parametrize("name", list(GAMES))
+def test_stream_chance_ranges_stay_in_bounds(name):
+    # every load of a chance block lies in [lo, hi) inside the value array,
+    # every shared-memory index in the buffer, and on these games every node's
+    # children lie in its range's staged run (consecutive chance nodes have
+    # consecutive child runs), so no node takes the global-memory fallback
+    g = GAMES[name]()
+    h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P32, lanes_per_set=cfr.STREAM_LANES))
+    try:
+        ex = lambda n: cfr.cfr_export_array(h, n).astype(np.int64)
+        c = cfr.cfr_get_counts(h)
+        ok, lch = ex("stream_ok"), ex("level_chance")
+        chb, chn = ex("ch_vb"), ex("ch_nch")
+        N = c["n_nodes"]
+        ranges = 0
+        for d in range(c["depth_blocks"]):
+            if not ok[d] or lch[d + 1] == lch[d]:
+                continue
+            assert (np.diff(chb[lch[d]:lch[d + 1]]) == chn[lch[d]:lch[d + 1] - 1]).all()
+            for i0, i1, lo, hi, staged, n4 in chance_ranges(chb, chn, lch[d], lch[d + 1]):
+                assert staged and lo % 4 == 0 and 0 <= lo and hi <= N - 1
+                assert 4 * n4 <= hi - lo < 4 * n4 + 4  # words, then a tail of at most 3 values
+                assert hi - lo <= CHANCE_CAP
+                cb, n = chb[i0:i1], chn[i0:i1]
+                assert (cb >= lo).all() and (cb + n <= hi).all()
+                assert chb[i0] - lo <= 3 and hi - lo - n.sum() <= 3
+                ranges += 1
+        if name.startswith("card"):
+            assert ranges > 0
+    finally:
+        cfr.cfr_destroy(h)
+
+
 def test_streaming_needs_fp32_member_order():
     g = gg.tiny_card()
     for kw in ({"precision": cfr.P64}, {"reach_order": cfr.REACH_BFS}):
