@@ -305,7 +305,10 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * (1, 4 for a tile, 0 inside one), bit 8 player 2), 33 its chunks [16 per
  * chunk: sets I0, I1, then the staged element ranges (start, count) of
  * reach ranks, child value slots, members and slots, widened to 16-byte
- * boundaries; 6 unused], 34 first chunk of each depth [D+1], 35 per depth
+ * boundaries, then the kind (0 sets; 1 chance: I0, I1 are narrow chance
+ * nodes, the ranges their children's value slots and their entries of the
+ * chance arrays, reach and slot ranges 0); 5 unused; each depth's set
+ * chunks come first], 34 first chunk of each depth [D+1], 35 per depth
  * whether it can stream [D] (all empty unless FP32 in member order with sets
  * of at most 8 actions).
  * Integer arrays are int32. *count receives the element count; out may be

@@ -9,11 +9,14 @@
 // slots), their members' own value slots, their slots' strategy, regret and
 // average, and their set descriptors. The host cuts each depth's sets into
 // chunks of whole groups (a tile of four sets, or one untiled set) whose
-// staged bytes fit one pipeline stage. Every CTA walks the chunks c =
-// blockIdx, blockIdx + grid, ... through a ring of kStreamStages stages. Its
-// kStreamCompute compute threads do the members' work; one more warp, the control
-// warp, issues each chunk's seven cp.async.bulk copies into a stage (the
-// stage's mbarrier counts their bytes) and runs every group's slot update.
+// staged bytes fit one pipeline stage; the depth's narrow chance nodes
+// follow as chance chunks (consecutive nodes, whose children are one run of
+// value slots, and their entries of the chance arrays), summed in the same
+// pipeline. Every CTA walks the chunks c = blockIdx, blockIdx + grid, ...
+// through a ring of kStreamStages stages. Its kStreamCompute compute threads
+// do the members' (or chance nodes') work; one more warp, the control warp,
+// issues each chunk's cp.async.bulk copies into a stage (the stage's
+// mbarrier counts their bytes) and runs every group's slot update.
 // The loads in flight cost no registers, so the memory pipe stays full at a
 // low warp count, and the compute warps never wait for a slot update (they
 // hand each group's partial sums over through a double-buffered array and a
@@ -42,6 +45,7 @@ constexpr int kStreamDynSmem = kStreamStages * kStreamStageBytes + kStreamSideSl
 constexpr int kStreamCompute = 256;               // compute threads of a streaming CTA (two CTAs per SM)
 constexpr int kStreamWarps = kStreamCompute / 32;
 constexpr int kStreamMinMembers = 32;             // mean members per set below which the autotuner does not try it
+constexpr int kStreamChanceMax = 4 * kStreamCompute;  // chance nodes per chance chunk at most
 
 // Per information set (member order), 32 bytes, read by the streaming form.
 struct SetInfo {
@@ -52,17 +56,23 @@ struct SetInfo {
   int32_t flags;         // bits 0-2: G (sets in the group it starts: 1 or 4; 0 inside a tile); bit 8: player 2
 };
 
-// One chunk of consecutive sets [I0, I1) and the element ranges it stages,
-// widened to 16-byte boundaries: reach ranks [ra, ra + nra) (even), value
-// slots [va, va + nva), members [ka, ka + nka), slots [sa, sa + nsa)
-// (multiples of 4).
+// One chunk and the element ranges it stages, widened to 16-byte
+// boundaries. A set chunk (kind kChunkSets): consecutive sets [I0, I1),
+// reach ranks [ra, ra + nra) (even), value slots [va, va + nva), members
+// [ka, ka + nka), slots [sa, sa + nsa) (multiples of 4). A chance chunk
+// (kind kChunkChance): consecutive narrow chance nodes [I0, I1) of the
+// depth, their children's value slots [va, va + nva) and their entries
+// [ka, ka + nka) of the chance arrays (first child slot, child count, own
+// value slot); ra = nra = sa = nsa = 0.
+constexpr int32_t kChunkSets = 0, kChunkChance = 1;
 struct StreamChunk {
   int32_t I0, I1;
   int32_t ra, nra;
   int32_t va, nva;
   int32_t ka, nka;
   int32_t sa, nsa;
-  int32_t pad[6];
+  int32_t kind;
+  int32_t pad[5];
 };
 
 static_assert(sizeof(SetInfo) == 32, "SetInfo is staged in 32-byte records");
@@ -94,6 +104,25 @@ __host__ __device__ inline StreamLayout stream_layout(const StreamChunk &c) {
 
 __host__ __device__ inline bool stream_fits(const StreamLayout &L) {
   return L.total <= (uint32_t)kStreamStageBytes && L.s_total <= (uint32_t)kStreamSideBytes;
+}
+
+// A chance chunk's stage: the children's values, then its entries of the
+// three chance arrays (nothing in the side slot).
+struct ChanceLayout {
+  uint32_t vb, nch, vs, total;  // offsets of ch_vb, ch_nch, ch_vs entries; bytes
+};
+
+__host__ __device__ inline ChanceLayout chance_layout(const StreamChunk &c) {
+  ChanceLayout L;
+  L.vb = 4u * (uint32_t)c.nva;
+  L.nch = L.vb + 4u * (uint32_t)c.nka;
+  L.vs = L.nch + 4u * (uint32_t)c.nka;
+  L.total = L.vs + 4u * (uint32_t)c.nka;
+  return L;
+}
+
+__host__ __device__ inline bool chance_fits(const StreamChunk &c) {
+  return c.nva > 0 && c.nka > 0 && c.I1 > c.I0 && chance_layout(c).total <= (uint32_t)kStreamStageBytes;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -139,7 +168,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char *stage, unsigned char *side,
                                              uint32_t bar, const float2 *reach, const float *v,
                                              const int32_t *mem_vs, const SetInfo *info, const float *sigma,
-                                             const double *R, const double *avg) {
+                                             const double *R, const double *avg, const GameView &g) {
+  if (d.kind == kChunkChance) {
+    if (!chance_fits(d)) return false;
+    const ChanceLayout C = chance_layout(d);
+    const uint32_t s = smem_u32(stage);
+    mbar_expect_tx(bar, C.total);  // the four sizes below add up to this
+    bulk_g2s(s, v + d.va, C.vb, bar);
+    bulk_g2s(s + C.vb, g.ch_vb + d.ka, C.nch - C.vb, bar);
+    bulk_g2s(s + C.nch, g.ch_nch + d.ka, C.vs - C.nch, bar);
+    bulk_g2s(s + C.vs, g.ch_vs + d.ka, C.total - C.vs, bar);
+    return true;
+  }
+  if (d.kind != kChunkSets) return false;
   const StreamLayout L = stream_layout(d);
   if (!stream_fits(L) || d.nra <= 0 || d.nva <= 0 || d.nka <= 0 || d.I1 <= d.I0 || d.nsa <= 0) return false;
   const uint32_t s = smem_u32(stage), t = smem_u32(side);
@@ -260,67 +301,31 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// The narrow chance nodes of a streaming depth, by the grid's first
-// nb_chance blocks: block b takes ranges of kStreamThreads consecutive nodes
-// (b, b + nb_chance, ...). Consecutive chance nodes of a depth have their
-// children in consecutive value slots, so a range's children form one run,
-// which all threads load into shared memory with independent 16-byte loads
-// (many in flight per thread) before thread t sums node t's children from
-// there. Each node's children are added left to right, as in bwd_chance: the
-// same value bit for bit. A node whose children lie outside the staged run,
-// or a run longer than the buffer, is summed from global memory.
-constexpr int kChanceUnroll = 8;
-__device__ __forceinline__ void stream_chance(const GameView &g, float *v, const LevelWork &w, int nb_chance,
-                                              float *buf, int32_t cap) {
-  const int tid = threadIdx.x, NT = blockDim.x;
-  for (int32_t i0 = w.ch0 + (int32_t)blockIdx.x * NT; i0 < w.ch1; i0 += nb_chance * NT) {
-    const int32_t i1 = min(i0 + NT, w.ch1);
-    const int32_t lo = __ldg(g.ch_vb + i0) & ~3;  // 16-byte aligned start (the value array is 256-byte aligned)
-    const int32_t hi = __ldg(g.ch_vb + i1 - 1) + __ldg(g.ch_nch + i1 - 1);
-    const bool staged = hi >= lo && hi - lo <= cap;  // uniform over the block
-    if (staged) {
-      const int32_t n4 = (hi - lo) >> 2;  // whole 16-byte words inside [lo, hi)
-      const float4 *v4 = reinterpret_cast<const float4 *>(v + lo);
-      float4 *b4 = reinterpret_cast<float4 *>(buf);
-      for (int32_t k0 = 0; k0 < n4; k0 += kChanceUnroll * NT) {
-        float4 r[kChanceUnroll];
-#pragma unroll
-        for (int u = 0; u < kChanceUnroll; ++u) {
-          const int32_t k = k0 + u * NT + tid;
-          if (k < n4) r[u] = v4[k];
-        }
-#pragma unroll
-        for (int u = 0; u < kChanceUnroll; ++u) {
-          const int32_t k = k0 + u * NT + tid;
-          if (k < n4) b4[k] = r[u];
-        }
-      }
-      const int32_t t = 4 * n4 + tid;  // the last 0-3 values
-      if (t < hi - lo) buf[t] = v[lo + t];
-      __syncthreads();
-    }
-    const int32_t i = i0 + tid;
-    if (i < i1) {
-      const int32_t cb = __ldg(g.ch_vb + i), n = __ldg(g.ch_nch + i);
-      float sum = 0.f;
-      if (staged && cb >= lo && cb + n <= hi) {
-        const float *p = buf + (cb - lo);
-        for (int32_t c = 0; c < n; ++c) sum = sum + p[c];
-      } else {
-        for (int32_t c = 0; c < n; ++c) sum = sum + v[cb + c];
-      }
-      v[__ldg(g.ch_vs + i)] = sum;
-    }
-    if (staged) __syncthreads();  // the buffer is reused by the next range
+// The compute threads' work on a staged chance chunk: thread t sums the
+// children of nodes I0 + t, I0 + t + kStreamCompute, ... left to right (as
+// bwd_chance does: the same value bit for bit) and writes the node's value.
+__device__ __forceinline__ void stream_chance_chunk(const StreamChunk &d, const unsigned char *stage, float *v) {
+  const ChanceLayout C = chance_layout(d);
+  const float *sv = reinterpret_cast<const float *>(stage);
+  const int32_t *svb = reinterpret_cast<const int32_t *>(stage + C.vb);
+  const int32_t *snc = reinterpret_cast<const int32_t *>(stage + C.nch);
+  const int32_t *svs = reinterpret_cast<const int32_t *>(stage + C.vs);
+  for (int32_t i = d.I0 + (int32_t)threadIdx.x; i < d.I1; i += kStreamCompute) {
+    const int32_t k = i - d.ka;
+    const float *p = sv + (svb[k] - d.va);
+    const int32_t n = snc[k];
+    float sum = 0.f;
+    for (int32_t c = 0; c < n; ++c) sum = sum + p[c];
+    v[svs[k]] = sum;
   }
 }
 
 // Threads of a streaming CTA: kStreamCompute compute threads and one control warp.
 constexpr int kStreamThreads = kStreamCompute + 32;
 
-// Grid: nb_chance blocks over narrow chance nodes (stream_chance), then the streaming CTAs
-// over chunks [c0, c1) of this depth (a depth with wide chance nodes does
-// not stream). Chunk i of a CTA uses stage i % kStreamStages (the compute
+// Grid: the streaming CTAs over chunks [c0, c1) of this depth (its set
+// chunks, then its chance chunks; a depth with wide chance nodes does not
+// stream). Chunk i of a CTA uses stage i % kStreamStages (the compute
 // threads' data) and side slot i % kStreamSideSlots (set records, R and
 // average for the control warp's slot updates). Barriers of a streaming CTA
 // (every wait bounded):
@@ -337,20 +342,16 @@ constexpr int kStreamThreads = kStreamCompute + 32;
 // works through chunks in order).
 template <int MAXA>
 __global__ void __launch_bounds__(kStreamThreads, 2)
-    bwd_stream_kernel(GameView g, StateView<float> st, LevelWork w, int nb_chance, const SetInfo *info,
-                      const StreamChunk *chunks, int32_t c0, int32_t c1, int rule, int upd, int *err) {
+    bwd_stream_kernel(GameView g, StateView<float> st, const SetInfo *info, const StreamChunk *chunks, int32_t c0,
+                      int32_t c1, int rule, int upd, int *err) {
   static_assert(kStreamSideSlots >= 2 * kStreamStages, "side slots must outlast the stages by a full ring");
   extern __shared__ __align__(128) unsigned char s_stage[];  // stages, then side slots
   __shared__ __align__(8) uint64_t s_full[kStreamStages], s_empty[kStreamStages], s_rfull[2], s_rempty[2];
   __shared__ StreamChunk s_desc[kStreamStages];
   __shared__ float s_red[2][kStreamWarps][4][2 * MAXA];
   pdl_enter();
-  if ((int)blockIdx.x < nb_chance) {
-    stream_chance(g, st.v, w, nb_chance, reinterpret_cast<float *>(s_stage), kStreamDynSmem / 4);
-    return;
-  }
-  const int32_t b = (int32_t)blockIdx.x - nb_chance;
-  const int32_t nb = (int32_t)gridDim.x - nb_chance;
+  const int32_t b = (int32_t)blockIdx.x;
+  const int32_t nb = (int32_t)gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31;
   const bool control = tid >= kStreamCompute;
   const bool producer = tid == kStreamCompute;
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     const int s = i % kStreamStages;
     s_desc[s] = dsc;
     return stream_issue(dsc, s_stage + s * kStreamStageBytes, s_side + (i % kStreamSideSlots) * kStreamSideBytes,
-                        smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg);
+                        smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg, g);
   };
   if (producer) {
     for (int s = 0; s < kStreamStages; ++s) {
@@ -407,15 +408,35 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
       return;
     }
     const StreamChunk d = s_desc[s];
-    const StreamLayout L = stream_layout(d);
     const unsigned char *stage = s_stage + s * kStreamStageBytes;
-    const unsigned char *side = s_side + (i % kStreamSideSlots) * kStreamSideBytes;
-    const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(control ? side + L.s_info : stage + L.info);
     // the descriptor of the chunk that refills this stage, loaded now so that
     // its latency overlaps this chunk's work
     const int32_t cn = c + kStreamStages * nb;
     StreamChunk nd;
     if (producer && cn < c1) nd = chunks[cn];
+    if (d.kind == kChunkChance) {
+      // no slot update: the control warp refills the stage as soon as the
+      // compute threads are done with it
+      if (!control) {
+        stream_chance_chunk(d, stage, st.v);
+        mbar_arrive(smem_u32(&s_empty[s]));
+      } else {
+        __syncwarp();  // every control lane has read this chunk's descriptor
+        if (producer && cn < c1) {
+          if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
+            atomicExch(err, 1);
+            drain(i + 1);
+            return;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (!issue(i + kStreamStages, nd)) atomicExch(err, 1);  // never issued: the next wait gives up
+        }
+      }
+      continue;
+    }
+    const StreamLayout L = stream_layout(d);
+    const unsigned char *side = s_side + (i % kStreamSideSlots) * kStreamSideBytes;
+    const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(control ? side + L.s_info : stage + L.info);
     for (int32_t I = d.I0; I < d.I1; ++grp) {
       const int G = sinfo[I - d.I0].flags & 7;
       const int p = grp & 1;

@@ -203,6 +203,21 @@ static void build_stream(cfr_handle *h) {
     k.nsa = (int32_t)(((shi + 3) & ~int64_t(3)) - k.sa);
     return k;
   };
+  // chance nodes [i0, i1) of one depth: their children's value slots
+  // [first child of i0, end of i1 - 1's) and their chance-array entries,
+  // widened to 16-byte boundaries
+  auto make_chance = [&](int32_t i0, int32_t i1) {
+    StreamChunk k{};
+    k.kind = kChunkChance;
+    k.I0 = i0;
+    k.I1 = i1;
+    const int64_t lo = c.ch_vb[i0], hi = (int64_t)c.ch_vb[i1 - 1] + c.ch_nch[i1 - 1];
+    k.va = (int32_t)(lo & ~int64_t(3));
+    k.nva = (int32_t)(std::max<int64_t>(((hi + 3) & ~int64_t(3)) - k.va, 4));
+    k.ka = i0 & ~3;
+    k.nka = ((i1 + 3) & ~3) - k.ka;
+    return k;
+  };
   for (int64_t d = 0; d < c.D; ++d) {
     h->stream_c0[d] = (int32_t)h->stream_chunks.size();
     const int32_t is0 = c.level_iset[2 * d], is1 = c.level_iset[2 * d + 2];
@@ -221,6 +236,20 @@ static void build_stream(cfr_handle *h) {
       }
       ch.push_back(make(I, J));
       I = J;
+    }
+    // then the depth's narrow chance nodes, in chunks of consecutive nodes
+    // whose children (consecutive value slots) and chance-array entries fit
+    // a stage; each node's child run must lie inside its chunk's
+    const int32_t q0 = c.level_chance[d], q1 = c.level_chance[d + 1];
+    for (int32_t i = q0; ok && i < q1;) {
+      int32_t j = i + 1;
+      if (!chance_fits(make_chance(i, j))) { ok = false; break; }
+      while (j < q1 && j - i < kStreamChanceMax && chance_fits(make_chance(i, j + 1))) ++j;
+      const StreamChunk k = make_chance(i, j);
+      for (int32_t q = i; q < j; ++q)
+        if (c.ch_vb[q] < k.va || (int64_t)c.ch_vb[q] + c.ch_nch[q] > (int64_t)k.va + k.nva) ok = false;
+      ch.push_back(k);
+      i = j;
     }
     if (ok) {
       h->stream_ok[d] = 1;
@@ -576,13 +605,14 @@ static int stream_ctas(const cfr_handle *h, int d) {
 }
 
 // Blocks of the backward launch of depth d (chance blocks, wide chunks, then
-// the information-set work).
+// the information-set work; the streaming form has only its CTAs over the
+// depth's set and chance chunks).
 static void bwd_blocks(const cfr_handle *h, int d, int *nb_ch, int *nb_wide, int *nb_is) {
   const LevelWork &w = h->levels[d];
   const int nch = d > 0 ? w.ch1 - w.ch0 : 0, nis = w.is1 - w.is0;  // a chance root is skipped
   const int lanes = h->level_lanes[d];
-  // the streaming form's chance blocks take ranges of kStreamThreads nodes
-  *nb_ch = nch > 0 ? grid_for(nch, lanes == kStreamLanes ? kStreamThreads : kThreads) : 0;
+  // the streaming form sums its chance nodes in chunks of its own
+  *nb_ch = nch > 0 && lanes != kStreamLanes ? grid_for(nch, kThreads) : 0;
   *nb_wide = d > 0 ? w.wc1 - w.wc0 : 0;
   if (lanes == kStreamLanes) *nb_is = nis > 0 ? stream_ctas(h, d) : 0;
   else *nb_is = nis > 0 ? grid_for(nis, kThreads / lanes) : 0;
@@ -601,9 +631,9 @@ static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3, bool pd
   bwd_blocks(h, d, &nb_ch, &nb_wide, &nb_is);
   const int lanes = h->level_lanes[d];
   if (lanes == kStreamLanes) {  // FP32 only (compile checks it); no wide chance nodes at this depth
-    CK(launch_bwd_stream(h->maxa_tier, nb_ch + nb_is, s, game_view(h), state_view<float>(h), w, nb_ch,
-                         h->p<SetInfo>(h->b_set_info), h->p<StreamChunk>(h->b_stream_chunks), h->stream_c0[d],
-                         h->stream_c0[d + 1], h->rule, upd, h->p<int>(h->b_err), pdl));
+    CK(launch_bwd_stream(h->maxa_tier, nb_is, s, game_view(h), state_view<float>(h), h->p<SetInfo>(h->b_set_info),
+                         h->p<StreamChunk>(h->b_stream_chunks), h->stream_c0[d], h->stream_c0[d + 1], h->rule, upd,
+                         h->p<int>(h->b_err), pdl));
     return CFR_OK;
   }
   // at least one block: the depth-0 launch also advances t

@@ -6,11 +6,10 @@ template cudaError_t launch_bwd_level<float>(int, int, int, cudaStream_t, GameVi
 
 namespace cfr {
 template <int MA>
-static cudaError_t stream_one(int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w, int nb_chance,
-                              const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
-                              int *err, bool pdl) {
-  return launch_k(bwd_stream_kernel<MA>, grid, kStreamThreads, (size_t)kStreamDynSmem, s, pdl, g, st, w,
-                  nb_chance, info, chunks, c0, c1, rule, upd, err);
+static cudaError_t stream_one(int grid, cudaStream_t s, GameView g, StateView<float> st, const SetInfo *info,
+                              const StreamChunk *chunks, int c0, int c1, int rule, int upd, int *err, bool pdl) {
+  return launch_k(bwd_stream_kernel<MA>, grid, kStreamThreads, (size_t)kStreamDynSmem, s, pdl, g, st, info, chunks,
+                  c0, c1, rule, upd, err);
 }
 
 cudaError_t prepare_bwd_stream() {
@@ -21,11 +20,11 @@ cudaError_t prepare_bwd_stream() {
   return e;
 }
 
-cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w,
-                              int nb_chance, const SetInfo *info, const StreamChunk *chunks, int c0, int c1,
-                              int rule, int upd, int *err, bool pdl) {
-  if (maxa == 4) return stream_one<4>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err, pdl);
-  if (maxa == 8) return stream_one<8>(grid, s, g, st, w, nb_chance, info, chunks, c0, c1, rule, upd, err, pdl);
+cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st,
+                              const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
+                              int *err, bool pdl) {
+  if (maxa == 4) return stream_one<4>(grid, s, g, st, info, chunks, c0, c1, rule, upd, err, pdl);
+  if (maxa == 8) return stream_one<8>(grid, s, g, st, info, chunks, c0, c1, rule, upd, err, pdl);
   return cudaErrorInvalidValue;
 }
 }  // namespace cfr

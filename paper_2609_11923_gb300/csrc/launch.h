@@ -27,11 +27,11 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), int grid, int block, size_t 
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// The streaming FP32 backward of one depth (bwd_stream_kernel); grid =
-// nb_chance + nb_wide + the streaming CTAs over chunks [c0, c1).
-cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st, LevelWork w,
-                              int nb_chance, const SetInfo *info, const StreamChunk *chunks, int c0, int c1,
-                              int rule, int upd, int *err, bool pdl);
+// The streaming FP32 backward of one depth (bwd_stream_kernel); grid = the
+// streaming CTAs over the depth's chunks [c0, c1) (set and chance chunks).
+cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st,
+                              const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
+                              int *err, bool pdl);
 // Allows the streaming kernel its dynamic shared memory (call before the
 // first launch, outside any stream capture; idempotent).
 cudaError_t prepare_bwd_stream();

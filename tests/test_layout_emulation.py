@@ -98,21 +98,24 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS, stream=Fa
         if d == 0:  # the root's value is not needed
             return
         if stream and sok[d]:
-            # the streaming kernel's chance blocks: ranges of 288 nodes, each
-            # range's children staged as one run [lo, hi) from a 16-byte
-            # boundary, every node summed from the staged copy
-            for i0 in range(lch[d], lch[d + 1], 288):
-                i1 = min(i0 + 288, lch[d + 1])
-                lo = chb[i0] & ~3
-                hi = chb[i1 - 1] + chn[i1 - 1]
-                assert hi >= lo and hi - lo <= (2 * 48 * 1024 + 4 * 2048) // 4
-                buf = staged(v, lo, hi - lo, float("nan"))
-                for i in range(i0, i1):
-                    assert chb[i] >= lo and chb[i] + chn[i] <= hi
+            # the streaming kernel's chance chunks: each node summed from
+            # its chunk's staged copies of the children's values and of the
+            # chance arrays, with the kernel's index arithmetic
+            for k in chunks[sc0[d]:sc0[d + 1]]:
+                if k[10] != 1:
+                    continue
+                I0, I1, va, nva, ka, nka = k[0], k[1], k[4], k[5], k[6], k[7]
+                sv = staged(v, va, nva, float("nan"))
+                svb, snc, svs = staged(list(chb), ka, nka, -1), staged(list(chn), ka, nka, -1), \
+                    staged(list(chs), ka, nka, -1)
+                for i in range(I0, I1):
+                    q = i - ka
+                    p0 = svb[q] - va
+                    assert 0 <= p0 and p0 + snc[q] <= nva
                     acc = 0.0
-                    for c in range(chb[i] - lo, chb[i] - lo + chn[i]):
-                        acc = acc + buf[c]
-                    v[chs[i]] = acc
+                    for c in range(p0, p0 + snc[q]):
+                        acc = acc + sv[c]
+                    v[svs[q]] = acc
         else:
             for i in range(lch[d], lch[d + 1]):
                 acc = 0.0
@@ -212,6 +215,8 @@ def emulate(h, iters, rule=oracle.CFR_PLUS, order=oracle.SIMULTANEOUS, stream=Fa
     def stream_depth(d, t, upd):
         nan2 = [float("nan"), float("nan")]
         for k in chunks[sc0[d]:sc0[d + 1]]:
+            if k[10] != 0:  # chance chunks: chance_sums
+                continue
             I0, I1, ra, nra, va, nva, ka, nka, sa, nsa = k[:10]
             st = (staged(reach, ra, nra, nan2), staged(v, va, nva, float("nan")), staged(list(mvs), ka, nka, -1),
                   staged(sigma, sa, nsa, float("nan")), staged(R, sa, nsa, float("nan")),

@@ -88,7 +88,11 @@ def test_stream_chunks_cover_the_sets_and_stay_in_bounds(name, tiles):
                 continue
             assert d > 0
             nxt = li[2 * d]
+            kinds = chunks[c0[d]:c0[d + 1], 10]
+            assert set(kinds) <= {0, 1} and (np.diff(kinds) >= 0).all()  # set chunks, then chance chunks
             for k in chunks[c0[d]:c0[d + 1]]:
+                if k[10] != 0:
+                    continue
                 I0, I1, ra, nra, va, nva, ka, nka, sa, nsa = k[:10]
                 assert I0 == nxt and I1 > I0
                 nxt = I1
@@ -137,51 +141,47 @@ def test_stream_chunks_cover_the_sets_and_stay_in_bounds(name, tiles):
         cfr.cfr_destroy(h)
 
 
-STREAM_THREADS = 288  # threads of a streaming CTA: a chance block's range of nodes
-CHANCE_CAP = (2 * STAGE + 4 * SIDE) // 4  # floats of a chance block's buffer (the whole dynamic shared memory)
-
-
-def chance_ranges(chb, chn, lo_i, hi_i):
-    """The chance blocks' ranges of the kernel (stream_chance): per range of
-    STREAM_THREADS consecutive nodes, the staged run [lo, hi) of value slots,
-    whether it is staged, the whole 16-byte words it loads and its tail."""
-    for i0 in range(lo_i, hi_i, STREAM_THREADS):
-        i1 = min(i0 + STREAM_THREADS, hi_i)
-        lo = chb[i0] & ~3
-        hi = chb[i1 - 1] + chn[i1 - 1]
-        staged = hi >= lo and hi - lo <= CHANCE_CAP
-        yield i0, i1, lo, hi, staged, (hi - lo) >> 2
+CHANCE_MAX = 1024  # chance nodes per chance chunk at most
 
 
 @pytest.mark.parametrize("name", list(GAMES))
-def test_stream_chance_ranges_stay_in_bounds(name):
-    # every load of a chance block lies in [lo, hi) inside the value array,
-    # every shared-memory index in the buffer, and on these games every node's
-    # children lie in its range's staged run (consecutive chance nodes have
-    # consecutive child runs), so no node takes the global-memory fallback
+def test_stream_chance_chunks_cover_the_chance_nodes_and_stay_in_bounds(name):
+    # a streaming depth's narrow chance nodes go in chance chunks, in order;
+    # each chunk stages its nodes' children (one run of value slots) and its
+    # entries of the three chance arrays: 16-byte aligned copies inside the
+    # padded buffers, a stage's bytes at most, and every index the kernel
+    # forms (a node's entry, its children in the run) inside what is staged
     g = GAMES[name]()
     h = cfr.cfr_compile(g, cfr.make_options(precision=cfr.P32, lanes_per_set=cfr.STREAM_LANES))
     try:
         ex = lambda n: cfr.cfr_export_array(h, n).astype(np.int64)
         c = cfr.cfr_get_counts(h)
-        ok, lch = ex("stream_ok"), ex("level_chance")
+        ok, lch, c0 = ex("stream_ok"), ex("level_chance"), ex("stream_c0")
+        chunks = ex("stream_chunks").reshape(-1, 16)
         chb, chn = ex("ch_vb"), ex("ch_nch")
-        N = c["n_nodes"]
-        ranges = 0
+        N, n_narrow = c["n_nodes"], len(chb)
+        nodes = 0
         for d in range(c["depth_blocks"]):
-            if not ok[d] or lch[d + 1] == lch[d]:
+            ks = [k for k in chunks[c0[d]:c0[d + 1]] if k[10] == 1]
+            if not ok[d]:
+                assert not ks
                 continue
-            assert (np.diff(chb[lch[d]:lch[d + 1]]) == chn[lch[d]:lch[d + 1] - 1]).all()
-            for i0, i1, lo, hi, staged, n4 in chance_ranges(chb, chn, lch[d], lch[d + 1]):
-                assert staged and lo % 4 == 0 and 0 <= lo and hi <= N - 1
-                assert 4 * n4 <= hi - lo < 4 * n4 + 4  # words, then a tail of at most 3 values
-                assert hi - lo <= CHANCE_CAP
-                cb, n = chb[i0:i1], chn[i0:i1]
-                assert (cb >= lo).all() and (cb + n <= hi).all()
-                assert chb[i0] - lo <= 3 and hi - lo - n.sum() <= 3
-                ranges += 1
+            nxt = lch[d]
+            for k in ks:
+                I0, I1, ra, nra, va, nva, ka, nka, sa, nsa = k[:10]
+                assert I0 == nxt and I1 > I0 and I1 - I0 <= CHANCE_MAX
+                nxt = I1
+                assert ra == nra == sa == nsa == 0 and (k[11:] == 0).all()
+                assert va % 4 == 0 and nva % 4 == 0 and ka % 4 == 0 and nka % 4 == 0
+                assert 4 * nva + 3 * 4 * nka <= STAGE
+                assert 0 <= va and 4 * (va + nva) <= padded(4 * N)
+                assert 0 <= ka <= I0 and I1 <= ka + nka and 4 * (ka + nka) <= padded(4 * n_narrow)
+                cb, n = chb[I0:I1], chn[I0:I1]
+                assert (cb >= va).all() and (cb + n <= va + nva).all()
+                nodes += I1 - I0
+            assert nxt == lch[d + 1]
         if name.startswith("card"):
-            assert ranges > 0
+            assert nodes > 0
     finally:
         cfr.cfr_destroy(h)
 
