@@ -310,7 +310,10 @@ int cfr_set_state(cfr_handle *h, const double *R, const double *avg, int64_t t, 
  * chance arrays, reach and slot ranges 0); 5 unused; each depth's set
  * chunks come first], 34 first chunk of each depth [D+1], 35 per depth
  * whether it can stream [D] (all empty unless FP32 in member order with sets
- * of at most 8 actions).
+ * of at most 8 actions), 36 blocks of each depth's pulling forward launch
+ * [D] (member order: one wave, the blocks all SMs hold at once, or fewer
+ * where the depth needs fewer; set by cfr_bind; 0 before the first bind and
+ * for the deepest depth).
  * Integer arrays are int32. *count receives the element count; out may be
  * NULL to query it. */
 int cfr_export_array(const cfr_handle *h, int which, void *out, int64_t capacity, int64_t *count);

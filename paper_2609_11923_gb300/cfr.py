@@ -39,7 +39,7 @@ EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "i
           "big_irank": 16, "mem_irank": 17, "level_int": 18, "vslot": 19, "iset_vb": 20, "mem_vs": 21,
           "ch_vb": 22, "ch_nch": 23, "ch_vs": 24, "wide_vb": 25, "wide_nch": 26, "wide_vs": 27, "tmpl_vs": 28,
           "int_edge": 29, "iset_rank": 30, "level_tiled": 31, "set_info": 32, "stream_chunks": 33, "stream_c0": 34,
-          "stream_ok": 35}
+          "stream_ok": 35, "pull_grid": 36}
 STREAM_LANES = 512  # lanes_per_set code of the streaming FP32 backward
 
 

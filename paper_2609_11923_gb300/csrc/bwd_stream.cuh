@@ -164,35 +164,43 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // Issues the copies of chunk d into a stage and a side slot (one thread),
 // all counted on the stage's mbarrier. Returns false (and issues nothing) if
-// the chunk does not fit.
+// the chunk does not fit. parts: kIssueRest the expected byte count and
+// every copy but the children's values, kIssueValues the children's values
+// (of everything a backward launch reads, the one input the backward launch
+// before it writes).
+constexpr int kIssueRest = 1, kIssueValues = 2, kIssueAll = 3;
 __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char *stage, unsigned char *side,
                                              uint32_t bar, const float2 *reach, const float *v,
                                              const int32_t *mem_vs, const SetInfo *info, const float *sigma,
-                                             const double *R, const double *avg, const GameView &g) {
+                                             const double *R, const double *avg, const GameView &g, int parts) {
   if (d.kind == kChunkChance) {
     if (!chance_fits(d)) return false;
     const ChanceLayout C = chance_layout(d);
     const uint32_t s = smem_u32(stage);
-    mbar_expect_tx(bar, C.total);  // the four sizes below add up to this
-    bulk_g2s(s, v + d.va, C.vb, bar);
-    bulk_g2s(s + C.vb, g.ch_vb + d.ka, C.nch - C.vb, bar);
-    bulk_g2s(s + C.nch, g.ch_nch + d.ka, C.vs - C.nch, bar);
-    bulk_g2s(s + C.vs, g.ch_vs + d.ka, C.total - C.vs, bar);
+    if (parts & kIssueRest) {
+      mbar_expect_tx(bar, C.total);  // the four sizes below add up to this
+      bulk_g2s(s + C.vb, g.ch_vb + d.ka, C.nch - C.vb, bar);
+      bulk_g2s(s + C.nch, g.ch_nch + d.ka, C.vs - C.nch, bar);
+      bulk_g2s(s + C.vs, g.ch_vs + d.ka, C.total - C.vs, bar);
+    }
+    if (parts & kIssueValues) bulk_g2s(s, v + d.va, C.vb, bar);
     return true;
   }
   if (d.kind != kChunkSets) return false;
   const StreamLayout L = stream_layout(d);
   if (!stream_fits(L) || d.nra <= 0 || d.nva <= 0 || d.nka <= 0 || d.I1 <= d.I0 || d.nsa <= 0) return false;
   const uint32_t s = smem_u32(stage), t = smem_u32(side);
-  mbar_expect_tx(bar, L.total + L.s_total);  // the eight sizes below add up to this
-  bulk_g2s(s + L.reach, reach + d.ra, L.val - L.reach, bar);
-  bulk_g2s(s + L.val, v + d.va, L.mem - L.val, bar);
-  bulk_g2s(s + L.mem, mem_vs + d.ka, L.info - L.mem, bar);
-  bulk_g2s(s + L.info, info + d.I0, L.sig - L.info, bar);
-  bulk_g2s(s + L.sig, sigma + d.sa, L.total - L.sig, bar);
-  bulk_g2s(t + L.s_info, info + d.I0, L.s_R - L.s_info, bar);
-  bulk_g2s(t + L.s_R, R + d.sa, L.s_avg - L.s_R, bar);
-  bulk_g2s(t + L.s_avg, avg + d.sa, L.s_total - L.s_avg, bar);
+  if (parts & kIssueRest) {
+    mbar_expect_tx(bar, L.total + L.s_total);  // the eight sizes below add up to this
+    bulk_g2s(s + L.reach, reach + d.ra, L.val - L.reach, bar);
+    bulk_g2s(s + L.mem, mem_vs + d.ka, L.info - L.mem, bar);
+    bulk_g2s(s + L.info, info + d.I0, L.sig - L.info, bar);
+    bulk_g2s(s + L.sig, sigma + d.sa, L.total - L.sig, bar);
+    bulk_g2s(t + L.s_info, info + d.I0, L.s_R - L.s_info, bar);
+    bulk_g2s(t + L.s_R, R + d.sa, L.s_avg - L.s_R, bar);
+    bulk_g2s(t + L.s_avg, avg + d.sa, L.s_total - L.s_avg, bar);
+  }
+  if (parts & kIssueValues) bulk_g2s(s + L.val, v + d.va, L.mem - L.val, bar);
   return true;
 }
 
@@ -343,13 +351,13 @@ constexpr int kStreamThreads = kStreamCompute + 32;
 template <int MAXA>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     bwd_stream_kernel(GameView g, StateView<float> st, const SetInfo *info, const StreamChunk *chunks, int32_t c0,
-                      int32_t c1, int rule, int upd, int *err) {
+                      int32_t c1, int rule, int upd, int *err, int early) {
   static_assert(kStreamSideSlots >= 2 * kStreamStages, "side slots must outlast the stages by a full ring");
   extern __shared__ __align__(128) unsigned char s_stage[];  // stages, then side slots
   __shared__ __align__(8) uint64_t s_full[kStreamStages], s_empty[kStreamStages], s_rfull[2], s_rempty[2];
   __shared__ StreamChunk s_desc[kStreamStages];
   __shared__ float s_red[2][kStreamWarps][4][2 * MAXA];
-  pdl_enter();
+  if (!early) pdl_enter();
   const int32_t b = (int32_t)blockIdx.x;
   const int32_t nb = (int32_t)gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -360,11 +368,11 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     if (tid == 0) atomicExch(err, 1);
     return;
   }
-  auto issue = [&](int32_t i, const StreamChunk &dsc) {
+  auto issue = [&](int32_t i, const StreamChunk &dsc, int parts) {
     const int s = i % kStreamStages;
     s_desc[s] = dsc;
     return stream_issue(dsc, s_stage + s * kStreamStageBytes, s_side + (i % kStreamSideSlots) * kStreamSideBytes,
-                        smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg, g);
+                        smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg, g, parts);
   };
   if (producer) {
     for (int s = 0; s < kStreamStages; ++s) {
@@ -377,15 +385,27 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int i = 0; i < kStreamStages; ++i) {  // the first chunks of this CTA
+    // the first chunks of this CTA. early: the launch before this one is
+    // the backward launch of the next depth, which writes only values of
+    // this depth's children (and its own slots), so everything else is
+    // copied before waiting for that launch to finish (programmatic
+    // dependent launch), and the children's values after
+    int issued = 0;
+    for (int i = 0; i < kStreamStages; ++i) {
       const int32_t c = c0 + b + i * nb;
       if (c >= c1) break;
-      if (!issue(i, chunks[c])) {
+      if (!issue(i, chunks[c], early ? kIssueRest : kIssueAll)) {
         atomicExch(err, 1);  // a chunk larger than a stage: never issued, every wait below gives up
         break;
       }
+      ++issued;
+    }
+    if (early) {
+      pdl_enter();
+      for (int i = 0; i < issued; ++i) issue(i, chunks[c0 + b + i * nb], kIssueValues);
     }
   }
+  if (early && !producer) pdl_enter();
   __syncthreads();  // barriers initialised, first copies issued (the only CTA-wide barrier)
   const double wt = avg_weight(*st.t + 1, rule);
   // error exit of the thread that issues copies: let every chunk it issued
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
             return;
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (!issue(i + kStreamStages, nd)) atomicExch(err, 1);  // never issued: the next wait gives up
+          if (!issue(i + kStreamStages, nd, kIssueAll)) atomicExch(err, 1);  // never issued: the next wait gives up
         }
       }
       continue;
@@ -476,7 +496,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
               return;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (!issue(i + kStreamStages, nd)) atomicExch(err, 1);  // never issued: the next wait gives up
+            if (!issue(i + kStreamStages, nd, kIssueAll)) atomicExch(err, 1);  // never issued: the next wait gives up
           }
         }
         stream_update<MAXA>(d, L, side, I, G, st.sigma, st.R, st.avg, wt, rule, upd, s_red[p]);

@@ -55,6 +55,7 @@ struct cfr_handle {
   int precision = CFR_P32, exec_form = CFR_EXEC_GRAPH, rule = 0, order = 0;
   int maxa_tier = 8;           // 4, 8 or 64: register arrays of the per-set code
   std::vector<int> level_lanes;  // lanes per information set, per depth
+  std::vector<int> pull_grid;    // member order: blocks of the forward launch of depth d (set at bind; 0 = none)
   int persist_lanes = 8;
   std::vector<LevelWork> levels;
   // arena layout
@@ -298,6 +299,7 @@ extern "C" int cfr_compile(const cfr_game_spec *spec, const cfr_options *opt, cf
   // (tiled depths: at most one tile of sets per warp's worth of lanes, so a
   // warp's member reads stay one run)
   h->level_lanes.assign(c.D, 8);
+  h->pull_grid.assign(c.D, 0);
   double tot_mem = 0.0;
   bool any_tiled = false;
   build_stream(h);
@@ -418,6 +420,39 @@ static int grid_for(int64_t work, int per_block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+static int device_sms() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 148;
+  }
+  return nsm;
+}
+
+// Blocks of the pulling forward launch of depth d (member order): at most
+// enough for its nodes, kPull per thread.
+static int pull_need(const cfr_handle *h, int64_t d) {
+  const LevelWork &n = h->levels[d + 1];
+  return grid_for((n.ie - n.ib + kPull - 1) / kPull, kThreads);
+}
+
+// The grid of every pulling forward launch: the blocks the SMs hold at
+// once (one wave), so that the grid-stride loop walks the nodes in rounds of
+// consecutive ranks and the parents a round gathers are still in L2 when the
+// next round's neighbours read them (two waves split every round's range
+// between the waves). Smaller grids run some depths faster alone but slow
+// the iteration down inside the graph, so the autotuner leaves this alone.
+template <typename T>
+static int default_pull_grids(cfr_handle *h) {
+  const Compiled &c = h->c;
+  if (c.int_edge.empty()) return CFR_OK;
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_pull_kernel<T>, kThreads, 0));
+  for (int64_t d = 0; d + 1 < c.D; ++d) h->pull_grid[d] = std::min(pull_need(h, d), std::max(occ, 1) * device_sms());
+  return CFR_OK;
+}
+
 // Forward launch of depth d. Member order: the internal nodes of depth d + 1
 // pull their reach (no launch for the deepest depth). Breadth-first and
 // value-slot orders: nb blocks over depth d's internal nodes push to their
@@ -430,7 +465,7 @@ static int launch_fwd(const cfr_handle *h, int64_t d, cudaStream_t s, const Game
   if (g.int_edge) {  // member order: the next depth's internal nodes pull their reach
     if (d + 1 >= h->c.D) return CFR_OK;
     const LevelWork &n = h->levels[d + 1];
-    const int nb = grid_for((n.ie - n.ib + kPull - 1) / kPull, kThreads);
+    const int nb = h->pull_grid[d] > 0 ? h->pull_grid[d] : pull_need(h, d);
     CK(launch_k(fwd_pull_kernel<T>, nb, kThreads, 0, s, pdl, g, sigma, reach, n.ib, n.ie));
     return CFR_OK;
   }
@@ -573,6 +608,7 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
   if ((rc = up(h->b_set_info, h->set_info.data(), sizeof(SetInfo) * h->set_info.size()))) return rc;
   if ((rc = up(h->b_stream_chunks, h->stream_chunks.data(), sizeof(StreamChunk) * h->stream_chunks.size()))) return rc;
   if (!h->stream_chunks.empty()) CK(prepare_bwd_stream());
+  if ((rc = h->precision == CFR_P64 ? default_pull_grids<double>(h) : default_pull_grids<float>(h))) return rc;
   if (c.n_wide) CK(cudaMemsetAsync(h->arena + h->b_wide_cnt.off, 0, 4 * c.n_wide, s));
   CK(cudaMemsetAsync(h->arena + h->b_bar.off, 0, 16, s));
   CK(cudaMemsetAsync(h->arena + h->b_err.off, 0, 16, s));
@@ -594,14 +630,8 @@ extern "C" int cfr_bind(cfr_handle *h, void *arena, size_t bytes, void *stream) 
 // Streaming CTAs of the streaming backward of depth d: two per SM, never
 // more than the depth has chunks.
 static int stream_ctas(const cfr_handle *h, int d) {
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      nsm = 148;
-  }
   const int n = h->stream_c0[d + 1] - h->stream_c0[d];
-  return std::max(1, std::min(n, 2 * nsm));
+  return std::max(1, std::min(n, 2 * device_sms()));
 }
 
 // Blocks of the backward launch of depth d (chance blocks, wide chunks, then
@@ -631,9 +661,11 @@ static int launch_bwd(cfr_handle *h, int d, cudaStream_t s, int upd = 3, bool pd
   bwd_blocks(h, d, &nb_ch, &nb_wide, &nb_is);
   const int lanes = h->level_lanes[d];
   if (lanes == kStreamLanes) {  // FP32 only (compile checks it); no wide chance nodes at this depth
+    // with programmatic dependent launch the launch before a backward launch
+    // of depth d < D - 1 is the backward launch of depth d + 1
     CK(launch_bwd_stream(h->maxa_tier, nb_is, s, game_view(h), state_view<float>(h), h->p<SetInfo>(h->b_set_info),
                          h->p<StreamChunk>(h->b_stream_chunks), h->stream_c0[d], h->stream_c0[d + 1], h->rule, upd,
-                         h->p<int>(h->b_err), pdl));
+                         h->p<int>(h->b_err), pdl, pdl && d + 1 < h->c.D));
     return CFR_OK;
   }
   // at least one block: the depth-0 launch also advances t
@@ -1055,6 +1087,7 @@ extern "C" int cfr_export_array(const cfr_handle *h, int which, void *out, int64
     case 33: src = h->stream_chunks.data(); n = 16 * (int64_t)h->stream_chunks.size(); break;
     case 34: src = h->stream_c0.data(); n = (int64_t)h->stream_c0.size(); break;
     case 35: src = h->stream_ok.data(); n = (int64_t)h->stream_ok.size(); break;
+    case 36: src = h->pull_grid.data(); n = (int64_t)h->pull_grid.size(); break;
     default: return set_err(CFR_ERR_ARG, "cfr_export_array: unknown array %d", which);
   }
   *count = n;
@@ -1299,7 +1332,7 @@ extern "C" int cfr_launch_floor(cfr_handle *h, int64_t n, void *stream, double *
     const LevelWork &w = h->levels[d];
     if (c.int_edge.empty()) grids.push_back(grid_for((w.ie - w.ib + 3) / 4, kThreads) + (w.wc1 - w.wc0));
     else if (d + 1 < c.D)  // member order: the launch of depth d pulls depth d + 1
-      grids.push_back(grid_for((h->levels[d + 1].ie - h->levels[d + 1].ib + kPull - 1) / kPull, kThreads));
+      grids.push_back(h->pull_grid[d] > 0 ? h->pull_grid[d] : pull_need(h, d));
   }
   for (int64_t d = c.D - 1; d >= 0; --d) {
     int nb_ch, nb_wide, nb_is;

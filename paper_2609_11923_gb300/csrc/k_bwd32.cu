@@ -7,9 +7,10 @@ template cudaError_t launch_bwd_level<float>(int, int, int, cudaStream_t, GameVi
 namespace cfr {
 template <int MA>
 static cudaError_t stream_one(int grid, cudaStream_t s, GameView g, StateView<float> st, const SetInfo *info,
-                              const StreamChunk *chunks, int c0, int c1, int rule, int upd, int *err, bool pdl) {
+                              const StreamChunk *chunks, int c0, int c1, int rule, int upd, int *err, bool pdl,
+                              int early) {
   return launch_k(bwd_stream_kernel<MA>, grid, kStreamThreads, (size_t)kStreamDynSmem, s, pdl, g, st, info, chunks,
-                  c0, c1, rule, upd, err);
+                  c0, c1, rule, upd, err, early);
 }
 
 cudaError_t prepare_bwd_stream() {
@@ -22,9 +23,10 @@ cudaError_t prepare_bwd_stream() {
 
 cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st,
                               const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
-                              int *err, bool pdl) {
-  if (maxa == 4) return stream_one<4>(grid, s, g, st, info, chunks, c0, c1, rule, upd, err, pdl);
-  if (maxa == 8) return stream_one<8>(grid, s, g, st, info, chunks, c0, c1, rule, upd, err, pdl);
+                              int *err, bool pdl, bool early) {
+  const int e = early ? 1 : 0;
+  if (maxa == 4) return stream_one<4>(grid, s, g, st, info, chunks, c0, c1, rule, upd, err, pdl, e);
+  if (maxa == 8) return stream_one<8>(grid, s, g, st, info, chunks, c0, c1, rule, upd, err, pdl, e);
   return cudaErrorInvalidValue;
 }
 }  // namespace cfr

@@ -29,9 +29,12 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), int grid, int block, size_t 
 
 // The streaming FP32 backward of one depth (bwd_stream_kernel); grid = the
 // streaming CTAs over the depth's chunks [c0, c1) (set and chance chunks).
+// early (with pdl only, and only when the launch before is the backward
+// launch of the next depth): copy every input but the children's values
+// before waiting for that launch.
 cudaError_t launch_bwd_stream(int maxa, int grid, cudaStream_t s, GameView g, StateView<float> st,
                               const SetInfo *info, const StreamChunk *chunks, int c0, int c1, int rule, int upd,
-                              int *err, bool pdl);
+                              int *err, bool pdl, bool early);
 // Allows the streaming kernel its dynamic shared memory (call before the
 // first launch, outside any stream capture; idempotent).
 cudaError_t prepare_bwd_stream();

@@ -38,7 +38,7 @@ def test_arrays_bit_exact(name, reach_order, tiles):
     h = cfr.cfr_compile(g, cfr.make_options(reach_order=reach_order, member_tiles=tiles))
     try:
         for key in cfr.EXPORT:
-            if key == "level_lanes":  # a runtime choice, not a compiled array
+            if key in ("level_lanes", "pull_grid"):  # runtime choices, not compiled arrays
                 continue
             if key == "set_info" or key.startswith("stream_"):  # derived from these arrays (test_stream_layout)
                 continue

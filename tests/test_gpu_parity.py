@@ -273,6 +273,29 @@ def test_autotune_keeps_fp64_parity_and_picks_valid_lanes():
     np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 300).avg_strategy())
 
 
+def test_pull_grids_are_one_wave_and_keep_fp64_parity():
+    # the pulling forward's grid: one wave (the blocks all SMs hold at once),
+    # never more than the depth's nodes need, unchanged by autotune; the grid
+    # does not change any result (each node's reach is computed alone)
+    g = gg.large_card(4, 4, 1, 1)
+    s = cfr.Solver(g, precision=cfr.P64, exec_form=cfr.EXEC_GRAPH)
+    D = s.counts["depth_blocks"]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    li = cfr.cfr_export_array(s.h, "level_int").astype(int)
+    nodes = [li[d + 2] - li[d + 1] for d in range(D - 1)]
+    need = [min(max(1, -(-n // (4 * 256))), 152 * 16) for n in nodes]  # blocks of 256 threads, 4 nodes each
+    grid0 = cfr.cfr_export_array(s.h, "pull_grid").astype(int)
+    assert len(grid0) == D and grid0[D - 1] == 0
+    for d in range(D - 1):
+        assert 1 <= grid0[d] <= need[d]
+        if need[d] <= sms:  # a wave holds at least one block per SM
+            assert grid0[d] == need[d]
+    s.autotune(reps=2)
+    np.testing.assert_array_equal(cfr.cfr_export_array(s.h, "pull_grid"), grid0)
+    s.iterate(200)
+    np.testing.assert_array_equal(s.avg_strategy(), oracle.solve(g, 200).avg_strategy())
+
+
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32, 256])
 def test_every_lane_count_matches_oracle_in_fp64(lanes):
     g = gg.large_card(3, 2, 1, 1)
