@@ -14,9 +14,9 @@
 // value slots, and their entries of the chance arrays), summed in the same
 // pipeline. Every CTA walks the chunks c = blockIdx, blockIdx + grid, ...
 // through a ring of kStreamStages stages. Its kStreamCompute compute threads
-// do the members' (or chance nodes') work; one more warp, the control warp,
-// issues each chunk's cp.async.bulk copies into a stage (the stage's
-// mbarrier counts their bytes) and runs every group's slot update.
+// do the members' (or chance nodes') work; the copy warp issues each chunk's
+// cp.async.bulk copies into a stage and a side slot (their mbarriers count
+// the bytes), and the update warp runs every group's slot update.
 // The loads in flight cost no registers, so the memory pipe stays full at a
 // low warp count, and the compute warps never wait for a slot update (they
 // hand each group's partial sums over through a double-buffered array and a
@@ -27,9 +27,9 @@
 // t serves set j = t % G of the group (G = 4 for a tile, 1 otherwise) and
 // members q = t / G, t / G + 256 / G, ... of that set, so a warp reads a
 // tile's reach as one contiguous run. Per-thread FP32 partial sums are
-// finished by a fixed-shape butterfly within the warp and, in the control
+// finished by a fixed-shape butterfly within the warp and, in the update
 // warp, a sum over the warps in warp order (deterministic run to run); the
-// control warp then updates the group's slots (one lane per slot) and writes
+// update warp then updates the group's slots (one lane per slot) and writes
 // sigma^{t+1}. The form pays where sets are long (hundreds of members).
 #pragma once
 #include "kernels.cuh"
@@ -39,7 +39,7 @@ namespace cfr {
 constexpr int kStreamLanes = 512;                 // lanes_per_set code of this form
 constexpr int kStreamStages = 2;                  // pipeline depth
 constexpr int kStreamStageBytes = 48 * 1024;      // bytes one chunk may stage for the compute threads
-constexpr int kStreamSideSlots = 4;               // ring of the control warp's per-chunk data
+constexpr int kStreamSideSlots = 4;               // ring of the update warp's per-chunk data
 constexpr int kStreamSideBytes = 2048;            // bytes of one side slot
 constexpr int kStreamDynSmem = kStreamStages * kStreamStageBytes + kStreamSideSlots * kStreamSideBytes;
 constexpr int kStreamCompute = 256;               // compute threads of a streaming CTA (two CTAs per SM)
@@ -79,7 +79,7 @@ static_assert(sizeof(SetInfo) == 32, "SetInfo is staged in 32-byte records");
 static_assert(sizeof(StreamChunk) == 64, "StreamChunk is 64 bytes");
 
 // Byte offsets of the staged arrays: in a stage (what the compute threads
-// read) and in a side slot (what the control warp reads for the slot
+// read) and in a side slot (what the update warp reads for the slot
 // updates, so that the stage can be refilled while it still works).
 struct StreamLayout {
   uint32_t reach, val, mem, info, sig, total;  // stage
@@ -162,15 +162,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// Issues the copies of chunk d into a stage and a side slot (one thread),
-// all counted on the stage's mbarrier. Returns false (and issues nothing) if
-// the chunk does not fit. parts: kIssueRest the expected byte count and
-// every copy but the children's values, kIssueValues the children's values
-// (of everything a backward launch reads, the one input the backward launch
-// before it writes).
+// Issues the copies of chunk d into a stage and a side slot (one thread):
+// the stage's copies counted on its mbarrier bar, the side slot's on sbar (a
+// chance chunk puts nothing in the side slot: its phase of sbar completes
+// with no bytes). Returns false (and issues nothing) if the chunk does not
+// fit. parts: kIssueRest the expected byte counts and every copy but the
+// children's values, kIssueValues the children's values (of everything a
+// backward launch reads, the one input the backward launch before it
+// writes).
 constexpr int kIssueRest = 1, kIssueValues = 2, kIssueAll = 3;
 __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char *stage, unsigned char *side,
-                                             uint32_t bar, const float2 *reach, const float *v,
+                                             uint32_t bar, uint32_t sbar, const float2 *reach, const float *v,
                                              const int32_t *mem_vs, const SetInfo *info, const float *sigma,
                                              const double *R, const double *avg, const GameView &g, int parts) {
   if (d.kind == kChunkChance) {
@@ -178,6 +180,7 @@ __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char
     const ChanceLayout C = chance_layout(d);
     const uint32_t s = smem_u32(stage);
     if (parts & kIssueRest) {
+      mbar_expect_tx(sbar, 0);  // nothing in the side slot: its phase completes at once
       mbar_expect_tx(bar, C.total);  // the four sizes below add up to this
       bulk_g2s(s + C.vb, g.ch_vb + d.ka, C.nch - C.vb, bar);
       bulk_g2s(s + C.nch, g.ch_nch + d.ka, C.vs - C.nch, bar);
@@ -191,14 +194,15 @@ __device__ __forceinline__ bool stream_issue(const StreamChunk &d, unsigned char
   if (!stream_fits(L) || d.nra <= 0 || d.nva <= 0 || d.nka <= 0 || d.I1 <= d.I0 || d.nsa <= 0) return false;
   const uint32_t s = smem_u32(stage), t = smem_u32(side);
   if (parts & kIssueRest) {
-    mbar_expect_tx(bar, L.total + L.s_total);  // the eight sizes below add up to this
+    mbar_expect_tx(sbar, L.s_total);  // the side slot's three copies
+    bulk_g2s(t + L.s_info, info + d.I0, L.s_R - L.s_info, sbar);
+    bulk_g2s(t + L.s_R, R + d.sa, L.s_avg - L.s_R, sbar);
+    bulk_g2s(t + L.s_avg, avg + d.sa, L.s_total - L.s_avg, sbar);
+    mbar_expect_tx(bar, L.total);  // the stage's five copies
     bulk_g2s(s + L.reach, reach + d.ra, L.val - L.reach, bar);
     bulk_g2s(s + L.mem, mem_vs + d.ka, L.info - L.mem, bar);
     bulk_g2s(s + L.info, info + d.I0, L.sig - L.info, bar);
     bulk_g2s(s + L.sig, sigma + d.sa, L.total - L.sig, bar);
-    bulk_g2s(t + L.s_info, info + d.I0, L.s_R - L.s_info, bar);
-    bulk_g2s(t + L.s_R, R + d.sa, L.s_avg - L.s_R, bar);
-    bulk_g2s(t + L.s_avg, avg + d.sa, L.s_total - L.s_avg, bar);
   }
   if (parts & kIssueValues) bulk_g2s(s + L.val, v + d.va, L.mem - L.val, bar);
   return true;
@@ -266,7 +270,7 @@ __device__ __forceinline__ void stream_members(const StreamChunk &d, const Strea
   }
 }
 
-// The slot update of one group by the control warp: lane = a * G + j
+// The slot update of one group by the update warp: lane = a * G + j
 // updates slot a of set j (the warps' partial sums added in warp order),
 // then writes sigma^{t+1} of the group's sets.
 template <int MAXA>
@@ -328,56 +332,70 @@ __device__ __forceinline__ void stream_chance_chunk(const StreamChunk &d, const 
   }
 }
 
-// Threads of a streaming CTA: kStreamCompute compute threads and one control warp.
-constexpr int kStreamThreads = kStreamCompute + 32;
+// Threads of a streaming CTA: kStreamCompute compute threads, the copy warp
+// (its first lane issues every bulk copy) and the update warp (the slot
+// updates).
+constexpr int kStreamThreads = kStreamCompute + 64;
 
 // Grid: the streaming CTAs over chunks [c0, c1) of this depth (its set
 // chunks, then its chance chunks; a depth with wide chance nodes does not
 // stream). Chunk i of a CTA uses stage i % kStreamStages (the compute
 // threads' data) and side slot i % kStreamSideSlots (set records, R and
-// average for the control warp's slot updates). Barriers of a streaming CTA
-// (every wait bounded):
-//   full[s]   the copies of the chunk in stage s and its side slot have
-//             landed (bytes counted)
+// average for the update warp). Barriers of a streaming CTA (every wait
+// bounded):
+//   full[s]   the copies of the chunk in stage s have landed (bytes counted)
 //   empty[s]  the compute threads are done with stage s
+//   sfull[k]  the copies of the chunk in side slot k have landed
+//   sfree[k]  the update warp is done with side slot k
 //   rfull[p]  the compute threads have written the partial sums red[p]
-//   rempty[p] the control warp has consumed red[p]
-// The compute warps never wait for a slot update, and a stage is refilled as
-// soon as the compute threads are done with it: the control warp issues the
-// refill when the chunk's last group has been handed over, before it updates
-// that group's slots (from the side slot, which the refill does not touch:
-// the side ring is two chunks deeper than the stages, and the control warp
-// works through chunks in order).
+//   rempty[p] the update warp has consumed red[p]
+// The copy warp refills stage s with chunk i + kStreamStages as soon as the
+// compute threads are done with chunk i and the update warp is done with
+// the side slot's previous chunk; the compute warps never wait for a slot
+// update, and the update warp, which works through the chunks in order,
+// never holds up a refill of a stage. Each barrier's phases are waited for
+// in order and a phase cannot complete twice before its waiter sees it: a
+// stage is refilled only after its chunk was consumed, a side slot only
+// after the update warp released it.
 template <int MAXA>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     bwd_stream_kernel(GameView g, StateView<float> st, const SetInfo *info, const StreamChunk *chunks, int32_t c0,
                       int32_t c1, int rule, int upd, int *err, int early) {
   static_assert(kStreamSideSlots >= 2 * kStreamStages, "side slots must outlast the stages by a full ring");
+  constexpr int S = kStreamStages, K = kStreamSideSlots;
   extern __shared__ __align__(128) unsigned char s_stage[];  // stages, then side slots
-  __shared__ __align__(8) uint64_t s_full[kStreamStages], s_empty[kStreamStages], s_rfull[2], s_rempty[2];
-  __shared__ StreamChunk s_desc[kStreamStages];
+  __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_sfull[K], s_sfree[K], s_rfull[2], s_rempty[2];
+  __shared__ StreamChunk s_desc[S], s_sdesc[K];
   __shared__ float s_red[2][kStreamWarps][4][2 * MAXA];
   if (!early) pdl_enter();
   const int32_t b = (int32_t)blockIdx.x;
   const int32_t nb = (int32_t)gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31;
-  const bool control = tid >= kStreamCompute;
+  const int role = tid < kStreamCompute ? 0 : (tid < kStreamCompute + 32 ? 1 : 2);  // compute, copy, update
   const bool producer = tid == kStreamCompute;
-  unsigned char *s_side = s_stage + kStreamStages * kStreamStageBytes;
+  unsigned char *s_side = s_stage + S * kStreamStageBytes;
   if ((smem_u32(s_stage) & 15u) != 0u) {  // bulk copies need 16-byte aligned destinations
     if (tid == 0) atomicExch(err, 1);
     return;
   }
   auto issue = [&](int32_t i, const StreamChunk &dsc, int parts) {
-    const int s = i % kStreamStages;
-    s_desc[s] = dsc;
-    return stream_issue(dsc, s_stage + s * kStreamStageBytes, s_side + (i % kStreamSideSlots) * kStreamSideBytes,
-                        smem_u32(&s_full[s]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg, g, parts);
+    const int s = i % S, k = i % K;
+    if (parts & kIssueRest) {  // before the copies whose barriers publish them
+      s_desc[s] = dsc;
+      s_sdesc[k] = dsc;
+    }
+    return stream_issue(dsc, s_stage + s * kStreamStageBytes, s_side + k * kStreamSideBytes, smem_u32(&s_full[s]),
+                        smem_u32(&s_sfull[k]), st.reach, st.v, g.mem_vs, info, st.sigma, st.R, st.avg, g, parts);
   };
+  int32_t issued = 0;  // chunks issued (copy thread)
   if (producer) {
-    for (int s = 0; s < kStreamStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&s_full[s]), 1);
       mbar_init(smem_u32(&s_empty[s]), kStreamCompute);
+    }
+    for (int k = 0; k < K; ++k) {
+      mbar_init(smem_u32(&s_sfull[k]), 1);
+      mbar_init(smem_u32(&s_sfree[k]), 32);
     }
     for (int p = 0; p < 2; ++p) {
       mbar_init(smem_u32(&s_rfull[p]), kStreamCompute);
@@ -390,8 +408,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     // this depth's children (and its own slots), so everything else is
     // copied before waiting for that launch to finish (programmatic
     // dependent launch), and the children's values after
-    int issued = 0;
-    for (int i = 0; i < kStreamStages; ++i) {
+    for (int i = 0; i < S; ++i) {
       const int32_t c = c0 + b + i * nb;
       if (c >= c1) break;
       if (!issue(i, chunks[c], early ? kIssueRest : kIssueAll)) {
@@ -407,106 +424,113 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   }
   if (early && !producer) pdl_enter();
   __syncthreads();  // barriers initialised, first copies issued (the only CTA-wide barrier)
-  const double wt = avg_weight(*st.t + 1, rule);
-  // error exit of the thread that issues copies: let every chunk it issued
-  // and nobody waited for land (bounded waits), then leave
-  auto drain = [&](int32_t i0) {
+
+  if (role == 1) {
     if (!producer) return;
-    for (int k = 0; k < kStreamStages; ++k)
-      if (c0 + b + (i0 + k) * nb < c1)
-        mbar_wait(smem_u32(&s_full[(i0 + k) % kStreamStages]), (uint32_t)(((i0 + k) / kStreamStages) & 1));
-  };
-  int32_t grp = 0;  // groups done by this CTA (selects red[grp & 1] and the barrier phases)
+    // refill stage i % S with chunk i + S once chunk i is consumed and the
+    // side slot's previous chunk released
+    int32_t seen = 0;  // chunks known to have landed
+    bool ok = issued == S || c0 + b + issued * nb >= c1;
+    for (int32_t i = 0; ok; ++i) {
+      const int32_t cn = c0 + b + (i + S) * nb;
+      if (cn >= c1) break;
+      const StreamChunk nd = chunks[cn];  // its latency overlaps the waits
+      const int s = i % S;
+      if (!mbar_wait(smem_u32(&s_empty[s]), (uint32_t)((i / S) & 1))) { ok = false; break; }
+      seen = i + 1;
+      const int32_t j = i + S - K;  // the side slot's previous chunk
+      if (j >= 0 && !mbar_wait(smem_u32(&s_sfree[(i + S) % K]), (uint32_t)((j / K) & 1))) { ok = false; break; }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (!issue(i + S, nd, kIssueAll)) { ok = false; break; }
+      issued = i + S + 1;
+    }
+    if (!ok) {
+      atomicExch(err, 1);
+      // let every copy in flight land before the thread leaves (bounded):
+      // the last chunks issued into each stage and side slot
+      for (int32_t i = max(seen, issued - S); i < issued; ++i)
+        mbar_wait(smem_u32(&s_full[i % S]), (uint32_t)((i / S) & 1));
+      for (int32_t i = max(0, issued - K); i < issued; ++i)
+        mbar_wait(smem_u32(&s_sfull[i % K]), (uint32_t)((i / K) & 1));
+    }
+    return;
+  }
+
+  if (role == 2) {
+    const double wt = avg_weight(*st.t + 1, rule);
+    int32_t grp = 0;  // groups done by this CTA (selects red[grp & 1] and the barrier phases)
+    for (int32_t i = 0;; ++i) {
+      const int32_t c = c0 + b + i * nb;
+      if (c >= c1) break;
+      const int k = i % K;
+      if (!mbar_wait(smem_u32(&s_sfull[k]), (uint32_t)((i / K) & 1))) {
+        atomicExch(err, 1);
+        return;
+      }
+      const StreamChunk d = s_sdesc[k];  // written before the side slot's copies were issued
+      if (d.kind == kChunkSets) {
+        const StreamLayout L = stream_layout(d);
+        const unsigned char *side = s_side + k * kStreamSideBytes;
+        const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(side + L.s_info);
+        for (int32_t I = d.I0; I < d.I1; ++grp) {
+          const int G = sinfo[I - d.I0].flags & 7;
+          const int p = grp & 1;
+          if (!mbar_wait(smem_u32(&s_rfull[p]), (uint32_t)((grp >> 1) & 1))) {
+            atomicExch(err, 1);
+            return;
+          }
+          stream_update<MAXA>(d, L, side, I, G, st.sigma, st.R, st.avg, wt, rule, upd, s_red[p]);
+          mbar_arrive(smem_u32(&s_rempty[p]));
+          I += G;
+        }
+      }
+      mbar_arrive(smem_u32(&s_sfree[k]));
+    }
+    return;
+  }
+
+  int32_t grp = 0;
   for (int32_t i = 0;; ++i) {
     const int32_t c = c0 + b + i * nb;
     if (c >= c1) break;
-    const int s = i % kStreamStages;
-    const uint32_t par = (uint32_t)((i / kStreamStages) & 1);
-    if (!mbar_wait(smem_u32(&s_full[s]), par)) {
+    const int s = i % S;
+    if (!mbar_wait(smem_u32(&s_full[s]), (uint32_t)((i / S) & 1))) {
       atomicExch(err, 1);
-      drain(i + 1);
       return;
     }
     const StreamChunk d = s_desc[s];
     const unsigned char *stage = s_stage + s * kStreamStageBytes;
-    // the descriptor of the chunk that refills this stage, loaded now so that
-    // its latency overlaps this chunk's work
-    const int32_t cn = c + kStreamStages * nb;
-    StreamChunk nd;
-    if (producer && cn < c1) nd = chunks[cn];
     if (d.kind == kChunkChance) {
-      // no slot update: the control warp refills the stage as soon as the
-      // compute threads are done with it
-      if (!control) {
-        stream_chance_chunk(d, stage, st.v);
-        mbar_arrive(smem_u32(&s_empty[s]));
-      } else {
-        __syncwarp();  // every control lane has read this chunk's descriptor
-        if (producer && cn < c1) {
-          if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
-            atomicExch(err, 1);
-            drain(i + 1);
-            return;
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (!issue(i + kStreamStages, nd, kIssueAll)) atomicExch(err, 1);  // never issued: the next wait gives up
-        }
-      }
+      stream_chance_chunk(d, stage, st.v);
+      mbar_arrive(smem_u32(&s_empty[s]));
       continue;
     }
     const StreamLayout L = stream_layout(d);
-    const unsigned char *side = s_side + (i % kStreamSideSlots) * kStreamSideBytes;
-    const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(control ? side + L.s_info : stage + L.info);
+    const SetInfo *sinfo = reinterpret_cast<const SetInfo *>(stage + L.info);
     for (int32_t I = d.I0; I < d.I1; ++grp) {
       const int G = sinfo[I - d.I0].flags & 7;
       const int p = grp & 1;
-      const uint32_t rpar = (uint32_t)((grp >> 1) & 1);
-      if (!control) {
-        float racc[MAXA], macc[MAXA];
-        stream_members<MAXA>(d, L, stage, I, G, st.v, racc, macc);
-        // red[p] is free once the control warp consumed it two groups ago
-        if (grp >= 2 && !mbar_wait(smem_u32(&s_rempty[p]), rpar ^ 1u)) {
-          atomicExch(err, 1);
-          return;
-        }
-        if (lane < G) {
-#pragma unroll
-          for (int a = 0; a < MAXA; ++a) {
-            s_red[p][tid >> 5][lane][a] = racc[a];
-            s_red[p][tid >> 5][lane][MAXA + a] = macc[a];
-          }
-        }
-        mbar_arrive(smem_u32(&s_rfull[p]));
-        if (I + G >= d.I1) mbar_arrive(smem_u32(&s_empty[s]));  // this thread is done with stage s
-      } else {
-        if (!mbar_wait(smem_u32(&s_rfull[p]), rpar)) {
-          atomicExch(err, 1);
-          drain(i + 1);
-          return;
-        }
-        if (I + G >= d.I1) {
-          // the chunk's last group is handed over: the compute threads are
-          // about done with stage s, so refill it (with the chunk
-          // kStreamStages ahead) before updating this group's slots
-          __syncwarp();  // every control lane has read this chunk's descriptor
-          if (producer && cn < c1) {
-            if (!mbar_wait(smem_u32(&s_empty[s]), par)) {
-              atomicExch(err, 1);
-              drain(i + 1);
-              return;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (!issue(i + kStreamStages, nd, kIssueAll)) atomicExch(err, 1);  // never issued: the next wait gives up
-          }
-        }
-        stream_update<MAXA>(d, L, side, I, G, st.sigma, st.R, st.avg, wt, rule, upd, s_red[p]);
-        mbar_arrive(smem_u32(&s_rempty[p]));
+      float racc[MAXA], macc[MAXA];
+      stream_members<MAXA>(d, L, stage, I, G, st.v, racc, macc);
+      // red[p] is free once the update warp consumed it two groups ago
+      if (grp >= 2 && !mbar_wait(smem_u32(&s_rempty[p]), (uint32_t)(((grp >> 1) & 1) ^ 1u))) {
+        atomicExch(err, 1);
+        return;
       }
+      if (lane < G) {
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) {
+          s_red[p][tid >> 5][lane][a] = racc[a];
+          s_red[p][tid >> 5][lane][MAXA + a] = macc[a];
+        }
+      }
+      mbar_arrive(smem_u32(&s_rfull[p]));
+      if (I + G >= d.I1) mbar_arrive(smem_u32(&s_empty[s]));  // this thread is done with stage s
       I += G;
     }
   }
-  // every chunk issued was waited on (full[s]) before the loop ended: no
-  // copy is in flight when the CTA leaves
+  // every chunk issued was waited on (full[s]) by the compute threads and
+  // (sfull[k]) by the update warp before they left
 }
 
 }  // namespace cfr
