@@ -1127,7 +1127,7 @@ extern "C" int cfr_level_bytes(const cfr_handle *h, int d, int64_t *fwd, int64_t
   int64_t nch = (c.level_chance[d + 1] - c.level_chance[d]) + (c.level_wide[d + 1] - c.level_wide[d]);
   if (d == 0 && nch > 0) nch = e = 0;  // a chance root's sum is not done in an iteration
   if (!c.int_edge.empty()) {  // member order: the launch of depth d fills depth d + 1 by pulling
-    *fwd = d + 1 < c.D ? 8 * nint_kids + 2 * T * nint + 2 * T * nint_kids + T * slots : 0;
+    *fwd = d + 1 < c.D ? 8 * nint_kids + 2 * T * c.level_pull_parents[d] + 2 * T * nint_kids + T * slots : 0;
     *bwd = 12 * sets + (32 + 2 * T) * slots + (4 + 3 * T) * dec + (12 + T) * nch + T * e;
     return CFR_OK;
   }

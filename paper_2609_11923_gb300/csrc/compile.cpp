@@ -411,6 +411,18 @@ int compile_game(const cfr_game_spec &s, Compiled &c, std::string &err, int reac
             c.int_edge[2 * (size_t)k + 1] = c.node_slot[h] < 0 ? -1 : c.node_slot[h] + a;
           }
         }
+        // the parents whose reach the pull of depth d reads: those with an
+        // internal child (a parent with terminal children only is not read)
+        std::vector<char> seen(r, 0);
+        c.level_pull_parents.assign(D, 0);
+        for (int64_t d = 0; d + 1 < D; ++d)
+          for (int32_t k = c.level_int[d + 1]; k < c.level_int[d + 2]; ++k) {
+            const int32_t q = c.int_edge[2 * (size_t)k];
+            if (q >= 0 && !seen[q]) {
+              seen[q] = 1;
+              ++c.level_pull_parents[d];
+            }
+          }
       } else {  // each internal node's record for the forward that pushes
         c.int_slot.resize(r);
         c.int_mask.resize(r);
@@ -527,7 +539,8 @@ int64_t algo_bytes_per_iter(const Compiled &c, int precision) {
   const bool chance_root = c.N > 1 && c.node_slot[0] < 0;
   const int64_t root_sum = chance_root ? (12 + T) + T * (c.child_begin[1] - c.child_begin[0]) : 0;
   if (!c.int_edge.empty()) {
-    const int64_t parents = c.D > 0 ? c.level_int[c.D - 1] : 0;  // internal nodes above the deepest depth
+    int64_t parents = 0;  // reach the pulls read: every internal node with an internal child
+    for (int64_t x : c.level_pull_parents) parents += x;
     const int64_t last_slots =
         c.D > 0 ? c.iset_slot[c.level_iset[2 * c.D]] - c.iset_slot[c.level_iset[2 * (c.D - 1)]] : 0;
     return 8 * int_kids + 2 * T * parents + 2 * T * int_kids + T * (c.A - last_slots) + 12 * c.I +

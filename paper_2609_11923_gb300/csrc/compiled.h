@@ -106,6 +106,7 @@ struct Compiled {
   std::vector<int32_t> spec_slot_of; // [A] spec slot of each compiled slot
   std::vector<int32_t> level_max_members; // [D] largest information set per depth
   std::vector<double> level_mean_members; // [D]
+  std::vector<int64_t> level_pull_parents; // [D] member order: distinct parents of depth d + 1's internal nodes
   std::vector<int32_t> spec_set_of;  // [I] the spec's id of each compiled set
 };
 

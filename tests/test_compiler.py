@@ -289,6 +289,18 @@ def test_iteration_bytes_are_the_sum_of_the_launches(name, reach_order, precisio
         assert c["algo_bytes_per_iter"] == sum(f + b for f, b in per_launch)
         if reach_order == cfr.REACH_MEMBERS:  # the deepest depth has no forward launch
             assert per_launch[-1][0] == 0
+            # the pull of depth d: edge records and own reach of depth d + 1's
+            # internal nodes, the reach of their distinct parents, the σ of
+            # depth d's slots (recounted here from the exported arrays)
+            T = 4 if precision == cfr.P32 else 8
+            li = cfr.cfr_export_array(h, "level_int").astype(int)
+            ie = cfr.cfr_export_array(h, "int_edge").astype(int).reshape(-1, 2)
+            isl, lis = cfr.cfr_export_array(h, "iset_slot").astype(int), cfr.cfr_export_array(h, "level_iset").astype(int)
+            for d in range(c["depth_blocks"] - 1):
+                kids = li[d + 2] - li[d + 1]
+                parents = len(set(ie[li[d + 1]:li[d + 2], 0].tolist()) - {-1})
+                slots = isl[lis[2 * d + 2]] - isl[lis[2 * d]]
+                assert per_launch[d][0] == 8 * kids + 2 * T * parents + 2 * T * kids + T * slots, d
     finally:
         cfr.cfr_destroy(h)
 
