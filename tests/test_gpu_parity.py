@@ -480,9 +480,14 @@ def test_rebinding_recaptures_instead_of_replaying_a_stale_graph():
     np.testing.assert_array_equal(avg, o.sbar)
 
 
-@pytest.mark.parametrize("name,make", [("rt", lambda: gg.random_tree(6, depth=10)),
-                                       ("card", lambda: gg.large_card(4, 4, 1, 1))])
-def test_graph_iterations_and_launch_overlap_leave_the_state_bitwise_unchanged(name, make):
+@pytest.mark.parametrize("name,make,lanes,order", [
+    ("rt", lambda: gg.random_tree(6, depth=10), 8, cfr.ORDER_SIMULTANEOUS),
+    ("card", lambda: gg.large_card(4, 4, 1, 1), 8, cfr.ORDER_SIMULTANEOUS),
+    # the streaming backward copies its first chunks' inputs other than the
+    # children's values before the programmatic-dependent wait
+    ("card_stream", lambda: gg.large_card(4, 4, 1, 1), cfr.STREAM_LANES, cfr.ORDER_SIMULTANEOUS),
+    ("card_stream_alt", lambda: gg.large_card(4, 2, 2, 2), cfr.STREAM_LANES, cfr.ORDER_ALTERNATING)])
+def test_graph_iterations_and_launch_overlap_leave_the_state_bitwise_unchanged(name, make, lanes, order):
     # k iterations per graph (the paper's alternative-execution table) and
     # programmatic dependent launch change how the launches are issued, not
     # what they compute: 37 = 3 x 10 + 7 iterations use both graphs
@@ -491,7 +496,10 @@ def test_graph_iterations_and_launch_overlap_leave_the_state_bitwise_unchanged(n
     for form, k, ov in ((cfr.EXEC_LEVELS, 0, cfr.OVERLAP_OFF), (cfr.EXEC_LEVELS, 0, cfr.OVERLAP_ON),
                         (cfr.EXEC_GRAPH, 0, cfr.OVERLAP_OFF), (cfr.EXEC_GRAPH, 1, cfr.OVERLAP_ON),
                         (cfr.EXEC_GRAPH, 10, cfr.OVERLAP_ON), (cfr.EXEC_GRAPH, 10, cfr.OVERLAP_OFF)):
-        s = solve_gpu(g, 0, precision=cfr.P32, form=form, lanes_per_set=8, graph_iters=k, launch_overlap=ov)
+        s = solve_gpu(g, 0, precision=cfr.P32, form=form, lanes_per_set=lanes, graph_iters=k, launch_overlap=ov,
+                      order=order)
+        if lanes == cfr.STREAM_LANES:
+            assert cfr.cfr_export_array(s.h, "stream_ok").any()
         for n in (20, 17):
             s.iterate(n)
         s.synchronize()
