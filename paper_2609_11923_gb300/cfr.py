@@ -30,7 +30,7 @@ RULE_CFR_PLUS, RULE_CFR, RULE_PCFR_PLUS = 0, 1, 2
 ORDER_SIMULTANEOUS, ORDER_ALTERNATING = 0, 1
 REACH_MEMBERS, REACH_BFS, REACH_SLOTS = 0, 1, 2
 TILES_AUTO, TILES_OFF, TILES_ON = 0, 1, 2
-OVERLAP_ON, OVERLAP_OFF = 0, 1
+OVERLAP_AUTO, OVERLAP_OFF, OVERLAP_ON = 0, 1, 2
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 DEBUG_FAIL_GRAPH_CAPTURE = 2
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
@@ -168,7 +168,7 @@ def spec_struct(spec) -> Tuple[GameSpecC, list]:
 
 def make_options(precision=P32, exec_form=EXEC_AUTO, rule=RULE_CFR_PLUS, lanes_per_set=0, persistent_ctas=0,
                  barrier_spin_limit=0, order=ORDER_SIMULTANEOUS, reach_order=REACH_MEMBERS,
-                 member_tiles=TILES_AUTO, launch_overlap=OVERLAP_ON, graph_iters=0) -> Options:
+                 member_tiles=TILES_AUTO, launch_overlap=OVERLAP_AUTO, graph_iters=0) -> Options:
     o = Options()
     o.precision, o.exec_form, o.rule = precision, exec_form, rule
     o.lanes_per_set, o.persistent_ctas, o.barrier_spin_limit = lanes_per_set, persistent_ctas, barrier_spin_limit
@@ -369,7 +369,7 @@ class Solver:
                  lanes_per_set: int = 0, persistent_ctas: int = 0, barrier_spin_limit: int = 0,
                  device: str = "cuda", stream=None, order: int = ORDER_SIMULTANEOUS,
                  reach_order: int = REACH_MEMBERS, member_tiles: int = TILES_AUTO,
-                 launch_overlap: int = OVERLAP_ON, graph_iters: int = 0):
+                 launch_overlap: int = OVERLAP_AUTO, graph_iters: int = 0):
         import torch
 
         self.torch = torch
