@@ -449,7 +449,7 @@ int cfr_profile_iteration(cfr_handle *h, double *fwd_ms, double *bwd_ms, void *s
  * `stream`; a barrier timeout returns CFR_ERR_TIMEOUT. */
 int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream);
 
-/* Fault-injection hooks for tests (no effect unless set; host-side only).
+/* Fault-injection hooks for tests (no effect unless set; set on the host).
  * CFR_DEBUG_BARRIER_MISSING_ARRIVALS = k: the persistent kernel's grid
  * barriers wait for k blocks that do not exist, so every wait runs into its
  * spin limit (cfr_options.barrier_spin_limit) and the launch ends with
@@ -459,8 +459,13 @@ int cfr_iterate_noalloc(cfr_handle *h, int64_t n, void *stream);
  * is treated as refused after it ends (the captured graph is discarded), so
  * cfr_iterate takes the capture-failure path of Section 4.3: one warning on
  * stderr per handle, then per-level launches of the same kernels in the same
- * order. */
-enum { CFR_DEBUG_BARRIER_MISSING_ARRIVALS = 1, CFR_DEBUG_FAIL_GRAPH_CAPTURE = 2 };
+ * order.
+ * CFR_DEBUG_STREAM_STALL = 1 (a bound handle; cleared by cfr_reset): the
+ * streaming backward's copy warp issues no copies beyond each CTA's first
+ * chunks, so the compute threads' and the update warp's waits for the next
+ * chunk run out (about a second each) and cfr_synchronize reports
+ * CFR_ERR_TIMEOUT. Nothing faults or hangs: every wait is bounded. */
+enum { CFR_DEBUG_BARRIER_MISSING_ARRIVALS = 1, CFR_DEBUG_FAIL_GRAPH_CAPTURE = 2, CFR_DEBUG_STREAM_STALL = 3 };
 int cfr_debug_set(cfr_handle *h, int key, int64_t value);
 
 /* Message of the calling thread's last failure (thread-local, valid until

@@ -33,6 +33,7 @@ TILES_AUTO, TILES_OFF, TILES_ON = 0, 1, 2
 OVERLAP_AUTO, OVERLAP_OFF, OVERLAP_ON = 0, 1, 2
 DEBUG_BARRIER_MISSING_ARRIVALS = 1
 DEBUG_FAIL_GRAPH_CAPTURE = 2
+DEBUG_STREAM_STALL = 3
 EXPORT = {"child_begin": 0, "node_slot": 1, "level_begin": 2, "iset_slot": 3, "iset_mem": 4, "mem_node": 5,
           "chance_list": 6, "level_chance": 7, "level_iset": 8, "new_of_spec": 9, "tmpl": 10,
           "spec_slot_of": 11, "level_lanes": 12, "int_slot": 13, "int_mask": 14, "int_cirank": 15,

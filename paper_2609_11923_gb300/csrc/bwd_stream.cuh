@@ -427,6 +427,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 
   if (role == 1) {
     if (!producer) return;
+    // fault-injection hook (err[1], set on the host): issue nothing more, so
+    // the other roles' bounded waits for the next chunk run out; the chunks
+    // already issued land and are consumed before the CTA leaves
+    if (reinterpret_cast<volatile const int *>(err)[1] != 0) return;
     // refill stage i % S with chunk i + S once chunk i is consumed and the
     // side slot's previous chunk released
     int32_t seen = 0;  // chunks known to have landed

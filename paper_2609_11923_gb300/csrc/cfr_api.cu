@@ -1118,6 +1118,13 @@ extern "C" int cfr_debug_set(cfr_handle *h, int key, int64_t value) {
     h->test_fail_capture = (int)value;
     return CFR_OK;
   }
+  if (key == CFR_DEBUG_STREAM_STALL) {  // the second word of the error array, read by the streaming kernel
+    if (value != 0 && value != 1) return set_err(CFR_ERR_ARG, "cfr_debug_set: bad value");
+    if (!h->bound) return set_err(CFR_ERR_NOT_BOUND, "cfr_debug_set: the stall flag needs a bound handle");
+    const int v = (int)value;
+    CK(cudaMemcpy(h->arena + h->b_err.off + 4, &v, 4, cudaMemcpyHostToDevice));
+    return CFR_OK;
+  }
   return set_err(CFR_ERR_ARG, "cfr_debug_set: unknown key %d", key);
 }
 

@@ -379,7 +379,8 @@ def test_binding_constants_mirror_the_header():
             values[name] = int(val)
     py = {"CFR_P64": cfr.P64, "CFR_P32": cfr.P32, "CFR_OK": cfr.CFR_OK,
           "CFR_DEBUG_BARRIER_MISSING_ARRIVALS": cfr.DEBUG_BARRIER_MISSING_ARRIVALS,
-          "CFR_DEBUG_FAIL_GRAPH_CAPTURE": cfr.DEBUG_FAIL_GRAPH_CAPTURE}
+          "CFR_DEBUG_FAIL_GRAPH_CAPTURE": cfr.DEBUG_FAIL_GRAPH_CAPTURE,
+          "CFR_DEBUG_STREAM_STALL": cfr.DEBUG_STREAM_STALL}
     py.update({"CFR_OVERLAP_AUTO": cfr.OVERLAP_AUTO, "CFR_OVERLAP_ON": cfr.OVERLAP_ON, "CFR_OVERLAP_OFF": cfr.OVERLAP_OFF})
     for prefix in ("EXEC_", "RULE_", "ORDER_", "REACH_", "TILES_"):
         py.update({"CFR_" + n: getattr(cfr, n) for n in dir(cfr) if n.startswith(prefix)})

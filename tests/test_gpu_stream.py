@@ -107,3 +107,29 @@ def test_autotune_may_pick_streaming_and_keeps_the_tolerance():
     s.iterate(1000)
     s.synchronize()
     assert abs(s.exploitability() - oracle.solve(g, 1000).exploitability()) <= 1e-4 * g.pot
+
+
+def test_stalled_copies_time_out_and_the_context_survives():
+    # the copy warp stops issuing after each CTA's first chunks: the compute
+    # threads' and the update warp's bounded waits for the next chunk run
+    # out, the launch ends, cfr_synchronize reports the timeout, and after a
+    # reset the same handle solves bitwise like a fresh one
+    g = gg.large_card(6, 4, 1, 2)  # 14.6M nodes: up to 1,518 chunks per depth
+    s = streaming(g, tiles=cfr.TILES_ON)
+    chunks = cfr.cfr_export_array(s.h, "stream_c0")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert (chunks[1:] - chunks[:-1]).max() > 2 * (2 * sms)  # some CTA has more chunks than its two stages
+    cfr.cfr_debug_set(s.h, cfr.DEBUG_STREAM_STALL, 1)
+    s.iterate(1)
+    with pytest.raises(cfr.CfrError) as ei:
+        s.synchronize()
+    assert ei.value.code == cfr.CFR_ERR_TIMEOUT
+    cfr.cfr_debug_set(s.h, cfr.DEBUG_STREAM_STALL, 0)
+    s.reset()
+    s.iterate(40)
+    s.synchronize()
+    ref = streaming(g, tiles=cfr.TILES_ON)
+    ref.iterate(40)
+    ref.synchronize()
+    np.testing.assert_array_equal(s.get_state()[0], ref.get_state()[0])
+    np.testing.assert_array_equal(s.get_state()[1], ref.get_state()[1])
