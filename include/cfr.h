@@ -99,8 +99,9 @@ typedef struct cfr_options {
                           actions; the persistent kernel then uses 32), or 512 = the streaming backward
                           (CFR_P32 in member order, sets of at most 8 actions): each depth's sets go in
                           chunks whose reach, child values, member slots, set descriptors, strategy,
-                          regrets and averages are staged in shared memory by bulk asynchronous copies
-                          (depths where a group of sets exceeds one 48 KiB stage keep the default; the
+                          regrets and averages are staged in shared memory by bulk asynchronous copies,
+                          and its narrow chance nodes in chunks of their children's values (depths
+                          where a group of sets exceeds one 48 KiB stage keep the default; the
                           form pays only for long sets, and cfr_autotune tries it where sets have at least
                           32 members on average) */
   int persistent_ctas; /* 0 = co-resident maximum; else a cap on the persistent grid */
